@@ -1,0 +1,163 @@
+/*
+ * FP64 oracle for the MemGS splatting + voxel-merge hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is a plain, slow, obviously correct CPU
+ * restatement of what the CUDA path computes.  Only the tests, the smoke check and
+ * the benchmark's CPU-baseline leg may load it.  It shares no code, header, table
+ * or constant with the CUDA library and the CUDA library never calls it.
+ *
+ * Everything is evaluated in double precision from inputs that are exact copies of
+ * the float32 parameters.  Sections followed:
+ *   - 3D Gaussian map, projection and covariance: Sec. II-C, Eq. 1 and Eq. 2.
+ *   - front-to-back colour and depth blending: Sec. II-E, Eq. 11, with the
+ *     transmittance product read as prod_{j<i}(1 - alpha_j).
+ *   - voxel merge: Sec. II-D, Eq. 3 (mask), Eq. 4 (squared Mahalanobis distance),
+ *     the chi-square 0.05 / 3 dof critical value 7.815, Eq. 6 (merged mean),
+ *     Eq. 7-9 (covariance as the 2-Wasserstein barycentre), Eq. 10 (solver
+ *     initialisation), colour/opacity inherited from the older Gaussian.
+ * The cutoffs (alpha >= 1/255, alpha <= 0.99, stop once T < 1e-4) and the tiling
+ * conventions (16x16 tiles, 3-sigma square extent, 0.3 px^2 dilation, near plane)
+ * are readings of the method that both sides implement.  The front-to-back order is
+ * the float32 rounding of the camera-space depth, ties broken by Gaussian index: a
+ * discrete decision taken from floating point is taken in the kernel's precision.
+ *
+ * All arrays are caller-owned, dense, row-major.  Functions return 0 on success and
+ * a negative value on invalid arguments.  No function keeps state between calls.
+ */
+#ifndef MEMGS_ORACLE_H
+#define MEMGS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double R[9];      /* world -> camera rotation, row-major */
+  double t[3];      /* world -> camera translation */
+  double fx, fy, cx, cy;
+  double near_z;    /* Gaussians with camera z <= near_z are culled */
+  int32_t width, height;
+} orc_camera;
+
+typedef struct {
+  int64_t n;
+  int32_t sh_degree;        /* 0..3, K = (deg+1)^2 coefficients per channel */
+  const double* means;      /* [n][3] */
+  const double* log_scales; /* [n][3] */
+  const double* quats;      /* [n][4] (w,x,y,z), normalised inside */
+  const double* opacity_logit; /* [n] */
+  const double* sh;         /* [n][K][3] */
+} orc_gaussians;
+
+/* Margins below which a discrete decision is called a near-tie (pixel flagged). */
+typedef struct {
+  double alpha_rel;   /* |alpha*255 - 1| */
+  double T_rel;       /* |T/1e-4 - 1| after a contribution */
+  double depth_rel;   /* distance of a depth to a float32 rounding midpoint, relative,
+                         for neighbouring contributors whose float32 keys are within 1 ulp */
+  double extent_px;   /* distance of a tile-rect edge (u +- r) to a tile boundary, px */
+  double radius_abs;  /* distance of 3*sqrt(lambda_max) to an integer */
+  double near_rel;    /* |tz - near| / near */
+  double clamp_rel;   /* |o*G - 0.99| / 0.99 (gradient switch) */
+} orc_margins;
+
+/* Per-Gaussian projection (Eq. 1-2, plus the tiling extent). */
+typedef struct {
+  double* mean2d;   /* [n][2] pixel coordinates u, v */
+  double* conic;    /* [n][3] inverse of the dilated 2D covariance (A, B, C) */
+  double* cov2d;    /* [n][3] dilated 2D covariance (a, b, c) */
+  double* rgb;      /* [n][3] colour after the max(0, .) clamp */
+  double* depth;    /* [n]    camera-space z */
+  double* opacity;  /* [n]    sigmoid(logit) */
+  int32_t* radius;  /* [n]    ceil(3 sqrt(lambda_max)); 0 when culled */
+  int32_t* rect;    /* [n][4] inclusive tile rect x0,y0,x1,y1; x1<x0 when empty */
+  int32_t* visible; /* [n]    1 when projected and the rect is non-empty */
+} orc_projection;
+
+int orc_project(const orc_gaussians* g, const orc_camera* cam, orc_projection* out);
+
+/* Real orthonormal spherical harmonics up to degree 3 at a unit direction:
+ * Y[k], k = l*l + l + m, and dY[k][3] the derivative of the polynomial form. */
+int orc_sh_basis(int32_t degree, const double dir[3], double* Y, double* dY);
+
+/* Forward render of one view.  Outputs are [H][W] planes (rgb is [3][H][W]).
+ * n_contrib: 1 + index (within the pixel's sorted tile list) of the last contributor.
+ * n_eval: list entries evaluated until the stop (or the list length).
+ * flags: bit0 alpha cutoff, bit1 T stop, bit2 depth order, bit3 extent/near,
+ *        bit4 opacity clamp near-tie.  tiles: optional list of tile ids to render
+ *        (others are left untouched); n_tiles < 0 renders every tile.
+ * decision_hash: hash of every pixel's contributor list (for finite differences). */
+int orc_render(const orc_gaussians* g, const orc_camera* cam, const orc_margins* m,
+               const int32_t* tiles, int32_t n_tiles,
+               double* rgb, double* depth, double* alpha, double* T_final,
+               int32_t* n_contrib, int32_t* n_eval, uint8_t* flags,
+               uint64_t* decision_hash, int32_t n_threads);
+
+/* Same image, computed pixel by pixel over all n Gaussians with the tile-rect
+ * predicate and an explicit (depth, index) ordering; no binning. */
+int orc_render_bruteforce(const orc_gaussians* g, const orc_camera* cam,
+                          double* rgb, double* depth, double* alpha);
+
+/* Reverse-mode gradient of L = sum(g_rgb*rgb) + sum(g_depth*depth) + sum(g_alpha*alpha)
+ * for one view.  Any cotangent pointer may be NULL (zero).  Gradients are ADDED
+ * into the outputs.  grad2d: optional [n][10] per-Gaussian screen-space gradient
+ * (du, dv, dA, dB, dC, d_opacity, dr, dg, db, d_depth).  taint: optional [n], set
+ * to 1 for Gaussians evaluated at a flagged pixel.  grad_stat / vis_count: optional
+ * [n], += |dL/dmean| of this view and += 1 when visible (Eq. 3 statistic). */
+typedef struct {
+  double* means; double* log_scales; double* quats; double* opacity_logit; double* sh;
+  double* grad2d; uint8_t* taint; double* grad_stat; double* vis_count;
+} orc_grads;
+
+int orc_render_backward(const orc_gaussians* g, const orc_camera* cam, const orc_margins* m,
+                        const int32_t* tiles, int32_t n_tiles,
+                        const double* g_rgb, const double* g_depth, const double* g_alpha,
+                        orc_grads* out, int32_t n_threads);
+
+/* ---- voxel merge (Sec. II-D) ---- */
+typedef struct {
+  double chi2;               /* 7.815 */
+  double grad_tau;           /* Eq. 3 tau, 1e-3 */
+  int32_t kf_min, kf_max;    /* Eq. 3 keyframe window */
+  const double* grad_stat;   /* [n] mean |dL/dmu| or NULL (all pass) */
+  const int32_t* kf_id;      /* [n] keyframe index or NULL (all pass) */
+  int32_t greedy;            /* 1: greedy disjoint pairs, 0: single minimum pair per voxel */
+} orc_merge_params;
+
+/* Voxel coordinates floor(mu/v) per axis, the quotient rounded to float32. */
+int orc_voxel_keys(int64_t n, const double* means, double voxel, int32_t* keys);
+
+/* Full merge.  Outputs have capacity n; *n_out receives the survivor count.
+ * partner[n]: index of the merge partner or -1.  tie_flag[n] (optional): 1 when the
+ * Gaussian is part of a near-tie (|d2 - chi2| < tie_rel*chi2 or two competing
+ * candidates of its voxel within tie_rel of each other). */
+int orc_voxel_merge(const orc_gaussians* g, const uint64_t* birth, double voxel,
+                    const orc_merge_params* p,
+                    double* out_means, double* out_log_scales, double* out_quats,
+                    double* out_opacity_logit, double* out_sh, uint64_t* out_birth,
+                    double* out_cov, /* [n_out][6] merged-or-copied covariance xx,xy,xz,yy,yz,zz */
+                    int32_t* partner, int64_t* n_out, double tie_rel, uint8_t* tie_flag);
+
+/* Eq. 9 closed form: equal-weight 2-Wasserstein barycentre of N(0,Si), N(0,Sj). */
+int orc_w2_barycentre(const double Si[9], const double Sj[9], double Sk[9]);
+/* Eq. 9 by L-BFGS over (q, s) from the Eq. 10 initialisation. Returns iterations. */
+int orc_w2_lbfgs(const double qi[4], const double si[3], const double qj[4], const double sj[3],
+                 double t, const double delta[3], double qk[4], double sk[3], double Sk[9],
+                 double* final_objective);
+/* Eq. 8: squared 2-Wasserstein distance between N(0,A) and N(0,B). */
+double orc_w2_sq(const double A[9], const double B[9]);
+/* Eq. 6 merged mean. */
+int orc_merge_mean(const double Si[9], const double mi[3], const double Sj[9], const double mj[3],
+                   double mk[3]);
+/* Sigma = R(q) diag(s^2) R(q)^T. */
+int orc_covariance(const double q[4], const double s[3], double S[9]);
+
+/* Adam (bias-corrected), one step over n values, state updated in place. */
+int orc_adam(int64_t n, double* param, const double* grad, double* m, double* v,
+             double lr, double b1, double b2, double eps, int32_t step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
