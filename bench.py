@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the batched mapping step: fwd+bwd frames/s at 1M Gaussians, 1200x680.
+
+One step = one pass of the whole hot path over one batch of 8 keyframes: projection
+of the 1M-Gaussian SH3 map into all 8 views, depth sort, tile sort, forward blend, L1
+loss gradient against the keyframe images, backward blend, per-Gaussian chain rule,
+Adam (lr 1e-3) and the voxel merge (v = 0.02 m) of the updated map.  ``value`` =
+views rendered and back-propagated per second over all ranks, inputs resident in HBM;
+``e2e`` = the same through host buffers (keyframe images copied in from pinned host
+memory each step, the loss read back each step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (there is no runnable reference implementation of the paper).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd frames/s @1M Gaussians 1200x680"
+WORKLOAD = "room1m_sh3"
+WORKLOAD_DESC = ("1M Gaussians on the walls of a 4x3x3 m room (20% near-duplicates), SH degree 3, "
+                 "8 keyframes at 1200x680 (fx=fy=600); step = render 8 views + L1 grad + backward + "
+                 "Adam lr 1e-3 + voxel_merge v=0.02 m")
+FWD_FLOP_EVAL, FWD_FLOP_CONTRIB = 10, 10      # per evaluated / per contributing (pixel, entry)
+BWD_FLOP_EVAL, BWD_FLOP_CONTRIB = 10, 47
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", type=float, default=0.5, help="fraction of one view's tiles for the oracle")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return {"unavailable": "nvidia-smi gave no samples"}
+        sm, mx, pw, reasons = [], 0.0, [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"unavailable": "unparsable nvidia-smi output"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "power_w_median": statistics.median(pw),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- oracle leg
+def oracle_sample(frac, seed=0):
+    """Oracle render + backward of one keyframe of the workload on a seeded tile sample;
+    returns (seconds, sampled fraction of the view, threads used)."""
+    from oracle import oracle
+    from paper_2509_13536_gb300 import scenegen as sg
+    scene, cams = sg.workload(WORKLOAD)
+    cam = cams[0]
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    rng = np.random.default_rng(seed)
+    n_t = max(1, int(round(frac * tx * ty)))
+    tiles = np.sort(rng.choice(tx * ty, n_t, replace=False)).astype(np.int32)
+    gr, gd, ga = (x[0] for x in sg.image_cotangents(1, cam.width, cam.height, seed))
+    threads = os.cpu_count() or 1
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.render(scene, cam, tiles=tiles, n_threads=threads)
+    oracle.render_backward(scene, cam, gr, gd, ga, tiles=tiles, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return dt, n_t / (tx * ty), threads
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, frac, threads = oracle_sample(min(args.cpu_sample, 0.02), seed=i)
+        if i >= args.warmup:
+            times.append(dt)
+    per_step = sum(times) / len(times)
+    value = frac / per_step
+    sample = (f"FP64 oracle render+backward of {frac:.1%} of the tiles of keyframe 0 per step "
+              f"(projection and binning of all 1M Gaussians included)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our leg
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_13536_gb300 import api, build, scenegen as sg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+    scene, cams = sg.workload(WORKLOAD)
+    V = len(cams)
+    H, W = cams[0].height, cams[0].width
+    # targets: keyframes rendered from the unperturbed map
+    g_true = api.Gaussians.from_scene(scene, dev)
+    tgt = api.new_images(cams, dev)
+    ws = api.RenderWorkspace(dev)
+    api.mgs_render(g_true, cams, tgt, ws)
+    target_rgb = torch.stack([t.rgb for t in tgt]).contiguous()
+    target_depth = torch.stack([t.depth for t in tgt]).contiguous()
+    del g_true, tgt
+    # the map being optimised: perturbed copy
+    rng = np.random.default_rng(1234 + rank)
+    pert = scene.copy()
+    pert.means += rng.normal(0, 0.005, pert.means.shape).astype(np.float32)
+    pert.sh += rng.normal(0, 0.02, pert.sh.shape).astype(np.float32)
+    g = api.Gaussians.from_scene(pert, dev)
+    grads = api.Grads.zeros_like(g)
+    m = api.Grads.zeros_like(g, stats=False)
+    v = api.Grads.zeros_like(g, stats=False)
+    rgb = torch.empty(V, 3, H, W, device=dev)
+    depth = torch.empty(V, H, W, device=dev)
+    alpha = torch.empty(V, H, W, device=dev)
+    out = [api.Image(rgb[i], depth[i], alpha[i]) for i in range(V)]
+    g_rgb = torch.empty_like(rgb)
+    g_depth = torch.empty_like(depth)
+    dL = [api.Image(g_rgb[i], g_depth[i], None) for i in range(V)]
+    loss = torch.zeros(1, device=dev)
+    merged = g.empty_like()
+    partner = torch.empty(g.n, dtype=torch.int32, device=dev)
+    vox = torch.empty(g.n, 3, dtype=torch.int32, device=dev)
+    mws = torch.empty(api.load().mgs_voxel_merge_workspace_size(g.n), dtype=torch.uint8, device=dev)
+    s_rgb = 1.0 / rgb.numel()
+    s_depth = 0.1 / depth.numel()
+    state = {"step": 0, "n_out": g.n}
+
+    def step():
+        state["step"] += 1
+        api.mgs_render(g, cams, out, ws)
+        loss.zero_()
+        api.mgs_l1_loss_grad(rgb, target_rgb, s_rgb, g_rgb, loss)
+        api.mgs_l1_loss_grad(depth, target_depth, s_depth, g_depth, loss)
+        api.mgs_render_backward(g, cams, dL, ws, grads)
+        api.mgs_adam_step(g, grads, m, v, 1e-3, 0.9, 0.999, 1e-8, state["step"], zero_grads=True)
+        res, _, _ = api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox)
+        state["n_out"] = res.n
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    with ClockSampler(local) as clocks:
+        api.profile_enable(True)
+        launches0 = api.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = api.launch_count() - launches0
+        prof = api.profile_read()
+        api.profile_enable(False)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    value = world * V / (ms / 1e3)
+
+    # end to end: keyframe images arrive from pinned host memory, the loss goes back
+    host_rgb = target_rgb.cpu().pin_memory()
+    host_depth = target_depth.cpu().pin_memory()
+    host_loss = torch.empty(1, pin_memory=True)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        target_rgb.copy_(host_rgb, non_blocking=True)
+        target_depth.copy_(host_depth, non_blocking=True)
+        step()
+        host_loss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t)
+    e2e_value = world * V / (ms_e2e / 1e3)
+    h2d = host_rgb.numel() * 4 + host_depth.numel() * 4
+
+    # roofline of the dominant kernel group, from a counting pass over the saved state
+    stats = api.render_stats(g, cams, ws)
+    kern = {k: {"ms_per_step": v[0] / args.steps, "launch_groups": v[1]} for k, v in prof.items() if v[1]}
+    props = torch.cuda.get_device_properties(dev)
+    csum = clocks.summary()
+    f_mhz = csum.get("sm_mhz") or 2070.0
+    fp32_peak = props.multi_processor_count * 128 * 2 * f_mhz * 1e6 / 1e12  # TFLOP/s (FMA = 2)
+    flops = {"blend_fwd": FWD_FLOP_EVAL * stats["evaluated"] + FWD_FLOP_CONTRIB * stats["contributing"],
+             "blend_bwd": BWD_FLOP_EVAL * stats["backward_walked"] + BWD_FLOP_CONTRIB * stats["contributing"]}
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    roofline = None
+    if dom in flops:
+        dur = kern[dom]["ms_per_step"] / 1e3
+        ach = flops[dom] / dur / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak, "traffic": None,
+                    "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {f_mhz:.0f} MHz "
+                                  "(median sampled SM clock)",
+                    "flops_per_launch": flops[dom]}
+    else:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except OSError:
+            pass
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                    "traffic": None}
+
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "n_gaussians": g.n, "views": V,
+                       "resolution": f"{W}x{H}", "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (236 MB parameters, 384 MB projected records, "
+                             f"{stats['keys']} tile keys per step)"},
+            "roofline": roofline, "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                                          "d2h_bytes_per_step": 4},
+            "gpu_launches": launches, "clocks": csum, "kernels": kern, "fragments": stats,
+            "merge_survivors": state["n_out"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, frac, threads = oracle_sample(args.cpu_sample)
+        line["cpu_baseline"] = {"value": frac / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",
+                                "sample": f"FP64 oracle render+backward of {frac:.1%} of the tiles of keyframe 0 "
+                                          f"(projection and binning of all 1M Gaussians included), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,245 @@
+/*
+ * memgs.h - C ABI of the GB300 (sm_103a) splatting + voxel-merge library.
+ *
+ * The library implements the data-parallel hot path of the MemGS mapping back-end:
+ * the tile-based differentiable 3D Gaussian Splatting rasteriser (forward and
+ * backward) of Sec. II-C / II-E and the voxel-space merge of Sec. II-D, plus the
+ * optimiser step that consumes the gradients.  Every step runs in hand-written
+ * CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions for every entry point
+ *   - Pointers are DEVICE pointers unless their name ends in _host.  The caller
+ *     owns all memory; the library allocates nothing.  Scratch space is a caller
+ *     workspace whose size comes from the matching *_workspace_size query.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on it unless stated otherwise.
+ *   - Return value: MGS_OK or an error code; mgs_last_error() gives a message
+ *     (thread-local).  On an argument error nothing is launched.  No exception and
+ *     no device trap crosses the ABI.
+ *   - Layouts are dense, row-major, structure-of-arrays:
+ *       means          f32 [n][3]  world frame
+ *       log_scales     attr[n][3]  scale = exp(log_scale)
+ *       quats          attr[n][4]  (w, x, y, z), need not be unit (normalised inside)
+ *       opacity_logit  attr[n]     opacity = sigmoid(logit)
+ *       sh             attr[n][K][3], K = (sh_degree+1)^2, real orthonormal SH basis
+ *       birth          u64 [n]     insertion stamp, smaller = older (merge only)
+ *     where attr is f32, f16 or bf16 (mgs_dtype); arithmetic is always f32.
+ *   - Camera: world->camera rotation R (row-major) and translation t; x right,
+ *     y down, z forward; pixel (u, v) is evaluated at the point (u, v).
+ */
+#ifndef MEMGS_H
+#define MEMGS_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MGS_MAX_VIEWS 32
+#define MGS_TILE 16
+
+typedef enum {
+  MGS_OK = 0,
+  MGS_ERR_INVALID = 1,     /* bad argument: nothing was launched */
+  MGS_ERR_WORKSPACE = 2,   /* workspace too small: nothing was written to outputs */
+  MGS_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  MGS_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+  MGS_ERR_UNSUPPORTED = 5  /* size or mode outside what the kernels handle */
+} mgs_status;
+
+typedef enum { MGS_F32 = 0, MGS_F16 = 1, MGS_BF16 = 2 } mgs_dtype;
+
+typedef struct {
+  int64_t n;
+  int32_t sh_degree;   /* 0..3 */
+  int32_t attr_dtype;  /* mgs_dtype of log_scales, quats, opacity_logit, sh */
+  const float* means;
+  const void* log_scales;
+  const void* quats;
+  const void* opacity_logit;
+  const void* sh;
+  const uint64_t* birth; /* may be NULL except for mgs_voxel_merge */
+} mgs_gaussians;
+
+typedef struct {
+  int64_t n;           /* capacity on input; unused on output (see n_out_host) */
+  int32_t sh_degree;
+  int32_t attr_dtype;
+  float* means;
+  void* log_scales;
+  void* quats;
+  void* opacity_logit;
+  void* sh;
+  uint64_t* birth;
+} mgs_gaussians_mut;
+
+typedef struct {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float near_z;        /* Gaussians with camera-space z <= near_z are culled (0.2) */
+  int32_t reserved;
+} mgs_camera;
+
+/* One view's image planes: rgb f32 [3][H][W], depth f32 [H][W], alpha f32 [H][W]. */
+typedef struct {
+  float* rgb;
+  float* depth;
+  float* alpha;
+} mgs_image;
+
+/* Gradient accumulators, f32, same layouts as the parameters (always f32).
+ * grad_stat / vis_count (optional, [n]) collect the Eq. 3 statistic: per view in
+ * which the Gaussian is drawn, += |dL/dmean| and += 1. */
+typedef struct {
+  float* means;
+  float* log_scales;
+  float* quats;
+  float* opacity_logit;
+  float* sh;
+  float* grad_stat;
+  float* vis_count;
+} mgs_grads;
+
+/* ------------------------------------------------------------------------------
+ * Rasteriser.  Sec. II-C Eq. 1 (projection mu_I = pi(T_CW mu_W), Sigma_I = J W Sigma
+ * W^T J^T), Eq. 2 (Sigma = R S S^T R^T) and Sec. II-E Eq. 11 (front-to-back colour
+ * and depth blending, product read as prod_{j<i}(1 - alpha_j)).
+ * Per pixel, Gaussians are taken in order of (float32 camera depth, index); a
+ * Gaussian is skipped when alpha = min(0.99, o exp(-d^T Sigma_I^-1 d / 2)) < 1/255
+ * and the pixel stops after the Gaussian that takes its transmittance below 1e-4.
+ * Sigma_I is dilated by 0.3 px^2, the Jacobian is taken at the ray clamped to 1.3x
+ * the half field of view, and a Gaussian covers the 16x16 tiles that meet the square
+ * of half-width ceil(3 sqrt(lambda_max)) around mu_I.  Outputs: rgb (black
+ * background), depth = sum_i d_i w_i with d_i the camera-space z of the mean (not
+ * normalised), alpha = 1 - T_final.
+ * ------------------------------------------------------------------------------ */
+
+/* Bytes of workspace for rendering n Gaussians into n_views views with room for
+ * key_capacity (Gaussian, tile) pairs.  Returns 0 on invalid arguments. */
+size_t mgs_render_workspace_size(int64_t n, const mgs_camera* cams_host, int32_t n_views,
+                                 int64_t key_capacity);
+
+/* Forward render of n_views views (1..MGS_MAX_VIEWS, resolutions may differ) in one
+ * pass: per-Gaussian projection for all views, one depth sort, one tile sort, one
+ * blend launch over every (view, tile).  cams_host / out_host: host arrays of
+ * n_views entries; out_host[v] planes are device pointers.  The workspace keeps the
+ * state the backward pass needs and must not be modified until then.
+ * *n_keys_host (optional) receives the number of (Gaussian, tile) pairs.  If they
+ * exceed the workspace's capacity, returns MGS_ERR_WORKSPACE without touching the
+ * outputs; grow the workspace for *n_keys_host keys and call again.
+ * Synchronises `stream` once (to read the key count). */
+mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams_host, int32_t n_views,
+                      const mgs_image* out_host, void* workspace, size_t workspace_bytes,
+                      int64_t* n_keys_host, void* stream);
+
+/* Reverse pass of the last mgs_render on `workspace` (same g, cams, n_views).
+ * dL_host[v] gives dL/drgb, dL/ddepth, dL/dalpha planes of view v (any plane may
+ * be NULL = zero).  Gradients of all views are ADDED to `grads` (f32).  Asynchronous. */
+mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams_host,
+                               int32_t n_views, const mgs_image* dL_host, void* workspace,
+                               size_t workspace_bytes, const mgs_grads* grads, void* stream);
+
+/* Per-Gaussian projection of one view into caller arrays (debugging / inspection):
+ * mean2d f32[n][2], conic f32[n][3], rgb f32[n][3], depth f32[n], radius i32[n],
+ * rect i32[n][4] (inclusive tile rect; x1 < x0 when not drawn).  Any pointer may be NULL. */
+mgs_status mgs_project(const mgs_gaussians* g, const mgs_camera* cam_host, float* mean2d,
+                       float* conic, float* rgb, float* depth, int32_t* radius, int32_t* rect,
+                       void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Voxel merge, Sec. II-D.  Eq. 3 mask: eligible iff grad_stat < grad_tau and
+ * kf_min <= kf_id <= kf_max (a NULL array makes its test pass).  Eligible Gaussians
+ * are grouped by voxel floor(mu / voxel_size) (float32 quotient, origin at 0).  In a
+ * voxel every pair (i older than j) gets Eq. 4's d^2 = (mu_j-mu_i)^T Sigma_i^-1
+ * (mu_j-mu_i); pairs with d^2 < chi2 (7.815, chi-square 0.05 with 3 dof) are similar.
+ * greedy=1: repeatedly merge the unmatched pair of smallest (d^2, birth_i, birth_j);
+ * greedy=0: only the smallest pair of each voxel.  A merged pair keeps G_i's slot:
+ * mean by Eq. 6, covariance the equal-weight 2-Wasserstein barycentre (the minimiser
+ * of Eq. 9, in closed form), stored as (quaternion with w >= 0, scales descending),
+ * opacity, SH and birth copied from the older G_i; G_j is dropped.  Survivors keep
+ * the input order.
+ * ------------------------------------------------------------------------------ */
+typedef struct {
+  float chi2;              /* 7.815 */
+  float grad_tau;          /* 1e-3 */
+  int32_t kf_min, kf_max;
+  const float* grad_stat;  /* [n] or NULL */
+  const int32_t* kf_id;    /* [n] or NULL */
+  int32_t greedy;          /* 1 or 0 */
+  int32_t reserved;
+} mgs_merge_params;
+
+size_t mgs_voxel_merge_workspace_size(int64_t n);
+
+/* out: capacity >= in->n, same sh_degree and attr_dtype.  partner (optional, [n]):
+ * index of the merge partner or -1.  voxel (optional, i32 [n][3]): voxel coordinates
+ * of eligible Gaussians (INT32_MIN for ineligible ones).  Synchronises `stream` and
+ * writes the survivor count to *n_out_host.  Voxel coordinates must fit in 21 bits
+ * signed (|mu / voxel_size| < 2^20), else MGS_ERR_UNSUPPORTED. */
+mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_merge_params* p,
+                           const mgs_gaussians_mut* out, int32_t* partner, int32_t* voxel,
+                           int64_t* n_out_host, void* workspace, size_t workspace_bytes,
+                           void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Optimiser: Adam with bias correction, in one launch over every parameter array of
+ * `params` (the optimiser is not named in the paper, Sec. II-E; Adam is this
+ * library's choice).  m and v are f32 state arrays shaped like the parameters
+ * (same mgs_gaussians_mut layout, f32 pointers in m_state / v_state).  Parameters
+ * stored in f16/bf16 are updated in f32 and rounded back.  step >= 1.  zero_grads = 1
+ * clears each gradient element after it is consumed (the next backward pass
+ * accumulates from zero without a separate clearing pass).  Asynchronous.
+ * ------------------------------------------------------------------------------ */
+mgs_status mgs_adam_step(const mgs_gaussians_mut* params, const mgs_grads* grads,
+                         const mgs_grads* m_state, const mgs_grads* v_state, float lr, float beta1,
+                         float beta2, float eps, int32_t step, int32_t zero_grads, void* stream);
+
+/* L1 loss helper for mapping steps: grad[i] = scale * sign(pred[i] - target[i]) and
+ * *loss += scale * sum |pred - target| (loss is a device f32 accumulator). */
+mgs_status mgs_l1_loss_grad(const float* pred, const float* target, int64_t n, float scale,
+                            float* grad, float* loss, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Device radix sort used by the rasteriser, exposed for testing: stable LSD sort
+ * of (key, value) u32 pairs on bits [begin_bit, end_bit).  keys/vals are sorted in
+ * place (the workspace holds the ping-pong buffers).  vals may be NULL: the values
+ * are then the input positions 0..n-1 and are written to vals_out.
+ * ------------------------------------------------------------------------------ */
+size_t mgs_sort_workspace_size(int64_t n);
+mgs_status mgs_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* vals_out, int64_t n,
+                          int32_t begin_bit, int32_t end_bit, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Diagnostics (not part of the method).
+ * mgs_launch_count: kernels launched by this library in this process so far.
+ * mgs_profile_enable(1) clears the per-kernel totals and starts bracketing each of
+ * the library's kernel groups with CUDA events on its stream; mgs_profile_read
+ * waits for the pending events and returns up to max_kinds entries: name (32 bytes
+ * each, NUL-terminated), total milliseconds and launch count.  Returns the number
+ * of kinds.
+ * mgs_render_stats: counting pass over the saved state of the last mgs_render on
+ * `workspace` (same g, cams, n_views): stats_host[0] = (pixel, entry) pairs the
+ * forward evaluated, [1] = contributing pairs (alpha >= 1/255), [2] = pairs the
+ * backward walks, [3] = (Gaussian, tile) keys.  Synchronises `stream`.
+ * ------------------------------------------------------------------------------ */
+uint64_t mgs_launch_count(void);
+void mgs_profile_enable(int32_t on);
+int32_t mgs_profile_read(int32_t max_kinds, char* names, double* ms_total, int64_t* launches);
+mgs_status mgs_render_stats(const mgs_gaussians* g, const mgs_camera* cams_host, int32_t n_views,
+                            void* workspace, size_t workspace_bytes, uint64_t* stats_host,
+                            void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mgs_last_error(void);
+
+/* Library version, e.g. "memgs 0.1 sm_103a". */
+const char* mgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,110 @@
+"""ctypes declarations of include/memgs.h (argument marshalling only).
+
+The names mirror the C ABI one to one.  Loading fails loudly when libmemgs.so has not
+been built: there is no fallback implementation of any entry point.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+MGS_MAX_VIEWS = 32
+MGS_OK, MGS_ERR_INVALID, MGS_ERR_WORKSPACE, MGS_ERR_CUDA, MGS_ERR_TIMEOUT, MGS_ERR_UNSUPPORTED = range(6)
+MGS_F32, MGS_F16, MGS_BF16 = 0, 1, 2
+STATUS_NAMES = {0: "MGS_OK", 1: "MGS_ERR_INVALID", 2: "MGS_ERR_WORKSPACE", 3: "MGS_ERR_CUDA",
+                4: "MGS_ERR_TIMEOUT", 5: "MGS_ERR_UNSUPPORTED"}
+
+EXPORTS = ["mgs_render_workspace_size", "mgs_render", "mgs_render_backward", "mgs_project",
+           "mgs_voxel_merge_workspace_size", "mgs_voxel_merge", "mgs_adam_step", "mgs_l1_loss_grad",
+           "mgs_sort_workspace_size", "mgs_sort_pairs", "mgs_last_error", "mgs_version",
+           "mgs_launch_count", "mgs_profile_enable", "mgs_profile_read", "mgs_render_stats"]
+
+
+class mgs_gaussians(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("attr_dtype", C.c_int32),
+                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("birth", C.c_void_p)]
+
+
+mgs_gaussians_mut = mgs_gaussians  # same layout, non-const pointers
+
+
+class mgs_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("near_z", C.c_float), ("reserved", C.c_int32)]
+
+
+class mgs_image(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("alpha", C.c_void_p)]
+
+
+class mgs_grads(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logit", "sh",
+                                          "grad_stat", "vis_count")]
+
+
+class mgs_merge_params(C.Structure):
+    _fields_ = [("chi2", C.c_float), ("grad_tau", C.c_float), ("kf_min", C.c_int32),
+                ("kf_max", C.c_int32), ("grad_stat", C.c_void_p), ("kf_id", C.c_void_p),
+                ("greedy", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MemgsError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libmemgs.so (built in-tree by ``build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise ImportError(f"libmemgs.so is not built ({path}); run paper_2509_13536_gb300.build.build()")
+        L = C.CDLL(path)
+        P, I64, I32, F, SZ = C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_size_t
+        sig = {
+            "mgs_render_workspace_size": (SZ, [I64, P, I32, I64]),
+            "mgs_render": (C.c_int, [P, P, I32, P, P, SZ, P, P]),
+            "mgs_render_backward": (C.c_int, [P, P, I32, P, P, SZ, P, P]),
+            "mgs_project": (C.c_int, [P, P, P, P, P, P, P, P, P]),
+            "mgs_voxel_merge_workspace_size": (SZ, [I64]),
+            "mgs_voxel_merge": (C.c_int, [P, F, P, P, P, P, P, P, SZ, P]),
+            "mgs_adam_step": (C.c_int, [P, P, P, P, F, F, F, F, I32, I32, P]),
+            "mgs_l1_loss_grad": (C.c_int, [P, P, I64, F, P, P, P]),
+            "mgs_sort_workspace_size": (SZ, [I64]),
+            "mgs_sort_pairs": (C.c_int, [P, P, P, I64, I32, I32, P, SZ, P]),
+            "mgs_launch_count": (C.c_uint64, []),
+            "mgs_profile_enable": (None, [I32]),
+            "mgs_profile_read": (I32, [I32, P, P, P]),
+            "mgs_render_stats": (C.c_int, [P, P, I32, P, SZ, P, P]),
+            "mgs_last_error": (C.c_char_p, []),
+            "mgs_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def check(status: int, where: str):
+    if status != MGS_OK:
+        msg = load().mgs_last_error().decode(errors="replace")
+        raise MemgsError(status, where, msg)

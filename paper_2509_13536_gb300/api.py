@@ -1,0 +1,386 @@
+"""Torch-facing wrappers of the libmemgs C ABI.
+
+Everything here marshals arguments: tensors become device pointers, the current
+torch CUDA stream becomes the ``stream`` argument, and every computation happens in
+the library's kernels.  Tensors must live on a CUDA device; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check, load
+
+_DTYPES = {torch.float32: _abi.MGS_F32, torch.float16: _abi.MGS_F16, torch.bfloat16: _abi.MGS_BF16}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libmemgs takes CUDA tensors only")
+    if not t.is_contiguous():
+        raise ValueError("libmemgs takes contiguous tensors only")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclasses.dataclass
+class Gaussians:
+    """Device-resident Gaussian map in the library's structure-of-arrays layout."""
+    means: torch.Tensor          # f32 [n,3]
+    log_scales: torch.Tensor     # attr [n,3]
+    quats: torch.Tensor          # attr [n,4]
+    opacity_logit: torch.Tensor  # attr [n]
+    sh: torch.Tensor             # attr [n,K,3]
+    birth: Optional[torch.Tensor] = None  # int64 [n] (stored as uint64 bit patterns)
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @property
+    def sh_degree(self) -> int:
+        return int(round(self.sh.shape[1] ** 0.5)) - 1
+
+    @property
+    def attr_dtype(self) -> torch.dtype:
+        return self.log_scales.dtype
+
+    @staticmethod
+    def from_scene(scene, device="cuda", attr_dtype=torch.float32) -> "Gaussians":
+        d = torch.device(device)
+        f = lambda a, dt=attr_dtype: torch.from_numpy(np.ascontiguousarray(a)).to(d).to(dt).contiguous()
+        return Gaussians(f(scene.means, torch.float32), f(scene.log_scales), f(scene.quats),
+                         f(scene.opacity_logit), f(scene.sh),
+                         torch.from_numpy(scene.birth.astype(np.int64)).to(d))
+
+    def params(self):
+        return [self.means, self.log_scales, self.quats, self.opacity_logit, self.sh]
+
+    def struct(self) -> _abi.mgs_gaussians:
+        if self.means.dtype != torch.float32:
+            raise ValueError("means must be float32")
+        dt = self.log_scales.dtype
+        for t in (self.quats, self.opacity_logit, self.sh):
+            if t.dtype != dt:
+                raise ValueError("log_scales, quats, opacity_logit and sh must share one dtype")
+        return _abi.mgs_gaussians(self.n, self.sh_degree, _DTYPES[dt], _ptr(self.means),
+                                  _ptr(self.log_scales), _ptr(self.quats), _ptr(self.opacity_logit),
+                                  _ptr(self.sh), _ptr(self.birth))
+
+    def empty_like(self) -> "Gaussians":
+        return Gaussians(*(torch.empty_like(t) for t in self.params()),
+                         None if self.birth is None else torch.empty_like(self.birth))
+
+
+def camera_struct(cam) -> _abi.mgs_camera:
+    c = _abi.mgs_camera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float32).reshape(-1)]
+    c.t[:] = [float(x) for x in np.asarray(cam.t, np.float32).reshape(-1)]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.near_z = float(getattr(cam, "near", 0.2))
+    return c
+
+
+def _cam_array(cams):
+    arr = (_abi.mgs_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = camera_struct(c)
+    return arr
+
+
+@dataclasses.dataclass
+class Image:
+    rgb: torch.Tensor    # [3,H,W]
+    depth: torch.Tensor  # [H,W]
+    alpha: torch.Tensor  # [H,W]
+
+
+def _image_array(images: Sequence[Optional[Image]]):
+    arr = (_abi.mgs_image * len(images))()
+    for i, im in enumerate(images):
+        if im is None:
+            arr[i] = _abi.mgs_image(None, None, None)
+        else:
+            arr[i] = _abi.mgs_image(_ptr(im.rgb), _ptr(im.depth), _ptr(im.alpha))
+    return arr
+
+
+def new_images(cams, device="cuda") -> List[Image]:
+    out = []
+    for c in cams:
+        H, W = int(c.height), int(c.width)
+        out.append(Image(torch.empty(3, H, W, device=device), torch.empty(H, W, device=device),
+                         torch.empty(H, W, device=device)))
+    return out
+
+
+@dataclasses.dataclass
+class Grads:
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logit: torch.Tensor
+    sh: torch.Tensor
+    grad_stat: Optional[torch.Tensor] = None
+    vis_count: Optional[torch.Tensor] = None
+
+    @staticmethod
+    def zeros_like(g: Gaussians, stats: bool = True) -> "Grads":
+        z = lambda t: torch.zeros(t.shape, dtype=torch.float32, device=t.device)
+        n = g.n
+        return Grads(z(g.means), z(g.log_scales), z(g.quats), z(g.opacity_logit), z(g.sh),
+                     torch.zeros(n, device=g.means.device) if stats else None,
+                     torch.zeros(n, device=g.means.device) if stats else None)
+
+    def tensors(self):
+        return [self.means, self.log_scales, self.quats, self.opacity_logit, self.sh]
+
+    def struct(self) -> _abi.mgs_grads:
+        return _abi.mgs_grads(_ptr(self.means), _ptr(self.log_scales), _ptr(self.quats),
+                              _ptr(self.opacity_logit), _ptr(self.sh), _ptr(self.grad_stat),
+                              _ptr(self.vis_count))
+
+
+class RenderWorkspace:
+    """Caller-owned scratch of mgs_render / mgs_render_backward, grown on demand."""
+
+    def __init__(self, device="cuda", key_headroom: float = 1.25):
+        self.device = torch.device(device)
+        self.buf: Optional[torch.Tensor] = None
+        self.headroom = key_headroom
+        self.n_keys = 0
+
+    def ensure(self, n, cams, key_capacity) -> torch.Tensor:
+        arr = _cam_array(cams)
+        need = load().mgs_render_workspace_size(n, arr, len(cams), int(key_capacity))
+        if need == 0:
+            raise ValueError("invalid render arguments")
+        if self.buf is None or self.buf.numel() < need:
+            self.buf = None
+            self.buf = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def mgs_render(g: Gaussians, cams, out: List[Image], ws: RenderWorkspace, stream=None) -> int:
+    """One call of mgs_render; grows the workspace and retries when it is too small."""
+    L = load()
+    gs = g.struct()
+    arr = _cam_array(cams)
+    imgs = _image_array(out)
+    if ws.buf is None:
+        ws.ensure(g.n, cams, max(1024, 8 * g.n * len(cams)))
+    for _ in range(3):
+        nk = C.c_int64(0)
+        st = L.mgs_render(C.byref(gs), arr, len(cams), imgs, _ptr(ws.buf), ws.buf.numel(), C.byref(nk),
+                          _stream(stream))
+        if st == _abi.MGS_ERR_WORKSPACE and nk.value > 0:
+            ws.ensure(g.n, cams, int(nk.value * ws.headroom) + 1024)
+            continue
+        check(st, "mgs_render")
+        ws.n_keys = nk.value
+        return nk.value
+    check(st, "mgs_render")
+    return 0
+
+
+def mgs_render_backward(g: Gaussians, cams, dL: Sequence[Optional[Image]], ws: RenderWorkspace,
+                        grads: Grads, stream=None):
+    L = load()
+    gs = g.struct()
+    check(L.mgs_render_backward(C.byref(gs), _cam_array(cams), len(cams), _image_array(dL),
+                                _ptr(ws.buf), ws.buf.numel(), C.byref(grads.struct()), _stream(stream)),
+          "mgs_render_backward")
+
+
+def render(g: Gaussians, cams, ws: Optional[RenderWorkspace] = None, stream=None):
+    """render(gaussians, cameras) -> list of Image (rgb [3,H,W], depth, alpha) per view."""
+    ws = ws or RenderWorkspace(g.means.device)
+    out = new_images(cams, g.means.device)
+    mgs_render(g, cams, out, ws, stream)
+    return out, ws
+
+
+def render_backward(g: Gaussians, cams, dL: Sequence[Optional[Image]], ws: RenderWorkspace,
+                    grads: Optional[Grads] = None, stream=None) -> Grads:
+    """render_backward(dL/dimage) -> dL/dgaussians (accumulated into ``grads``)."""
+    grads = grads or Grads.zeros_like(g)
+    mgs_render_backward(g, cams, dL, ws, grads, stream)
+    return grads
+
+
+def mgs_project(g: Gaussians, cam, stream=None):
+    n, dev = g.n, g.means.device
+    out = dict(mean2d=torch.zeros(n, 2, device=dev), conic=torch.zeros(n, 3, device=dev),
+               rgb=torch.zeros(n, 3, device=dev), depth=torch.zeros(n, device=dev),
+               radius=torch.zeros(n, dtype=torch.int32, device=dev),
+               rect=torch.zeros(n, 4, dtype=torch.int32, device=dev))
+    c = camera_struct(cam)
+    check(load().mgs_project(C.byref(g.struct()), C.byref(c), _ptr(out["mean2d"]), _ptr(out["conic"]),
+                             _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["radius"]),
+                             _ptr(out["rect"]), _stream(stream)), "mgs_project")
+    return out
+
+
+project = mgs_project
+
+
+def mgs_voxel_merge(g: Gaussians, voxel_size: float, chi2: float = 7.815, greedy: bool = True,
+                    grad_stat: Optional[torch.Tensor] = None, grad_tau: float = 1e-3,
+                    kf_id: Optional[torch.Tensor] = None, kf_min: int = 0, kf_max: int = 0,
+                    workspace: Optional[torch.Tensor] = None, out: Optional[Gaussians] = None,
+                    partner: Optional[torch.Tensor] = None, vox: Optional[torch.Tensor] = None,
+                    stream=None):
+    """voxel_merge(gaussians, voxel_size, thresholds) -> (gaussians, partner, voxel coords).
+
+    ``workspace``, ``out``, ``partner`` and ``vox`` may be passed preallocated."""
+    if g.birth is None:
+        raise ValueError("voxel merge needs birth stamps")
+    L = load()
+    n, dev = g.n, g.means.device
+    need = L.mgs_voxel_merge_workspace_size(n)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    out = out if out is not None else g.empty_like()
+    partner = partner if partner is not None else torch.empty(n, dtype=torch.int32, device=dev)
+    vox = vox if vox is not None else torch.empty(n, 3, dtype=torch.int32, device=dev)
+    p = _abi.mgs_merge_params(chi2, grad_tau, kf_min, kf_max, _ptr(grad_stat), _ptr(kf_id),
+                              1 if greedy else 0, 0)
+    n_out = C.c_int64(0)
+    check(L.mgs_voxel_merge(C.byref(g.struct()), float(voxel_size), C.byref(p), C.byref(out.struct()),
+                            _ptr(partner), _ptr(vox), C.byref(n_out), _ptr(workspace),
+                            workspace.numel(), _stream(stream)), "mgs_voxel_merge")
+    k = n_out.value
+    res = Gaussians(out.means[:k], out.log_scales[:k], out.quats[:k], out.opacity_logit[:k], out.sh[:k],
+                    out.birth[:k])
+    return res, partner, vox
+
+
+voxel_merge = mgs_voxel_merge
+
+
+def mgs_adam_step(g: Gaussians, grads: Grads, m: Grads, v: Grads, lr: float, beta1=0.9,
+                  beta2=0.999, eps=1e-8, step: int = 1, zero_grads: bool = False, stream=None):
+    check(load().mgs_adam_step(C.byref(g.struct()), C.byref(grads.struct()), C.byref(m.struct()),
+                               C.byref(v.struct()), lr, beta1, beta2, eps, step, 1 if zero_grads else 0,
+                               _stream(stream)), "mgs_adam_step")
+
+
+adam_step = mgs_adam_step
+
+
+def mgs_l1_loss_grad(pred: torch.Tensor, target: torch.Tensor, scale: float, grad: torch.Tensor,
+                     loss: Optional[torch.Tensor] = None, stream=None):
+    check(load().mgs_l1_loss_grad(_ptr(pred), _ptr(target), pred.numel(), scale, _ptr(grad), _ptr(loss),
+                                  _stream(stream)), "mgs_l1_loss_grad")
+
+
+def mgs_sort_pairs(keys: torch.Tensor, vals: Optional[torch.Tensor] = None, begin_bit=0, end_bit=32,
+                   stream=None):
+    """Stable sort of int32-stored u32 keys (in place); returns the values / permutation."""
+    L = load()
+    n = keys.numel()
+    ws = torch.empty(L.mgs_sort_workspace_size(n), dtype=torch.uint8, device=keys.device)
+    out = None if vals is not None else torch.empty(n, dtype=torch.int32, device=keys.device)
+    check(L.mgs_sort_pairs(_ptr(keys), _ptr(vals), _ptr(out), n, begin_bit, end_bit, _ptr(ws), ws.numel(),
+                           _stream(stream)), "mgs_sort_pairs")
+    return vals if vals is not None else out
+
+
+def version() -> str:
+    return load().mgs_version().decode()
+
+
+def launch_count() -> int:
+    return int(load().mgs_launch_count())
+
+
+def profile_enable(on: bool):
+    load().mgs_profile_enable(1 if on else 0)
+
+
+def profile_read():
+    """{kernel group: (total ms, launches)} recorded since profile_enable(True)."""
+    L = load()
+    k = 32
+    names = C.create_string_buffer(32 * k)
+    ms = (C.c_double * k)()
+    cnt = (C.c_int64 * k)()
+    n = L.mgs_profile_read(k, names, ms, cnt)
+    raw = names.raw
+    out = {}
+    for i in range(min(n, k)):
+        nm = raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[i]), int(cnt[i]))
+    return out
+
+
+def render_stats(g: Gaussians, cams, ws: RenderWorkspace, stream=None):
+    """Fragment counts of the last render on ``ws``: evaluated, contributing, walked by the
+    backward pass, and (Gaussian, tile) keys."""
+    st = (C.c_uint64 * 4)()
+    check(load().mgs_render_stats(C.byref(g.struct()), _cam_array(cams), len(cams), _ptr(ws.buf),
+                                  ws.buf.numel(), st, _stream(stream)), "mgs_render_stats")
+    return dict(evaluated=int(st[0]), contributing=int(st[1]), backward_walked=int(st[2]), keys=int(st[3]))
+
+
+# ---------------------------------------------------------------------------------
+class RenderFn(torch.autograd.Function):
+    """Differentiable multi-view render through libmemgs.
+
+    apply(means, log_scales, quats, opacity_logit, sh, cams, ws) -> (rgb [V,3,H,W],
+    depth [V,H,W], alpha [V,H,W]) for views of one resolution.  The backward pass is
+    mgs_render_backward on the same workspace; parameter gradients are f32.
+    """
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logit, sh, cams, ws):
+        g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), opacity_logit.detach(),
+                      sh.detach())
+        V = len(cams)
+        H, W = int(cams[0].height), int(cams[0].width)
+        rgb = torch.empty(V, 3, H, W, device=means.device)
+        depth = torch.empty(V, H, W, device=means.device)
+        alpha = torch.empty(V, H, W, device=means.device)
+        out = [Image(rgb[v], depth[v], alpha[v]) for v in range(V)]
+        mgs_render(g, cams, out, ws)
+        ctx.cams, ctx.ws = cams, ws
+        ctx.save_for_backward(means, log_scales, quats, opacity_logit, sh)
+        return rgb, depth, alpha
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_alpha):
+        means, log_scales, quats, opacity_logit, sh = ctx.saved_tensors
+        g = Gaussians(means, log_scales, quats, opacity_logit, sh)
+        V = len(ctx.cams)
+        c = lambda t: None if t is None else t.contiguous()
+        g_rgb, g_depth, g_alpha = c(g_rgb), c(g_depth), c(g_alpha)
+        dL = [Image(None if g_rgb is None else g_rgb[v], None if g_depth is None else g_depth[v],
+                    None if g_alpha is None else g_alpha[v]) for v in range(V)]
+        arr = (_abi.mgs_image * V)()
+        for v, im in enumerate(dL):
+            arr[v] = _abi.mgs_image(_ptr(im.rgb), _ptr(im.depth), _ptr(im.alpha))
+        grads = Grads.zeros_like(g, stats=False)
+        check(load().mgs_render_backward(C.byref(g.struct()), _cam_array(ctx.cams), V, arr,
+                                         _ptr(ctx.ws.buf), ctx.ws.buf.numel(), C.byref(grads.struct()),
+                                         _stream()), "mgs_render_backward")
+        cast = lambda gr, p: gr if p.dtype == torch.float32 else gr.to(p.dtype)
+        return (grads.means, cast(grads.log_scales, log_scales), cast(grads.quats, quats),
+                cast(grads.opacity_logit, opacity_logit), cast(grads.sh, sh), None, None)
+
+
+def render_views(g: Gaussians, cams, ws: Optional[RenderWorkspace] = None):
+    """Differentiable render of same-resolution views: returns (rgb, depth, alpha) tensors."""
+    ws = ws or RenderWorkspace(g.means.device)
+    return RenderFn.apply(g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, cams, ws)

@@ -1,0 +1,440 @@
+// C ABI of libmemgs: argument validation, workspace carving and launch sequencing.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace mgs {
+
+// kernels of the other translation units
+cudaError_t launch_preprocess(const mgs_gaussians& g, const ViewTable& vt, float4* rec, uint2* rects,
+                              uint32_t* touched, uint32_t* dkeys, unsigned long long* counters,
+                              cudaStream_t s);
+cudaError_t launch_preprocess_bwd(const mgs_gaussians& g, const ViewTable& vt, const float4* moments,
+                                  const uint32_t* touched, const mgs_grads& gr, cudaStream_t s);
+cudaError_t launch_project_one(const mgs_gaussians& g, const View& V, float* mean2d, float* conic,
+                               float* rgb, float* depth, int32_t* radius, int32_t* rect, cudaStream_t s);
+cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const uint32_t* offsets,
+                        const uint2* rects, const ViewTable& vt, uint32_t* tkeys, uint32_t* tvals,
+                        cudaStream_t s);
+cudaError_t launch_blend_fwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
+                             const uint2* ranges, cudaStream_t s);
+cudaError_t launch_blend_bwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
+                             const uint2* ranges, float4* moments, cudaStream_t s);
+cudaError_t launch_frag_stats(const ViewTable& vt, const float4* rec, const uint32_t* vals,
+                              const uint2* ranges, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_adam(const mgs_gaussians_mut& p, const mgs_grads& g, const mgs_grads& m,
+                        const mgs_grads& v, float lr, float b1, float b2, float eps, int step,
+                        int zero_grads, cudaStream_t s);
+cudaError_t launch_l1(const float* pred, const float* target, int64_t n, float scale, float* grad,
+                      float* loss, cudaStream_t s);
+struct MergeWs;
+size_t merge_workspace_bytes(int64_t n, MergeWs* ws, char* base);
+cudaError_t run_voxel_merge(const mgs_gaussians& in, float voxel, const mgs_merge_params& p,
+                            const mgs_gaussians_mut& out, int32_t* partner, int32_t* vox,
+                            int64_t* n_out_host, char* ws_base, cudaStream_t s, int* unsupported);
+
+namespace {
+thread_local std::string g_error;
+
+mgs_status fail(mgs_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+// ---------------- render workspace ----------------
+struct RenderLayout {
+  int64_t N = 0, VN = 0, pixels = 0, tiles = 0, key_cap = 0;
+  size_t hdr, rec, rects, touched, dkeys[2], dvals[2], offsets, tkeys[2], tvals[2], ranges,
+      tfinal, ncontrib, moments, scratch, total;
+};
+
+bool cams_valid(const mgs_camera* cams, int nv, std::string* why) {
+  if (!cams || nv < 1 || nv > MGS_MAX_VIEWS) {
+    *why = "n_views must be in [1, MGS_MAX_VIEWS] with a camera array";
+    return false;
+  }
+  for (int v = 0; v < nv; ++v) {
+    const mgs_camera& c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || c.width > 65535 * MGS_TILE || c.height > 65535 * MGS_TILE ||
+        !(c.fx > 0) || !(c.fy > 0) || !(c.near_z > 0) || !std::isfinite(c.cx) || !std::isfinite(c.cy)) {
+      *why = "camera " + std::to_string(v) + ": need width, height, fx, fy, near_z > 0";
+      return false;
+    }
+  }
+  return true;
+}
+
+RenderLayout render_layout(int64_t n, const mgs_camera* cams, int nv, int64_t key_cap) {
+  RenderLayout L;
+  L.N = n;
+  L.VN = n * nv;
+  for (int v = 0; v < nv; ++v) {
+    L.pixels += (int64_t)cams[v].width * cams[v].height;
+    L.tiles += div_up(cams[v].width, MGS_TILE) * div_up(cams[v].height, MGS_TILE);
+  }
+  L.key_cap = key_cap;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(std::max<size_t>(bytes, 1)); return o; };
+  const size_t vn = (size_t)std::max<int64_t>(L.VN, 1), kc = (size_t)std::max<int64_t>(key_cap, 1);
+  L.hdr = take(256);
+  L.rec = take(48 * vn);
+  L.rects = take(8 * vn);
+  L.touched = take(4 * vn);
+  L.dkeys[0] = take(4 * vn);
+  L.dkeys[1] = take(4 * vn);
+  L.dvals[0] = take(4 * vn);
+  L.dvals[1] = take(4 * vn);
+  L.offsets = take(4 * vn);
+  L.tkeys[0] = take(4 * kc);
+  L.tkeys[1] = take(4 * kc);
+  L.tvals[0] = take(4 * kc);
+  L.tvals[1] = take(4 * kc);
+  L.ranges = take(8 * (size_t)L.tiles);
+  L.tfinal = take(4 * (size_t)L.pixels);
+  L.ncontrib = take(4 * (size_t)L.pixels);
+  L.moments = take(48 * vn);
+  L.scratch = take(4 * (size_t)sort_scratch_words(std::max<int64_t>(L.VN, key_cap)));
+  L.total = off;
+  return L;
+}
+
+// Largest key capacity whose layout fits in `bytes` (-1 if not even zero keys fit).
+int64_t key_capacity_for(int64_t n, const mgs_camera* cams, int nv, size_t bytes) {
+  if (render_layout(n, cams, nv, 0).total > bytes) return -1;
+  int64_t lo = 0, hi = 1;
+  while (render_layout(n, cams, nv, hi).total <= bytes && hi < (int64_t(1) << 40)) hi *= 2;
+  while (hi - lo > 1) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (render_layout(n, cams, nv, mid).total <= bytes) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+int tile_bits(int64_t tiles) {
+  int b = 1;
+  while ((int64_t(1) << b) < tiles) ++b;
+  return b;
+}
+
+template <class T>
+T* at(void* base, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(base) + off); }
+
+void fill_view(View& V, const mgs_camera& c) {
+  std::memcpy(V.R, c.R, sizeof(V.R));
+  std::memcpy(V.t, c.t, sizeof(V.t));
+  V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy; V.near_z = c.near_z;
+  for (int k = 0; k < 3; ++k) V.C[k] = -(c.R[k] * c.t[0] + c.R[3 + k] * c.t[1] + c.R[6 + k] * c.t[2]);
+  V.limx = kFovClamp * (0.5f * (float)c.width / c.fx);
+  V.limy = kFovClamp * (0.5f * (float)c.height / c.fy);
+  V.width = c.width; V.height = c.height;
+  V.tiles_x = (int)div_up(c.width, MGS_TILE);
+  V.tiles_y = (int)div_up(c.height, MGS_TILE);
+}
+
+ViewTable make_table(const mgs_camera* cams, int nv, const RenderLayout& L, void* ws) {
+  ViewTable vt{};
+  vt.n_views = nv;
+  int tb = 0;
+  int64_t pb = 0;
+  for (int v = 0; v < nv; ++v) {
+    View& V = vt.v[v];
+    fill_view(V, cams[v]);
+    V.tile_base = tb;
+    tb += V.tiles_x * V.tiles_y;
+    V.T_final = at<float>(ws, L.tfinal) + pb;
+    V.n_contrib = at<uint32_t>(ws, L.ncontrib) + pb;
+    pb += (int64_t)V.width * V.height;
+  }
+  vt.n_tiles = tb;
+  return vt;
+}
+
+std::string check_gaussians(const mgs_gaussians* g, bool need_birth) {
+  if (!g) return "gaussians pointer is NULL";
+  if (g->n < 0) return "n < 0";
+  if (g->sh_degree < 0 || g->sh_degree > 3) return "sh_degree must be 0..3";
+  if (g->attr_dtype < MGS_F32 || g->attr_dtype > MGS_BF16) return "attr_dtype must be MGS_F32, MGS_F16 or MGS_BF16";
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logit || !g->sh))
+    return "parameter pointer is NULL";
+  if (need_birth && g->n > 0 && !g->birth) return "birth is NULL";
+  return "";
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_error = msg; }
+mgs_status cuda_status(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return MGS_ERR_CUDA;
+}
+
+}  // namespace mgs
+
+using namespace mgs;
+
+extern "C" {
+
+const char* mgs_last_error(void) { return g_error.c_str(); }
+const char* mgs_version(void) { return "memgs 0.1 sm_103a"; }
+
+size_t mgs_render_workspace_size(int64_t n, const mgs_camera* cams, int32_t n_views,
+                                 int64_t key_capacity) {
+  std::string why;
+  if (n < 0 || key_capacity < 0 || !cams_valid(cams, n_views, &why)) return 0;
+  return render_layout(n, cams, n_views, key_capacity).total;
+}
+
+mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_views,
+                      const mgs_image* out, void* workspace, size_t workspace_bytes,
+                      int64_t* n_keys_host, void* stream) {
+  set_error("");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::string why = check_gaussians(g, false);
+  if (!why.empty()) return fail(MGS_ERR_INVALID, why);
+  if (!cams_valid(cams, n_views, &why)) return fail(MGS_ERR_INVALID, why);
+  if (!out || !workspace) return fail(MGS_ERR_INVALID, "out or workspace is NULL");
+  for (int v = 0; v < n_views; ++v)
+    if (!out[v].rgb || !out[v].depth || !out[v].alpha) return fail(MGS_ERR_INVALID, "image plane is NULL");
+  if (g->n * n_views >= (int64_t)UINT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "n * n_views must be < 2^32");
+  int64_t cap = key_capacity_for(g->n, cams, n_views, workspace_bytes);
+  if (cap < 0) {
+    if (n_keys_host) *n_keys_host = 0;
+    return fail(MGS_ERR_WORKSPACE, "workspace smaller than the zero-key layout");
+  }
+  RenderLayout L = render_layout(g->n, cams, n_views, cap);
+  ViewTable vt = make_table(cams, n_views, L, workspace);
+  for (int v = 0; v < n_views; ++v) {
+    vt.v[v].rgb = out[v].rgb;
+    vt.v[v].depth = out[v].depth;
+    vt.v[v].alpha = out[v].alpha;
+  }
+  auto* counters = at<unsigned long long>(workspace, L.hdr);
+  auto* rec = at<float4>(workspace, L.rec);
+  auto* rects = at<uint2>(workspace, L.rects);
+  auto* touched = at<uint32_t>(workspace, L.touched);
+  uint32_t* dk[2] = {at<uint32_t>(workspace, L.dkeys[0]), at<uint32_t>(workspace, L.dkeys[1])};
+  uint32_t* dv[2] = {at<uint32_t>(workspace, L.dvals[0]), at<uint32_t>(workspace, L.dvals[1])};
+  uint32_t* tk[2] = {at<uint32_t>(workspace, L.tkeys[0]), at<uint32_t>(workspace, L.tkeys[1])};
+  uint32_t* tv[2] = {at<uint32_t>(workspace, L.tvals[0]), at<uint32_t>(workspace, L.tvals[1])};
+  auto* offsets = at<uint32_t>(workspace, L.offsets);
+  auto* ranges = at<uint2>(workspace, L.ranges);
+  auto* scratch = at<uint32_t>(workspace, L.scratch);
+
+  {
+    ProfScope ps(kProfPreprocess, s);
+    MGS_TRY_CUDA(cudaMemsetAsync(counters, 0, 256, s));
+    MGS_TRY_CUDA(launch_preprocess(*g, vt, rec, rects, touched, dk[0], counters, s));
+  }
+  unsigned long long cnt[2] = {0, 0};
+  MGS_TRY_CUDA(cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+  MGS_TRY_CUDA(cudaStreamSynchronize(s));
+  const int64_t n_keys = (int64_t)cnt[0], n_vis = (int64_t)cnt[1];
+  if (n_keys_host) *n_keys_host = n_keys;
+  if (n_keys >= (int64_t)UINT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "more than 2^32-1 (Gaussian, tile) pairs");
+  if (n_keys > cap)
+    return fail(MGS_ERR_WORKSPACE, "workspace holds " + std::to_string(cap) + " keys, render needs " +
+                                       std::to_string(n_keys));
+  cudaError_t e = cudaSuccess;
+  int dcur = 0;
+  if (L.VN > 0) {
+    // front-to-back order of every (view, Gaussian) item: float32 depth bits, then item index
+    ProfScope ps(kProfDepthSort, s);
+    dcur = radix_sort_pairs(dk, dv, L.VN, 0, 32, true, scratch, s, &e);
+    if (e != cudaSuccess) return cuda_status(e, "depth sort");
+    MGS_TRY_CUDA(scan_exclusive_u32(touched, dv[dcur], offsets, n_vis, scratch, nullptr, s));
+  }
+  {
+    ProfScope ps(kProfEmit, s);
+    MGS_TRY_CUDA(launch_emit(n_vis, g->n, dv[dcur], offsets, rects, vt, tk[0], tv[0], s));
+  }
+  int tcur = 0;
+  {
+    ProfScope ps(kProfTileSort, s);
+    tcur = radix_sort_pairs(tk, tv, n_keys, 0, tile_bits(vt.n_tiles), false, scratch, s, &e);
+    if (e != cudaSuccess) return cuda_status(e, "tile sort");
+    MGS_TRY_CUDA(cudaMemsetAsync(ranges, 0, 8 * (size_t)vt.n_tiles, s));
+    MGS_TRY_CUDA(build_ranges(tk[tcur], n_keys, ranges, s));
+  }
+  {
+    ProfScope ps(kProfBlendFwd, s);
+    MGS_TRY_CUDA(launch_blend_fwd(vt, rec, tv[tcur], ranges, s));
+  }
+  return MGS_OK;
+}
+
+mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_views,
+                               const mgs_image* dL, void* workspace, size_t workspace_bytes,
+                               const mgs_grads* grads, void* stream) {
+  set_error("");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::string why = check_gaussians(g, false);
+  if (!why.empty()) return fail(MGS_ERR_INVALID, why);
+  if (!cams_valid(cams, n_views, &why)) return fail(MGS_ERR_INVALID, why);
+  if (!dL || !workspace || !grads) return fail(MGS_ERR_INVALID, "dL, workspace or grads is NULL");
+  if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit || !grads->sh))
+    return fail(MGS_ERR_INVALID, "gradient pointer is NULL");
+  int64_t cap = key_capacity_for(g->n, cams, n_views, workspace_bytes);
+  if (cap < 0) return fail(MGS_ERR_WORKSPACE, "workspace smaller than the zero-key layout");
+  RenderLayout L = render_layout(g->n, cams, n_views, cap);
+  ViewTable vt = make_table(cams, n_views, L, workspace);
+  for (int v = 0; v < n_views; ++v) {
+    vt.v[v].g_rgb = dL[v].rgb;
+    vt.v[v].g_depth = dL[v].depth;
+    vt.v[v].g_alpha = dL[v].alpha;
+  }
+  uint32_t* tv[2] = {at<uint32_t>(workspace, L.tvals[0]), at<uint32_t>(workspace, L.tvals[1])};
+  int tcur = radix_passes(0, tile_bits(vt.n_tiles)) & 1;
+  auto* moments = at<float4>(workspace, L.moments);
+  {
+    ProfScope ps(kProfBlendBwd, s);
+    MGS_TRY_CUDA(cudaMemsetAsync(moments, 0, 48 * (size_t)L.VN, s));
+    MGS_TRY_CUDA(launch_blend_bwd(vt, at<float4>(workspace, L.rec), tv[tcur], at<uint2>(workspace, L.ranges),
+                                  moments, s));
+  }
+  {
+    ProfScope ps(kProfPreprocessBwd, s);
+    MGS_TRY_CUDA(launch_preprocess_bwd(*g, vt, moments, at<uint32_t>(workspace, L.touched), *grads, s));
+  }
+  return MGS_OK;
+}
+
+mgs_status mgs_render_stats(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_views, void* workspace,
+                            size_t workspace_bytes, uint64_t* stats, void* stream) {
+  set_error("");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::string why = check_gaussians(g, false);
+  if (!why.empty()) return fail(MGS_ERR_INVALID, why);
+  if (!cams_valid(cams, n_views, &why)) return fail(MGS_ERR_INVALID, why);
+  if (!workspace || !stats) return fail(MGS_ERR_INVALID, "workspace or stats is NULL");
+  int64_t cap = key_capacity_for(g->n, cams, n_views, workspace_bytes);
+  if (cap < 0) return fail(MGS_ERR_WORKSPACE, "workspace smaller than the zero-key layout");
+  RenderLayout L = render_layout(g->n, cams, n_views, cap);
+  ViewTable vt = make_table(cams, n_views, L, workspace);
+  uint32_t* tv[2] = {at<uint32_t>(workspace, L.tvals[0]), at<uint32_t>(workspace, L.tvals[1])};
+  int tcur = radix_passes(0, tile_bits(vt.n_tiles)) & 1;
+  auto* hdr = at<unsigned long long>(workspace, L.hdr);
+  MGS_TRY_CUDA(cudaMemsetAsync(hdr + 4, 0, 32, s));
+  MGS_TRY_CUDA(launch_frag_stats(vt, at<float4>(workspace, L.rec), tv[tcur], at<uint2>(workspace, L.ranges),
+                                 hdr + 4, s));
+  unsigned long long h[8];
+  MGS_TRY_CUDA(cudaMemcpyAsync(h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MGS_TRY_CUDA(cudaStreamSynchronize(s));
+  stats[0] = h[4];
+  stats[1] = h[5];
+  stats[2] = h[6];
+  stats[3] = h[0];
+  return MGS_OK;
+}
+
+mgs_status mgs_project(const mgs_gaussians* g, const mgs_camera* cam, float* mean2d, float* conic,
+                       float* rgb, float* depth, int32_t* radius, int32_t* rect, void* stream) {
+  set_error("");
+  std::string why = check_gaussians(g, false);
+  if (!why.empty()) return fail(MGS_ERR_INVALID, why);
+  if (!cams_valid(cam, 1, &why)) return fail(MGS_ERR_INVALID, why);
+  View V{};
+  fill_view(V, *cam);
+  MGS_TRY_CUDA(launch_project_one(*g, V, mean2d, conic, rgb, depth, radius, rect, (cudaStream_t)stream));
+  return MGS_OK;
+}
+
+size_t mgs_voxel_merge_workspace_size(int64_t n) {
+  if (n < 0) return 0;
+  return merge_workspace_bytes(n, nullptr, nullptr);
+}
+
+mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_merge_params* p,
+                           const mgs_gaussians_mut* out, int32_t* partner, int32_t* voxel,
+                           int64_t* n_out_host, void* workspace, size_t workspace_bytes, void* stream) {
+  set_error("");
+  std::string why = check_gaussians(in, true);
+  if (!why.empty()) return fail(MGS_ERR_INVALID, why);
+  if (!p || !out || !n_out_host) return fail(MGS_ERR_INVALID, "params, out or n_out_host is NULL");
+  if (!(voxel_size > 0) || !std::isfinite(voxel_size)) return fail(MGS_ERR_INVALID, "voxel_size must be > 0");
+  if (!(p->chi2 > 0)) return fail(MGS_ERR_INVALID, "chi2 must be > 0");
+  if (out->n < in->n || out->sh_degree != in->sh_degree || out->attr_dtype != in->attr_dtype)
+    return fail(MGS_ERR_INVALID, "out must have capacity >= n and the same sh_degree / attr_dtype");
+  if (in->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logit || !out->sh))
+    return fail(MGS_ERR_INVALID, "output pointer is NULL");
+  if (in->n >= (int64_t)INT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "n must be < 2^31");
+  if (!workspace || workspace_bytes < merge_workspace_bytes(in->n, nullptr, nullptr))
+    return fail(MGS_ERR_WORKSPACE, "merge workspace too small");
+  if (in->n == 0) {
+    *n_out_host = 0;
+    return MGS_OK;
+  }
+  int unsupported = 0;
+  ProfScope ps(kProfMerge, (cudaStream_t)stream);
+  cudaError_t e = run_voxel_merge(*in, voxel_size, *p, *out, partner, voxel, n_out_host,
+                                  static_cast<char*>(workspace), (cudaStream_t)stream, &unsupported);
+  if (e != cudaSuccess) return cuda_status(e, "voxel merge");
+  if (unsupported == 1) return fail(MGS_ERR_UNSUPPORTED, "voxel coordinate outside +-2^20");
+  if (unsupported == 2) return fail(MGS_ERR_UNSUPPORTED, "a voxel holds more than 256 eligible Gaussians");
+  if (unsupported == 3) return fail(MGS_ERR_UNSUPPORTED, "occupied voxel box needs more than 31 key bits");
+  return MGS_OK;
+}
+
+mgs_status mgs_adam_step(const mgs_gaussians_mut* params, const mgs_grads* grads, const mgs_grads* m,
+                         const mgs_grads* v, float lr, float beta1, float beta2, float eps,
+                         int32_t step, int32_t zero_grads, void* stream) {
+  set_error("");
+  if (!params || !grads || !m || !v) return fail(MGS_ERR_INVALID, "NULL argument");
+  if (params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3 || step < 1)
+    return fail(MGS_ERR_INVALID, "need n >= 0, sh_degree 0..3, step >= 1");
+  if (params->attr_dtype < MGS_F32 || params->attr_dtype > MGS_BF16) return fail(MGS_ERR_INVALID, "bad attr_dtype");
+  if (!(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return fail(MGS_ERR_INVALID, "need 0 <= beta < 1 and eps > 0");
+  ProfScope ps(kProfAdam, (cudaStream_t)stream);
+  MGS_TRY_CUDA(launch_adam(*params, *grads, *m, *v, lr, beta1, beta2, eps, step, zero_grads ? 1 : 0,
+                           (cudaStream_t)stream));
+  return MGS_OK;
+}
+
+mgs_status mgs_l1_loss_grad(const float* pred, const float* target, int64_t n, float scale,
+                            float* grad, float* loss, void* stream) {
+  set_error("");
+  if (n < 0 || (n > 0 && (!pred || !target || !grad))) return fail(MGS_ERR_INVALID, "bad arguments");
+  ProfScope ps(kProfLoss, (cudaStream_t)stream);
+  MGS_TRY_CUDA(launch_l1(pred, target, n, scale, grad, loss, (cudaStream_t)stream));
+  return MGS_OK;
+}
+
+size_t mgs_sort_workspace_size(int64_t n) {
+  if (n < 0) return 0;
+  size_t m = (size_t)std::max<int64_t>(n, 1);
+  return 3 * align_up(4 * m) + align_up(4 * (size_t)sort_scratch_words(n));
+}
+
+mgs_status mgs_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* vals_out, int64_t n,
+                          int32_t begin_bit, int32_t end_bit, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+  set_error("");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n < 0 || begin_bit < 0 || end_bit > 32 || begin_bit >= end_bit)
+    return fail(MGS_ERR_INVALID, "need n >= 0 and 0 <= begin_bit < end_bit <= 32");
+  if (n >= (int64_t)UINT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "n must be < 2^32");
+  if (n > 0 && (!keys || (!vals && !vals_out))) return fail(MGS_ERR_INVALID, "NULL keys or values");
+  if (!workspace || workspace_bytes < mgs_sort_workspace_size(n)) return fail(MGS_ERR_WORKSPACE, "sort workspace too small");
+  if (n == 0) return MGS_OK;
+  size_t m = align_up(4 * (size_t)n);
+  char* w = static_cast<char*>(workspace);
+  uint32_t* kalt = reinterpret_cast<uint32_t*>(w);
+  uint32_t* valt = reinterpret_cast<uint32_t*>(w + m);
+  uint32_t* vtmp = reinterpret_cast<uint32_t*>(w + 2 * m);
+  uint32_t* scratch = reinterpret_cast<uint32_t*>(w + 3 * m);
+  bool iota = vals == nullptr;
+  uint32_t* vdst = iota ? vals_out : vals;
+  uint32_t* K[2] = {keys, kalt};
+  uint32_t* V[2] = {iota ? vtmp : vals, valt};
+  cudaError_t e;
+  int cur = radix_sort_pairs(K, V, n, begin_bit, end_bit, iota, scratch, s, &e);
+  if (e != cudaSuccess) return cuda_status(e, "radix sort");
+  if (cur == 1) MGS_TRY_CUDA(cudaMemcpyAsync(keys, kalt, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  if (V[cur] != vdst) MGS_TRY_CUDA(cudaMemcpyAsync(vdst, V[cur], 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  return MGS_OK;
+}
+
+}  // extern "C"

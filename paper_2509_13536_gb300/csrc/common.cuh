@@ -1,0 +1,194 @@
+// Device-side helpers shared by the sm_103a kernels of libmemgs.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "memgs.h"
+
+namespace mgs {
+
+constexpr int kTile = MGS_TILE;             // tile edge, px
+constexpr int kTilePix = kTile * kTile;     // 256 pixels = 256 threads per tile CTA
+constexpr float kAlphaMin = 1.0f / 255.0f;  // skip below
+constexpr float kAlphaMax = 0.99f;          // clamp
+constexpr float kTStop = 1e-4f;             // stop once T falls below
+constexpr float kDilation = 0.3f;           // px^2 added to the 2D covariance diagonal
+constexpr float kFovClamp = 1.3f;           // ray clamp factor in the Jacobian
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Real orthonormal spherical harmonics, Cartesian forms on the unit sphere; each
+// constant is the normalisation written next to it.
+constexpr float kSh0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
+constexpr float kSh1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
+constexpr float kSh2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+constexpr float kSh2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+constexpr float kSh2c = 0.54627421529603959f;  // sqrt(15/pi)/4
+constexpr float kSh3a = 0.59004358992664352f;  // sqrt(35/(2 pi))/4
+constexpr float kSh3b = 2.8906114426405538f;   // sqrt(105/pi)/2
+constexpr float kSh3c = 0.45704579946446577f;  // sqrt(21/(2 pi))/4
+constexpr float kSh3d = 0.3731763325901154f;   // sqrt(7/pi)/4
+constexpr float kSh3e = 1.4453057213202769f;   // sqrt(105/pi)/4
+
+// Per-view constants, passed by value to every kernel of a render call.
+struct View {
+  float R[9], t[3];
+  float fx, fy, cx, cy, near_z;
+  float C[3];          // camera centre in world coordinates
+  float limx, limy;    // 1.3 * half field of view (tangent)
+  int width, height, tiles_x, tiles_y;
+  int tile_base;       // first global tile id of this view
+  float* rgb;          // forward outputs
+  float* depth;
+  float* alpha;
+  const float* g_rgb;  // backward cotangents (may be null)
+  const float* g_depth;
+  const float* g_alpha;
+  float* T_final;      // per-pixel saved state (workspace)
+  uint32_t* n_contrib;
+};
+
+struct ViewTable {
+  int n_views;
+  int n_tiles;         // sum over views
+  View v[MGS_MAX_VIEWS];
+};
+
+__device__ __forceinline__ int view_of_tile(const ViewTable& vt, int tile) {
+  int v = 0;
+  while (v + 1 < vt.n_views && vt.v[v + 1].tile_base <= tile) ++v;
+  return v;
+}
+
+// --- storage types: attributes may be f32, f16 or bf16; arithmetic is f32 ---
+__device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void st(float* p, float x) { *p = x; }
+__device__ __forceinline__ void st(__half* p, float x) { *p = __float2half_rn(x); }
+__device__ __forceinline__ void st(__nv_bfloat16* p, float x) { *p = __float2bfloat16_rn(x); }
+
+// --- error-free transformations (double-float arithmetic in f32) ---
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF s = two_sum(a.hi, b.hi);
+  float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, lo);
+}
+// x / y for double-float x, y (one Newton correction).
+__device__ __forceinline__ DF df_div(DF x, DF y) {
+  float q1 = __fdiv_rn(x.hi, y.hi);
+  DF p = two_prod(q1, y.hi);
+  float r = __fsub_rn(__fsub_rn(x.hi, p.hi), p.lo);
+  r = __fadd_rn(r, __fsub_rn(x.lo, __fmul_rn(q1, y.lo)));
+  float q2 = __fdiv_rn(r, y.hi);
+  return fast_two_sum(q1, q2);
+}
+// a * x + c with f32 a, c and double-float x.
+__device__ __forceinline__ DF df_axpc(float a, DF x, float c) {
+  DF p = two_prod(a, x.hi);
+  p.lo = __fmaf_rn(a, x.lo, p.lo);
+  DF s = two_sum(p.hi, c);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, p.lo));
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Rotation matrix of the unit quaternion (w, x, y, z), row-major.
+__device__ __forceinline__ void quat_rot(const float q[4], float R[9]) {
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Gradient of sum_ij G_ij R_ij with respect to the unit quaternion.
+__device__ __forceinline__ void quat_rot_vjp(const float q[4], const float G[9], float dq[4]) {
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  dq[0] = 2.f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
+  dq[1] = 2.f * (y * G[1] + z * G[2] + y * G[3] - 2.f * x * G[4] - w * G[5] + z * G[6] + w * G[7] - 2.f * x * G[8]);
+  dq[2] = 2.f * (-2.f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] - w * G[6] + z * G[7] - 2.f * y * G[8]);
+  dq[3] = 2.f * (-2.f * z * G[0] - w * G[1] + x * G[2] + w * G[3] - 2.f * z * G[4] + y * G[5] + x * G[6] + y * G[7]);
+}
+
+// Spherical-harmonic basis at unit direction d (K = (DEG+1)^2 values) and, when
+// dY != nullptr, the gradient of each Cartesian polynomial with respect to d.
+template <int DEG>
+__device__ __forceinline__ void sh_basis(const float d[3], float* Y, float (*dY)[3]) {
+  float x = d[0], y = d[1], z = d[2];
+  Y[0] = kSh0;
+  if (dY) { dY[0][0] = dY[0][1] = dY[0][2] = 0.f; }
+  if (DEG < 1) return;
+  Y[1] = kSh1 * y; Y[2] = kSh1 * z; Y[3] = kSh1 * x;
+  if (dY) {
+    dY[1][0] = 0.f; dY[1][1] = kSh1; dY[1][2] = 0.f;
+    dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = kSh1;
+    dY[3][0] = kSh1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+  }
+  if (DEG < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kSh2a * x * y;
+  Y[5] = kSh2a * y * z;
+  Y[6] = kSh2b * (3.f * zz - 1.f);
+  Y[7] = kSh2a * x * z;
+  Y[8] = kSh2c * (xx - yy);
+  if (dY) {
+    dY[4][0] = kSh2a * y; dY[4][1] = kSh2a * x; dY[4][2] = 0.f;
+    dY[5][0] = 0.f; dY[5][1] = kSh2a * z; dY[5][2] = kSh2a * y;
+    dY[6][0] = 0.f; dY[6][1] = 0.f; dY[6][2] = kSh2b * 6.f * z;
+    dY[7][0] = kSh2a * z; dY[7][1] = 0.f; dY[7][2] = kSh2a * x;
+    dY[8][0] = kSh2c * 2.f * x; dY[8][1] = -kSh2c * 2.f * y; dY[8][2] = 0.f;
+  }
+  if (DEG < 3) return;
+  Y[9] = kSh3a * y * (3.f * xx - yy);
+  Y[10] = kSh3b * x * y * z;
+  Y[11] = kSh3c * y * (5.f * zz - 1.f);
+  Y[12] = kSh3d * z * (5.f * zz - 3.f);
+  Y[13] = kSh3c * x * (5.f * zz - 1.f);
+  Y[14] = kSh3e * z * (xx - yy);
+  Y[15] = kSh3a * x * (xx - 3.f * yy);
+  if (dY) {
+    dY[9][0] = kSh3a * 6.f * x * y; dY[9][1] = kSh3a * 3.f * (xx - yy); dY[9][2] = 0.f;
+    dY[10][0] = kSh3b * y * z; dY[10][1] = kSh3b * x * z; dY[10][2] = kSh3b * x * y;
+    dY[11][0] = 0.f; dY[11][1] = kSh3c * (5.f * zz - 1.f); dY[11][2] = kSh3c * 10.f * y * z;
+    dY[12][0] = 0.f; dY[12][1] = 0.f; dY[12][2] = kSh3d * (15.f * zz - 3.f);
+    dY[13][0] = kSh3c * (5.f * zz - 1.f); dY[13][1] = 0.f; dY[13][2] = kSh3c * 10.f * x * z;
+    dY[14][0] = kSh3e * 2.f * x * z; dY[14][1] = -kSh3e * 2.f * y * z; dY[14][2] = kSh3e * (xx - yy);
+    dY[15][0] = kSh3a * 3.f * (xx - yy); dY[15][1] = -kSh3a * 6.f * x * y; dY[15][2] = 0.f;
+  }
+}
+
+// Fragment evaluation shared by the forward and backward blend so that both take
+// identical decisions.  xy: Gaussian centre relative to the tile origin; co: conic
+// pre-scaled by -log2(e)/2 (A, C) and -log2(e) (B), plus opacity.  Returns the
+// exponent in base 2 (> 0 means "skip").
+__device__ __forceinline__ float frag_exp2(float2 xy, float4 co, float pxf, float pyf, float& dx,
+                                           float& dy) {
+  dx = __fsub_rn(xy.x, pxf);
+  dy = __fsub_rn(xy.y, pyf);
+  float t = __fmaf_rn(co.x, dx, __fmul_rn(co.y, dy));
+  return __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(co.z, dy), dy));
+}
+
+}  // namespace mgs

@@ -1,0 +1,64 @@
+// Host-side declarations shared by the translation units of libmemgs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "common.cuh"
+
+namespace mgs {
+
+// ---- error reporting (thread-local message behind mgs_last_error) ----
+void set_error(const std::string& msg);
+mgs_status cuda_status(cudaError_t e, const char* what);
+#define MGS_TRY_CUDA(expr)                                 \
+  do {                                                     \
+    cudaError_t e_ = (expr);                               \
+    if (e_ != cudaSuccess) return cuda_status(e_, #expr);  \
+  } while (0)
+#define MGS_CHECK_LAUNCH(what) MGS_TRY_CUDA(cudaGetLastError())
+
+// ---- diagnostics (diag.cu) ----
+void count_launch(int n = 1);
+enum ProfKind { kProfPreprocess, kProfDepthSort, kProfEmit, kProfTileSort, kProfBlendFwd, kProfBlendBwd,
+                kProfPreprocessBwd, kProfAdam, kProfLoss, kProfMerge, kProfKinds };
+// Brackets a group of launches with CUDA events when profiling is on (no-op otherwise).
+struct ProfScope {
+  ProfScope(int kind, cudaStream_t s);
+  ~ProfScope();
+  int kind;
+  cudaStream_t s;
+  void* ev;
+};
+
+// ---- scan / radix sort (sort.cu) ----
+constexpr int kSortThreads = 256;
+constexpr int kSortPerThread = 16;
+constexpr int kSortTile = kSortThreads * kSortPerThread;  // 4096 items per block
+
+inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// u32 words of scratch needed to sort or scan n items.
+int64_t sort_scratch_words(int64_t n);
+
+// Exclusive scan out[i] = sum_{k<i} in[gather ? gather[k] : k]; out may alias in.
+// *total_dev (optional) receives the sum.  scratch: sort_scratch_words(n) words.
+cudaError_t scan_exclusive_u32(const uint32_t* in, const uint32_t* gather, uint32_t* out,
+                               int64_t n, uint32_t* scratch, uint32_t* total_dev,
+                               cudaStream_t s);
+
+// Stable LSD radix sort of (k[0], v[0]) on bits [begin, end).  When vals_iota the input
+// values are the positions 0..n-1 (v[0] is not read).  Returns the index (0 or 1) of the
+// buffer pair that holds the result.
+int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, int end_bit,
+                     bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err);
+inline int radix_passes(int begin_bit, int end_bit) {
+  return end_bit > begin_bit ? (end_bit - begin_bit + 7) / 8 : 0;
+}
+
+// [start, end) of every key value present in sorted keys (absent values untouched).
+cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint2* ranges, cudaStream_t s);
+
+}  // namespace mgs

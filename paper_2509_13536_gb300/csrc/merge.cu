@@ -1,0 +1,613 @@
+// Voxel-space merge of geometrically similar Gaussians (Sec. II-D), sm_103a.
+//
+//  1. k_voxel_prep   Eq. 3 mask, voxel coordinates floor(mu/v) (IEEE f32 quotient),
+//                    bounding box of the occupied voxels.
+//  2. k_voxel_pack   voxel coordinates packed relative to the box into one u32 key
+//                    (ineligible Gaussians get the all-ones key and sort last).
+//  3. radix sort of (key, index); segment heads -> one (start, end) per voxel.
+//  4. k_voxel_pairs  one warp per voxel (<= 32 members; larger voxels go to a
+//                    block-per-voxel kernel, <= 256 members): members ranked by
+//                    (birth, index), Eq. 4 for every older/younger pair, greedy
+//                    disjoint pairing on (d2, birth_i, birth_j, i, j) below chi2,
+//                    then the merge of each accepted pair: Eq. 6 mean, the
+//                    equal-weight 2-Wasserstein barycentre (minimiser of Eq. 9) in
+//                    closed form, eigen-decomposition back to (quaternion, scales).
+//  5. ordered compaction: survivors keep input order, merged values in G_i's slot.
+#include "internal.h"
+
+namespace mgs {
+
+struct MergeWs {
+  int32_t* vox;            // [n][3] voxel coordinates of eligible Gaussians
+  uint32_t* keys[2];       // [n]
+  uint32_t* perm[2];       // [n]
+  uint32_t* flags;         // [n] segment heads, then keep flags
+  uint32_t* pos;           // [n] exclusive scans
+  uint32_t* starts;        // [n + 1]
+  int32_t* partner;        // [n]
+  float* mmean;            // [n][3] merged mean (valid where the Gaussian survives a merge)
+  float* mquat;            // [n][4]
+  float* mlogs;            // [n][3]
+  uint32_t* big;           // [n] voxel ids with more than 32 members
+  int32_t* hdr;            // 16 ints: bbox min xyz, max xyz, n_elig, err, n_vox, n_big, n_out
+  uint32_t* scratch;       // sort / scan scratch
+};
+
+namespace {
+
+constexpr int kWarpVoxel = 32;
+constexpr int kBlockVoxel = 256;
+constexpr uint32_t kNoKey = 0xffffffffu;
+
+__device__ __forceinline__ bool older(uint64_t ba, int64_t a, uint64_t bb, int64_t b) {
+  return ba < bb || (ba == bb && a < b);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_qs(const T* qs, const T* ls, int64_t i, float q[4], float s[3]) {
+  for (int k = 0; k < 4; ++k) q[k] = ld(qs + 4 * i + k);
+  float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int k = 0; k < 4; ++k) q[k] *= n;
+  for (int k = 0; k < 3; ++k) s[k] = expf(ld(ls + 3 * i + k));
+}
+
+// R diag(d) R^T as 6 unique entries xx xy xz yy yz zz
+__device__ __forceinline__ void rdrt(const float R[9], const float d[3], float o[6]) {
+  o[0] = R[0] * R[0] * d[0] + R[1] * R[1] * d[1] + R[2] * R[2] * d[2];
+  o[1] = R[0] * R[3] * d[0] + R[1] * R[4] * d[1] + R[2] * R[5] * d[2];
+  o[2] = R[0] * R[6] * d[0] + R[1] * R[7] * d[1] + R[2] * R[8] * d[2];
+  o[3] = R[3] * R[3] * d[0] + R[4] * R[4] * d[1] + R[5] * R[5] * d[2];
+  o[4] = R[3] * R[6] * d[0] + R[4] * R[7] * d[1] + R[5] * R[8] * d[2];
+  o[5] = R[6] * R[6] * d[0] + R[7] * R[7] * d[1] + R[8] * R[8] * d[2];
+}
+
+template <typename T>
+__device__ __forceinline__ void precision_of(const T* qs, const T* ls, int64_t i, float P[6]) {
+  float q[4], s[3], R[9];
+  load_qs(qs, ls, i, q, s);
+  quat_rot(q, R);
+  float d[3] = {1.f / (s[0] * s[0]), 1.f / (s[1] * s[1]), 1.f / (s[2] * s[2])};
+  rdrt(R, d, P);
+}
+
+__device__ __forceinline__ float mahalanobis2(const float P[6], const float* mi, const float* mj) {
+  float d0 = mj[0] - mi[0], d1 = mj[1] - mi[1], d2 = mj[2] - mi[2];
+  return P[0] * d0 * d0 + P[3] * d1 * d1 + P[5] * d2 * d2 +
+         2.f * (P[1] * d0 * d1 + P[2] * d0 * d2 + P[4] * d1 * d2);
+}
+
+// Cyclic Jacobi on a symmetric 3x3 (full row-major A), eigenvectors in the columns of V.
+__device__ void jacobi3(float A[9], float V[9]) {
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.f : 0.f;
+  const int P[3] = {0, 0, 1}, Q[3] = {1, 2, 2};
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    float off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    float dia = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+    if (off <= 1e-14f * dia) break;
+    for (int r = 0; r < 3; ++r) {
+      int p = P[r], q = Q[r];
+      float apq = A[3 * p + q];
+      if (apq == 0.f) continue;
+      float theta = (A[3 * q + q] - A[3 * p + p]) / (2.f * apq);
+      float tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+      float c = rsqrtf(tt * tt + 1.f), s = tt * c;
+      for (int k = 0; k < 3; ++k) {
+        float akp = A[3 * k + p], akq = A[3 * k + q];
+        A[3 * k + p] = c * akp - s * akq;
+        A[3 * k + q] = s * akp + c * akq;
+      }
+      for (int k = 0; k < 3; ++k) {
+        float apk = A[3 * p + k], aqk = A[3 * q + k];
+        A[3 * p + k] = c * apk - s * aqk;
+        A[3 * q + k] = s * apk + c * aqk;
+      }
+      for (int k = 0; k < 3; ++k) {
+        float vkp = V[3 * k + p], vkq = V[3 * k + q];
+        V[3 * k + p] = c * vkp - s * vkq;
+        V[3 * k + q] = s * vkp + c * vkq;
+      }
+    }
+  }
+}
+
+// Unit quaternion (w >= 0) of a proper rotation matrix.
+__device__ void rot_quat(const float R[9], float q[4]) {
+  float tr = R[0] + R[4] + R[8];
+  if (tr > 0.f) {
+    float S = sqrtf(tr + 1.f) * 2.f;
+    q[0] = 0.25f * S; q[1] = (R[7] - R[5]) / S; q[2] = (R[2] - R[6]) / S; q[3] = (R[3] - R[1]) / S;
+  } else if (R[0] > R[4] && R[0] > R[8]) {
+    float S = sqrtf(1.f + R[0] - R[4] - R[8]) * 2.f;
+    q[0] = (R[7] - R[5]) / S; q[1] = 0.25f * S; q[2] = (R[1] + R[3]) / S; q[3] = (R[2] + R[6]) / S;
+  } else if (R[4] > R[8]) {
+    float S = sqrtf(1.f + R[4] - R[0] - R[8]) * 2.f;
+    q[0] = (R[2] - R[6]) / S; q[1] = (R[1] + R[3]) / S; q[2] = 0.25f * S; q[3] = (R[5] + R[7]) / S;
+  } else {
+    float S = sqrtf(1.f + R[8] - R[0] - R[4]) * 2.f;
+    q[0] = (R[3] - R[1]) / S; q[1] = (R[2] + R[6]) / S; q[2] = (R[5] + R[7]) / S; q[3] = 0.25f * S;
+  }
+  float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (q[0] < 0.f) n = -n;
+  for (int k = 0; k < 4; ++k) q[k] *= n;
+}
+
+// Merge of G_i (older) and G_j: Eq. 6 mean and the closed-form minimiser of Eq. 9,
+// computed in the eigenbasis of Sigma_i where Sigma_i = diag(si^2).
+template <typename T>
+__device__ void merge_pair(const float* means, const T* qs, const T* ls, int64_t i, int64_t j,
+                           float mk[3], float qk[4], float lk[3]) {
+  float qi[4], si[3], qj[4], sj[3], Ri[9], Rj[9];
+  load_qs(qs, ls, i, qi, si);
+  load_qs(qs, ls, j, qj, sj);
+  quat_rot(qi, Ri);
+  quat_rot(qj, Rj);
+  // Sigma_j in the basis of R_i: Bj = Ri^T Rj diag(sj^2) Rj^T Ri
+  float Mr[9];  // Ri^T Rj
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Mr[3 * a + b] = Ri[a] * Rj[b] + Ri[3 + a] * Rj[3 + b] + Ri[6 + a] * Rj[6 + b];
+  float sj2[3] = {sj[0] * sj[0], sj[1] * sj[1], sj[2] * sj[2]};
+  float Bj[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      Bj[3 * a + b] = Mr[3 * a] * Mr[3 * b] * sj2[0] + Mr[3 * a + 1] * Mr[3 * b + 1] * sj2[1] + Mr[3 * a + 2] * Mr[3 * b + 2] * sj2[2];
+  // Eq. 6 as mu_i + (Pi + Pj)^-1 Pj (mu_j - mu_i), in the R_i basis: Pi = diag(1/si^2).
+  float dm[3], dmr[3];
+  for (int k = 0; k < 3; ++k) dm[k] = means[3 * j + k] - means[3 * i + k];
+  for (int a = 0; a < 3; ++a) dmr[a] = Ri[a] * dm[0] + Ri[3 + a] * dm[1] + Ri[6 + a] * dm[2];
+  float Pj[9], isj2[3] = {1.f / sj2[0], 1.f / sj2[1], 1.f / sj2[2]};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      Pj[3 * a + b] = Mr[3 * a] * Mr[3 * b] * isj2[0] + Mr[3 * a + 1] * Mr[3 * b + 1] * isj2[1] + Mr[3 * a + 2] * Mr[3 * b + 2] * isj2[2];
+  float Ps[9];
+  for (int k = 0; k < 9; ++k) Ps[k] = Pj[k];
+  for (int k = 0; k < 3; ++k) Ps[4 * k] += 1.f / (si[k] * si[k]);
+  float rhs[3];
+  for (int a = 0; a < 3; ++a) rhs[a] = Pj[3 * a] * dmr[0] + Pj[3 * a + 1] * dmr[1] + Pj[3 * a + 2] * dmr[2];
+  float c00 = Ps[4] * Ps[8] - Ps[5] * Ps[7], c01 = Ps[2] * Ps[7] - Ps[1] * Ps[8], c02 = Ps[1] * Ps[5] - Ps[2] * Ps[4];
+  float c11 = Ps[0] * Ps[8] - Ps[2] * Ps[6], c12 = Ps[2] * Ps[3] - Ps[0] * Ps[5], c22 = Ps[0] * Ps[4] - Ps[1] * Ps[3];
+  float det = Ps[0] * c00 + Ps[1] * (Ps[5] * Ps[6] - Ps[3] * Ps[8]) + Ps[2] * (Ps[3] * Ps[7] - Ps[4] * Ps[6]);
+  float id = 1.f / det;
+  float xr[3] = {(c00 * rhs[0] + c01 * rhs[1] + c02 * rhs[2]) * id,
+                 (c01 * rhs[0] + c11 * rhs[1] + c12 * rhs[2]) * id,
+                 (c02 * rhs[0] + c12 * rhs[1] + c22 * rhs[2]) * id};
+  for (int k = 0; k < 3; ++k)
+    mk[k] = means[3 * i + k] + (Ri[3 * k] * xr[0] + Ri[3 * k + 1] * xr[1] + Ri[3 * k + 2] * xr[2]);
+  // X = (D Bj D)^(1/2), D = diag(si); Tm = D^-1 X D^-1; Mk = (I + Tm)/2; Sk = Mk D^2 Mk.
+  float A[9], V[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) A[3 * a + b] = si[a] * Bj[3 * a + b] * si[b];
+  jacobi3(A, V);
+  float ev[3] = {sqrtf(fmaxf(A[0], 0.f)), sqrtf(fmaxf(A[4], 0.f)), sqrtf(fmaxf(A[8], 0.f))};
+  float Mk[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      float x = V[3 * a] * V[3 * b] * ev[0] + V[3 * a + 1] * V[3 * b + 1] * ev[1] + V[3 * a + 2] * V[3 * b + 2] * ev[2];
+      Mk[3 * a + b] = 0.5f * ((a == b ? 1.f : 0.f) + x / (si[a] * si[b]));
+    }
+  float Sk[9];  // Mk diag(si^2) Mk, still in the R_i basis
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b) {
+      float x = 0.f;
+      for (int k = 0; k < 3; ++k) x += Mk[3 * a + k] * si[k] * si[k] * Mk[3 * k + b];
+      Sk[3 * a + b] = Sk[3 * b + a] = x;
+    }
+  // eigen-decomposition of Sk -> (quaternion, scales), scales descending, det +1
+  jacobi3(Sk, V);
+  float lam[3] = {Sk[0], Sk[4], Sk[8]};
+  int o0 = 0, o1 = 1, o2 = 2;
+  if (lam[o0] < lam[o1]) { int tmp = o0; o0 = o1; o1 = tmp; }
+  if (lam[o1] < lam[o2]) { int tmp = o1; o1 = o2; o2 = tmp; }
+  if (lam[o0] < lam[o1]) { int tmp = o0; o0 = o1; o1 = tmp; }
+  int ord[3] = {o0, o1, o2};
+  float E[9];  // world-frame eigenvectors in columns: Ri * V[:, ord]
+  for (int c = 0; c < 3; ++c)
+    for (int r = 0; r < 3; ++r)
+      E[3 * r + c] = Ri[3 * r] * V[ord[c]] + Ri[3 * r + 1] * V[3 + ord[c]] + Ri[3 * r + 2] * V[6 + ord[c]];
+  float dE = E[0] * (E[4] * E[8] - E[5] * E[7]) - E[1] * (E[3] * E[8] - E[5] * E[6]) + E[2] * (E[3] * E[7] - E[4] * E[6]);
+  if (dE < 0.f)
+    for (int r = 0; r < 3; ++r) E[3 * r + 2] = -E[3 * r + 2];
+  rot_quat(E, qk);
+  for (int c = 0; c < 3; ++c) lk[c] = 0.5f * logf(fmaxf(lam[ord[c]], 1e-30f));
+}
+
+template <typename T>
+__global__ void k_voxel_prep(int64_t n, const float* __restrict__ means, float voxel,
+                             mgs_merge_params p, int32_t* __restrict__ vox, int32_t* hdr) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int mn[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, mx[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+  int elig = 0, bad = 0;
+  if (i < n) {
+    bool e = true;
+    if (p.grad_stat) e = e && p.grad_stat[i] < p.grad_tau;
+    if (p.kf_id) e = e && p.kf_id[i] >= p.kf_min && p.kf_id[i] <= p.kf_max;
+    if (e) {
+      for (int k = 0; k < 3; ++k) {
+        float q = floorf(__fdiv_rn(means[3 * i + k], voxel));
+        if (!(q >= -1048576.f && q < 1048576.f)) { bad = 1; q = 0.f; }
+        int c = (int)q;
+        vox[3 * i + k] = c;
+        mn[k] = c; mx[k] = c;
+      }
+      elig = 1;
+    } else {
+      for (int k = 0; k < 3; ++k) vox[3 * i + k] = INT32_MIN;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    for (int k = 0; k < 3; ++k) {
+      mn[k] = min(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+      mx[k] = max(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+    }
+    elig += __shfl_xor_sync(0xffffffffu, elig, o);
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0 && elig) {
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&hdr[k], mn[k]);
+      atomicMax(&hdr[3 + k], mx[k]);
+    }
+    atomicAdd(&hdr[6], elig);
+    if (bad) atomicOr(&hdr[7], 1);
+  }
+}
+
+__global__ void k_voxel_pack(int64_t n, const int32_t* __restrict__ vox, const int32_t* __restrict__ hdr,
+                             int by, int bz, uint32_t* __restrict__ keys) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x = vox[3 * i];
+  if (x == INT32_MIN) { keys[i] = kNoKey; return; }
+  uint32_t rx = (uint32_t)(x - hdr[0]), ry = (uint32_t)(vox[3 * i + 1] - hdr[1]), rz = (uint32_t)(vox[3 * i + 2] - hdr[2]);
+  keys[i] = (rx << (by + bz)) | (ry << bz) | rz;
+}
+
+__global__ void k_heads(int64_t n_elig, const uint32_t* __restrict__ keys, uint32_t* __restrict__ flags) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_elig) return;
+  flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
+}
+
+__global__ void k_starts(int64_t n_elig, const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                         uint32_t* __restrict__ starts, const uint32_t* n_vox) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n_elig && flags[k]) starts[pos[k]] = (uint32_t)k;
+  if (k == 0) starts[*n_vox] = (uint32_t)n_elig;
+}
+
+struct PairCand {
+  float d2;
+  int a, b;  // member ranks (a older)
+};
+
+// Warp path: a voxel with 2..32 members.
+template <typename T>
+__global__ void __launch_bounds__(128) k_voxel_pairs(
+    const float* __restrict__ means, const T* __restrict__ qs, const T* __restrict__ ls,
+    const uint64_t* __restrict__ birth, const uint32_t* __restrict__ perm,
+    const uint32_t* __restrict__ starts, const uint32_t* __restrict__ n_vox_p, float chi2, int greedy,
+    int32_t* __restrict__ partner, float* __restrict__ mmean, float* __restrict__ mquat,
+    float* __restrict__ mlogs, uint32_t* __restrict__ big, uint32_t* __restrict__ n_big) {
+  __shared__ float s_d2[4][kWarpVoxel][kWarpVoxel + 1];
+  __shared__ int64_t s_idx[4][kWarpVoxel];
+  __shared__ uint64_t s_birth[4][kWarpVoxel];
+  __shared__ int s_pairs[4][kWarpVoxel / 2][2];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t v = (int64_t)blockIdx.x * 4 + wib;
+  if (v >= (int64_t)*n_vox_p) return;
+  const uint32_t st = starts[v], en = starts[v + 1];
+  const int nm = (int)(en - st);
+  if (nm < 2) return;
+  if (nm > kWarpVoxel) {
+    if (lane == 0) big[atomicAdd(n_big, 1u)] = (uint32_t)v;
+    return;
+  }
+  int64_t my = lane < nm ? (int64_t)perm[st + lane] : -1;
+  uint64_t mb = lane < nm ? birth[my] : ~0ull;
+  int rank = 0;
+  for (int m = 0; m < nm; ++m) {
+    int64_t oi = __shfl_sync(0xffffffffu, my, m);
+    uint64_t ob = __shfl_sync(0xffffffffu, mb, m);
+    if (lane < nm && older(ob, oi, mb, my)) ++rank;
+  }
+  if (lane < nm) { s_idx[wib][rank] = my; s_birth[wib][rank] = mb; }
+  __syncwarp();
+  // Eq. 4 rows: lane a (older) against every younger b
+  if (lane < nm) {
+    int64_t ia = s_idx[wib][lane];
+    float P[6];
+    precision_of(qs, ls, ia, P);
+    const float* ma = means + 3 * ia;
+    float mav[3] = {ma[0], ma[1], ma[2]};
+    for (int b = lane + 1; b < nm; ++b) {
+      const float* mb3 = means + 3 * s_idx[wib][b];
+      float mbv[3] = {mb3[0], mb3[1], mb3[2]};
+      s_d2[wib][lane][b] = mahalanobis2(P, mav, mbv);
+    }
+  }
+  __syncwarp();
+  uint32_t matched = 0;
+  int np = 0;
+  for (int round = 0; round < nm / 2; ++round) {
+    PairCand best{INFINITY, -1, -1};
+    if (lane < nm && !((matched >> lane) & 1u)) {
+      for (int b = lane + 1; b < nm; ++b) {
+        if ((matched >> b) & 1u) continue;
+        float d2 = s_d2[wib][lane][b];
+        if (d2 < chi2 && d2 < best.d2) best = PairCand{d2, lane, b};  // lane fixed: later b has later rank
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      PairCand oc{__shfl_xor_sync(0xffffffffu, best.d2, o), __shfl_xor_sync(0xffffffffu, best.a, o),
+                  __shfl_xor_sync(0xffffffffu, best.b, o)};
+      bool take;
+      if (oc.a < 0) take = false;
+      else if (best.a < 0) take = true;
+      else if (oc.d2 != best.d2) take = oc.d2 < best.d2;
+      else {
+        uint64_t b1 = s_birth[wib][best.a], b2 = s_birth[wib][best.b];
+        uint64_t c1 = s_birth[wib][oc.a], c2 = s_birth[wib][oc.b];
+        int64_t i1 = s_idx[wib][best.a], i2 = s_idx[wib][best.b];
+        int64_t j1 = s_idx[wib][oc.a], j2 = s_idx[wib][oc.b];
+        if (c1 != b1) take = c1 < b1;
+        else if (c2 != b2) take = c2 < b2;
+        else if (j1 != i1) take = j1 < i1;
+        else take = j2 < i2;
+      }
+      if (take) best = oc;
+    }
+    if (best.a < 0) break;
+    matched |= (1u << best.a) | (1u << best.b);
+    if (lane == 0) { s_pairs[wib][np][0] = best.a; s_pairs[wib][np][1] = best.b; }
+    ++np;
+    if (!greedy) break;
+  }
+  __syncwarp();
+  if (lane < np) {
+    int64_t i = s_idx[wib][s_pairs[wib][lane][0]], j = s_idx[wib][s_pairs[wib][lane][1]];
+    float mk[3], qk[4], lk[3];
+    merge_pair(means, qs, ls, i, j, mk, qk, lk);
+    partner[i] = (int32_t)j;
+    partner[j] = (int32_t)i;
+    for (int k = 0; k < 3; ++k) { mmean[3 * i + k] = mk[k]; mlogs[3 * i + k] = lk[k]; }
+    for (int k = 0; k < 4; ++k) mquat[4 * i + k] = qk[k];
+  }
+}
+
+// Block path: a voxel with 33..256 members; d2 evaluated on the fly each round.
+template <typename T>
+__global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
+    const float* __restrict__ means, const T* __restrict__ qs, const T* __restrict__ ls,
+    const uint64_t* __restrict__ birth, const uint32_t* __restrict__ perm,
+    const uint32_t* __restrict__ starts, const uint32_t* __restrict__ big,
+    const uint32_t* __restrict__ n_big_p, float chi2, int greedy, int32_t* __restrict__ partner,
+    float* __restrict__ mmean, float* __restrict__ mquat, float* __restrict__ mlogs, int32_t* err) {
+  __shared__ int64_t s_idx[kBlockVoxel];
+  __shared__ uint64_t s_birth[kBlockVoxel];
+  __shared__ float s_mu[kBlockVoxel][3];
+  __shared__ float s_P[kBlockVoxel][6];
+  __shared__ int s_match[kBlockVoxel];
+  __shared__ float r_d2[kBlockVoxel];
+  __shared__ int r_a[kBlockVoxel], r_b[kBlockVoxel];
+  __shared__ int s_pairs[kBlockVoxel / 2][2];
+  __shared__ int s_np;
+  if (blockIdx.x >= *n_big_p) return;
+  const uint32_t v = big[blockIdx.x];
+  const uint32_t st = starts[v], en = starts[v + 1];
+  const int nm = (int)(en - st);
+  const int t = threadIdx.x;
+  if (nm > kBlockVoxel) {
+    if (t == 0) atomicOr(err, 2);
+    return;
+  }
+  int64_t my = t < nm ? (int64_t)perm[st + t] : -1;
+  uint64_t mb = t < nm ? birth[my] : ~0ull;
+  if (t < nm) { s_idx[t] = my; s_birth[t] = mb; }
+  __syncthreads();
+  int rank = 0;
+  if (t < nm)
+    for (int m = 0; m < nm; ++m)
+      if (older(s_birth[m], s_idx[m], mb, my)) ++rank;
+  __syncthreads();
+  if (t < nm) {
+    s_idx[rank] = my;
+    s_birth[rank] = mb;
+    s_match[rank] = 0;
+    for (int k = 0; k < 3; ++k) s_mu[rank][k] = means[3 * my + k];
+    precision_of(qs, ls, my, s_P[rank]);
+  }
+  if (t == 0) s_np = 0;
+  __syncthreads();
+  const int npairs = nm * (nm - 1) / 2;
+  for (int round = 0; round < nm / 2; ++round) {
+    float bd = INFINITY;
+    int ba = -1, bb = -1;
+    for (int pi = t; pi < npairs; pi += kBlockVoxel) {
+      // decode pair index -> (a, b), a < b
+      int a = 0, rem = pi;
+      while (rem >= nm - 1 - a) { rem -= nm - 1 - a; ++a; }
+      int b = a + 1 + rem;
+      if (s_match[a] || s_match[b]) continue;
+      float d2 = mahalanobis2(s_P[a], s_mu[a], s_mu[b]);
+      if (d2 >= chi2) continue;
+      bool take = ba < 0 || d2 < bd || (d2 == bd && (a < ba || (a == ba && b < bb)));
+      if (take) { bd = d2; ba = a; bb = b; }
+    }
+    r_d2[t] = bd; r_a[t] = ba; r_b[t] = bb;
+    __syncthreads();
+    for (int stp = kBlockVoxel / 2; stp; stp >>= 1) {
+      if (t < stp) {
+        int oa = r_a[t + stp];
+        bool take;
+        if (oa < 0) take = false;
+        else if (r_a[t] < 0) take = true;
+        else if (r_d2[t + stp] != r_d2[t]) take = r_d2[t + stp] < r_d2[t];
+        else take = oa < r_a[t] || (oa == r_a[t] && r_b[t + stp] < r_b[t]);  // rank order = (birth, index)
+        if (take) { r_d2[t] = r_d2[t + stp]; r_a[t] = oa; r_b[t] = r_b[t + stp]; }
+      }
+      __syncthreads();
+    }
+    int a = r_a[0], b = r_b[0];
+    __syncthreads();
+    if (a < 0) break;
+    if (t == 0) { s_match[a] = 1; s_match[b] = 1; s_pairs[s_np][0] = a; s_pairs[s_np][1] = b; s_np++; }
+    __syncthreads();
+    if (!greedy) break;
+  }
+  __syncthreads();
+  for (int k = t; k < s_np; k += kBlockVoxel) {
+    int64_t i = s_idx[s_pairs[k][0]], j = s_idx[s_pairs[k][1]];
+    float mk[3], qk[4], lk[3];
+    merge_pair(means, qs, ls, i, j, mk, qk, lk);
+    partner[i] = (int32_t)j;
+    partner[j] = (int32_t)i;
+    for (int c = 0; c < 3; ++c) { mmean[3 * i + c] = mk[c]; mlogs[3 * i + c] = lk[c]; }
+    for (int c = 0; c < 4; ++c) mquat[4 * i + c] = qk[c];
+  }
+}
+
+__global__ void k_keep(int64_t n, const int32_t* __restrict__ partner, const uint64_t* __restrict__ birth,
+                       uint32_t* __restrict__ keep) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t j = partner[i];
+  keep[i] = (j >= 0 && older(birth[j], j, birth[i], i)) ? 0u : 1u;
+}
+
+template <typename T>
+__global__ void k_compact(int64_t n, int K3, const float* __restrict__ means, const T* __restrict__ ls,
+                          const T* __restrict__ qs, const T* __restrict__ ol, const T* __restrict__ sh,
+                          const uint64_t* __restrict__ birth, const uint32_t* __restrict__ keep,
+                          const uint32_t* __restrict__ pos, const int32_t* __restrict__ partner,
+                          const float* __restrict__ mmean, const float* __restrict__ mquat,
+                          const float* __restrict__ mlogs, float* omeans, T* ols, T* oqs, T* ool,
+                          T* osh, uint64_t* obirth) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !keep[i]) return;
+  int64_t w = pos[i];
+  if (partner[i] >= 0) {
+    for (int k = 0; k < 3; ++k) { omeans[3 * w + k] = mmean[3 * i + k]; st(ols + 3 * w + k, mlogs[3 * i + k]); }
+    for (int k = 0; k < 4; ++k) st(oqs + 4 * w + k, mquat[4 * i + k]);
+  } else {
+    for (int k = 0; k < 3; ++k) { omeans[3 * w + k] = means[3 * i + k]; ols[3 * w + k] = ls[3 * i + k]; }
+    for (int k = 0; k < 4; ++k) oqs[4 * w + k] = qs[4 * i + k];
+  }
+  ool[w] = ol[i];
+  for (int k = 0; k < K3; ++k) osh[(int64_t)K3 * w + k] = sh[(int64_t)K3 * i + k];
+  if (obirth) obirth[w] = birth[i];
+}
+
+template <typename T>
+cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params& p,
+                    const mgs_gaussians_mut& out, int32_t* partner_out, int32_t* vox_out,
+                    int64_t* n_out_host, MergeWs& ws, cudaStream_t s, int* unsupported) {
+  const int64_t n = in.n;
+  const T* ls = (const T*)in.log_scales;
+  const T* qs = (const T*)in.quats;
+  const T* ol = (const T*)in.opacity_logit;
+  const T* sh = (const T*)in.sh;
+  const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
+  const unsigned grid = (unsigned)div_up(n, 256);
+  int32_t init[16] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, INT32_MIN, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(ws.hdr, init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  int32_t* partner = partner_out ? partner_out : ws.partner;
+  e = cudaMemsetAsync(partner, 0xff, sizeof(int32_t) * n, s);
+  if (e != cudaSuccess) return e;
+  int32_t* vox = vox_out ? vox_out : ws.vox;
+  k_voxel_prep<T><<<grid, 256, 0, s>>>(n, in.means, voxel, p, vox, ws.hdr);
+  count_launch();
+  int32_t h[16];
+  e = cudaMemcpyAsync(h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  if (h[7]) { *unsupported = 1; return cudaSuccess; }
+  const int64_t n_elig = h[6];
+  if (n_elig >= 2) {
+    auto bits_of = [](int64_t range) { int b = 0; while ((int64_t(1) << b) < range) ++b; return b; };
+    int bx = bits_of((int64_t)h[3] - h[0] + 1), by = bits_of((int64_t)h[4] - h[1] + 1), bz = bits_of((int64_t)h[5] - h[2] + 1);
+    if (bx + by + bz > 31) { *unsupported = 3; return cudaSuccess; }
+    k_voxel_pack<<<grid, 256, 0, s>>>(n, vox, ws.hdr, by, bz, ws.keys[0]);
+    count_launch();
+    int cur = radix_sort_pairs(ws.keys, ws.perm, n, 0, std::max(1, bx + by + bz + 1), true, ws.scratch, s, &e);
+    if (e != cudaSuccess) return e;
+    const uint32_t* keys = ws.keys[cur];
+    const uint32_t* perm = ws.perm[cur];
+    unsigned ge = (unsigned)div_up(n_elig, 256);
+    k_heads<<<ge, 256, 0, s>>>(n_elig, keys, ws.flags);
+    count_launch();
+    uint32_t* n_vox = (uint32_t*)(ws.hdr + 8);
+    uint32_t* n_big = (uint32_t*)(ws.hdr + 9);
+    e = scan_exclusive_u32(ws.flags, nullptr, ws.pos, n_elig, ws.scratch, n_vox, s);
+    if (e != cudaSuccess) return e;
+    k_starts<<<ge, 256, 0, s>>>(n_elig, ws.flags, ws.pos, ws.starts, n_vox);
+    count_launch(3);  // with the two pairing kernels below
+    unsigned gv = (unsigned)div_up(n_elig, 4);
+    k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, qs, ls, in.birth, perm, ws.starts, n_vox, p.chi2,
+                                        p.greedy, partner, ws.mmean, ws.mquat, ws.mlogs, ws.big, n_big);
+    k_voxel_pairs_big<T><<<(unsigned)std::max<int64_t>(1, n_elig / 33), kBlockVoxel, 0, s>>>(
+        in.means, qs, ls, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
+        ws.mmean, ws.mquat, ws.mlogs, ws.hdr + 7);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_keep<<<grid, 256, 0, s>>>(n, partner, in.birth, ws.flags);
+  count_launch(2);  // with the compaction below
+  uint32_t* n_out_dev = (uint32_t*)(ws.hdr + 10);
+  e = scan_exclusive_u32(ws.flags, nullptr, ws.pos, n, ws.scratch, n_out_dev, s);
+  if (e != cudaSuccess) return e;
+  k_compact<T><<<grid, 256, 0, s>>>(n, K3, in.means, ls, qs, ol, sh, in.birth, ws.flags, ws.pos, partner,
+                                    ws.mmean, ws.mquat, ws.mlogs, out.means, (T*)out.log_scales,
+                                    (T*)out.quats, (T*)out.opacity_logit, (T*)out.sh, out.birth);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  if (h[7] & 2) { *unsupported = 2; return cudaSuccess; }
+  *n_out_host = (int64_t)(uint32_t)h[10];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+size_t merge_workspace_bytes(int64_t n, MergeWs* ws, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align_up(bytes); return p; };
+  int64_t m = std::max<int64_t>(n, 1);
+  MergeWs w{};
+  w.hdr = (int32_t*)take(64);
+  w.vox = (int32_t*)take(12 * m);
+  w.keys[0] = (uint32_t*)take(4 * m);
+  w.keys[1] = (uint32_t*)take(4 * m);
+  w.perm[0] = (uint32_t*)take(4 * m);
+  w.perm[1] = (uint32_t*)take(4 * m);
+  w.flags = (uint32_t*)take(4 * m);
+  w.pos = (uint32_t*)take(4 * m);
+  w.starts = (uint32_t*)take(4 * (m + 1));
+  w.partner = (int32_t*)take(4 * m);
+  w.mmean = (float*)take(12 * m);
+  w.mquat = (float*)take(16 * m);
+  w.mlogs = (float*)take(12 * m);
+  w.big = (uint32_t*)take(4 * m);
+  w.scratch = (uint32_t*)take(4 * sort_scratch_words(m));
+  if (ws) *ws = w;
+  return off;
+}
+
+// Returns a cuda error; *unsupported != 0 for a size outside what the kernels handle.
+cudaError_t run_voxel_merge(const mgs_gaussians& in, float voxel, const mgs_merge_params& p,
+                            const mgs_gaussians_mut& out, int32_t* partner, int32_t* vox,
+                            int64_t* n_out_host, char* ws_base, cudaStream_t s, int* unsupported) {
+  MergeWs ws;
+  merge_workspace_bytes(in.n, &ws, ws_base);
+  *unsupported = 0;
+  switch (in.attr_dtype) {
+    case MGS_F16: return merge_t<__half>(in, voxel, p, out, partner, vox, n_out_host, ws, s, unsupported);
+    case MGS_BF16: return merge_t<__nv_bfloat16>(in, voxel, p, out, partner, vox, n_out_host, ws, s, unsupported);
+    default: return merge_t<float>(in, voxel, p, out, partner, vox, n_out_host, ws, s, unsupported);
+  }
+}
+
+}  // namespace mgs

@@ -1,0 +1,481 @@
+// Per-Gaussian projection (Sec. II-C, Eq. 1-2) and its reverse pass, sm_103a.
+//
+// One thread owns one Gaussian and loops over every view of the call, so each
+// parameter byte is read from HBM once per call however many keyframes are drawn.
+// The camera-space mean and the projected centre are carried in double-float
+// (two f32 words) so that the depth key and the pixel-space centre are correctly
+// rounded; everything else is plain f32.
+#include "internal.h"
+
+namespace mgs {
+namespace {
+
+struct GaussPre {
+  float mu[3];
+  float qn[4], qnorm;
+  float Rq[9];
+  float s[3];
+  float S3[6];  // xx xy xz yy yz zz
+  float o;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_gauss(int64_t g, const float* means, const T* ls, const T* qs,
+                                           const T* ol, GaussPre& G) {
+  for (int k = 0; k < 3; ++k) G.mu[k] = __ldg(means + 3 * g + k);
+  float q[4];
+  for (int k = 0; k < 4; ++k) q[k] = ld(qs + 4 * g + k);
+  G.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  float inv = 1.f / G.qnorm;
+  for (int k = 0; k < 4; ++k) G.qn[k] = q[k] * inv;
+  quat_rot(G.qn, G.Rq);
+  for (int k = 0; k < 3; ++k) G.s[k] = expf(ld(ls + 3 * g + k));
+  float s2[3] = {G.s[0] * G.s[0], G.s[1] * G.s[1], G.s[2] * G.s[2]};
+  const float* R = G.Rq;
+  G.S3[0] = R[0] * R[0] * s2[0] + R[1] * R[1] * s2[1] + R[2] * R[2] * s2[2];
+  G.S3[1] = R[0] * R[3] * s2[0] + R[1] * R[4] * s2[1] + R[2] * R[5] * s2[2];
+  G.S3[2] = R[0] * R[6] * s2[0] + R[1] * R[7] * s2[1] + R[2] * R[8] * s2[2];
+  G.S3[3] = R[3] * R[3] * s2[0] + R[4] * R[4] * s2[1] + R[5] * R[5] * s2[2];
+  G.S3[4] = R[3] * R[6] * s2[0] + R[4] * R[7] * s2[1] + R[5] * R[8] * s2[2];
+  G.S3[5] = R[6] * R[6] * s2[0] + R[7] * R[7] * s2[1] + R[8] * R[8] * s2[2];
+  G.o = 1.f / (1.f + expf(-ld(ol + g)));
+}
+
+template <int DEG, typename T>
+__device__ __forceinline__ void load_sh(int64_t g, const T* sh, float* c) {
+  constexpr int K3 = (DEG + 1) * (DEG + 1) * 3;
+  const T* p = sh + g * K3;
+#pragma unroll
+  for (int k = 0; k < K3; ++k) c[k] = ld(p + k);
+}
+
+struct ViewGeom {
+  bool ok;                // in front of the near plane with a positive-definite 2D covariance
+  float tx, ty, tz;
+  float u_hi, u_lo, v_hi, v_lo;
+  float xr, yr;
+  bool clampx, clampy;
+  float T[6];             // J W
+  float a, b, c;          // dilated 2D covariance
+  float A, B, C;          // its inverse
+  float dir[3], vnorm;
+};
+
+__device__ __forceinline__ void view_geom(const GaussPre& G, const View& V, ViewGeom& P) {
+  DF p[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    DF acc = two_prod(V.R[3 * r + 0], G.mu[0]);
+    acc = df_add(acc, two_prod(V.R[3 * r + 1], G.mu[1]));
+    acc = df_add(acc, two_prod(V.R[3 * r + 2], G.mu[2]));
+    p[r] = df_add(acc, DF{V.t[r], 0.f});
+  }
+  P.tx = p[0].hi; P.ty = p[1].hi; P.tz = p[2].hi;
+  P.ok = P.tz > V.near_z;
+  if (!P.ok) return;
+  DF uq = df_axpc(V.fx, df_div(p[0], p[2]), V.cx);
+  DF vq = df_axpc(V.fy, df_div(p[1], p[2]), V.cy);
+  P.u_hi = uq.hi; P.u_lo = uq.lo; P.v_hi = vq.hi; P.v_lo = vq.lo;
+  float tz = P.tz, itz = 1.f / tz;
+  P.xr = P.tx * itz;
+  P.yr = P.ty * itz;
+  P.clampx = P.xr < -V.limx || P.xr > V.limx;
+  P.clampy = P.yr < -V.limy || P.yr > V.limy;
+  float xc = fminf(V.limx, fmaxf(-V.limx, P.xr));
+  float yc = fminf(V.limy, fmaxf(-V.limy, P.yr));
+  float J00 = V.fx * itz, J02 = -V.fx * xc * itz, J11 = V.fy * itz, J12 = -V.fy * yc * itz;
+  const float* W = V.R;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    P.T[c] = J00 * W[c] + J02 * W[6 + c];
+    P.T[3 + c] = J11 * W[3 + c] + J12 * W[6 + c];
+  }
+  const float* S = G.S3;
+  float M0[3], M1[3];  // T S3
+  M0[0] = P.T[0] * S[0] + P.T[1] * S[1] + P.T[2] * S[2];
+  M0[1] = P.T[0] * S[1] + P.T[1] * S[3] + P.T[2] * S[4];
+  M0[2] = P.T[0] * S[2] + P.T[1] * S[4] + P.T[2] * S[5];
+  M1[0] = P.T[3] * S[0] + P.T[4] * S[1] + P.T[5] * S[2];
+  M1[1] = P.T[3] * S[1] + P.T[4] * S[3] + P.T[5] * S[4];
+  M1[2] = P.T[3] * S[2] + P.T[4] * S[4] + P.T[5] * S[5];
+  P.a = M0[0] * P.T[0] + M0[1] * P.T[1] + M0[2] * P.T[2] + kDilation;
+  P.b = M0[0] * P.T[3] + M0[1] * P.T[4] + M0[2] * P.T[5];
+  P.c = M1[0] * P.T[3] + M1[1] * P.T[4] + M1[2] * P.T[5] + kDilation;
+  float det = P.a * P.c - P.b * P.b;
+  P.ok = det > 0.f;
+  if (!P.ok) return;
+  float idet = 1.f / det;
+  P.A = P.c * idet;
+  P.B = -P.b * idet;
+  P.C = P.a * idet;
+  float d[3] = {G.mu[0] - V.C[0], G.mu[1] - V.C[1], G.mu[2] - V.C[2]};
+  P.vnorm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  float iv = 1.f / P.vnorm;
+  P.dir[0] = d[0] * iv; P.dir[1] = d[1] * iv; P.dir[2] = d[2] * iv;
+}
+
+// Tile rect of the square of half-width r around the centre (inclusive bounds).
+__device__ __forceinline__ bool tile_rect(const ViewGeom& P, const View& V, int& r, int rc[4]) {
+  float mid = 0.5f * (P.a + P.c);
+  float det = P.a * P.c - P.b * P.b;
+  float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+  r = (int)ceilf(3.f * sqrtf(lam));
+  float rf = (float)r;
+  float fx0 = floorf(__fsub_rn(P.u_hi, rf) * 0.0625f), fx1 = floorf(__fadd_rn(P.u_hi, rf) * 0.0625f);
+  float fy0 = floorf(__fsub_rn(P.v_hi, rf) * 0.0625f), fy1 = floorf(__fadd_rn(P.v_hi, rf) * 0.0625f);
+  rc[0] = (int)fmaxf(0.f, fminf(fx0, (float)V.tiles_x));
+  rc[1] = (int)fmaxf(0.f, fminf(fy0, (float)V.tiles_y));
+  rc[2] = (int)fminf((float)(V.tiles_x - 1), fmaxf(fx1, -1.f));
+  rc[3] = (int)fminf((float)(V.tiles_y - 1), fmaxf(fy1, -1.f));
+  return rc[0] <= rc[2] && rc[1] <= rc[3];
+}
+
+template <int DEG>
+__device__ __forceinline__ void colour(const float* c, const float dir[3], float raw[3]) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  float Y[K];
+  sh_basis<DEG>(dir, Y, nullptr);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float acc = 0.5f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc = __fmaf_rn(c[3 * k + ch], Y[k], acc);
+    raw[ch] = acc;
+  }
+}
+
+template <int DEG, typename T>
+__global__ void __launch_bounds__(256) k_preprocess(int64_t N, const float* __restrict__ means,
+                                                    const T* __restrict__ ls, const T* __restrict__ qs,
+                                                    const T* __restrict__ ol, const T* __restrict__ sh,
+                                                    const __grid_constant__ ViewTable vt,
+                                                    float4* __restrict__ rec, uint2* __restrict__ rects,
+                                                    uint32_t* __restrict__ touched,
+                                                    uint32_t* __restrict__ dkeys,
+                                                    unsigned long long* __restrict__ counters) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long my_keys = 0;
+  unsigned int my_vis = 0;
+  if (g < N) {
+    GaussPre G;
+    load_gauss(g, means, ls, qs, ol, G);
+    constexpr int K3 = (DEG + 1) * (DEG + 1) * 3;
+    float c[K3];
+    load_sh<DEG>(g, sh, c);
+    for (int v = 0; v < vt.n_views; ++v) {
+      const View& V = vt.v[v];
+      int64_t item = (int64_t)v * N + g;
+      ViewGeom P;
+      view_geom(G, V, P);
+      int r = 0, rc[4];
+      bool vis = P.ok && tile_rect(P, V, r, rc);
+      if (vis) {
+        float raw[3];
+        colour<DEG>(c, P.dir, raw);
+        rec[3 * item + 0] = make_float4(P.u_hi, P.v_hi, P.u_lo, P.v_lo);
+        rec[3 * item + 1] = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, G.o);
+        rec[3 * item + 2] = make_float4(fmaxf(0.f, raw[0]), fmaxf(0.f, raw[1]), fmaxf(0.f, raw[2]), P.tz);
+        rects[item] = make_uint2((uint32_t)rc[0] | ((uint32_t)rc[1] << 16), (uint32_t)rc[2] | ((uint32_t)rc[3] << 16));
+        uint32_t area = (uint32_t)(rc[2] - rc[0] + 1) * (uint32_t)(rc[3] - rc[1] + 1);
+        touched[item] = area;
+        dkeys[item] = __float_as_uint(P.tz);
+        my_keys += area;
+        my_vis += 1;
+      } else {
+        touched[item] = 0;
+        dkeys[item] = 0xffffffffu;
+      }
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    my_keys += __shfl_xor_sync(0xffffffffu, my_keys, o);
+    my_vis += __shfl_xor_sync(0xffffffffu, my_vis, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (my_keys || my_vis)) {
+    atomicAdd(&counters[0], my_keys);
+    atomicAdd(&counters[1], (unsigned long long)my_vis);
+  }
+}
+
+template <int DEG, typename T>
+__global__ void __launch_bounds__(256) k_project_one(int64_t N, const float* __restrict__ means,
+                                                     const T* __restrict__ ls, const T* __restrict__ qs,
+                                                     const T* __restrict__ ol, const T* __restrict__ sh,
+                                                     const __grid_constant__ View V, float* mean2d,
+                                                     float* conic, float* rgb, float* depth,
+                                                     int32_t* radius, int32_t* rect) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  GaussPre G;
+  load_gauss(g, means, ls, qs, ol, G);
+  ViewGeom P;
+  view_geom(G, V, P);
+  int r = 0, rc[4] = {0, 0, -1, -1};
+  bool drawn = P.ok && tile_rect(P, V, r, rc);
+  if (!P.ok) { r = 0; rc[0] = rc[1] = 0; rc[2] = rc[3] = -1; }
+  if (depth) depth[g] = P.tz;
+  if (mean2d) {
+    mean2d[2 * g] = P.ok ? P.u_hi + P.u_lo : 0.f;
+    mean2d[2 * g + 1] = P.ok ? P.v_hi + P.v_lo : 0.f;
+  }
+  if (conic) {
+    conic[3 * g] = P.ok ? P.A : 0.f;
+    conic[3 * g + 1] = P.ok ? P.B : 0.f;
+    conic[3 * g + 2] = P.ok ? P.C : 0.f;
+  }
+  if (radius) radius[g] = P.ok ? r : 0;
+  if (rect)
+    for (int k = 0; k < 4; ++k) rect[4 * g + k] = rc[k];
+  if (rgb) {
+    constexpr int K3 = (DEG + 1) * (DEG + 1) * 3;
+    float c[K3];
+    load_sh<DEG>(g, sh, c);
+    float raw[3] = {0.f, 0.f, 0.f};
+    if (P.ok) colour<DEG>(c, P.dir, raw);
+    for (int ch = 0; ch < 3; ++ch) rgb[3 * g + ch] = P.ok ? fmaxf(0.f, raw[ch]) : 0.f;
+  }
+  (void)drawn;
+}
+
+// ---------------- reverse pass ----------------
+// moments of a (view, Gaussian) item, accumulated by the backward blend over pixels p:
+//   m0 = sum gp, m1 = sum gp dx, m2 = sum gp dy, m3 = sum gp dx^2, m4 = sum gp dx dy,
+//   m5 = sum gp dy^2, m6..8 = sum w dL/drgb, m9 = sum w dL/ddepth,
+// with gp = dL/dpower, w the blend weight and (dx, dy) = centre - pixel.
+template <int DEG, typename T>
+__global__ void __launch_bounds__(128) k_preprocess_bwd(int64_t N, const float* __restrict__ means,
+                                                        const T* __restrict__ ls, const T* __restrict__ qs,
+                                                        const T* __restrict__ ol, const T* __restrict__ sh,
+                                                        const __grid_constant__ ViewTable vt,
+                                                        const float4* __restrict__ moments,
+                                                        const uint32_t* __restrict__ touched,
+                                                        mgs_grads grads) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  GaussPre G;
+  load_gauss(g, means, ls, qs, ol, G);
+  float c[3 * K];
+  load_sh<DEG>(g, sh, c);
+  float dmu[3] = {0.f, 0.f, 0.f}, dS3[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dop = 0.f;
+  float dsh[3 * K];
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
+  float stat = 0.f, vis = 0.f;
+  for (int v = 0; v < vt.n_views; ++v) {
+    int64_t item = (int64_t)v * N + g;
+    if (touched[item] == 0) continue;
+    const View& V = vt.v[v];
+    float4 q0 = moments[3 * item], q1 = moments[3 * item + 1], q2 = moments[3 * item + 2];
+    ViewGeom P;
+    view_geom(G, V, P);
+    float m0 = q0.x, m1 = q0.y, m2 = q0.z, m3 = q0.w, m4 = q1.x, m5 = q1.y;
+    float du = -(P.A * m1 + P.B * m2), dv = -(P.B * m1 + P.C * m2);
+    float dA = -0.5f * m3, dB = -m4, dC = -0.5f * m5;
+    dop += m0 / G.o;
+    float dcol[3] = {q1.z, q1.w, q2.x};
+    float dd = q2.y;
+    float dm[3] = {0.f, 0.f, 0.f};
+    // colour
+    {
+      float Y[K], dY[K][3];
+      sh_basis<DEG>(P.dir, Y, dY);
+      float ddir[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float raw = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) raw = __fmaf_rn(c[3 * k + ch], Y[k], raw);
+        if (raw < 0.f) continue;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          dsh[3 * k + ch] += dcol[ch] * Y[k];
+          if (DEG > 0) {
+            float w = dcol[ch] * c[3 * k + ch];
+            ddir[0] += w * dY[k][0];
+            ddir[1] += w * dY[k][1];
+            ddir[2] += w * dY[k][2];
+          }
+        }
+      }
+      if (DEG > 0) {
+        float dt = ddir[0] * P.dir[0] + ddir[1] * P.dir[1] + ddir[2] * P.dir[2];
+        float iv = 1.f / P.vnorm;
+        for (int k = 0; k < 3; ++k) dm[k] += (ddir[k] - P.dir[k] * dt) * iv;
+      }
+    }
+    // centre and depth
+    float tx = P.tx, ty = P.ty, tz = P.tz, itz = 1.f / tz, itz2 = itz * itz;
+    float dp[3] = {du * V.fx * itz, dv * V.fy * itz, dd - (du * V.fx * tx + dv * V.fy * ty) * itz2};
+    // conic -> 2D covariance: Gs = -M Gm M, M = [[A,B],[B,C]], Gm = [[dA, dB/2],[dB/2, dC]]
+    float hB = 0.5f * dB;
+    float t00 = P.A * dA + P.B * hB, t01 = P.A * hB + P.B * dC;
+    float t10 = P.B * dA + P.C * hB, t11 = P.B * hB + P.C * dC;
+    float G00 = -(t00 * P.A + t01 * P.B), G01 = -(t00 * P.B + t01 * P.C);
+    float G11 = -(t10 * P.B + t11 * P.C);
+    // cov = T S3 T^T + 0.3 I  ->  dS3 += T^T Gs T ; dT = 2 Gs T S3
+    float GT0[3], GT1[3];
+    for (int k = 0; k < 3; ++k) {
+      GT0[k] = G00 * P.T[k] + G01 * P.T[3 + k];
+      GT1[k] = G01 * P.T[k] + G11 * P.T[3 + k];
+    }
+    dS3[0] += P.T[0] * GT0[0] + P.T[3] * GT1[0];
+    dS3[1] += P.T[0] * GT0[1] + P.T[3] * GT1[1];
+    dS3[2] += P.T[0] * GT0[2] + P.T[3] * GT1[2];
+    dS3[3] += P.T[1] * GT0[1] + P.T[4] * GT1[1];
+    dS3[4] += P.T[1] * GT0[2] + P.T[4] * GT1[2];
+    dS3[5] += P.T[2] * GT0[2] + P.T[5] * GT1[2];
+    const float* S = G.S3;
+    float dT0[3], dT1[3];
+    dT0[0] = 2.f * (GT0[0] * S[0] + GT0[1] * S[1] + GT0[2] * S[2]);
+    dT0[1] = 2.f * (GT0[0] * S[1] + GT0[1] * S[3] + GT0[2] * S[4]);
+    dT0[2] = 2.f * (GT0[0] * S[2] + GT0[1] * S[4] + GT0[2] * S[5]);
+    dT1[0] = 2.f * (GT1[0] * S[0] + GT1[1] * S[1] + GT1[2] * S[2]);
+    dT1[1] = 2.f * (GT1[0] * S[1] + GT1[1] * S[3] + GT1[2] * S[4]);
+    dT1[2] = 2.f * (GT1[0] * S[2] + GT1[1] * S[4] + GT1[2] * S[5]);
+    const float* W = V.R;
+    float dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
+    float dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
+    float dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
+    float dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
+    dp[2] -= (V.fx * dJ00 + V.fy * dJ11) * itz2;
+    if (!P.clampx) {
+      dp[0] -= V.fx * itz2 * dJ02;
+      dp[2] += 2.f * V.fx * tx * itz2 * itz * dJ02;
+    } else {
+      float xc = fminf(V.limx, fmaxf(-V.limx, P.xr));
+      dp[2] += V.fx * xc * itz2 * dJ02;
+    }
+    if (!P.clampy) {
+      dp[1] -= V.fy * itz2 * dJ12;
+      dp[2] += 2.f * V.fy * ty * itz2 * itz * dJ12;
+    } else {
+      float yc = fminf(V.limy, fmaxf(-V.limy, P.yr));
+      dp[2] += V.fy * yc * itz2 * dJ12;
+    }
+    for (int k = 0; k < 3; ++k) dm[k] += W[k] * dp[0] + W[3 + k] * dp[1] + W[6 + k] * dp[2];
+    for (int k = 0; k < 3; ++k) dmu[k] += dm[k];
+    stat += sqrtf(dm[0] * dm[0] + dm[1] * dm[1] + dm[2] * dm[2]);
+    vis += 1.f;
+  }
+  if (vis == 0.f) return;
+  // S3 = Rq diag(s^2) Rq^T  ->  log-scales and quaternion
+  const float* R = G.Rq;
+  float H[9] = {dS3[0], dS3[1], dS3[2], dS3[1], dS3[3], dS3[4], dS3[2], dS3[4], dS3[5]};
+  float HR[9];
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) HR[3 * a + k] = H[3 * a] * R[k] + H[3 * a + 1] * R[3 + k] + H[3 * a + 2] * R[6 + k];
+  float dls[3], dR[9];
+  for (int k = 0; k < 3; ++k) {
+    float rhr = R[k] * HR[k] + R[3 + k] * HR[3 + k] + R[6 + k] * HR[6 + k];
+    float s2 = G.s[k] * G.s[k];
+    dls[k] = 2.f * s2 * rhr;
+    for (int a = 0; a < 3; ++a) dR[3 * a + k] = 2.f * HR[3 * a + k] * s2;
+  }
+  float dqn[4];
+  quat_rot_vjp(G.qn, dR, dqn);
+  float dot = dqn[0] * G.qn[0] + dqn[1] * G.qn[1] + dqn[2] * G.qn[2] + dqn[3] * G.qn[3];
+  float iq = 1.f / G.qnorm;
+  for (int k = 0; k < 3; ++k) grads.means[3 * g + k] += dmu[k];
+  for (int k = 0; k < 3; ++k) grads.log_scales[3 * g + k] += dls[k];
+  for (int k = 0; k < 4; ++k) grads.quats[4 * g + k] += (dqn[k] - G.qn[k] * dot) * iq;
+  grads.opacity_logit[g] += dop * G.o * (1.f - G.o);
+  float* gsh = grads.sh + g * 3 * K;
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) gsh[k] += dsh[k];
+  if (grads.grad_stat) grads.grad_stat[g] += stat;
+  if (grads.vis_count) grads.vis_count[g] += vis;
+}
+
+template <typename T>
+cudaError_t launch_pre_t(int deg, int64_t N, const mgs_gaussians& g, const ViewTable& vt,
+                         float4* rec, uint2* rects, uint32_t* touched, uint32_t* dkeys,
+                         unsigned long long* counters, cudaStream_t s) {
+  unsigned grid = (unsigned)div_up(N, 256);
+  const T* ls = (const T*)g.log_scales;
+  const T* qs = (const T*)g.quats;
+  const T* ol = (const T*)g.opacity_logit;
+  const T* sh = (const T*)g.sh;
+  switch (deg) {
+    case 0: k_preprocess<0, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
+    case 1: k_preprocess<1, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
+    case 2: k_preprocess<2, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
+    default: k_preprocess<3, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bwd_t(int deg, int64_t N, const mgs_gaussians& g, const ViewTable& vt,
+                         const float4* moments, const uint32_t* touched, const mgs_grads& gr,
+                         cudaStream_t s) {
+  unsigned grid = (unsigned)div_up(N, 128);
+  const T* ls = (const T*)g.log_scales;
+  const T* qs = (const T*)g.quats;
+  const T* ol = (const T*)g.opacity_logit;
+  const T* sh = (const T*)g.sh;
+  switch (deg) {
+    case 0: k_preprocess_bwd<0, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, gr); break;
+    case 1: k_preprocess_bwd<1, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, gr); break;
+    case 2: k_preprocess_bwd<2, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, gr); break;
+    default: k_preprocess_bwd<3, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, gr); break;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_proj_t(int deg, int64_t N, const mgs_gaussians& g, const View& V, float* mean2d,
+                          float* conic, float* rgb, float* depth, int32_t* radius, int32_t* rect,
+                          cudaStream_t s) {
+  unsigned grid = (unsigned)div_up(N, 256);
+  const T* ls = (const T*)g.log_scales;
+  const T* qs = (const T*)g.quats;
+  const T* ol = (const T*)g.opacity_logit;
+  const T* sh = (const T*)g.sh;
+  switch (deg) {
+    case 0: k_project_one<0, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
+    case 1: k_project_one<1, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
+    case 2: k_project_one<2, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
+    default: k_project_one<3, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const mgs_gaussians& g, const ViewTable& vt, float4* rec,
+                              uint2* rects, uint32_t* touched, uint32_t* dkeys,
+                              unsigned long long* counters, cudaStream_t s) {
+  if (g.n <= 0) return cudaSuccess;
+  switch (g.attr_dtype) {
+    case MGS_F16: return launch_pre_t<__half>(g.sh_degree, g.n, g, vt, rec, rects, touched, dkeys, counters, s);
+    case MGS_BF16: return launch_pre_t<__nv_bfloat16>(g.sh_degree, g.n, g, vt, rec, rects, touched, dkeys, counters, s);
+    default: return launch_pre_t<float>(g.sh_degree, g.n, g, vt, rec, rects, touched, dkeys, counters, s);
+  }
+}
+
+cudaError_t launch_preprocess_bwd(const mgs_gaussians& g, const ViewTable& vt, const float4* moments,
+                                  const uint32_t* touched, const mgs_grads& gr, cudaStream_t s) {
+  if (g.n <= 0) return cudaSuccess;
+  switch (g.attr_dtype) {
+    case MGS_F16: return launch_bwd_t<__half>(g.sh_degree, g.n, g, vt, moments, touched, gr, s);
+    case MGS_BF16: return launch_bwd_t<__nv_bfloat16>(g.sh_degree, g.n, g, vt, moments, touched, gr, s);
+    default: return launch_bwd_t<float>(g.sh_degree, g.n, g, vt, moments, touched, gr, s);
+  }
+}
+
+cudaError_t launch_project_one(const mgs_gaussians& g, const View& V, float* mean2d, float* conic,
+                               float* rgb, float* depth, int32_t* radius, int32_t* rect,
+                               cudaStream_t s) {
+  if (g.n <= 0) return cudaSuccess;
+  switch (g.attr_dtype) {
+    case MGS_F16: return launch_proj_t<__half>(g.sh_degree, g.n, g, V, mean2d, conic, rgb, depth, radius, rect, s);
+    case MGS_BF16: return launch_proj_t<__nv_bfloat16>(g.sh_degree, g.n, g, V, mean2d, conic, rgb, depth, radius, rect, s);
+    default: return launch_proj_t<float>(g.sh_degree, g.n, g, V, mean2d, conic, rgb, depth, radius, rect, s);
+  }
+}
+
+}  // namespace mgs

@@ -1,0 +1,351 @@
+// Tile blend kernels (Sec. II-E, Eq. 11), forward and reverse, sm_103a.
+//
+// One CTA of 256 threads owns one 16x16 tile of one view.  Forward: batches of
+// 256 sorted entries are gathered into shared memory (one entry per thread) and
+// every thread walks them front to back for its pixel, with transmittance and the
+// colour/depth sums in registers; the CTA leaves as soon as all its pixels stopped.
+//
+// Reverse: the tile's entries are walked back to front in batches of 32.  In the
+// pixel phase each thread runs the usual back-to-front recursion for its pixel
+// (T recovered by division, colour-behind S accumulated) and writes two numbers per
+// (pixel, entry) into shared memory: gp = dL/dpower and the blend weight w.  In the
+// Gaussian phase each lane owns one entry and sums, over the 32 pixels of its warp,
+// the ten moments the per-Gaussian chain rule needs; the eight warps' partial sums
+// meet in shared memory and one thread per entry issues three 16-byte vector atomics.
+// There is no per-fragment shuffle or atomic.
+#include "internal.h"
+
+namespace mgs {
+namespace {
+
+__global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ ViewTable vt,
+                                                        const float4* __restrict__ rec,
+                                                        const uint32_t* __restrict__ vals,
+                                                        const uint2* __restrict__ ranges) {
+  __shared__ float2 s_xy[kTilePix];
+  __shared__ float4 s_co[kTilePix];
+  __shared__ float4 s_col[kTilePix];
+  const int tile = blockIdx.x;
+  const View& V = vt.v[view_of_tile(vt, tile)];
+  const int local = tile - V.tile_base;
+  const int x0 = (local % V.tiles_x) * kTile, y0 = (local / V.tiles_x) * kTile;
+  const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+  const int px = x0 + lx, py = y0 + ly;
+  const bool inside = px < V.width && py < V.height;
+  const float pxf = (float)lx, pyf = (float)ly, x0f = (float)x0, y0f = (float)y0;
+  const uint2 range = ranges[tile];
+  const int n = (int)(range.y - range.x);
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+  uint32_t last = 0;
+  bool done = !inside;
+  for (int b = 0; b < n; b += kTilePix) {
+    if (__syncthreads_count(!done) == 0) break;
+    int e = b + threadIdx.x;
+    if (e < n) {
+      uint32_t idx = vals[range.x + e];
+      float4 r0 = rec[3 * (size_t)idx], r1 = rec[3 * (size_t)idx + 1], r2 = rec[3 * (size_t)idx + 2];
+      s_xy[threadIdx.x] = make_float2(__fadd_rn(__fsub_rn(r0.x, x0f), r0.z), __fadd_rn(__fsub_rn(r0.y, y0f), r0.w));
+      s_co[threadIdx.x] = r1;
+      s_col[threadIdx.x] = r2;
+    }
+    __syncthreads();
+    const int cnt = min(kTilePix, n - b);
+    if (!done) {
+      for (int j = 0; j < cnt; ++j) {
+        float dx, dy;
+        float4 co = s_co[j];
+        float p2 = frag_exp2(s_xy[j], co, pxf, pyf, dx, dy);
+        if (p2 > 0.f) continue;
+        float a = __fmul_rn(co.w, ex2_approx(p2));
+        float al = fminf(kAlphaMax, a);
+        if (al < kAlphaMin) continue;
+        float4 c = s_col[j];
+        float w = __fmul_rn(al, T);
+        C0 = __fmaf_rn(c.x, w, C0);
+        C1 = __fmaf_rn(c.y, w, C1);
+        C2 = __fmaf_rn(c.z, w, C2);
+        D = __fmaf_rn(c.w, w, D);
+        T = __fsub_rn(T, w);
+        last = (uint32_t)(b + j + 1);
+        if (T < kTStop) {
+          done = true;
+          break;
+        }
+      }
+    }
+  }
+  if (inside) {
+    size_t o = (size_t)py * V.width + px, HW = (size_t)V.width * V.height;
+    V.rgb[o] = C0;
+    V.rgb[HW + o] = C1;
+    V.rgb[2 * HW + o] = C2;
+    V.depth[o] = D;
+    V.alpha[o] = 1.f - T;
+    V.T_final[o] = T;
+    V.n_contrib[o] = last;
+  }
+}
+
+constexpr int kBwdBatch = 32;
+constexpr int kBwdStride = kBwdBatch + 1;  // padded row: conflict-free both ways
+constexpr int kBwdWarps = kTilePix / 32;
+constexpr int kMom = 10;
+
+struct BwdSmem {
+  union {
+    struct {
+      float gp[kTilePix][kBwdStride];
+      float w[kTilePix][kBwdStride];
+    } pix;
+    float red[kBwdWarps][kMom][32];
+  } u;
+  float4 g[kTilePix];       // per pixel dL/d(r, g, b, depth)
+  float2 xy[kBwdBatch];
+  float4 co[kBwdBatch];
+  float4 col[kBwdBatch];
+  uint32_t idx[kBwdBatch];
+  int lmax;
+};
+
+__global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ ViewTable vt,
+                                                        const float4* __restrict__ rec,
+                                                        const uint32_t* __restrict__ vals,
+                                                        const uint2* __restrict__ ranges,
+                                                        float4* __restrict__ moments) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
+  const int tile = blockIdx.x;
+  const View& V = vt.v[view_of_tile(vt, tile)];
+  const int local = tile - V.tile_base;
+  const int x0 = (local % V.tiles_x) * kTile, y0 = (local / V.tiles_x) * kTile;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int lx = t & (kTile - 1), ly = t / kTile;
+  const int px = x0 + lx, py = y0 + ly;
+  const bool inside = px < V.width && py < V.height;
+  const float pxf = (float)lx, pyf = (float)ly, x0f = (float)x0, y0f = (float)y0;
+  const uint2 range = ranges[tile];
+  if (t == 0) S.lmax = 0;
+  size_t o = (size_t)py * V.width + px, HW = (size_t)V.width * V.height;
+  uint32_t nc = 0;
+  float T = 1.f, Tf = 1.f, gR = 0.f, gG = 0.f, gB = 0.f, gD = 0.f, gA = 0.f;
+  if (inside) {
+    nc = V.n_contrib[o];
+    Tf = V.T_final[o];
+    T = Tf;
+    if (V.g_rgb) { gR = V.g_rgb[o]; gG = V.g_rgb[HW + o]; gB = V.g_rgb[2 * HW + o]; }
+    if (V.g_depth) gD = V.g_depth[o];
+    if (V.g_alpha) gA = V.g_alpha[o];
+  }
+  S.g[t] = make_float4(gR, gG, gB, gD);
+  __syncthreads();
+  if (nc) atomicMax(&S.lmax, (int)nc);
+  __syncthreads();
+  const int L = S.lmax;
+  const float gAT = gA * Tf;
+  float S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
+  for (int base = ((L - 1) / kBwdBatch) * kBwdBatch; L > 0 && base >= 0; base -= kBwdBatch) {
+    const int cnt = min(kBwdBatch, L - base);
+    if (t < cnt) {
+      uint32_t idx = vals[range.x + base + t];
+      float4 r0 = rec[3 * (size_t)idx], r1 = rec[3 * (size_t)idx + 1], r2 = rec[3 * (size_t)idx + 2];
+      S.xy[t] = make_float2(__fadd_rn(__fsub_rn(r0.x, x0f), r0.z), __fadd_rn(__fsub_rn(r0.y, y0f), r0.w));
+      S.co[t] = r1;
+      S.col[t] = r2;
+      S.idx[t] = idx;
+    }
+    __syncthreads();
+    // pixel phase: back-to-front recursion for this thread's pixel
+    for (int j = kBwdBatch - 1; j >= 0; --j) {
+      float gp = 0.f, w = 0.f;
+      if (j < cnt && (uint32_t)(base + j) < nc) {
+        float dx, dy;
+        float4 co = S.co[j];
+        float p2 = frag_exp2(S.xy[j], co, pxf, pyf, dx, dy);
+        if (p2 <= 0.f) {
+          float a = __fmul_rn(co.w, ex2_approx(p2));
+          float al = fminf(kAlphaMax, a);
+          if (al >= kAlphaMin) {
+            float4 c = S.col[j];
+            float om = 1.f - al;
+            float rom = __fdividef(1.f, om);
+            float Tb = T * rom;
+            w = al * Tb;
+            float e0 = c.x - S0, e1 = c.y - S1, e2 = c.z - S2, eD = c.w - SD;
+            float dLda = Tb * (e0 * gR + e1 * gG + e2 * gB + eD * gD) + gAT * rom;
+            S0 = fmaf(al, e0, S0);
+            S1 = fmaf(al, e1, S1);
+            S2 = fmaf(al, e2, S2);
+            SD = fmaf(al, eD, SD);
+            gp = a <= kAlphaMax ? dLda * a : 0.f;
+            T = Tb;
+          }
+        }
+      }
+      S.u.pix.gp[t][j] = gp;
+      S.u.pix.w[t][j] = w;
+    }
+    __syncthreads();
+    // Gaussian phase: lane = entry, warp = 32 pixels (two tile rows)
+    float m[kMom];
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) m[k] = 0.f;
+    if (lane < cnt) {
+      const float2 xy = S.xy[lane];
+#pragma unroll 4
+      for (int k = 0; k < 32; ++k) {
+        const int p = warp * 32 + k;
+        float gp = S.u.pix.gp[p][lane], w = S.u.pix.w[p][lane];
+        float dx = __fsub_rn(xy.x, (float)(p & (kTile - 1)));
+        float dy = __fsub_rn(xy.y, (float)(p / kTile));
+        float4 gg = S.g[p];
+        float gdx = gp * dx, gdy = gp * dy;
+        m[0] += gp;
+        m[1] += gdx;
+        m[2] += gdy;
+        m[3] = fmaf(gdx, dx, m[3]);
+        m[4] = fmaf(gdx, dy, m[4]);
+        m[5] = fmaf(gdy, dy, m[5]);
+        m[6] = fmaf(w, gg.x, m[6]);
+        m[7] = fmaf(w, gg.y, m[7]);
+        m[8] = fmaf(w, gg.z, m[8]);
+        m[9] = fmaf(w, gg.w, m[9]);
+      }
+    }
+    __syncthreads();  // gp / w no longer needed: reuse the space for partial sums
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) S.u.red[warp][k][lane] = m[k];
+    __syncthreads();
+    if (t < cnt) {
+      float r[kMom];
+#pragma unroll
+      for (int k = 0; k < kMom; ++k) {
+        float acc = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < kBwdWarps; ++ww) acc += S.u.red[ww][k][t];
+        r[k] = acc;
+      }
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < kMom; ++k) any |= (r[k] != 0.f);
+      if (any) {
+        float4* dst = moments + 3 * (size_t)S.idx[t];
+        atomicAdd(dst, make_float4(r[0], r[1], r[2], r[3]));
+        atomicAdd(dst + 1, make_float4(r[4], r[5], r[6], r[7]));
+        atomicAdd(dst + 2, make_float4(r[8], r[9], 0.f, 0.f));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One thread per visible (view, Gaussian) item, in front-to-back order: writes one
+// (global tile id, item) pair per tile of its rect, at the item's scanned offset.
+__global__ void __launch_bounds__(256) k_emit(int64_t n_vis, int64_t N, const uint32_t* __restrict__ dvals,
+                                              const uint32_t* __restrict__ offsets,
+                                              const uint2* __restrict__ rects,
+                                              const __grid_constant__ ViewTable vt,
+                                              uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_vis) return;
+  uint32_t item = dvals[k];
+  int v = (int)((int64_t)item / N);
+  uint2 rc = rects[item];
+  int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
+  uint32_t o = offsets[k];
+  const int base = vt.v[v].tile_base, tx = vt.v[v].tiles_x;
+  for (int y = y0; y <= y1; ++y)
+    for (int x = x0; x <= x1; ++x) {
+      tkeys[o] = (uint32_t)(base + y * tx + x);
+      tvals[o] = item;
+      ++o;
+    }
+}
+
+// Counting pass over the saved forward state: per pixel, entries evaluated by the
+// forward pass (up to its stop, else the whole range), how many of them contributed,
+// and how many the backward pass walks (up to the last contributor).
+__global__ void __launch_bounds__(kTilePix) k_frag_stats(const __grid_constant__ ViewTable vt,
+                                                         const float4* __restrict__ rec,
+                                                         const uint32_t* __restrict__ vals,
+                                                         const uint2* __restrict__ ranges,
+                                                         unsigned long long* __restrict__ out) {
+  const int tile = blockIdx.x;
+  const View& V = vt.v[view_of_tile(vt, tile)];
+  const int local = tile - V.tile_base;
+  const int x0 = (local % V.tiles_x) * kTile, y0 = (local / V.tiles_x) * kTile;
+  const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+  const int px = x0 + lx, py = y0 + ly;
+  unsigned long long ev = 0, co = 0, bw = 0;
+  if (px < V.width && py < V.height) {
+    size_t o = (size_t)py * V.width + px;
+    uint32_t nc = V.n_contrib[o];
+    float Tf = V.T_final[o];
+    uint2 range = ranges[tile];
+    uint32_t ne = Tf < kTStop ? nc : range.y - range.x;
+    const float x0f = (float)x0, y0f = (float)y0;
+    for (uint32_t e = 0; e < ne; ++e) {
+      uint32_t idx = vals[range.x + e];
+      float4 r0 = rec[3 * (size_t)idx], r1 = rec[3 * (size_t)idx + 1];
+      float2 xy = make_float2(__fadd_rn(__fsub_rn(r0.x, x0f), r0.z), __fadd_rn(__fsub_rn(r0.y, y0f), r0.w));
+      float dx, dy;
+      float p2 = frag_exp2(xy, r1, (float)lx, (float)ly, dx, dy);
+      if (p2 > 0.f) continue;
+      float a = __fmul_rn(r1.w, ex2_approx(p2));
+      if (fminf(kAlphaMax, a) >= kAlphaMin) ++co;
+    }
+    ev = ne;
+    bw = nc;
+  }
+  for (int s = 16; s; s >>= 1) {
+    ev += __shfl_xor_sync(0xffffffffu, ev, s);
+    co += __shfl_xor_sync(0xffffffffu, co, s);
+    bw += __shfl_xor_sync(0xffffffffu, bw, s);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], ev);
+    atomicAdd(&out[1], co);
+    atomicAdd(&out[2], bw);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_frag_stats(const ViewTable& vt, const float4* rec, const uint32_t* vals,
+                              const uint2* ranges, unsigned long long* out, cudaStream_t s) {
+  if (vt.n_tiles <= 0) return cudaSuccess;
+  k_frag_stats<<<vt.n_tiles, kTilePix, 0, s>>>(vt, rec, vals, ranges, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const uint32_t* offsets,
+                        const uint2* rects, const ViewTable& vt, uint32_t* tkeys, uint32_t* tvals,
+                        cudaStream_t s) {
+  if (n_vis <= 0) return cudaSuccess;
+  k_emit<<<(unsigned)div_up(n_vis, 256), 256, 0, s>>>(n_vis, N, dvals, offsets, rects, vt, tkeys, tvals);
+  count_launch();
+  return cudaGetLastError();
+}
+
+size_t blend_bwd_smem() { return sizeof(BwdSmem); }
+
+cudaError_t launch_blend_fwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
+                             const uint2* ranges, cudaStream_t s) {
+  if (vt.n_tiles <= 0) return cudaSuccess;
+  k_blend_fwd<<<vt.n_tiles, kTilePix, 0, s>>>(vt, rec, vals, ranges);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend_bwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
+                             const uint2* ranges, float4* moments, cudaStream_t s) {
+  if (vt.n_tiles <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_blend_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(BwdSmem));
+  if (e != cudaSuccess) return e;
+  k_blend_bwd<<<vt.n_tiles, kTilePix, sizeof(BwdSmem), s>>>(vt, rec, vals, ranges, moments);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace mgs

@@ -1,0 +1,255 @@
+// Device-wide exclusive scan and stable LSD radix sort (8-bit digits) for sm_103a.
+//
+// Reduce-then-scan structure, no inter-block waiting: every pass is a histogram
+// kernel, a scan of the digit-major histogram table, and a stable scatter.  Blocks
+// own 4096 consecutive items; inside a block, items are ranked round by round (256
+// at a time) with warp match masks and per-warp digit counters in shared memory,
+// which keeps equal keys in input order.
+#include "internal.h"
+
+namespace mgs {
+namespace {
+
+constexpr int kWarps = kSortThreads / 32;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// --- scan ---
+__global__ void __launch_bounds__(kSortThreads) k_scan_reduce(const uint32_t* __restrict__ in,
+                                                              const uint32_t* __restrict__ gather,
+                                                              int64_t n, uint32_t* __restrict__ sums) {
+  int64_t base = (int64_t)blockIdx.x * kSortTile;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < kSortPerThread; ++i) {
+    int64_t k = base + i * kSortThreads + threadIdx.x;
+    if (k < n) acc += in[gather ? gather[k] : k];
+  }
+  __shared__ uint32_t s[kWarps];
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kWarps; ++w) t += s[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of sums[0..nb) in place by one block; sums[nb] = total.
+__global__ void __launch_bounds__(1024) k_scan_spine(uint32_t* sums, int64_t nb, uint32_t* total) {
+  __shared__ uint32_t s[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += 1024) {
+    int64_t k = base + threadIdx.x;
+    uint32_t x = k < nb ? sums[k] : 0u;
+    uint32_t inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((threadIdx.x & 31) >= o) inc += y;
+    }
+    if ((threadIdx.x & 31) == 31) s[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint32_t w = s[threadIdx.x], wi = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (threadIdx.x >= o) wi += y;
+      }
+      s[threadIdx.x] = wi - w;
+    }
+    __syncthreads();
+    uint32_t excl = carry + s[threadIdx.x >> 5] + inc - x;
+    if (k < nb) sums[k] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sums[nb] = carry;
+    if (total) *total = carry;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* in,
+                                                            const uint32_t* __restrict__ gather,
+                                                            int64_t n, const uint32_t* __restrict__ sums,
+                                                            uint32_t* out) {
+  __shared__ uint32_t tile[kSortTile];
+  __shared__ uint32_t s[kWarps];
+  int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+  for (int i = 0; i < kSortPerThread; ++i) {
+    int idx = i * kSortThreads + threadIdx.x;
+    int64_t k = base + idx;
+    tile[idx] = k < n ? in[gather ? gather[k] : k] : 0u;
+  }
+  __syncthreads();
+  uint32_t loc[kSortPerThread];
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < kSortPerThread; ++i) {
+    loc[i] = acc;
+    acc += tile[threadIdx.x * kSortPerThread + i];
+  }
+  uint32_t inc = acc;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if ((threadIdx.x & 31) >= o) inc += y;
+  }
+  if ((threadIdx.x & 31) == 31) s[threadIdx.x >> 5] = inc;
+  __syncthreads();
+  uint32_t wpre = 0;
+  for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wpre += s[w];
+  uint32_t off = sums[blockIdx.x] + wpre + inc - acc;
+#pragma unroll
+  for (int i = 0; i < kSortPerThread; ++i) tile[threadIdx.x * kSortPerThread + i] = off + loc[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kSortPerThread; ++i) {
+    int idx = i * kSortThreads + threadIdx.x;
+    int64_t k = base + idx;
+    if (k < n) out[k] = tile[idx];
+  }
+}
+
+// --- radix sort ---
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                             int64_t n, int shift, int nb,
+                                                             uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int i = 0; i < kSortPerThread; ++i) {
+    int64_t k = base + i * kSortThreads + threadIdx.x;
+    uint32_t d = k < n ? (keys[k] >> shift) & 255u : 256u;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d < 256u && (peers & lanemask_lt()) == 0) atomicAdd(&h[d], __popc(peers));
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
+    int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout) {
+  __shared__ uint32_t s_wc[2][kWarps][256];
+  __shared__ uint32_t s_run[256];
+  __shared__ uint32_t s_off[256];
+  const int t = threadIdx.x, w = t >> 5;
+  s_off[t] = hist[(int64_t)t * nb + blockIdx.x];
+  s_run[t] = 0;
+#pragma unroll
+  for (int ww = 0; ww < kWarps; ++ww) s_wc[0][ww][t] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const uint32_t lt = lanemask_lt();
+  for (int r = 0; r < kSortPerThread; ++r) {
+    const int b = r & 1;
+    int64_t k = base + r * kSortThreads + t;
+    bool valid = k < n;
+    uint32_t key = valid ? kin[k] : 0u;
+    uint32_t val = valid ? (vin ? vin[k] : (uint32_t)k) : 0u;
+    uint32_t d = valid ? (key >> shift) & 255u : 256u;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t rank = __popc(peers & lt);
+    if (valid && rank == 0) s_wc[b][w][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t run = s_run[t];
+#pragma unroll
+      for (int ww = 0; ww < kWarps; ++ww) {
+        uint32_t c = s_wc[b][ww][t];
+        s_wc[b][ww][t] = run;
+        run += c;
+        s_wc[b ^ 1][ww][t] = 0;
+      }
+      s_run[t] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = s_off[d] + s_wc[b][w][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+  }
+}
+
+__global__ void k_ranges(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  uint32_t key = keys[k];
+  if (k == 0 || keys[k - 1] != key) ranges[key].x = (uint32_t)k;
+  if (k == n - 1 || keys[k + 1] != key) ranges[key].y = (uint32_t)(k + 1);
+}
+
+}  // namespace
+
+int64_t sort_scratch_words(int64_t n) {
+  int64_t nb = div_up(std::max<int64_t>(n, 1), kSortTile);
+  int64_t hist = 256 * nb;
+  int64_t spine = div_up(std::max<int64_t>(hist, n), kSortTile) + 1;
+  return align_up((size_t)hist, 64) + align_up((size_t)spine, 64);
+}
+
+cudaError_t scan_exclusive_u32(const uint32_t* in, const uint32_t* gather, uint32_t* out,
+                               int64_t n, uint32_t* scratch, uint32_t* total_dev, cudaStream_t s) {
+  if (n <= 0) {
+    if (total_dev) return cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
+    return cudaSuccess;
+  }
+  int64_t nb = div_up(n, kSortTile);
+  uint32_t* sums = scratch;
+  k_scan_reduce<<<(unsigned)nb, kSortThreads, 0, s>>>(in, gather, n, sums);
+  k_scan_spine<<<1, 1024, 0, s>>>(sums, nb, total_dev);
+  k_scan_down<<<(unsigned)nb, kSortThreads, 0, s>>>(in, gather, n, sums, out);
+  count_launch(3);
+  return cudaGetLastError();
+}
+
+int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, int end_bit,
+                     bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err) {
+  *err = cudaSuccess;
+  int cur = 0;
+  if (n <= 0) return 0;
+  int nb = (int)div_up(n, kSortTile);
+  uint32_t* hist = scratch;
+  uint32_t* spine = scratch + align_up((size_t)256 * nb, 64);
+  bool first = true;
+  for (int shift = begin_bit; shift < end_bit; shift += 8) {
+    k_radix_hist<<<nb, kSortThreads, 0, s>>>(k[cur], n, shift, nb, hist);
+    count_launch(2);
+    *err = scan_exclusive_u32(hist, nullptr, hist, (int64_t)256 * nb, spine, nullptr, s);
+    if (*err != cudaSuccess) return cur;
+    const uint32_t* vin = (first && vals_iota) ? nullptr : v[cur];
+    k_radix_scatter<<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, nb, hist, k[cur ^ 1],
+                                                v[cur ^ 1]);
+    cur ^= 1;
+    first = false;
+    *err = cudaGetLastError();
+    if (*err != cudaSuccess) return cur;
+  }
+  if (first && vals_iota) {
+    // no pass ran: materialise the identity permutation
+    *err = cudaErrorInvalidValue;
+  }
+  return cur;
+}
+
+cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint2* ranges, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_ranges<<<(unsigned)div_up(n, 256), 256, 0, s>>>(keys, n, ranges);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace mgs

@@ -1,0 +1,132 @@
+"""GPU parity of the voxel merge (Sec. II-D, Eq. 3-10) and of Adam, through the C ABI.
+Voxel coordinates and merge clusters must match the oracle bit for bit on inputs
+scrubbed of near-threshold ties; values within the stated tolerances."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_13536_gb300 import api, scenegen as sg
+from tests import _gpu
+from tests.test_oracle_merge import _voxel_scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_13536_gb300 import build
+    build.build()
+
+
+def scrub(orc, scene, voxel, rounds=6, **kw):
+    """Drop Gaussians that take part in a near-tie (|d2 - chi2| or two competing
+    candidates within 1e-4 relative), until none is left."""
+    for _ in range(rounds):
+        out = orc.voxel_merge(scene, voxel, tie_rel=1e-4, **kw)
+        bad = out["tie"] != 0
+        if not bad.any():
+            return scene, out
+        scene = scene.subset(np.nonzero(~bad)[0])
+    raise AssertionError("tie scrub did not converge")
+
+
+def cov_of(q, ls):
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                  2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                  2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1).reshape(-1, 3, 3)
+    s2 = np.exp(2 * ls)
+    S = np.einsum("nik,nk,njk->nij", R, s2, R)
+    return S[:, [0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]]
+
+
+def compare_merge(orc, scene, voxel, greedy=True, **kw):
+    scene, ref = scrub(orc, scene, voxel, greedy=greedy, **kw)
+    g = api.Gaussians.from_scene(scene, "cuda")
+    dev_kw = {k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) else v)
+              for k, v in kw.items()}
+    out, partner, vox = api.mgs_voxel_merge(g, voxel, greedy=greedy, **dev_kw)
+    torch.cuda.synchronize()
+    part = partner.cpu().numpy()
+    np.testing.assert_array_equal(part, ref["partner"])
+    keys = orc.voxel_keys(scene.means, voxel)
+    v = vox.cpu().numpy()
+    elig = v[:, 0] != np.iinfo(np.int32).min
+    np.testing.assert_array_equal(v[elig], keys[elig])
+    assert out.n == ref["n_out"]
+    np.testing.assert_array_equal(out.birth.cpu().numpy().astype(np.uint64), ref["birth"])
+    np.testing.assert_array_equal(_gpu.to_np(out.opacity_logit), ref["opacity_logit"])
+    np.testing.assert_array_equal(_gpu.to_np(out.sh), ref["sh"])
+    np.testing.assert_allclose(_gpu.to_np(out.means), ref["means"], rtol=1e-5, atol=1e-7)
+    S = cov_of(_gpu.to_np(out.quats), _gpu.to_np(out.log_scales))
+    Sr = ref["cov"]
+    full = lambda c: c[:, [0, 1, 2, 1, 3, 4, 2, 4, 5]]
+    rel = np.linalg.norm(full(S) - full(Sr), axis=1) / np.linalg.norm(full(Sr), axis=1)
+    assert rel.max() < 1e-4, rel.max()
+    return int((part >= 0).sum() // 2), scene.n
+
+
+@pytest.mark.parametrize("greedy", [True, False])
+def test_merge_small_voxels(orc, greedy):
+    rng = np.random.default_rng(3)
+    sc = _voxel_scene(rng, 200, 6)
+    pairs, n = compare_merge(orc, sc, 0.02, greedy=greedy)
+    assert pairs > 50
+
+
+def test_merge_crowded_voxels_use_block_path(orc):
+    rng = np.random.default_rng(4)
+    sc = _voxel_scene(rng, 6, 45)  # > 32 members per voxel
+    pairs, n = compare_merge(orc, sc, 0.02)
+    assert pairs > 20
+
+
+def test_merge_mask_eq3(orc):
+    rng = np.random.default_rng(5)
+    sc = _voxel_scene(rng, 100, 5)
+    gs = rng.uniform(0, 2e-3, sc.n).astype(np.float32)
+    kf = rng.integers(0, 10, sc.n).astype(np.int32)
+    compare_merge(orc, sc, 0.02, grad_stat=gs, grad_tau=1e-3, kf_id=kf, kf_min=2, kf_max=7)
+
+
+def test_merge_room300k_bit_exact_clusters(orc):
+    scene, _ = sg.workload("room300k")
+    pairs, n = compare_merge(orc, scene, 0.02)
+    print("room300k merged pairs", pairs, "of", n)
+    assert pairs > 1000
+
+
+def test_adam_matches_oracle(orc):
+    rng = np.random.default_rng(6)
+    scene = sg.box_scene(3000, 1, sh_degree=3)
+    g = api.Gaussians.from_scene(scene, "cuda")
+    grads = api.Grads.zeros_like(g, stats=False)
+    m = api.Grads.zeros_like(g, stats=False)
+    v = api.Grads.zeros_like(g, stats=False)
+    ref_p = [p.astype(np.float64).copy() for p in (scene.means, scene.log_scales, scene.quats,
+                                                     scene.opacity_logit, scene.sh)]
+    ref_m = [np.zeros_like(p) for p in ref_p]
+    ref_v = [np.zeros_like(p) for p in ref_p]
+    for step in range(1, 4):
+        gs = [rng.normal(size=p.shape).astype(np.float32) for p in ref_p]
+        for t, x in zip(grads.tensors(), gs):
+            t.copy_(torch.from_numpy(x))
+        api.mgs_adam_step(g, grads, m, v, 1e-3, 0.9, 0.999, 1e-8, step)
+        for p, gg, mm, vv in zip(ref_p, gs, ref_m, ref_v):
+            orc.adam(p, gg, mm, vv, 1e-3, 0.9, 0.999, 1e-8, step)
+    torch.cuda.synchronize()
+    for t, p in zip(g.params(), ref_p):
+        np.testing.assert_allclose(_gpu.to_np(t), p, rtol=0, atol=2e-6 * max(1.0, np.abs(p).max()))
+
+
+def test_l1_loss_grad():
+    rng = np.random.default_rng(7)
+    a = torch.from_numpy(rng.normal(size=100_001).astype(np.float32)).cuda()
+    b = torch.from_numpy(rng.normal(size=100_001).astype(np.float32)).cuda()
+    grad = torch.empty_like(a)
+    loss = torch.zeros(1, device="cuda")
+    api.mgs_l1_loss_grad(a, b, 0.5, grad, loss)
+    torch.cuda.synchronize()
+    assert torch.equal(grad, 0.5 * torch.sign(a - b))
+    assert abs(float(loss) - 0.5 * float((a - b).abs().sum())) < 1e-3 * float(loss)
