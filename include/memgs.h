@@ -185,10 +185,11 @@ mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_
                            void* stream);
 
 /* ------------------------------------------------------------------------------
- * Optimiser: Adam with bias correction, in one launch over every parameter array of
- * `params` (the optimiser is not named in the paper, Sec. II-E; Adam is this
+ * Optimiser: Adam with bias correction over every parameter array of `params`
+ * (one streaming launch per array; the optimiser is not named in the paper, Sec. II-E; Adam is this
  * library's choice).  m and v are f32 state arrays shaped like the parameters
- * (same mgs_gaussians_mut layout, f32 pointers in m_state / v_state).  Parameters
+ * (same mgs_gaussians_mut layout, f32 pointers in m_state / v_state), 16-byte
+ * aligned like the parameter and gradient arrays.  Parameters
  * stored in f16/bf16 are updated in f32 and rounded back.  step >= 1.  zero_grads = 1
  * clears each gradient element after it is consumed (the next backward pass
  * accumulates from zero without a separate clearing pass).  Asynchronous.

@@ -1097,10 +1097,14 @@ int orc_voxel_merge(const orc_gaussians* g, const uint64_t* birth, double voxel,
     std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) {
       return std::tie(x.d2, x.bi, x.bj, x.i, x.j) < std::tie(y.d2, y.bi, y.bj, y.i, y.j);
     });
+    // The greedy outcome depends only on the order of candidates that share a member.
     if (tie_flag)
-      for (size_t k = 1; k < cands.size(); ++k)
-        if (cands[k].d2 - cands[k - 1].d2 <= tie_rel * cands[k].d2)
-          tie_flag[cands[k].i] = tie_flag[cands[k].j] = tie_flag[cands[k - 1].i] = tie_flag[cands[k - 1].j] = 1;
+      for (size_t k = 0; k < cands.size(); ++k)
+        for (size_t l = k + 1; l < cands.size() && cands[l].d2 - cands[k].d2 <= tie_rel * cands[l].d2; ++l) {
+          const Cand &x = cands[k], &y = cands[l];
+          if (x.i == y.i || x.i == y.j || x.j == y.i || x.j == y.j)
+            tie_flag[x.i] = tie_flag[x.j] = tie_flag[y.i] = tie_flag[y.j] = 1;
+        }
     for (const Cand& c : cands) {
       if (part[c.i] >= 0 || part[c.j] >= 0) continue;
       part[c.i] = c.j;

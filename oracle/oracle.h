@@ -130,8 +130,8 @@ int orc_voxel_keys(int64_t n, const double* means, double voxel, int32_t* keys);
 
 /* Full merge.  Outputs have capacity n; *n_out receives the survivor count.
  * partner[n]: index of the merge partner or -1.  tie_flag[n] (optional): 1 when the
- * Gaussian is part of a near-tie (|d2 - chi2| < tie_rel*chi2 or two competing
- * candidates of its voxel within tie_rel of each other). */
+ * Gaussian is part of a near-tie (|d2 - chi2| < tie_rel*chi2, or two candidates of
+ * its voxel that share a member with d2 within tie_rel of each other). */
 int orc_voxel_merge(const orc_gaussians* g, const uint64_t* birth, double voxel,
                     const orc_merge_params* p,
                     double* out_means, double* out_log_scales, double* out_quats,

@@ -5,48 +5,56 @@
 namespace mgs {
 namespace {
 
-struct AdamSeg {
-  void* p;          // parameter (f32/f16/bf16)
-  int dtype;
-  float* g;
-  float* m;
-  float* v;
-  int64_t n;
-  int64_t start;    // first global element of this segment
-};
-struct AdamArgs {
-  AdamSeg seg[5];
-  int nseg;
-  int64_t total;
+struct AdamHyper {
   float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
   int zero_grads;
 };
 
-template <typename T>
-__device__ __forceinline__ void adam_one(T* p, float* g, float* m, float* v, int64_t i,
-                                         const AdamArgs& a) {
-  float gi = g[i];
-  if (a.zero_grads) g[i] = 0.f;
-  float mi = a.b1 * m[i] + (1.f - a.b1) * gi;
-  float vi = a.b2 * v[i] + (1.f - a.b2) * gi * gi;
-  m[i] = mi;
-  v[i] = vi;
-  float mh = mi / a.c1, vh = vi / a.c2;
-  float x = ld(p + i) - a.lr * mh / (sqrtf(vh) + a.eps);
-  st(p + i, x);
+__device__ __forceinline__ float adam_update(float p, float& g, float& m, float& v, const AdamHyper& h) {
+  float gi = g;
+  m = h.b1 * m + (1.f - h.b1) * gi;
+  v = h.b2 * v + (1.f - h.b2) * gi * gi;
+  if (h.zero_grads) g = 0.f;
+  return p - h.lr * (m / h.c1) / (sqrtf(v / h.c2) + h.eps);
 }
 
-__global__ void __launch_bounds__(256) k_adam(const __grid_constant__ AdamArgs a) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.total;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    int s = 0;
-    while (s + 1 < a.nseg && a.seg[s + 1].start <= k) ++s;
-    const AdamSeg& S = a.seg[s];
-    int64_t i = k - S.start;
-    switch (S.dtype) {
-      case MGS_F16: adam_one((__half*)S.p, S.g, S.m, S.v, i, a); break;
-      case MGS_BF16: adam_one((__nv_bfloat16*)S.p, S.g, S.m, S.v, i, a); break;
-      default: adam_one((float*)S.p, S.g, S.m, S.v, i, a); break;
+// One parameter array; each thread owns 4 consecutive elements (16-byte vector
+// accesses on the f32 gradient and moment arrays).
+template <typename T>
+__global__ void __launch_bounds__(256) k_adam(T* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
+                                              float* __restrict__ v, int64_t n, const AdamHyper h) {
+  int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i >= n) return;
+  if (i + 4 <= n) {
+    float4 gg = *reinterpret_cast<float4*>(g + i), mm = *reinterpret_cast<float4*>(m + i),
+           vv = *reinterpret_cast<float4*>(v + i);
+    float pp[4];
+    if constexpr (sizeof(T) == 4) {
+      float4 q = *reinterpret_cast<float4*>(p + i);
+      pp[0] = q.x; pp[1] = q.y; pp[2] = q.z; pp[3] = q.w;
+    } else {
+      for (int k = 0; k < 4; ++k) pp[k] = ld(p + i + k);
+    }
+    pp[0] = adam_update(pp[0], gg.x, mm.x, vv.x, h);
+    pp[1] = adam_update(pp[1], gg.y, mm.y, vv.y, h);
+    pp[2] = adam_update(pp[2], gg.z, mm.z, vv.z, h);
+    pp[3] = adam_update(pp[3], gg.w, mm.w, vv.w, h);
+    *reinterpret_cast<float4*>(m + i) = mm;
+    *reinterpret_cast<float4*>(v + i) = vv;
+    if (h.zero_grads) *reinterpret_cast<float4*>(g + i) = gg;
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(p + i) = make_float4(pp[0], pp[1], pp[2], pp[3]);
+    } else {
+      for (int k = 0; k < 4; ++k) st(p + i + k, pp[k]);
+    }
+  } else {
+    for (int64_t k = i; k < n; ++k) {
+      float gk = g[k], mk = m[k], vk = v[k];
+      float x = adam_update(ld(p + k), gk, mk, vk, h);
+      m[k] = mk;
+      v[k] = vk;
+      if (h.zero_grads) g[k] = gk;
+      st(p + k, x);
     }
   }
 }
@@ -80,30 +88,25 @@ int sm_count() {
 cudaError_t launch_adam(const mgs_gaussians_mut& p, const mgs_grads& g, const mgs_grads& m,
                         const mgs_grads& v, float lr, float b1, float b2, float eps, int step,
                         int zero_grads, cudaStream_t s) {
-  AdamArgs a{};
-  a.zero_grads = zero_grads;
+  AdamHyper h{lr, b1, b2, eps, 1.f - powf(b1, (float)step), 1.f - powf(b2, (float)step), zero_grads};
   const int64_t n = p.n;
   const int64_t K3 = (int64_t)(p.sh_degree + 1) * (p.sh_degree + 1) * 3;
-  struct { void* p; int dt; float* g; float* m; float* v; int64_t n; } list[5] = {
+  struct Seg { void* p; int dt; float* g; float* m; float* v; int64_t n; } list[5] = {
       {p.means, MGS_F32, g.means, m.means, v.means, 3 * n},
       {p.log_scales, p.attr_dtype, g.log_scales, m.log_scales, v.log_scales, 3 * n},
       {p.quats, p.attr_dtype, g.quats, m.quats, v.quats, 4 * n},
       {p.opacity_logit, p.attr_dtype, g.opacity_logit, m.opacity_logit, v.opacity_logit, n},
       {p.sh, p.attr_dtype, g.sh, m.sh, v.sh, K3 * n}};
-  int64_t start = 0;
-  for (int k = 0; k < 5; ++k) {
-    a.seg[k] = AdamSeg{list[k].p, list[k].dt, list[k].g, list[k].m, list[k].v, list[k].n, start};
-    start += list[k].n;
+  for (const Seg& q : list) {
+    if (q.n <= 0) continue;
+    unsigned grid = (unsigned)div_up(q.n, 1024);
+    switch (q.dt) {
+      case MGS_F16: k_adam<__half><<<grid, 256, 0, s>>>((__half*)q.p, q.g, q.m, q.v, q.n, h); break;
+      case MGS_BF16: k_adam<__nv_bfloat16><<<grid, 256, 0, s>>>((__nv_bfloat16*)q.p, q.g, q.m, q.v, q.n, h); break;
+      default: k_adam<float><<<grid, 256, 0, s>>>((float*)q.p, q.g, q.m, q.v, q.n, h); break;
+    }
+    count_launch();
   }
-  a.nseg = 5;
-  a.total = start;
-  a.lr = lr; a.b1 = b1; a.b2 = b2; a.eps = eps;
-  a.c1 = 1.f - powf(b1, (float)step);
-  a.c2 = 1.f - powf(b2, (float)step);
-  if (a.total == 0) return cudaSuccess;
-  int64_t blocks = std::min<int64_t>(div_up(a.total, 256), (int64_t)sm_count() * 8);
-  k_adam<<<(unsigned)blocks, 256, 0, s>>>(a);
-  count_launch();
   return cudaGetLastError();
 }
 

@@ -13,12 +13,13 @@ cudaError_t launch_preprocess(const mgs_gaussians& g, const ViewTable& vt, float
                               uint32_t* touched, uint32_t* dkeys, unsigned long long* counters,
                               cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const mgs_gaussians& g, const ViewTable& vt, const float4* moments,
-                                  const uint32_t* touched, const mgs_grads& gr, cudaStream_t s);
+                                  const uint32_t* touched, const uint2* rects, const mgs_grads& gr,
+                                  cudaStream_t s);
 cudaError_t launch_project_one(const mgs_gaussians& g, const View& V, float* mean2d, float* conic,
                                float* rgb, float* depth, int32_t* radius, int32_t* rect, cudaStream_t s);
 cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const uint32_t* offsets,
-                        const uint2* rects, const ViewTable& vt, uint32_t* tkeys, uint32_t* tvals,
-                        cudaStream_t s);
+                        const uint32_t* touched, const uint2* rects, const float4* rec, const ViewTable& vt,
+                        uint32_t* tkeys, uint32_t* tvals, cudaStream_t s);
 cudaError_t launch_blend_fwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
                              const uint2* ranges, cudaStream_t s);
 cudaError_t launch_blend_bwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
@@ -113,9 +114,10 @@ int64_t key_capacity_for(int64_t n, const mgs_camera* cams, int nv, size_t bytes
   return lo;
 }
 
+// Bits of a tile key: ids 0..tiles-1 plus the sentinel id `tiles`.
 int tile_bits(int64_t tiles) {
   int b = 1;
-  while ((int64_t(1) << b) < tiles) ++b;
+  while ((int64_t(1) << b) < tiles + 1) ++b;
   return b;
 }
 
@@ -248,7 +250,7 @@ mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_
   }
   {
     ProfScope ps(kProfEmit, s);
-    MGS_TRY_CUDA(launch_emit(n_vis, g->n, dv[dcur], offsets, rects, vt, tk[0], tv[0], s));
+    MGS_TRY_CUDA(launch_emit(n_vis, g->n, dv[dcur], offsets, touched, rects, rec, vt, tk[0], tv[0], s));
   }
   int tcur = 0;
   {
@@ -256,7 +258,7 @@ mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_
     tcur = radix_sort_pairs(tk, tv, n_keys, 0, tile_bits(vt.n_tiles), false, scratch, s, &e);
     if (e != cudaSuccess) return cuda_status(e, "tile sort");
     MGS_TRY_CUDA(cudaMemsetAsync(ranges, 0, 8 * (size_t)vt.n_tiles, s));
-    MGS_TRY_CUDA(build_ranges(tk[tcur], n_keys, ranges, s));
+    MGS_TRY_CUDA(build_ranges(tk[tcur], n_keys, (uint32_t)vt.n_tiles, ranges, s));
   }
   {
     ProfScope ps(kProfBlendFwd, s);
@@ -296,7 +298,8 @@ mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams, i
   }
   {
     ProfScope ps(kProfPreprocessBwd, s);
-    MGS_TRY_CUDA(launch_preprocess_bwd(*g, vt, moments, at<uint32_t>(workspace, L.touched), *grads, s));
+    MGS_TRY_CUDA(launch_preprocess_bwd(*g, vt, moments, at<uint32_t>(workspace, L.touched),
+                                       at<uint2>(workspace, L.rects), *grads, s));
   }
   return MGS_OK;
 }

@@ -191,4 +191,86 @@ __device__ __forceinline__ float frag_exp2(float2 xy, float4 co, float pxf, floa
   return __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(co.z, dy), dy));
 }
 
+// ---- exact tile culling ----------------------------------------------------------
+// A Gaussian can only pass the alpha >= 1/255 test where o 2^p2 >= 1/255, i.e. inside
+// the ellipse  a dx^2 + 2 b dx dy + c dy^2 <= kappa  with (a, 2b, c) = -(A', B', C')
+// from the projected record and kappa = log2(255 o).  Tiles of the 3-sigma rect that
+// this ellipse (slightly enlarged against f32 rounding) does not reach hold no pixel
+// where the Gaussian contributes, so dropping them changes no output.  Both the
+// counting pass and the key emission evaluate these functions on the same stored
+// record values with explicit round-to-nearest intrinsics, so they agree exactly.
+struct Cull {
+  float a, b, c, det, kappa, ex, ey, ux, uy;
+  bool none;   // no pixel can reach the cutoff
+  bool full;   // degenerate form: keep the whole rect
+};
+
+__device__ __forceinline__ Cull make_cull(float4 r0, float4 r1) {
+  Cull q;
+  q.ux = r0.x;
+  q.uy = r0.y;
+  q.a = -r1.x;
+  q.b = __fmul_rn(-0.5f, r1.y);
+  q.c = -r1.z;
+  float k = log2f(__fmul_rn(255.f, r1.w));
+  q.kappa = __fadd_rn(__fmul_rn(k, 1.0001f), 1e-3f);
+  q.none = !(q.kappa > 0.f);
+  q.det = __fsub_rn(__fmul_rn(q.a, q.c), __fmul_rn(q.b, q.b));
+  q.full = !(q.det > 0.f) || !(q.a > 0.f) || !(q.c > 0.f);
+  if (q.none || q.full) { q.ex = q.ey = 0.f; return q; }
+  q.ex = __fadd_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(q.kappa, q.c), q.det)), 1e-2f);
+  q.ey = __fadd_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(q.kappa, q.a), q.det)), 1e-2f);
+  return q;
+}
+
+__device__ __forceinline__ int tiles_lo(float X) {  // first tile whose last pixel centre >= X
+  return (int)fmaxf(-1.f, fminf(65536.f, ceilf(__fmul_rn(__fsub_rn(X, 15.f), 0.0625f))));
+}
+__device__ __forceinline__ int tiles_hi(float X) {  // last tile whose first pixel centre <= X
+  return (int)fmaxf(-1.f, fminf(65536.f, floorf(__fmul_rn(X, 0.0625f))));
+}
+
+// Rows of the rect [y0, y1] the ellipse can reach.
+__device__ __forceinline__ void cull_rows(const Cull& q, int& y0, int& y1) {
+  if (q.full) return;
+  if (q.none) { y1 = y0 - 1; return; }
+  y0 = max(y0, tiles_lo(__fsub_rn(q.uy, q.ey)));
+  y1 = min(y1, tiles_hi(__fadd_rn(q.uy, q.ey)));
+}
+
+// Columns of tile row ty (inside rect columns [x0, x1]) the ellipse can reach.
+__device__ __forceinline__ void cull_cols(const Cull& q, int ty, int& x0, int& x1) {
+  if (q.full) return;
+  if (q.none) { x1 = x0 - 1; return; }
+  float lo = fmaxf(__fsub_rn((float)(ty * kTile), q.uy), -q.ey);
+  float hi = fminf(__fsub_rn((float)(ty * kTile + kTile - 1), q.uy), q.ey);
+  if (lo > hi) { x1 = x0 - 1; return; }
+  auto half = [&](float dy) {  // sqrt(a kappa - det dy^2) / a
+    float r = __fsub_rn(__fmul_rn(q.a, q.kappa), __fmul_rn(q.det, __fmul_rn(dy, dy)));
+    return __fdiv_rn(__fsqrt_rn(fmaxf(r, 0.f)), q.a);
+  };
+  auto mid = [&](float dy) { return __fdiv_rn(__fmul_rn(-q.b, dy), q.a); };
+  float dyL = __fdiv_rn(__fmul_rn(q.b, q.ex), q.c);  // height of the leftmost point
+  float xmin, xmax;
+  if (dyL >= lo && dyL <= hi) xmin = -q.ex;
+  else xmin = fminf(__fsub_rn(mid(lo), half(lo)), __fsub_rn(mid(hi), half(hi)));
+  if (-dyL >= lo && -dyL <= hi) xmax = q.ex;
+  else xmax = fmaxf(__fadd_rn(mid(lo), half(lo)), __fadd_rn(mid(hi), half(hi)));
+  x0 = max(x0, tiles_lo(__fsub_rn(__fadd_rn(q.ux, xmin), 1e-2f)));
+  x1 = min(x1, tiles_hi(__fadd_rn(__fadd_rn(q.ux, xmax), 1e-2f)));
+}
+
+// Number of tiles of the inclusive rect rc the Gaussian can contribute to.
+__device__ __forceinline__ uint32_t cull_count(const Cull& q, const int rc[4]) {
+  int y0 = rc[1], y1 = rc[3];
+  cull_rows(q, y0, y1);
+  uint32_t n = 0;
+  for (int y = y0; y <= y1; ++y) {
+    int x0 = rc[0], x1 = rc[2];
+    cull_cols(q, y, x0, x1);
+    if (x1 >= x0) n += (uint32_t)(x1 - x0 + 1);
+  }
+  return n;
+}
+
 }  // namespace mgs

@@ -58,7 +58,7 @@ inline int radix_passes(int begin_bit, int end_bit) {
   return end_bit > begin_bit ? (end_bit - begin_bit + 7) / 8 : 0;
 }
 
-// [start, end) of every key value present in sorted keys (absent values untouched).
-cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint2* ranges, cudaStream_t s);
+// [start, end) of every key value < n_valid present in sorted keys (absent values untouched).
+cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s);
 
 }  // namespace mgs

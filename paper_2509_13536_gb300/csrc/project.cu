@@ -169,22 +169,24 @@ __global__ void __launch_bounds__(256) k_preprocess(int64_t N, const float* __re
       view_geom(G, V, P);
       int r = 0, rc[4];
       bool vis = P.ok && tile_rect(P, V, r, rc);
+      uint32_t count = 0;
       if (vis) {
         float raw[3];
         colour<DEG>(c, P.dir, raw);
-        rec[3 * item + 0] = make_float4(P.u_hi, P.v_hi, P.u_lo, P.v_lo);
-        rec[3 * item + 1] = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, G.o);
+        float4 r0 = make_float4(P.u_hi, P.v_hi, P.u_lo, P.v_lo);
+        float4 r1 = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, G.o);
+        rec[3 * item + 0] = r0;
+        rec[3 * item + 1] = r1;
         rec[3 * item + 2] = make_float4(fmaxf(0.f, raw[0]), fmaxf(0.f, raw[1]), fmaxf(0.f, raw[2]), P.tz);
         rects[item] = make_uint2((uint32_t)rc[0] | ((uint32_t)rc[1] << 16), (uint32_t)rc[2] | ((uint32_t)rc[3] << 16));
-        uint32_t area = (uint32_t)(rc[2] - rc[0] + 1) * (uint32_t)(rc[3] - rc[1] + 1);
-        touched[item] = area;
-        dkeys[item] = __float_as_uint(P.tz);
-        my_keys += area;
-        my_vis += 1;
+        count = cull_count(make_cull(r0, r1), rc);
       } else {
-        touched[item] = 0;
-        dkeys[item] = 0xffffffffu;
+        rects[item] = make_uint2(1u, 0u);  // empty rect: x0 = 1 > x1 = 0
       }
+      touched[item] = count;
+      dkeys[item] = count ? __float_as_uint(P.tz) : 0xffffffffu;
+      my_keys += count;
+      my_vis += count ? 1u : 0u;
     }
   }
   for (int o = 16; o; o >>= 1) {
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(int64_t N, const float* 
                                                         const __grid_constant__ ViewTable vt,
                                                         const float4* __restrict__ moments,
                                                         const uint32_t* __restrict__ touched,
+                                                        const uint2* __restrict__ rects,
                                                         mgs_grads grads) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
@@ -264,7 +267,10 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(int64_t N, const float* 
   float stat = 0.f, vis = 0.f;
   for (int v = 0; v < vt.n_views; ++v) {
     int64_t item = (int64_t)v * N + g;
-    if (touched[item] == 0) continue;
+    uint2 rc = rects[item];
+    if ((rc.x & 0xffff) > (rc.y & 0xffff)) continue;  // not drawn in this view
+    vis += 1.f;
+    if (touched[item] == 0) continue;  // drawn, but reaches no pixel: zero gradient
     const View& V = vt.v[v];
     float4 q0 = moments[3 * item], q1 = moments[3 * item + 1], q2 = moments[3 * item + 2];
     ViewGeom P;
@@ -356,7 +362,6 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(int64_t N, const float* 
     for (int k = 0; k < 3; ++k) dm[k] += W[k] * dp[0] + W[3 + k] * dp[1] + W[6 + k] * dp[2];
     for (int k = 0; k < 3; ++k) dmu[k] += dm[k];
     stat += sqrtf(dm[0] * dm[0] + dm[1] * dm[1] + dm[2] * dm[2]);
-    vis += 1.f;
   }
   if (vis == 0.f) return;
   // S3 = Rq diag(s^2) Rq^T  ->  log-scales and quaternion
@@ -408,18 +413,18 @@ cudaError_t launch_pre_t(int deg, int64_t N, const mgs_gaussians& g, const ViewT
 
 template <typename T>
 cudaError_t launch_bwd_t(int deg, int64_t N, const mgs_gaussians& g, const ViewTable& vt,
-                         const float4* moments, const uint32_t* touched, const mgs_grads& gr,
-                         cudaStream_t s) {
+                         const float4* moments, const uint32_t* touched, const uint2* rects,
+                         const mgs_grads& gr, cudaStream_t s) {
   unsigned grid = (unsigned)div_up(N, 128);
   const T* ls = (const T*)g.log_scales;
   const T* qs = (const T*)g.quats;
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
-    case 0: k_preprocess_bwd<0, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, gr); break;
-    case 1: k_preprocess_bwd<1, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, gr); break;
-    case 2: k_preprocess_bwd<2, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, gr); break;
-    default: k_preprocess_bwd<3, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, gr); break;
+    case 0: k_preprocess_bwd<0, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, rects, gr); break;
+    case 1: k_preprocess_bwd<1, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, rects, gr); break;
+    case 2: k_preprocess_bwd<2, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, rects, gr); break;
+    default: k_preprocess_bwd<3, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, rects, gr); break;
   }
   count_launch();
   return cudaGetLastError();
@@ -458,12 +463,13 @@ cudaError_t launch_preprocess(const mgs_gaussians& g, const ViewTable& vt, float
 }
 
 cudaError_t launch_preprocess_bwd(const mgs_gaussians& g, const ViewTable& vt, const float4* moments,
-                                  const uint32_t* touched, const mgs_grads& gr, cudaStream_t s) {
+                                  const uint32_t* touched, const uint2* rects, const mgs_grads& gr,
+                                  cudaStream_t s) {
   if (g.n <= 0) return cudaSuccess;
   switch (g.attr_dtype) {
-    case MGS_F16: return launch_bwd_t<__half>(g.sh_degree, g.n, g, vt, moments, touched, gr, s);
-    case MGS_BF16: return launch_bwd_t<__nv_bfloat16>(g.sh_degree, g.n, g, vt, moments, touched, gr, s);
-    default: return launch_bwd_t<float>(g.sh_degree, g.n, g, vt, moments, touched, gr, s);
+    case MGS_F16: return launch_bwd_t<__half>(g.sh_degree, g.n, g, vt, moments, touched, rects, gr, s);
+    case MGS_BF16: return launch_bwd_t<__nv_bfloat16>(g.sh_degree, g.n, g, vt, moments, touched, rects, gr, s);
+    default: return launch_bwd_t<float>(g.sh_degree, g.n, g, vt, moments, touched, rects, gr, s);
   }
 }
 

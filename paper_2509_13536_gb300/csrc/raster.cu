@@ -238,27 +238,57 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
   }
 }
 
-// One thread per visible (view, Gaussian) item, in front-to-back order: writes one
-// (global tile id, item) pair per tile of its rect, at the item's scanned offset.
+// Key emission, one warp per 32 consecutive items of the front-to-back order: the
+// warp takes the items one at a time and its lanes write that item's (tile, item)
+// pairs row by row, for the tiles its alpha >= 1/255 ellipse reaches.  An item never
+// writes more than the count the projection pass gave it; any shortfall is padded with
+// the sentinel tile id n_tiles, which sorts last and is ignored by the range build.
 __global__ void __launch_bounds__(256) k_emit(int64_t n_vis, int64_t N, const uint32_t* __restrict__ dvals,
                                               const uint32_t* __restrict__ offsets,
-                                              const uint2* __restrict__ rects,
+                                              const uint32_t* __restrict__ touched,
+                                              const uint2* __restrict__ rects, const float4* __restrict__ rec,
                                               const __grid_constant__ ViewTable vt,
                                               uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_vis) return;
-  uint32_t item = dvals[k];
-  int v = (int)((int64_t)item / N);
-  uint2 rc = rects[item];
-  int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
-  uint32_t o = offsets[k];
-  const int base = vt.v[v].tile_base, tx = vt.v[v].tiles_x;
-  for (int y = y0; y <= y1; ++y)
-    for (int x = x0; x <= x1; ++x) {
-      tkeys[o] = (uint32_t)(base + y * tx + x);
-      tvals[o] = item;
-      ++o;
+  const int lane = threadIdx.x & 31;
+  const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~int64_t(31);
+  if (first >= n_vis) return;
+  const int64_t k = first + lane;
+  uint32_t my_item = 0, my_off = 0, my_cnt = 0;
+  if (k < n_vis) {
+    my_item = dvals[k];
+    my_off = offsets[k];
+    my_cnt = touched[my_item];
+  }
+  const int n_here = (int)(n_vis - first < 32 ? n_vis - first : 32);
+  for (int i = 0; i < n_here; ++i) {
+    const uint32_t item = __shfl_sync(0xffffffffu, my_item, i);
+    const uint32_t off = __shfl_sync(0xffffffffu, my_off, i);
+    const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, i);
+    const int v = (int)((int64_t)item / N);
+    const View& V = vt.v[v];
+    const uint2 rc = rects[item];
+    const Cull q = make_cull(rec[3 * (size_t)item], rec[3 * (size_t)item + 1]);
+    int y0 = rc.x >> 16, y1 = rc.y >> 16;
+    cull_rows(q, y0, y1);
+    uint32_t w = 0;
+    for (int y = y0; y <= y1 && w < cnt; ++y) {
+      int x0 = rc.x & 0xffff, x1 = rc.y & 0xffff;
+      cull_cols(q, y, x0, x1);
+      const int nx = x1 - x0 + 1;
+      for (int dx = lane; dx < nx; dx += 32) {
+        uint32_t pos = w + (uint32_t)dx;
+        if (pos < cnt) {
+          tkeys[off + pos] = (uint32_t)(V.tile_base + y * V.tiles_x + x0 + dx);
+          tvals[off + pos] = item;
+        }
+      }
+      if (nx > 0) w += (uint32_t)nx;
     }
+    for (uint32_t pos = w + lane; pos < cnt; pos += 32) {
+      tkeys[off + pos] = (uint32_t)vt.n_tiles;
+      tvals[off + pos] = item;
+    }
+  }
 }
 
 // Counting pass over the saved forward state: per pixel, entries evaluated by the
@@ -319,10 +349,11 @@ cudaError_t launch_frag_stats(const ViewTable& vt, const float4* rec, const uint
 }
 
 cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const uint32_t* offsets,
-                        const uint2* rects, const ViewTable& vt, uint32_t* tkeys, uint32_t* tvals,
-                        cudaStream_t s) {
+                        const uint32_t* touched, const uint2* rects, const float4* rec, const ViewTable& vt,
+                        uint32_t* tkeys, uint32_t* tvals, cudaStream_t s) {
   if (n_vis <= 0) return cudaSuccess;
-  k_emit<<<(unsigned)div_up(n_vis, 256), 256, 0, s>>>(n_vis, N, dvals, offsets, rects, vt, tkeys, tvals);
+  k_emit<<<(unsigned)div_up(n_vis, 256), 256, 0, s>>>(n_vis, N, dvals, offsets, touched, rects, rec, vt, tkeys,
+                                                       tvals);
   count_launch();
   return cudaGetLastError();
 }

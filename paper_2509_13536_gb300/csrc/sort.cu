@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* in,
 
 // --- radix sort ---
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
-                                                             int64_t n, int shift, int nb,
+                                                             int64_t n, int shift, uint32_t mask, int nb,
                                                              uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 #pragma unroll 4
   for (int i = 0; i < kSortPerThread; ++i) {
     int64_t k = base + i * kSortThreads + threadIdx.x;
-    uint32_t d = k < n ? (keys[k] >> shift) & 255u : 256u;
+    uint32_t d = k < n ? (keys[k] >> shift) & mask : 256u;
     uint32_t peers = __match_any_sync(0xffffffffu, d);
     if (d < 256u && (peers & lanemask_lt()) == 0) atomicAdd(&h[d], __popc(peers));
   }
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
-    int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
+    uint32_t mask, int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout) {
   __shared__ uint32_t s_wc[2][kWarps][256];
   __shared__ uint32_t s_run[256];
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     bool valid = k < n;
     uint32_t key = valid ? kin[k] : 0u;
     uint32_t val = valid ? (vin ? vin[k] : (uint32_t)k) : 0u;
-    uint32_t d = valid ? (key >> shift) & 255u : 256u;
+    uint32_t d = valid ? (key >> shift) & mask : 256u;
     uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t rank = __popc(peers & lt);
     if (valid && rank == 0) s_wc[b][w][d] = __popc(peers);
@@ -184,10 +184,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   }
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
+__global__ void k_ranges(const uint32_t* __restrict__ keys, int64_t n, uint32_t n_valid,
+                         uint2* __restrict__ ranges) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   uint32_t key = keys[k];
+  if (key >= n_valid) return;  // sentinel keys
   if (k == 0 || keys[k - 1] != key) ranges[key].x = (uint32_t)k;
   if (k == n - 1 || keys[k + 1] != key) ranges[key].y = (uint32_t)(k + 1);
 }
@@ -226,12 +228,13 @@ int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, i
   uint32_t* spine = scratch + align_up((size_t)256 * nb, 64);
   bool first = true;
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
-    k_radix_hist<<<nb, kSortThreads, 0, s>>>(k[cur], n, shift, nb, hist);
+    const uint32_t mask = (1u << std::min(8, end_bit - shift)) - 1u;
+    k_radix_hist<<<nb, kSortThreads, 0, s>>>(k[cur], n, shift, mask, nb, hist);
     count_launch(2);
     *err = scan_exclusive_u32(hist, nullptr, hist, (int64_t)256 * nb, spine, nullptr, s);
     if (*err != cudaSuccess) return cur;
     const uint32_t* vin = (first && vals_iota) ? nullptr : v[cur];
-    k_radix_scatter<<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, nb, hist, k[cur ^ 1],
+    k_radix_scatter<<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, mask, nb, hist, k[cur ^ 1],
                                                 v[cur ^ 1]);
     cur ^= 1;
     first = false;
@@ -245,9 +248,9 @@ int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, i
   return cur;
 }
 
-cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint2* ranges, cudaStream_t s) {
+cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_ranges<<<(unsigned)div_up(n, 256), 256, 0, s>>>(keys, n, ranges);
+  k_ranges<<<(unsigned)div_up(n, 256), 256, 0, s>>>(keys, n, n_valid, ranges);
   count_launch();
   return cudaGetLastError();
 }

@@ -17,7 +17,7 @@ def make_scene(means, scales, quats, opacities, colours, sh_degree=0, sh=None, b
     k = (sh_degree + 1) ** 2
     if sh is None:
         sh = np.zeros((n, k, 3))
-        sh[:, 0, :] = (np.asarray(colours, np.float64) - 0.5) / Y00
+        sh[:, 0, :] = (np.asarray(colours, np.float64).reshape(n, 3) - 0.5) / Y00
     f = np.float32
     return sg.Scene(np.asarray(means, f).reshape(n, 3), np.log(np.asarray(scales, np.float64)).astype(f).reshape(n, 3),
                     np.asarray(quats, f).reshape(n, 4),

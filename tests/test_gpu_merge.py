@@ -77,7 +77,7 @@ def test_merge_small_voxels(orc, greedy):
 
 def test_merge_crowded_voxels_use_block_path(orc):
     rng = np.random.default_rng(4)
-    sc = _voxel_scene(rng, 6, 45)  # > 32 members per voxel
+    sc = _voxel_scene(rng, 8, 40)  # > 32 members per voxel
     pairs, n = compare_merge(orc, sc, 0.02)
     assert pairs > 20
 
