@@ -234,6 +234,24 @@ mgs_status mgs_render_stats(const mgs_gaussians* g, const mgs_camera* cams_host,
                             void* workspace, size_t workspace_bytes, uint64_t* stats_host,
                             void* stream);
 
+/* ------------------------------------------------------------------------------
+ * Sort without allocation.  The paper has no counterpart; this entry point serves
+ * callers that cannot call cudaMalloc (or hand a workspace to every call): hosts that
+ * reserve all device memory in their own pool up front, plugins given no allocator,
+ * and latency-critical loops where a device allocation would synchronise the device
+ * and stall work on other streams.  Same result as mgs_sort_pairs, with the scratch
+ * in a statically sized device array inside the library: n <= MGS_SORT_NOALLOC_MAX
+ * (1,048,576 pairs; about 13 MB held on every GPU that loads the library until the
+ * process exits).  Larger n returns MGS_ERR_UNSUPPORTED.  It calls no cudaMalloc or
+ * cudaFree.  The first call on a device looks up the array's device address (once
+ * per device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race, so serialise them.  Asynchronous on `stream`.
+ * ------------------------------------------------------------------------------ */
+#define MGS_SORT_NOALLOC_MAX (1 << 20)
+mgs_status mgs_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, uint32_t* vals_out, int64_t n,
+                                  int32_t begin_bit, int32_t end_bit, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* mgs_last_error(void);
 

@@ -12,6 +12,7 @@ import threading
 from . import build as _build
 
 MGS_MAX_VIEWS = 32
+MGS_SORT_NOALLOC_MAX = 1 << 20
 MGS_OK, MGS_ERR_INVALID, MGS_ERR_WORKSPACE, MGS_ERR_CUDA, MGS_ERR_TIMEOUT, MGS_ERR_UNSUPPORTED = range(6)
 MGS_F32, MGS_F16, MGS_BF16 = 0, 1, 2
 STATUS_NAMES = {0: "MGS_OK", 1: "MGS_ERR_INVALID", 2: "MGS_ERR_WORKSPACE", 3: "MGS_ERR_CUDA",
@@ -20,7 +21,8 @@ STATUS_NAMES = {0: "MGS_OK", 1: "MGS_ERR_INVALID", 2: "MGS_ERR_WORKSPACE", 3: "M
 EXPORTS = ["mgs_render_workspace_size", "mgs_render", "mgs_render_backward", "mgs_project",
            "mgs_voxel_merge_workspace_size", "mgs_voxel_merge", "mgs_adam_step", "mgs_l1_loss_grad",
            "mgs_sort_workspace_size", "mgs_sort_pairs", "mgs_last_error", "mgs_version",
-           "mgs_launch_count", "mgs_profile_enable", "mgs_profile_read", "mgs_render_stats"]
+           "mgs_launch_count", "mgs_profile_enable", "mgs_profile_read", "mgs_render_stats",
+           "mgs_sort_pairs_noalloc"]
 
 
 class mgs_gaussians(C.Structure):
@@ -89,6 +91,7 @@ def load():
             "mgs_l1_loss_grad": (C.c_int, [P, P, I64, F, P, P, P]),
             "mgs_sort_workspace_size": (SZ, [I64]),
             "mgs_sort_pairs": (C.c_int, [P, P, P, I64, I32, I32, P, SZ, P]),
+            "mgs_sort_pairs_noalloc": (C.c_int, [P, P, P, I64, I32, I32, P]),
             "mgs_launch_count": (C.c_uint64, []),
             "mgs_profile_enable": (None, [I32]),
             "mgs_profile_read": (I32, [I32, P, P, P]),
