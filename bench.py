@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=float, default=0.5, help="fraction of one view's tiles for the oracle")
+    p.add_argument("--views", type=int, default=8, help="keyframes per step (8 = the benchmark workload)")
+    p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
 
@@ -172,6 +174,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     build.build()
     scene, cams = sg.workload(WORKLOAD)
+    cams = cams[:args.views]
     V = len(cams)
     H, W = cams[0].height, cams[0].width
     # targets: keyframes rendered from the unperturbed map
@@ -249,6 +252,8 @@ def run_ours(args):
     value = world * V / (ms / 1e3)
 
     # end to end: keyframe images arrive from pinned host memory, the loss goes back
+    if args.no_e2e:
+        args.steps_e2e = 0
     host_rgb = target_rgb.cpu().pin_memory()
     host_depth = target_depth.cpu().pin_memory()
     host_loss = torch.empty(1, pin_memory=True)
@@ -257,7 +262,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record(stream)
-    for _ in range(args.steps):
+    for _ in range(getattr(args, "steps_e2e", args.steps)):
         target_rgb.copy_(host_rgb, non_blocking=True)
         target_depth.copy_(host_depth, non_blocking=True)
         step()
@@ -265,7 +270,7 @@ def run_ours(args):
         torch.cuda.current_stream().synchronize()
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3) / args.steps
+    ms_e2e = e2.elapsed_time(e3) / max(1, getattr(args, "steps_e2e", args.steps))
     if world > 1:
         t = torch.tensor([ms_e2e], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
