@@ -66,7 +66,8 @@ class MemgsError(RuntimeError):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The in-tree build, or the library named by MEMGS_LIB (a deployment override)."""
+    return os.environ.get("MEMGS_LIB") or _build.LIB
 
 
 def load():

@@ -195,15 +195,21 @@ __device__ __forceinline__ float frag_exp2(float2 xy, float4 co, float pxf, floa
 // A Gaussian can only pass the alpha >= 1/255 test where o 2^p2 >= 1/255, i.e. inside
 // the ellipse  a dx^2 + 2 b dx dy + c dy^2 <= kappa  with (a, 2b, c) = -(A', B', C')
 // from the projected record and kappa = log2(255 o).  Tiles of the 3-sigma rect that
-// this ellipse (slightly enlarged against f32 rounding) does not reach hold no pixel
-// where the Gaussian contributes, so dropping them changes no output.  Both the
-// counting pass and the key emission evaluate these functions on the same stored
-// record values with explicit round-to-nearest intrinsics, so they agree exactly.
+// this ellipse does not reach hold no pixel where the Gaussian contributes, so
+// dropping them changes no output.  The ellipse is enlarged (kappa by 1e-4 relative +
+// 1e-3, extents by 1e-2 px), far beyond the error of the approximate MUFU
+// reciprocal / square root / log used here and of the blend's own f32 evaluation.
+// Both the counting pass and the key emission evaluate these functions on the same
+// stored record values with explicit intrinsics, so they agree exactly.
 struct Cull {
-  float a, b, c, det, kappa, ex, ey, ux, uy;
+  float a, b, c, det, kappa, ex, ey, ux, uy, ia, bia, dyL;
   bool none;   // no pixel can reach the cutoff
   bool full;   // degenerate form: keep the whole rect
 };
+
+__device__ __forceinline__ float sqrt_approx(float x) {  // x >= 0
+  return x > 0.f ? __fmul_rn(x, rsqrtf(x)) : 0.f;
+}
 
 __device__ __forceinline__ Cull make_cull(float4 r0, float4 r1) {
   Cull q;
@@ -212,14 +218,18 @@ __device__ __forceinline__ Cull make_cull(float4 r0, float4 r1) {
   q.a = -r1.x;
   q.b = __fmul_rn(-0.5f, r1.y);
   q.c = -r1.z;
-  float k = log2f(__fmul_rn(255.f, r1.w));
-  q.kappa = __fadd_rn(__fmul_rn(k, 1.0001f), 1e-3f);
+  q.kappa = __fmaf_rn(__log2f(__fmul_rn(255.f, r1.w)), 1.0001f, 1e-3f);
   q.none = !(q.kappa > 0.f);
   q.det = __fsub_rn(__fmul_rn(q.a, q.c), __fmul_rn(q.b, q.b));
   q.full = !(q.det > 0.f) || !(q.a > 0.f) || !(q.c > 0.f);
-  if (q.none || q.full) { q.ex = q.ey = 0.f; return q; }
-  q.ex = __fadd_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(q.kappa, q.c), q.det)), 1e-2f);
-  q.ey = __fadd_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(q.kappa, q.a), q.det)), 1e-2f);
+  q.ex = q.ey = q.ia = q.bia = q.dyL = 0.f;
+  if (q.none || q.full) return q;
+  const float kd = __fdividef(q.kappa, q.det);
+  q.ex = __fadd_rn(sqrt_approx(__fmul_rn(kd, q.c)), 1e-2f);
+  q.ey = __fadd_rn(sqrt_approx(__fmul_rn(kd, q.a)), 1e-2f);
+  q.ia = __fdividef(1.f, q.a);
+  q.bia = __fmul_rn(q.b, q.ia);
+  q.dyL = __fdividef(__fmul_rn(q.b, q.ex), q.c);  // height of the leftmost point
   return q;
 }
 
@@ -238,24 +248,24 @@ __device__ __forceinline__ void cull_rows(const Cull& q, int& y0, int& y1) {
   y1 = min(y1, tiles_hi(__fadd_rn(q.uy, q.ey)));
 }
 
-// Columns of tile row ty (inside rect columns [x0, x1]) the ellipse can reach.
+// Columns of tile row ty (inside rect columns [x0, x1]) the ellipse can reach: the
+// x-extent of the ellipse within the row's band of pixel centres, taken at the band
+// ends or at the ellipse's leftmost / rightmost point when that lies in the band.
 __device__ __forceinline__ void cull_cols(const Cull& q, int ty, int& x0, int& x1) {
   if (q.full) return;
   if (q.none) { x1 = x0 - 1; return; }
   float lo = fmaxf(__fsub_rn((float)(ty * kTile), q.uy), -q.ey);
   float hi = fminf(__fsub_rn((float)(ty * kTile + kTile - 1), q.uy), q.ey);
   if (lo > hi) { x1 = x0 - 1; return; }
-  auto half = [&](float dy) {  // sqrt(a kappa - det dy^2) / a
-    float r = __fsub_rn(__fmul_rn(q.a, q.kappa), __fmul_rn(q.det, __fmul_rn(dy, dy)));
-    return __fdiv_rn(__fsqrt_rn(fmaxf(r, 0.f)), q.a);
-  };
-  auto mid = [&](float dy) { return __fdiv_rn(__fmul_rn(-q.b, dy), q.a); };
-  float dyL = __fdiv_rn(__fmul_rn(q.b, q.ex), q.c);  // height of the leftmost point
+  const float ak = __fmul_rn(q.a, q.kappa);
+  const float hl = __fmul_rn(sqrt_approx(__fsub_rn(ak, __fmul_rn(q.det, __fmul_rn(lo, lo)))), q.ia);
+  const float hh = __fmul_rn(sqrt_approx(__fsub_rn(ak, __fmul_rn(q.det, __fmul_rn(hi, hi)))), q.ia);
+  const float ml = __fmul_rn(-q.bia, lo), mh = __fmul_rn(-q.bia, hi);
   float xmin, xmax;
-  if (dyL >= lo && dyL <= hi) xmin = -q.ex;
-  else xmin = fminf(__fsub_rn(mid(lo), half(lo)), __fsub_rn(mid(hi), half(hi)));
-  if (-dyL >= lo && -dyL <= hi) xmax = q.ex;
-  else xmax = fmaxf(__fadd_rn(mid(lo), half(lo)), __fadd_rn(mid(hi), half(hi)));
+  if (q.dyL >= lo && q.dyL <= hi) xmin = -q.ex;
+  else xmin = fminf(__fsub_rn(ml, hl), __fsub_rn(mh, hh));
+  if (-q.dyL >= lo && -q.dyL <= hi) xmax = q.ex;
+  else xmax = fmaxf(__fadd_rn(ml, hl), __fadd_rn(mh, hh));
   x0 = max(x0, tiles_lo(__fsub_rn(__fadd_rn(q.ux, xmin), 1e-2f)));
   x1 = min(x1, tiles_hi(__fadd_rn(__fadd_rn(q.ux, xmax), 1e-2f)));
 }

@@ -29,7 +29,8 @@ struct MergeWs {
   float* mquat;            // [n][4]
   float* mlogs;            // [n][3]
   uint32_t* big;           // [n] voxel ids with more than 32 members
-  int32_t* hdr;            // 16 ints: bbox min xyz, max xyz, n_elig, err, n_vox, n_big, n_out
+  uint2* pairs;            // [n/2 + 1] accepted (older, younger) pairs
+  int32_t* hdr;            // 16 ints: bbox min xyz, max xyz, n_elig, err, n_vox, n_big, n_out, n_pairs
   uint32_t* scratch;       // sort / scan scratch
 };
 
@@ -285,8 +286,8 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     const float* __restrict__ means, const T* __restrict__ qs, const T* __restrict__ ls,
     const uint64_t* __restrict__ birth, const uint32_t* __restrict__ perm,
     const uint32_t* __restrict__ starts, const uint32_t* __restrict__ n_vox_p, float chi2, int greedy,
-    int32_t* __restrict__ partner, float* __restrict__ mmean, float* __restrict__ mquat,
-    float* __restrict__ mlogs, uint32_t* __restrict__ big, uint32_t* __restrict__ n_big) {
+    int32_t* __restrict__ partner, uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs,
+    uint32_t* __restrict__ big, uint32_t* __restrict__ n_big) {
   __shared__ float s_d2[4][kWarpVoxel][kWarpVoxel + 1];
   __shared__ int64_t s_idx[4][kWarpVoxel];
   __shared__ uint64_t s_birth[4][kWarpVoxel];
@@ -362,14 +363,14 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     if (!greedy) break;
   }
   __syncwarp();
+  uint32_t slot = 0;
+  if (lane == 0 && np > 0) slot = atomicAdd(n_pairs, (uint32_t)np);
+  slot = __shfl_sync(0xffffffffu, slot, 0);
   if (lane < np) {
     int64_t i = s_idx[wib][s_pairs[wib][lane][0]], j = s_idx[wib][s_pairs[wib][lane][1]];
-    float mk[3], qk[4], lk[3];
-    merge_pair(means, qs, ls, i, j, mk, qk, lk);
     partner[i] = (int32_t)j;
     partner[j] = (int32_t)i;
-    for (int k = 0; k < 3; ++k) { mmean[3 * i + k] = mk[k]; mlogs[3 * i + k] = lk[k]; }
-    for (int k = 0; k < 4; ++k) mquat[4 * i + k] = qk[k];
+    pairs[slot + lane] = make_uint2((uint32_t)i, (uint32_t)j);
   }
 }
 
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
     const uint64_t* __restrict__ birth, const uint32_t* __restrict__ perm,
     const uint32_t* __restrict__ starts, const uint32_t* __restrict__ big,
     const uint32_t* __restrict__ n_big_p, float chi2, int greedy, int32_t* __restrict__ partner,
-    float* __restrict__ mmean, float* __restrict__ mquat, float* __restrict__ mlogs, int32_t* err) {
+    uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs, int32_t* err) {
   __shared__ int64_t s_idx[kBlockVoxel];
   __shared__ uint64_t s_birth[kBlockVoxel];
   __shared__ float s_mu[kBlockVoxel][3];
@@ -453,16 +454,33 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
     __syncthreads();
     if (!greedy) break;
   }
+  __shared__ uint32_t s_slot;
+  if (t == 0) s_slot = s_np ? atomicAdd(n_pairs, (uint32_t)s_np) : 0u;
   __syncthreads();
   for (int k = t; k < s_np; k += kBlockVoxel) {
     int64_t i = s_idx[s_pairs[k][0]], j = s_idx[s_pairs[k][1]];
-    float mk[3], qk[4], lk[3];
-    merge_pair(means, qs, ls, i, j, mk, qk, lk);
     partner[i] = (int32_t)j;
     partner[j] = (int32_t)i;
-    for (int c = 0; c < 3; ++c) { mmean[3 * i + c] = mk[c]; mlogs[3 * i + c] = lk[c]; }
-    for (int c = 0; c < 4; ++c) mquat[4 * i + c] = qk[c];
+    pairs[s_slot + k] = make_uint2((uint32_t)i, (uint32_t)j);
   }
+}
+
+// One thread per accepted pair: Eq. 6 mean and the Eq. 9 barycentre, written in the
+// older Gaussian's slot of the merged-value arrays.
+template <typename T>
+__global__ void __launch_bounds__(128) k_merge_pairs(const float* __restrict__ means, const T* __restrict__ qs,
+                                                     const T* __restrict__ ls, const uint2* __restrict__ pairs,
+                                                     const uint32_t* __restrict__ n_pairs_p,
+                                                     float* __restrict__ mmean, float* __restrict__ mquat,
+                                                     float* __restrict__ mlogs) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (int64_t)*n_pairs_p) return;
+  const uint2 pr = pairs[k];
+  const int64_t i = pr.x, j = pr.y;
+  float mk[3], qk[4], lk[3];
+  merge_pair(means, qs, ls, i, j, mk, qk, lk);
+  for (int c = 0; c < 3; ++c) { mmean[3 * i + c] = mk[c]; mlogs[3 * i + c] = lk[c]; }
+  for (int c = 0; c < 4; ++c) mquat[4 * i + c] = qk[c];
 }
 
 __global__ void k_keep(int64_t n, const int32_t* __restrict__ partner, const uint64_t* __restrict__ birth,
@@ -543,11 +561,15 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
     k_starts<<<ge, 256, 0, s>>>(n_elig, ws.flags, ws.pos, ws.starts, n_vox);
     count_launch(3);  // with the two pairing kernels below
     unsigned gv = (unsigned)div_up(n_elig, 4);
+    uint32_t* n_pairs = (uint32_t*)(ws.hdr + 11);
     k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, qs, ls, in.birth, perm, ws.starts, n_vox, p.chi2,
-                                        p.greedy, partner, ws.mmean, ws.mquat, ws.mlogs, ws.big, n_big);
+                                        p.greedy, partner, ws.pairs, n_pairs, ws.big, n_big);
     k_voxel_pairs_big<T><<<(unsigned)std::max<int64_t>(1, n_elig / 33), kBlockVoxel, 0, s>>>(
         in.means, qs, ls, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
-        ws.mmean, ws.mquat, ws.mlogs, ws.hdr + 7);
+        ws.pairs, n_pairs, ws.hdr + 7);
+    k_merge_pairs<T><<<(unsigned)div_up(n_elig / 2 + 1, 128), 128, 0, s>>>(in.means, qs, ls, ws.pairs, n_pairs,
+                                                                          ws.mmean, ws.mquat, ws.mlogs);
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -591,6 +613,7 @@ size_t merge_workspace_bytes(int64_t n, MergeWs* ws, char* base) {
   w.mquat = (float*)take(16 * m);
   w.mlogs = (float*)take(12 * m);
   w.big = (uint32_t*)take(4 * m);
+  w.pairs = (uint2*)take(8 * (m / 2 + 1));
   w.scratch = (uint32_t*)take(4 * sort_scratch_words(m));
   if (ws) *ws = w;
   return off;

@@ -6,13 +6,19 @@
 // colour/depth sums in registers; the CTA leaves as soon as all its pixels stopped.
 //
 // Reverse: the tile's entries are walked back to front in batches of 32.  In the
-// pixel phase each thread runs the usual back-to-front recursion for its pixel
-// (T recovered by division, colour-behind S accumulated) and writes two numbers per
+// pixel phase each thread runs the back-to-front recursion for its pixel (T recovered
+// by division; of the colour and depth behind each Gaussian only their dot product
+// with the pixel's cotangent is needed, one scalar) and writes two numbers per
 // (pixel, entry) into shared memory: gp = dL/dpower and the blend weight w.  In the
 // Gaussian phase each lane owns one entry and sums, over the 32 pixels of its warp,
 // the ten moments the per-Gaussian chain rule needs; the eight warps' partial sums
 // meet in shared memory and one thread per entry issues three 16-byte vector atomics.
 // There is no per-fragment shuffle or atomic.
+//
+// Both per-fragment loops are branch-free: a Gaussian that fails the alpha test (or
+// comes after the pixel stopped) enters with alpha = 0, which leaves every running
+// quantity unchanged.  A warp then issues one path instead of the union of the
+// contributing and skipping paths of its 32 pixels.
 #include "internal.h"
 
 namespace mgs {
@@ -50,26 +56,28 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
     }
     __syncthreads();
     const int cnt = min(kTilePix, n - b);
-    if (!done) {
-      for (int j = 0; j < cnt; ++j) {
-        float dx, dy;
-        float4 co = s_co[j];
-        float p2 = frag_exp2(s_xy[j], co, pxf, pyf, dx, dy);
-        if (p2 > 0.f) continue;
-        float a = __fmul_rn(co.w, ex2_approx(p2));
-        float al = fminf(kAlphaMax, a);
-        if (al < kAlphaMin) continue;
-        float4 c = s_col[j];
-        float w = __fmul_rn(al, T);
-        C0 = __fmaf_rn(c.x, w, C0);
-        C1 = __fmaf_rn(c.y, w, C1);
-        C2 = __fmaf_rn(c.z, w, C2);
-        D = __fmaf_rn(c.w, w, D);
-        T = __fsub_rn(T, w);
-        last = (uint32_t)(b + j + 1);
-        if (T < kTStop) {
-          done = true;
-          break;
+    for (int j0 = 0; j0 < cnt; j0 += 8) {
+      if (__all_sync(0xffffffffu, done)) break;
+      const int jn = min(8, cnt - j0);
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        if (jj < jn) {
+          const int j = j0 + jj;
+          float dx, dy;
+          const float4 co = s_co[j];
+          const float p2 = frag_exp2(s_xy[j], co, pxf, pyf, dx, dy);
+          const float a = __fmul_rn(co.w, ex2_approx(p2));
+          const float al = fminf(kAlphaMax, a);
+          const bool on = !done && p2 <= 0.f && al >= kAlphaMin;
+          const float4 c = s_col[j];
+          const float w = on ? __fmul_rn(al, T) : 0.f;
+          C0 = __fmaf_rn(c.x, w, C0);
+          C1 = __fmaf_rn(c.y, w, C1);
+          C2 = __fmaf_rn(c.z, w, C2);
+          D = __fmaf_rn(c.w, w, D);
+          T = __fsub_rn(T, w);
+          last = on ? (uint32_t)(b + j + 1) : last;
+          done = done || (on && T < kTStop);
         }
       }
     }
@@ -87,6 +95,7 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
 }
 
 constexpr int kBwdBatch = 32;
+
 constexpr int kBwdStride = kBwdBatch + 1;  // padded row: conflict-free both ways
 constexpr int kBwdWarps = kTilePix / 32;
 constexpr int kMom = 10;
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
   __syncthreads();
   const int L = S.lmax;
   const float gAT = gA * Tf;
-  float S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
+  float sig = 0.f;
   for (int base = ((L - 1) / kBwdBatch) * kBwdBatch; L > 0 && base >= 0; base -= kBwdBatch) {
     const int cnt = min(kBwdBatch, L - base);
     if (t < cnt) {
@@ -154,35 +163,35 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
       S.idx[t] = idx;
     }
     __syncthreads();
-    // pixel phase: back-to-front recursion for this thread's pixel
-    for (int j = kBwdBatch - 1; j >= 0; --j) {
-      float gp = 0.f, w = 0.f;
-      if (j < cnt && (uint32_t)(base + j) < nc) {
-        float dx, dy;
-        float4 co = S.co[j];
-        float p2 = frag_exp2(S.xy[j], co, pxf, pyf, dx, dy);
-        if (p2 <= 0.f) {
-          float a = __fmul_rn(co.w, ex2_approx(p2));
-          float al = fminf(kAlphaMax, a);
-          if (al >= kAlphaMin) {
-            float4 c = S.col[j];
-            float om = 1.f - al;
-            float rom = __fdividef(1.f, om);
-            float Tb = T * rom;
-            w = al * Tb;
-            float e0 = c.x - S0, e1 = c.y - S1, e2 = c.z - S2, eD = c.w - SD;
-            float dLda = Tb * (e0 * gR + e1 * gG + e2 * gB + eD * gD) + gAT * rom;
-            S0 = fmaf(al, e0, S0);
-            S1 = fmaf(al, e1, S1);
-            S2 = fmaf(al, e2, S2);
-            SD = fmaf(al, eD, SD);
-            gp = a <= kAlphaMax ? dLda * a : 0.f;
-            T = Tb;
-          }
+    // pixel phase: branch-free back-to-front recursion; sigma = S . g (colour and depth
+    // behind, dotted with the pixel's cotangent) is all the recursion needs
+    if (__any_sync(0xffffffffu, (uint32_t)base < nc)) {
+      for (int j = kBwdBatch - 1; j >= 0; --j) {
+        if (j < cnt) {
+          float dx, dy;
+          const float4 co = S.co[j];
+          const float p2 = frag_exp2(S.xy[j], co, pxf, pyf, dx, dy);
+          const float a = __fmul_rn(co.w, ex2_approx(p2));
+          const float al = fminf(kAlphaMax, a);
+          const bool on = (uint32_t)(base + j) < nc && p2 <= 0.f && al >= kAlphaMin;
+          const float alc = on ? al : 0.f;
+          const float4 c = S.col[j];
+          const float rom = __fdividef(1.f, 1.f - alc);
+          const float Tb = T * rom;
+          const float cg = fmaf(c.x, gR, fmaf(c.y, gG, fmaf(c.z, gB, c.w * gD)));
+          const float d = cg - sig;
+          const float dLda = fmaf(Tb, d, gAT * rom);
+          sig = fmaf(alc, d, sig);
+          S.u.pix.gp[t][j] = (on && a <= kAlphaMax) ? dLda * a : 0.f;
+          S.u.pix.w[t][j] = alc * Tb;
+          T = Tb;
         }
       }
-      S.u.pix.gp[t][j] = gp;
-      S.u.pix.w[t][j] = w;
+    } else {
+      for (int j = 0; j < cnt; ++j) {
+        S.u.pix.gp[t][j] = 0.f;
+        S.u.pix.w[t][j] = 0.f;
+      }
     }
     __syncthreads();
     // Gaussian phase: lane = entry, warp = 32 pixels (two tile rows)
@@ -238,11 +247,44 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
   }
 }
 
-// Key emission, one warp per 32 consecutive items of the front-to-back order: the
-// warp takes the items one at a time and its lanes write that item's (tile, item)
-// pairs row by row, for the tiles its alpha >= 1/255 ellipse reaches.  An item never
-// writes more than the count the projection pass gave it; any shortfall is padded with
-// the sentinel tile id n_tiles, which sorts last and is ignored by the range build.
+// Key emission over the items in front-to-back order, one thread per item: the
+// thread writes one (global tile id, item) pair per tile its alpha >= 1/255 ellipse
+// reaches (row by row).  Items with more than 32 keys are written cooperatively by
+// the whole warp afterwards.  An item never writes more than the count the projection
+// pass gave it; any shortfall is padded with the sentinel tile id n_tiles, which sorts
+// last and is ignored by the range build.
+__device__ __forceinline__ void emit_item(uint32_t item, uint32_t off, uint32_t cnt, int lane, int stride,
+                                          const uint2* __restrict__ rects, const float4* __restrict__ rec,
+                                          int64_t N, const ViewTable& vt, uint32_t* __restrict__ tkeys,
+                                          uint32_t* __restrict__ tvals) {
+  const int v = (int)((int64_t)item / N);
+  const View& V = vt.v[v];
+  const uint2 rc = rects[item];
+  const Cull q = make_cull(rec[3 * (size_t)item], rec[3 * (size_t)item + 1]);
+  int y0 = rc.x >> 16, y1 = rc.y >> 16;
+  cull_rows(q, y0, y1);
+  uint32_t w = 0;
+  for (int y = y0; y <= y1 && w < cnt; ++y) {
+    int x0 = rc.x & 0xffff, x1 = rc.y & 0xffff;
+    cull_cols(q, y, x0, x1);
+    const int nx = x1 - x0 + 1;
+    for (int dx = lane; dx < nx; dx += stride) {
+      const uint32_t pos = w + (uint32_t)dx;
+      if (pos < cnt) {
+        tkeys[off + pos] = (uint32_t)(V.tile_base + y * V.tiles_x + x0 + dx);
+        tvals[off + pos] = item;
+      }
+    }
+    if (nx > 0) w += (uint32_t)nx;
+  }
+  for (uint32_t pos = w + lane; pos < cnt; pos += stride) {
+    tkeys[off + pos] = (uint32_t)vt.n_tiles;
+    tvals[off + pos] = item;
+  }
+}
+
+constexpr uint32_t kEmitCoop = 32;
+
 __global__ void __launch_bounds__(256) k_emit(int64_t n_vis, int64_t N, const uint32_t* __restrict__ dvals,
                                               const uint32_t* __restrict__ offsets,
                                               const uint32_t* __restrict__ touched,
@@ -250,44 +292,23 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n_vis, int64_t N, const ui
                                               const __grid_constant__ ViewTable vt,
                                               uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals) {
   const int lane = threadIdx.x & 31;
-  const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~int64_t(31);
-  if (first >= n_vis) return;
-  const int64_t k = first + lane;
-  uint32_t my_item = 0, my_off = 0, my_cnt = 0;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((k & ~int64_t(31)) >= n_vis) return;  // whole warp beyond the end
+  uint32_t item = 0, off = 0, cnt = 0;
   if (k < n_vis) {
-    my_item = dvals[k];
-    my_off = offsets[k];
-    my_cnt = touched[my_item];
+    item = dvals[k];
+    off = offsets[k];
+    cnt = touched[item];
   }
-  const int n_here = (int)(n_vis - first < 32 ? n_vis - first : 32);
-  for (int i = 0; i < n_here; ++i) {
-    const uint32_t item = __shfl_sync(0xffffffffu, my_item, i);
-    const uint32_t off = __shfl_sync(0xffffffffu, my_off, i);
-    const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, i);
-    const int v = (int)((int64_t)item / N);
-    const View& V = vt.v[v];
-    const uint2 rc = rects[item];
-    const Cull q = make_cull(rec[3 * (size_t)item], rec[3 * (size_t)item + 1]);
-    int y0 = rc.x >> 16, y1 = rc.y >> 16;
-    cull_rows(q, y0, y1);
-    uint32_t w = 0;
-    for (int y = y0; y <= y1 && w < cnt; ++y) {
-      int x0 = rc.x & 0xffff, x1 = rc.y & 0xffff;
-      cull_cols(q, y, x0, x1);
-      const int nx = x1 - x0 + 1;
-      for (int dx = lane; dx < nx; dx += 32) {
-        uint32_t pos = w + (uint32_t)dx;
-        if (pos < cnt) {
-          tkeys[off + pos] = (uint32_t)(V.tile_base + y * V.tiles_x + x0 + dx);
-          tvals[off + pos] = item;
-        }
-      }
-      if (nx > 0) w += (uint32_t)nx;
-    }
-    for (uint32_t pos = w + lane; pos < cnt; pos += 32) {
-      tkeys[off + pos] = (uint32_t)vt.n_tiles;
-      tvals[off + pos] = item;
-    }
+  if (cnt > 0 && cnt <= kEmitCoop) emit_item(item, off, cnt, 0, 1, rects, rec, N, vt, tkeys, tvals);
+  uint32_t big = __ballot_sync(0xffffffffu, cnt > kEmitCoop);
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    const uint32_t it = __shfl_sync(0xffffffffu, item, src);
+    const uint32_t of = __shfl_sync(0xffffffffu, off, src);
+    const uint32_t cn = __shfl_sync(0xffffffffu, cnt, src);
+    emit_item(it, of, cn, lane, 32, rects, rec, N, vt, tkeys, tvals);
   }
 }
 
