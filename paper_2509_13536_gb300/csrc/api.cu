@@ -319,16 +319,20 @@ mgs_status mgs_render_stats(const mgs_gaussians* g, const mgs_camera* cams, int3
   uint32_t* tv[2] = {at<uint32_t>(workspace, L.tvals[0]), at<uint32_t>(workspace, L.tvals[1])};
   int tcur = radix_passes(0, tile_bits(vt.n_tiles)) & 1;
   auto* hdr = at<unsigned long long>(workspace, L.hdr);
-  MGS_TRY_CUDA(cudaMemsetAsync(hdr + 4, 0, 32, s));
+  MGS_TRY_CUDA(cudaMemsetAsync(hdr + 8, 0, 8 * 8, s));
   MGS_TRY_CUDA(launch_frag_stats(vt, at<float4>(workspace, L.rec), tv[tcur], at<uint2>(workspace, L.ranges),
-                                 hdr + 4, s));
-  unsigned long long h[8];
+                                 hdr + 8, s));
+  unsigned long long h[16];
   MGS_TRY_CUDA(cudaMemcpyAsync(h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s));
   MGS_TRY_CUDA(cudaStreamSynchronize(s));
-  stats[0] = h[4];
-  stats[1] = h[5];
-  stats[2] = h[6];
+  stats[0] = h[8];
+  stats[1] = h[9];
+  stats[2] = h[10];
   stats[3] = h[0];
+  stats[4] = h[11];
+  stats[5] = h[12];
+  stats[6] = h[13];
+  stats[7] = h[14];
   return MGS_OK;
 }
 

@@ -347,15 +347,31 @@ __global__ void __launch_bounds__(kTilePix) k_frag_stats(const __grid_constant__
     ev = ne;
     bw = nc;
   }
+  // padded work: a warp (tile) issues its longest pixel's list for all its lanes (pixels)
+  unsigned long long ev_w = ev, bw_w = bw;
   for (int s = 16; s; s >>= 1) {
     ev += __shfl_xor_sync(0xffffffffu, ev, s);
     co += __shfl_xor_sync(0xffffffffu, co, s);
     bw += __shfl_xor_sync(0xffffffffu, bw, s);
+    ev_w = max(ev_w, __shfl_xor_sync(0xffffffffu, ev_w, s));
+    bw_w = max(bw_w, __shfl_xor_sync(0xffffffffu, bw_w, s));
   }
+  __shared__ unsigned long long s_max[2];
+  if (threadIdx.x == 0) s_max[0] = s_max[1] = 0;
+  __syncthreads();
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&out[0], ev);
     atomicAdd(&out[1], co);
     atomicAdd(&out[2], bw);
+    atomicAdd(&out[5], 32ull * ev_w);
+    atomicAdd(&out[6], 32ull * bw_w);
+    atomicMax(&s_max[0], ev_w);
+    atomicMax(&s_max[1], bw_w);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&out[3], (unsigned long long)kTilePix * s_max[0]);
+    atomicAdd(&out[4], (unsigned long long)kTilePix * s_max[1]);
   }
 }
 

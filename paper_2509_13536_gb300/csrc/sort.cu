@@ -120,67 +120,136 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* in,
 }
 
 // --- radix sort ---
+// Per-block digit histogram of one pass.  Each thread reads 16 consecutive keys with
+// vector loads and counts runs of equal digits in registers; a run costs one atomic
+// on the warp's private shared histogram (keys emitted per Gaussian, and high digits,
+// come in long runs).
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                              int64_t n, int shift, uint32_t mask, int nb,
                                                              uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
+  __shared__ uint32_t h[kWarps][256];
+  const int t = threadIdx.x, w = t >> 5;
+#pragma unroll
+  for (int ww = 0; ww < kWarps; ++ww) h[ww][t] = 0;
   __syncthreads();
-  int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-  for (int i = 0; i < kSortPerThread; ++i) {
-    int64_t k = base + i * kSortThreads + threadIdx.x;
-    uint32_t d = k < n ? (keys[k] >> shift) & mask : 256u;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (d < 256u && (peers & lanemask_lt()) == 0) atomicAdd(&h[d], __popc(peers));
+  const int64_t i0 = (int64_t)blockIdx.x * kSortTile + (int64_t)t * kSortPerThread;
+  uint32_t k[kSortPerThread];
+  if (i0 + kSortPerThread <= n) {
+    const uint4* p = reinterpret_cast<const uint4*>(keys + i0);
+#pragma unroll
+    for (int q = 0; q < kSortPerThread / 4; ++q) {
+      const uint4 v = p[q];
+      k[4 * q] = v.x; k[4 * q + 1] = v.y; k[4 * q + 2] = v.z; k[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kSortPerThread; ++q) k[q] = i0 + q < n ? keys[i0 + q] : 0u;
+  }
+  const int m = (int)(n - i0 < kSortPerThread ? (n - i0 > 0 ? n - i0 : 0) : kSortPerThread);
+  if (m > 0) {
+    uint32_t cur = (k[0] >> shift) & mask, cnt = 1;
+#pragma unroll
+    for (int q = 1; q < kSortPerThread; ++q) {
+      if (q < m) {
+        const uint32_t d = (k[q] >> shift) & mask;
+        if (d == cur) {
+          ++cnt;
+        } else {
+          atomicAdd(&h[w][cur], cnt);
+          cur = d;
+          cnt = 1;
+        }
+      }
+    }
+    atomicAdd(&h[w][cur], cnt);
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+  uint32_t tot = 0;
+#pragma unroll
+  for (int ww = 0; ww < kWarps; ++ww) tot += h[ww][t];
+  hist[(int64_t)t * nb + blockIdx.x] = tot;
 }
 
+// Stable scatter of one pass.  Warp w owns the contiguous items [512 w, 512 w + 512) of
+// the block's 4096 and ranks them round by round (32 at a time) with match masks and
+// warp-local digit counters, so stability needs no block barrier per round.  One
+// block-wide prefix over the warps' counts then gives every item its position in the
+// block's digit-sorted order; items are staged in shared memory in that order and
+// written out as coalesced runs per digit.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
     uint32_t mask, int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout) {
-  __shared__ uint32_t s_wc[2][kWarps][256];
-  __shared__ uint32_t s_run[256];
-  __shared__ uint32_t s_off[256];
-  const int t = threadIdx.x, w = t >> 5;
-  s_off[t] = hist[(int64_t)t * nb + blockIdx.x];
-  s_run[t] = 0;
+  constexpr int kPerWarp = kSortTile / kWarps;  // 512
+  constexpr int kRounds = kPerWarp / 32;        // 16
+  __shared__ uint32_t s_wcnt[kWarps][256];      // per-warp digit counts, then exclusive offsets
+  __shared__ uint32_t s_goff[256];              // global start of (digit, this block)
+  __shared__ uint32_t s_boff[256];              // start of the digit in the block's sorted order
+  __shared__ uint32_t s_key[kSortTile];
+  __shared__ uint32_t s_val[kSortTile];
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const int n_here = (int)(n - base < kSortTile ? n - base : (int64_t)kSortTile);
 #pragma unroll
-  for (int ww = 0; ww < kWarps; ++ww) s_wc[0][ww][t] = 0;
+  for (int ww = 0; ww < kWarps; ++ww) s_wcnt[ww][t] = 0;
+  s_goff[t] = hist[(int64_t)t * nb + blockIdx.x];
   __syncthreads();
-  int64_t base = (int64_t)blockIdx.x * kSortTile;
   const uint32_t lt = lanemask_lt();
-  for (int r = 0; r < kSortPerThread; ++r) {
-    const int b = r & 1;
-    int64_t k = base + r * kSortThreads + t;
-    bool valid = k < n;
-    uint32_t key = valid ? kin[k] : 0u;
-    uint32_t val = valid ? (vin ? vin[k] : (uint32_t)k) : 0u;
-    uint32_t d = valid ? (key >> shift) & mask : 256u;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t rank = __popc(peers & lt);
-    if (valid && rank == 0) s_wc[b][w][d] = __popc(peers);
-    __syncthreads();
-    {
-      uint32_t run = s_run[t];
+  uint32_t key[kRounds], val[kRounds], rank[kRounds];
 #pragma unroll
-      for (int ww = 0; ww < kWarps; ++ww) {
-        uint32_t c = s_wc[b][ww][t];
-        s_wc[b][ww][t] = run;
-        run += c;
-        s_wc[b ^ 1][ww][t] = 0;
-      }
-      s_run[t] = run;
+  for (int r = 0; r < kRounds; ++r) {
+    const int i = w * kPerWarp + r * 32 + lane;
+    const bool valid = i < n_here;
+    key[r] = valid ? kin[base + i] : 0u;
+    val[r] = valid ? (vin ? vin[base + i] : (uint32_t)(base + i)) : 0u;
+    const uint32_t d = valid ? (key[r] >> shift) & mask : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = valid ? s_wcnt[w][d] : 0u;
+    rank[r] = before + __popc(peers & lt);
+    __syncwarp();
+    if (valid && (peers & lt) == 0) s_wcnt[w][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // thread t = digit t: offsets of the warps within the digit, and the digit's block start
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+      const uint32_t c = s_wcnt[ww][t];
+      s_wcnt[ww][t] = run;
+      run += c;
     }
+    // exclusive scan of the per-digit block totals (run) over the 256 digits
+    uint32_t inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    __shared__ uint32_t s_wsum[kWarps];
+    if (lane == 31) s_wsum[w] = inc;
     __syncthreads();
-    if (valid) {
-      uint32_t pos = s_off[d] + s_wc[b][w][d] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+    uint32_t pre = 0;
+    for (int ww = 0; ww < w; ++ww) pre += s_wsum[ww];
+    s_boff[t] = pre + inc - run;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int i = w * kPerWarp + r * 32 + lane;
+    if (i < n_here) {
+      const uint32_t d = (key[r] >> shift) & mask;
+      const uint32_t pos = s_boff[d] + s_wcnt[w][d] + rank[r];
+      s_key[pos] = key[r];
+      s_val[pos] = val[r];
     }
+  }
+  __syncthreads();
+  for (int i = t; i < n_here; i += kSortThreads) {
+    const uint32_t k = s_key[i];
+    const uint32_t d = (k >> shift) & mask;
+    const uint32_t pos = s_goff[d] + (uint32_t)i - s_boff[d];
+    kout[pos] = k;
+    vout[pos] = s_val[i];
   }
 }
 
