@@ -49,6 +49,10 @@ def parse():
     p.add_argument("--cpu-sample", type=float, default=0.5, help="fraction of one view's tiles for the oracle")
     p.add_argument("--views", type=int, default=8, help="keyframes per step (8 = the benchmark workload)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-precision", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=2000)
+    p.add_argument("--serve-rate", type=float, default=200.0)
     return p.parse_args()
 
 
@@ -161,6 +165,136 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our leg
+def precision_leg(args, api, torch, scene, cams, make_step, dev):
+    """The mapping step with FP16 / BF16 attribute storage beside FP32: frames/s, bytes
+    per Gaussian, and accuracy against the FP64 oracle fed the FP32 attributes on a
+    seeded tile sample of keyframe 0 (PSNR, max-abs on unflagged pixels, gradient
+    relative error per parameter group with the cotangent confined to those tiles)."""
+    from oracle import oracle
+    cam = cams[0]
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    rng = np.random.default_rng(7)
+    tiles = np.sort(rng.choice(tx * ty, 48, replace=False)).astype(np.int32)
+    mask = np.zeros((cam.height, cam.width), bool)
+    for t in tiles:
+        y, x = divmod(int(t), tx)
+        mask[y * 16:y * 16 + 16, x * 16:x * 16 + 16] = True
+    crng = np.random.default_rng(8)
+    cot = [(crng.uniform(-1, 1, (3, cam.height, cam.width)) * mask).astype(np.float32),
+           (crng.uniform(-1, 1, (cam.height, cam.width)) * mask).astype(np.float32),
+           (crng.uniform(-1, 1, (cam.height, cam.width)) * mask).astype(np.float32)]
+    ref = oracle.render(scene, cam, tiles=tiles)
+    ref_g = oracle.render_backward(scene, cam, *cot, tiles=tiles)
+    ok = mask & (ref["flags"] == 0)
+    out = {}
+    modes = (("f32", torch.float32, torch.float32), ("f16", torch.float16, torch.float32),
+             ("bf16", torch.bfloat16, torch.float32), ("f16_all", torch.float16, torch.float16),
+             ("bf16_all", torch.bfloat16, torch.bfloat16))
+    for name, dt, gdt in modes:
+        g = api.Gaussians.from_scene(scene, dev, dt, gdt)
+        imgs, wsp = api.render(g, [cam])
+        dL = [api.Image(*(torch.from_numpy(x).to(dev) for x in cot))]
+        grads = api.render_backward(g, [cam], dL, wsp)
+        torch.cuda.synchronize()
+        rgb = imgs[0].rgb.cpu().numpy().astype(np.float64)
+        mse = float(np.mean((rgb - ref["rgb"])[:, mask] ** 2))
+        maxabs = float(np.abs(rgb - ref["rgb"])[:, ok].max())
+        rel = {}
+        keep = ref_g["taint"] == 0
+        for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+            a = getattr(grads, k).cpu().numpy().astype(np.float64)[keep]
+            b = ref_g[k][keep]
+            rel[k] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+        del imgs, wsp, grads
+        step, st = make_step(g)
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        k_steps = max(2, args.steps // 2)
+        for _ in range(k_steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k_steps
+        out[name] = {"frames_per_s": len(cams) / (ms / 1e3), "ms_per_step": ms,
+                     "bytes_per_gaussian": sum(t[0].numel() * t.element_size() for t in g.params()),
+                     "psnr_db_vs_fp64_oracle": 10 * np.log10(1.0 / max(mse, 1e-30)),
+                     "max_abs_unflagged": maxabs, "grad_rel_err_max": max(rel.values()), "grad_rel_err": rel}
+        del g, step, st
+        torch.cuda.empty_cache()
+    out["sample"] = f"keyframe 0, {len(tiles)} seeded tiles ({int(mask.sum())} px); oracle fed the FP32 attributes"
+    out["modes"] = ("f16/bf16: opacity and SH stored reduced, means/log-scales/quaternions f32; "
+                    "*_all: log-scales and quaternions reduced too")
+    return out
+
+
+SERVE_RES = [(320, 240), (640, 480), (1200, 680), (1920, 1080)]
+
+
+def serving_leg(args, api, torch, sg, dev):
+    """Render serving: 4 resident maps (0.5M, 1M, 2M, 3M Gaussians, SH3, FP16 storage),
+    Poisson arrivals at 200 req/s, each request a random map, pose and resolution.  The
+    continuous-batching server is compared with the same trace served one request at a
+    time from plain FP32 maps.  Latency = arrival -> image ready."""
+    import threading
+    sizes = [500_000, 1_000_000, 2_000_000, 3_000_000]
+    scenes = [sg.room_scene(n, 40 + i, sh_degree=3) for i, n in enumerate(sizes)]
+    rng = np.random.default_rng(4)
+    n_req = args.serve_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, n_req))
+    reqs = []
+    for i in range(n_req):
+        w, h = SERVE_RES[rng.integers(len(SERVE_RES))]
+        reqs.append((int(rng.integers(len(sizes))), sg.room_poses(1, int(rng.integers(1 << 30)), w, h)[0]))
+    ring = {r: [api.new_images([sg.box_camera(*r)], dev)[0] for _ in range(16)] for r in SERVE_RES}
+    warm = min(200, n_req // 10)
+
+    def run(dtype, slots, batch, arena_gb):
+        maps = [api.Gaussians.from_scene(sc, dev, dtype) for sc in scenes]
+        server = api.Server(int(arena_gb * (1 << 30)), n_slots=slots, max_batch_views=batch, device=dev)
+        ids = [server.add_scene(g) for g in maps]
+        got = {}
+        stop = [False]
+
+        def collect():
+            while not stop[0] or len(got) < n_req:
+                for tag, ts, ta, td, st in server.poll(256, wait_s=0.05):
+                    got[tag] = (ts, ta, td, st)
+                if stop[0] and len(got) >= n_req:
+                    break
+
+        th = threading.Thread(target=collect, daemon=True)
+        th.start()
+        t0 = server.clock() + 0.2
+        for i, (sid, cam) in enumerate(reqs):
+            target = t0 + float(arrivals[i])
+            d = target - server.clock()
+            if d > 0:
+                time.sleep(d)
+            key = (cam.width, cam.height)
+            server.submit(ids[sid], cam, ring[key][i % 16], i, target)
+        stop[0] = True
+        th.join(timeout=600)
+        server.close()
+        lat = np.array([got[i][2] - got[i][0] for i in range(warm, n_req) if i in got and got[i][3] == 0])
+        t_first = t0 + float(arrivals[warm])
+        t_last = max(got[i][2] for i in range(warm, n_req) if i in got)
+        res = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+               "frames_per_s": len(lat) / (t_last - t_first), "completed": int(len(lat)),
+               "failed": int(sum(1 for i in range(warm, n_req) if i in got and got[i][3] != 0))}
+        del maps
+        torch.cuda.empty_cache()
+        return res
+
+    served = run(torch.float16, 8, 8, 24)
+    sequential = run(torch.float32, 1, 1, 8)
+    return {"requests": n_req, "warmup_requests": warm, "rate_per_s": args.serve_rate,
+            "maps": "0.5M/1M/2M/3M Gaussians, SH3", "resolutions": [f"{w}x{h}" for w, h in SERVE_RES],
+            "continuous_batching_fp16": served, "one_at_a_time_fp32": sequential}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -190,36 +324,44 @@ def run_ours(args):
     pert = scene.copy()
     pert.means += rng.normal(0, 0.005, pert.means.shape).astype(np.float32)
     pert.sh += rng.normal(0, 0.02, pert.sh.shape).astype(np.float32)
-    g = api.Gaussians.from_scene(pert, dev)
-    grads = api.Grads.zeros_like(g)
-    m = api.Grads.zeros_like(g, stats=False)
-    v = api.Grads.zeros_like(g, stats=False)
-    rgb = torch.empty(V, 3, H, W, device=dev)
-    depth = torch.empty(V, H, W, device=dev)
-    alpha = torch.empty(V, H, W, device=dev)
-    out = [api.Image(rgb[i], depth[i], alpha[i]) for i in range(V)]
-    g_rgb = torch.empty_like(rgb)
-    g_depth = torch.empty_like(depth)
-    dL = [api.Image(g_rgb[i], g_depth[i], None) for i in range(V)]
-    loss = torch.zeros(1, device=dev)
-    merged = g.empty_like()
-    partner = torch.empty(g.n, dtype=torch.int32, device=dev)
-    vox = torch.empty(g.n, 3, dtype=torch.int32, device=dev)
-    mws = torch.empty(api.load().mgs_voxel_merge_workspace_size(g.n), dtype=torch.uint8, device=dev)
-    s_rgb = 1.0 / rgb.numel()
-    s_depth = 0.1 / depth.numel()
-    state = {"step": 0, "n_out": g.n}
+    def make_step(g):
+        """One mapping step on map g (all buffers allocated here, none inside the step)."""
+        grads = api.Grads.zeros_like(g)
+        m = api.Grads.zeros_like(g, stats=False)
+        v = api.Grads.zeros_like(g, stats=False)
+        rgb = torch.empty(V, 3, H, W, device=dev)
+        depth = torch.empty(V, H, W, device=dev)
+        alpha = torch.empty(V, H, W, device=dev)
+        out = [api.Image(rgb[i], depth[i], alpha[i]) for i in range(V)]
+        g_rgb = torch.empty_like(rgb)
+        g_depth = torch.empty_like(depth)
+        dL = [api.Image(g_rgb[i], g_depth[i], None) for i in range(V)]
+        loss = torch.zeros(1, device=dev)
+        merged = g.empty_like()
+        partner = torch.empty(g.n, dtype=torch.int32, device=dev)
+        vox = torch.empty(g.n, 3, dtype=torch.int32, device=dev)
+        mws = torch.empty(api.load().mgs_voxel_merge_workspace_size(g.n), dtype=torch.uint8, device=dev)
+        ws = api.RenderWorkspace(dev)
+        s_rgb = 1.0 / rgb.numel()
+        s_depth = 0.1 / depth.numel()
+        state = {"step": 0, "n_out": g.n, "ws": ws, "loss": loss}
 
-    def step():
-        state["step"] += 1
-        api.mgs_render(g, cams, out, ws)
-        loss.zero_()
-        api.mgs_l1_loss_grad(rgb, target_rgb, s_rgb, g_rgb, loss)
-        api.mgs_l1_loss_grad(depth, target_depth, s_depth, g_depth, loss)
-        api.mgs_render_backward(g, cams, dL, ws, grads)
-        api.mgs_adam_step(g, grads, m, v, 1e-3, 0.9, 0.999, 1e-8, state["step"], zero_grads=True)
-        res, _, _ = api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox)
-        state["n_out"] = res.n
+        def step():
+            state["step"] += 1
+            api.mgs_render(g, cams, out, ws)
+            loss.zero_()
+            api.mgs_l1_loss_grad(rgb, target_rgb, s_rgb, g_rgb, loss)
+            api.mgs_l1_loss_grad(depth, target_depth, s_depth, g_depth, loss)
+            api.mgs_render_backward(g, cams, dL, ws, grads)
+            api.mgs_adam_step(g, grads, m, v, 1e-3, 0.9, 0.999, 1e-8, state["step"], zero_grads=True)
+            res, _, _ = api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox)
+            state["n_out"] = res.n
+
+        return step, state
+
+    g = api.Gaussians.from_scene(pert, dev)
+    step, state = make_step(g)
+    ws, loss = state["ws"], state["loss"]
 
     def barrier():
         if world > 1:
@@ -307,6 +449,13 @@ def run_ours(args):
         roofline = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                     "traffic": None}
 
+    precision = None
+    if world == 1 and not args.no_precision:
+        precision = precision_leg(args, api, torch, pert, cams, make_step, dev)
+    serving = None
+    if world == 1 and not args.no_serving:
+        serving = serving_leg(args, api, torch, sg, dev)
+
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -318,6 +467,10 @@ def run_ours(args):
                                           "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "clocks": csum, "kernels": kern, "fragments": stats,
             "merge_survivors": state["n_out"]}
+    if precision:
+        line["precision"] = precision
+    if serving:
+        line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, frac, threads = oracle_sample(args.cpu_sample)
         line["cpu_baseline"] = {"value": frac / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",

@@ -18,12 +18,14 @@
  *     no device trap crosses the ABI.
  *   - Layouts are dense, row-major, structure-of-arrays:
  *       means          f32 [n][3]  world frame
- *       log_scales     attr[n][3]  scale = exp(log_scale)
- *       quats          attr[n][4]  (w, x, y, z), need not be unit (normalised inside)
+ *       log_scales     geom[n][3]  scale = exp(log_scale)
+ *       quats          geom[n][4]  (w, x, y, z), need not be unit (normalised inside)
  *       opacity_logit  attr[n]     opacity = sigmoid(logit)
  *       sh             attr[n][K][3], K = (sh_degree+1)^2, real orthonormal SH basis
  *       birth          u64 [n]     insertion stamp, smaller = older (merge only)
- *     where attr is f32, f16 or bf16 (mgs_dtype); arithmetic is always f32.
+ *     where geom and attr are each f32, f16 or bf16 (mgs_dtype); arithmetic is always
+ *     f32.  Reduced-precision maps normally keep geom in f32: quantising the covariance
+ *     parameters moves gradients by ~1e-2 relative, the appearance ones by <= 3.4e-3.
  *   - Camera: world->camera rotation R (row-major) and translation t; x right,
  *     y down, z forward; pixel (u, v) is evaluated at the point (u, v).
  */
@@ -53,7 +55,9 @@ typedef enum { MGS_F32 = 0, MGS_F16 = 1, MGS_BF16 = 2 } mgs_dtype;
 typedef struct {
   int64_t n;
   int32_t sh_degree;   /* 0..3 */
-  int32_t attr_dtype;  /* mgs_dtype of log_scales, quats, opacity_logit, sh */
+  int32_t attr_dtype;  /* mgs_dtype of opacity_logit and sh */
+  int32_t geom_dtype;  /* mgs_dtype of log_scales and quats */
+  int32_t reserved;
   const float* means;
   const void* log_scales;
   const void* quats;
@@ -66,6 +70,8 @@ typedef struct {
   int64_t n;           /* capacity on input; unused on output (see n_out_host) */
   int32_t sh_degree;
   int32_t attr_dtype;
+  int32_t geom_dtype;
+  int32_t reserved;
   float* means;
   void* log_scales;
   void* quats;
@@ -174,7 +180,7 @@ typedef struct {
 
 size_t mgs_voxel_merge_workspace_size(int64_t n);
 
-/* out: capacity >= in->n, same sh_degree and attr_dtype.  partner (optional, [n]):
+/* out: capacity >= in->n, same sh_degree, attr_dtype and geom_dtype.  partner (optional, [n]):
  * index of the merge partner or -1.  voxel (optional, i32 [n][3]): voxel coordinates
  * of eligible Gaussians (INT32_MIN for ineligible ones).  Synchronises `stream` and
  * writes the survivor count to *n_out_host.  Voxel coordinates must fit in 21 bits
@@ -190,7 +196,7 @@ mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_
  * library's choice).  m and v are f32 state arrays shaped like the parameters
  * (same mgs_gaussians_mut layout, f32 pointers in m_state / v_state), 16-byte
  * aligned like the parameter and gradient arrays.  Parameters
- * stored in f16/bf16 are updated in f32 and rounded back.  step >= 1.  zero_grads = 1
+ * stored in f16/bf16 (either group) are updated in f32 and rounded back.  step >= 1.  zero_grads = 1
  * clears each gradient element after it is consumed (the next backward pass
  * accumulates from zero without a separate clearing pass).  Asynchronous.
  * ------------------------------------------------------------------------------ */
@@ -213,6 +219,42 @@ size_t mgs_sort_workspace_size(int64_t n);
 mgs_status mgs_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* vals_out, int64_t n,
                           int32_t begin_bit, int32_t end_bit, void* workspace,
                           size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Render serving with continuous batching (not in the paper: the serving form of the
+ * Sec. II-E rasteriser).  Resident scene maps are registered once; requests (scene,
+ * camera, output planes) are submitted at any time.  A dispatcher thread admits the
+ * oldest pending request when a worker slot is free and its workspace fits in free
+ * memory of the caller's device arena (first-fit; the server allocates no device
+ * memory), folding every pending request of the same scene into the same multi-view
+ * mgs_render launch (up to max_batch_views).  Each slot has its own stream and
+ * thread, so batches overlap on the device.  Results are bit-identical to rendering
+ * each request alone (the forward pass is deterministic).  The gaussians and output
+ * buffers must stay valid until the request completes; destroying the server drops
+ * requests not yet admitted.
+ * ------------------------------------------------------------------------------ */
+typedef struct mgs_server mgs_server;
+typedef struct {
+  int32_t n_slots;          /* concurrent batches (1..64) */
+  int32_t max_batch_views;  /* 1..MGS_MAX_VIEWS */
+  int32_t device;           /* CUDA device ordinal */
+  int32_t reserved;
+  void* arena;              /* caller-owned device memory for workspaces */
+  size_t arena_bytes;
+} mgs_server_config;
+
+mgs_status mgs_server_create(const mgs_server_config* cfg, mgs_server** out_host);
+mgs_status mgs_server_add_scene(mgs_server* s, const mgs_gaussians* g, int32_t* scene_id_host);
+/* t_submit: arrival time on mgs_server_clock() (<= 0: now); tag: caller's request id. */
+mgs_status mgs_server_submit(mgs_server* s, int32_t scene_id, const mgs_camera* cam_host,
+                             const mgs_image* out_host, int64_t tag, double t_submit);
+/* Completed requests (up to max; waits up to wait_s seconds for the first one):
+ * arrival, admission and completion times in seconds, and the mgs_status of each. */
+int32_t mgs_server_poll(mgs_server* s, int32_t max, int64_t* tags_host, double* t_submit_host,
+                        double* t_start_host, double* t_done_host, int32_t* status_host,
+                        double wait_s);
+double mgs_server_clock(void);
+mgs_status mgs_server_destroy(mgs_server* s);
 
 /* ------------------------------------------------------------------------------
  * Diagnostics (not part of the method).

@@ -22,12 +22,13 @@ EXPORTS = ["mgs_render_workspace_size", "mgs_render", "mgs_render_backward", "mg
            "mgs_voxel_merge_workspace_size", "mgs_voxel_merge", "mgs_adam_step", "mgs_l1_loss_grad",
            "mgs_sort_workspace_size", "mgs_sort_pairs", "mgs_last_error", "mgs_version",
            "mgs_launch_count", "mgs_profile_enable", "mgs_profile_read", "mgs_render_stats",
-           "mgs_sort_pairs_noalloc"]
+           "mgs_sort_pairs_noalloc", "mgs_server_create", "mgs_server_add_scene", "mgs_server_submit",
+           "mgs_server_poll", "mgs_server_clock", "mgs_server_destroy"]
 
 
 class mgs_gaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("attr_dtype", C.c_int32),
-                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("geom_dtype", C.c_int32), ("reserved", C.c_int32), ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("birth", C.c_void_p)]
 
 
@@ -47,6 +48,11 @@ class mgs_image(C.Structure):
 class mgs_grads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logit", "sh",
                                           "grad_stat", "vis_count")]
+
+
+class mgs_server_config(C.Structure):
+    _fields_ = [("n_slots", C.c_int32), ("max_batch_views", C.c_int32), ("device", C.c_int32),
+                ("reserved", C.c_int32), ("arena", C.c_void_p), ("arena_bytes", C.c_size_t)]
 
 
 class mgs_merge_params(C.Structure):
@@ -93,6 +99,12 @@ def load():
             "mgs_sort_workspace_size": (SZ, [I64]),
             "mgs_sort_pairs": (C.c_int, [P, P, P, I64, I32, I32, P, SZ, P]),
             "mgs_sort_pairs_noalloc": (C.c_int, [P, P, P, I64, I32, I32, P]),
+            "mgs_server_create": (C.c_int, [P, P]),
+            "mgs_server_add_scene": (C.c_int, [P, P, P]),
+            "mgs_server_submit": (C.c_int, [P, I32, P, P, I64, C.c_double]),
+            "mgs_server_poll": (I32, [P, I32, P, P, P, P, P, C.c_double]),
+            "mgs_server_clock": (C.c_double, []),
+            "mgs_server_destroy": (C.c_int, [P]),
             "mgs_launch_count": (C.c_uint64, []),
             "mgs_profile_enable": (None, [I32]),
             "mgs_profile_read": (I32, [I32, P, P, P]),

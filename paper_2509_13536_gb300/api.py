@@ -54,15 +54,23 @@ class Gaussians:
 
     @property
     def attr_dtype(self) -> torch.dtype:
+        """Storage type of the appearance group (opacity logit, SH)."""
+        return self.sh.dtype
+
+    @property
+    def geom_dtype(self) -> torch.dtype:
+        """Storage type of the geometry group (log-scales, quaternions)."""
         return self.log_scales.dtype
 
     @staticmethod
-    def from_scene(scene, device="cuda", attr_dtype=torch.float32) -> "Gaussians":
+    def from_scene(scene, device="cuda", attr_dtype=torch.float32, geom_dtype=torch.float32) -> "Gaussians":
+        """Upload a scene; opacity/SH stored as attr_dtype, log-scales/quaternions as
+        geom_dtype (means are always f32)."""
         d = torch.device(device)
-        f = lambda a, dt=attr_dtype: torch.from_numpy(np.ascontiguousarray(a)).to(d).to(dt).contiguous()
-        return Gaussians(f(scene.means, torch.float32), f(scene.log_scales), f(scene.quats),
-                         f(scene.opacity_logit), f(scene.sh),
-                         torch.from_numpy(scene.birth.astype(np.int64)).to(d))
+        f = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(d).to(dt).contiguous()
+        return Gaussians(f(scene.means, torch.float32), f(scene.log_scales, geom_dtype),
+                         f(scene.quats, geom_dtype), f(scene.opacity_logit, attr_dtype),
+                         f(scene.sh, attr_dtype), torch.from_numpy(scene.birth.astype(np.int64)).to(d))
 
     def params(self):
         return [self.means, self.log_scales, self.quats, self.opacity_logit, self.sh]
@@ -70,11 +78,10 @@ class Gaussians:
     def struct(self) -> _abi.mgs_gaussians:
         if self.means.dtype != torch.float32:
             raise ValueError("means must be float32")
-        dt = self.log_scales.dtype
-        for t in (self.quats, self.opacity_logit, self.sh):
-            if t.dtype != dt:
-                raise ValueError("log_scales, quats, opacity_logit and sh must share one dtype")
-        return _abi.mgs_gaussians(self.n, self.sh_degree, _DTYPES[dt], _ptr(self.means),
+        if self.quats.dtype != self.log_scales.dtype or self.opacity_logit.dtype != self.sh.dtype:
+            raise ValueError("log_scales/quats and opacity_logit/sh must each share one dtype")
+        return _abi.mgs_gaussians(self.n, self.sh_degree, _DTYPES[self.sh.dtype], _DTYPES[self.log_scales.dtype],
+                                  0, _ptr(self.means),
                                   _ptr(self.log_scales), _ptr(self.quats), _ptr(self.opacity_logit),
                                   _ptr(self.sh), _ptr(self.birth))
 
@@ -386,3 +393,58 @@ def render_views(g: Gaussians, cams, ws: Optional[RenderWorkspace] = None):
     """Differentiable render of same-resolution views: returns (rgb, depth, alpha) tensors."""
     ws = ws or RenderWorkspace(g.means.device)
     return RenderFn.apply(g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, cams, ws)
+
+
+class Server:
+    """Continuous-batching render server (mgs_server_*): resident scenes, asynchronous
+    requests, admission by free memory of a device arena owned by this object."""
+
+    def __init__(self, arena_bytes: int, n_slots: int = 8, max_batch_views: int = 8, device=None):
+        self.device = torch.device(device or "cuda")
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
+        cfg = _abi.mgs_server_config(n_slots, max_batch_views, self.device.index or 0, 0,
+                                     _ptr(self.arena), int(arena_bytes))
+        self.h = C.c_void_p()
+        check(load().mgs_server_create(C.byref(cfg), C.byref(self.h)), "mgs_server_create")
+        self.scenes = []
+        self.keep = {}
+
+    def add_scene(self, g: Gaussians) -> int:
+        sid = C.c_int32(0)
+        check(load().mgs_server_add_scene(self.h, C.byref(g.struct()), C.byref(sid)), "mgs_server_add_scene")
+        self.scenes.append(g)
+        return sid.value
+
+    def submit(self, scene_id: int, cam, out: Image, tag: int, t_submit: float = 0.0):
+        c = camera_struct(cam)
+        im = _abi.mgs_image(_ptr(out.rgb), _ptr(out.depth), _ptr(out.alpha))
+        self.keep[tag] = out
+        check(load().mgs_server_submit(self.h, scene_id, C.byref(c), C.byref(im), tag, t_submit),
+              "mgs_server_submit")
+
+    def poll(self, max_n: int = 256, wait_s: float = 0.0):
+        """[(tag, t_submit, t_start, t_done, status)] of completed requests."""
+        tags = (C.c_int64 * max_n)()
+        ts, t0, t1 = (C.c_double * max_n)(), (C.c_double * max_n)(), (C.c_double * max_n)()
+        st = (C.c_int32 * max_n)()
+        n = load().mgs_server_poll(self.h, max_n, tags, ts, t0, t1, st, wait_s)
+        res = []
+        for i in range(n):
+            self.keep.pop(tags[i], None)
+            res.append((tags[i], ts[i], t0[i], t1[i], st[i]))
+        return res
+
+    @staticmethod
+    def clock() -> float:
+        return float(load().mgs_server_clock())
+
+    def close(self):
+        if self.h:
+            load().mgs_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -69,6 +69,33 @@ __device__ __forceinline__ void st(float* p, float x) { *p = x; }
 __device__ __forceinline__ void st(__half* p, float x) { *p = __float2half_rn(x); }
 __device__ __forceinline__ void st(__nv_bfloat16* p, float x) { *p = __float2bfloat16_rn(x); }
 
+// Geometry group of a map (log-scales, quaternions) with its runtime storage type.
+struct Geom {
+  const void* ls;
+  const void* qs;
+  int dt;
+};
+
+// runtime-typed access for the small geometry groups (log-scales, quaternions)
+__device__ __forceinline__ float ld_dt(const void* p, int dt, int64_t i) {
+  switch (dt) {
+    case MGS_F16: return __half2float(static_cast<const __half*>(p)[i]);
+    case MGS_BF16: return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+    default: return __ldg(static_cast<const float*>(p) + i);
+  }
+}
+__device__ __forceinline__ void st_dt(void* p, int dt, int64_t i, float x) {
+  switch (dt) {
+    case MGS_F16: static_cast<__half*>(p)[i] = __float2half_rn(x); break;
+    case MGS_BF16: static_cast<__nv_bfloat16*>(p)[i] = __float2bfloat16_rn(x); break;
+    default: static_cast<float*>(p)[i] = x; break;
+  }
+}
+__device__ __forceinline__ void cp_dt(void* dst, const void* src, int dt, int64_t i, int64_t j) {
+  if (dt == MGS_F32) static_cast<float*>(dst)[i] = static_cast<const float*>(src)[j];
+  else static_cast<uint16_t*>(dst)[i] = static_cast<const uint16_t*>(src)[j];
+}
+
 // --- error-free transformations (double-float arithmetic in f32) ---
 struct DF {
   float hi, lo;

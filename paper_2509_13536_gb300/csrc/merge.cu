@@ -44,12 +44,11 @@ __device__ __forceinline__ bool older(uint64_t ba, int64_t a, uint64_t bb, int64
   return ba < bb || (ba == bb && a < b);
 }
 
-template <typename T>
-__device__ __forceinline__ void load_qs(const T* qs, const T* ls, int64_t i, float q[4], float s[3]) {
-  for (int k = 0; k < 4; ++k) q[k] = ld(qs + 4 * i + k);
+__device__ __forceinline__ void load_qs(const Geom& geo, int64_t i, float q[4], float s[3]) {
+  for (int k = 0; k < 4; ++k) q[k] = ld_dt(geo.qs, geo.dt, 4 * i + k);
   float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   for (int k = 0; k < 4; ++k) q[k] *= n;
-  for (int k = 0; k < 3; ++k) s[k] = expf(ld(ls + 3 * i + k));
+  for (int k = 0; k < 3; ++k) s[k] = expf(ld_dt(geo.ls, geo.dt, 3 * i + k));
 }
 
 // R diag(d) R^T as 6 unique entries xx xy xz yy yz zz
@@ -62,10 +61,9 @@ __device__ __forceinline__ void rdrt(const float R[9], const float d[3], float o
   o[5] = R[6] * R[6] * d[0] + R[7] * R[7] * d[1] + R[8] * R[8] * d[2];
 }
 
-template <typename T>
-__device__ __forceinline__ void precision_of(const T* qs, const T* ls, int64_t i, float P[6]) {
+__device__ __forceinline__ void precision_of(const Geom& geo, int64_t i, float P[6]) {
   float q[4], s[3], R[9];
-  load_qs(qs, ls, i, q, s);
+  load_qs(geo, i, q, s);
   quat_rot(q, R);
   float d[3] = {1.f / (s[0] * s[0]), 1.f / (s[1] * s[1]), 1.f / (s[2] * s[2])};
   rdrt(R, d, P);
@@ -134,12 +132,11 @@ __device__ void rot_quat(const float R[9], float q[4]) {
 
 // Merge of G_i (older) and G_j: Eq. 6 mean and the closed-form minimiser of Eq. 9,
 // computed in the eigenbasis of Sigma_i where Sigma_i = diag(si^2).
-template <typename T>
-__device__ void merge_pair(const float* means, const T* qs, const T* ls, int64_t i, int64_t j,
+__device__ void merge_pair(const float* means, const Geom& geo, int64_t i, int64_t j,
                            float mk[3], float qk[4], float lk[3]) {
   float qi[4], si[3], qj[4], sj[3], Ri[9], Rj[9];
-  load_qs(qs, ls, i, qi, si);
-  load_qs(qs, ls, j, qj, sj);
+  load_qs(geo, i, qi, si);
+  load_qs(geo, j, qj, sj);
   quat_rot(qi, Ri);
   quat_rot(qj, Rj);
   // Sigma_j in the basis of R_i: Bj = Ri^T Rj diag(sj^2) Rj^T Ri
@@ -283,7 +280,7 @@ struct PairCand {
 // Warp path: a voxel with 2..32 members.
 template <typename T>
 __global__ void __launch_bounds__(128) k_voxel_pairs(
-    const float* __restrict__ means, const T* __restrict__ qs, const T* __restrict__ ls,
+    const float* __restrict__ means, const Geom geo,
     const uint64_t* __restrict__ birth, const uint32_t* __restrict__ perm,
     const uint32_t* __restrict__ starts, const uint32_t* __restrict__ n_vox_p, float chi2, int greedy,
     int32_t* __restrict__ partner, uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs,
@@ -316,7 +313,7 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
   if (lane < nm) {
     int64_t ia = s_idx[wib][lane];
     float P[6];
-    precision_of(qs, ls, ia, P);
+    precision_of(geo, ia, P);
     const float* ma = means + 3 * ia;
     float mav[3] = {ma[0], ma[1], ma[2]};
     for (int b = lane + 1; b < nm; ++b) {
@@ -377,7 +374,7 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
 // Block path: a voxel with 33..256 members; d2 evaluated on the fly each round.
 template <typename T>
 __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
-    const float* __restrict__ means, const T* __restrict__ qs, const T* __restrict__ ls,
+    const float* __restrict__ means, const Geom geo,
     const uint64_t* __restrict__ birth, const uint32_t* __restrict__ perm,
     const uint32_t* __restrict__ starts, const uint32_t* __restrict__ big,
     const uint32_t* __restrict__ n_big_p, float chi2, int greedy, int32_t* __restrict__ partner,
@@ -414,7 +411,7 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
     s_birth[rank] = mb;
     s_match[rank] = 0;
     for (int k = 0; k < 3; ++k) s_mu[rank][k] = means[3 * my + k];
-    precision_of(qs, ls, my, s_P[rank]);
+    precision_of(geo, my, s_P[rank]);
   }
   if (t == 0) s_np = 0;
   __syncthreads();
@@ -468,8 +465,8 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
 // One thread per accepted pair: Eq. 6 mean and the Eq. 9 barycentre, written in the
 // older Gaussian's slot of the merged-value arrays.
 template <typename T>
-__global__ void __launch_bounds__(128) k_merge_pairs(const float* __restrict__ means, const T* __restrict__ qs,
-                                                     const T* __restrict__ ls, const uint2* __restrict__ pairs,
+__global__ void __launch_bounds__(128) k_merge_pairs(const float* __restrict__ means, const Geom geo,
+                                                     const uint2* __restrict__ pairs,
                                                      const uint32_t* __restrict__ n_pairs_p,
                                                      float* __restrict__ mmean, float* __restrict__ mquat,
                                                      float* __restrict__ mlogs) {
@@ -478,7 +475,7 @@ __global__ void __launch_bounds__(128) k_merge_pairs(const float* __restrict__ m
   const uint2 pr = pairs[k];
   const int64_t i = pr.x, j = pr.y;
   float mk[3], qk[4], lk[3];
-  merge_pair(means, qs, ls, i, j, mk, qk, lk);
+  merge_pair(means, geo, i, j, mk, qk, lk);
   for (int c = 0; c < 3; ++c) { mmean[3 * i + c] = mk[c]; mlogs[3 * i + c] = lk[c]; }
   for (int c = 0; c < 4; ++c) mquat[4 * i + c] = qk[c];
 }
@@ -492,22 +489,22 @@ __global__ void k_keep(int64_t n, const int32_t* __restrict__ partner, const uin
 }
 
 template <typename T>
-__global__ void k_compact(int64_t n, int K3, const float* __restrict__ means, const T* __restrict__ ls,
-                          const T* __restrict__ qs, const T* __restrict__ ol, const T* __restrict__ sh,
+__global__ void k_compact(int64_t n, int K3, const float* __restrict__ means, const Geom geo,
+                          const T* __restrict__ ol, const T* __restrict__ sh,
                           const uint64_t* __restrict__ birth, const uint32_t* __restrict__ keep,
                           const uint32_t* __restrict__ pos, const int32_t* __restrict__ partner,
                           const float* __restrict__ mmean, const float* __restrict__ mquat,
-                          const float* __restrict__ mlogs, float* omeans, T* ols, T* oqs, T* ool,
+                          const float* __restrict__ mlogs, float* omeans, void* ols, void* oqs, T* ool,
                           T* osh, uint64_t* obirth) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || !keep[i]) return;
   int64_t w = pos[i];
   if (partner[i] >= 0) {
-    for (int k = 0; k < 3; ++k) { omeans[3 * w + k] = mmean[3 * i + k]; st(ols + 3 * w + k, mlogs[3 * i + k]); }
-    for (int k = 0; k < 4; ++k) st(oqs + 4 * w + k, mquat[4 * i + k]);
+    for (int k = 0; k < 3; ++k) { omeans[3 * w + k] = mmean[3 * i + k]; st_dt(ols, geo.dt, 3 * w + k, mlogs[3 * i + k]); }
+    for (int k = 0; k < 4; ++k) st_dt(oqs, geo.dt, 4 * w + k, mquat[4 * i + k]);
   } else {
-    for (int k = 0; k < 3; ++k) { omeans[3 * w + k] = means[3 * i + k]; ols[3 * w + k] = ls[3 * i + k]; }
-    for (int k = 0; k < 4; ++k) oqs[4 * w + k] = qs[4 * i + k];
+    for (int k = 0; k < 3; ++k) { omeans[3 * w + k] = means[3 * i + k]; cp_dt(ols, geo.ls, geo.dt, 3 * w + k, 3 * i + k); }
+    for (int k = 0; k < 4; ++k) cp_dt(oqs, geo.qs, geo.dt, 4 * w + k, 4 * i + k);
   }
   ool[w] = ol[i];
   for (int k = 0; k < K3; ++k) osh[(int64_t)K3 * w + k] = sh[(int64_t)K3 * i + k];
@@ -519,8 +516,7 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
                     const mgs_gaussians_mut& out, int32_t* partner_out, int32_t* vox_out,
                     int64_t* n_out_host, MergeWs& ws, cudaStream_t s, int* unsupported) {
   const int64_t n = in.n;
-  const T* ls = (const T*)in.log_scales;
-  const T* qs = (const T*)in.quats;
+  const Geom geo{in.log_scales, in.quats, in.geom_dtype};
   const T* ol = (const T*)in.opacity_logit;
   const T* sh = (const T*)in.sh;
   const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
@@ -562,12 +558,12 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
     count_launch(3);  // with the two pairing kernels below
     unsigned gv = (unsigned)div_up(n_elig, 4);
     uint32_t* n_pairs = (uint32_t*)(ws.hdr + 11);
-    k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, qs, ls, in.birth, perm, ws.starts, n_vox, p.chi2,
+    k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, geo, in.birth, perm, ws.starts, n_vox, p.chi2,
                                         p.greedy, partner, ws.pairs, n_pairs, ws.big, n_big);
     k_voxel_pairs_big<T><<<(unsigned)std::max<int64_t>(1, n_elig / 33), kBlockVoxel, 0, s>>>(
-        in.means, qs, ls, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
+        in.means, geo, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
         ws.pairs, n_pairs, ws.hdr + 7);
-    k_merge_pairs<T><<<(unsigned)div_up(n_elig / 2 + 1, 128), 128, 0, s>>>(in.means, qs, ls, ws.pairs, n_pairs,
+    k_merge_pairs<T><<<(unsigned)div_up(n_elig / 2 + 1, 128), 128, 0, s>>>(in.means, geo, ws.pairs, n_pairs,
                                                                           ws.mmean, ws.mquat, ws.mlogs);
     count_launch();
     e = cudaGetLastError();
@@ -578,9 +574,9 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
   uint32_t* n_out_dev = (uint32_t*)(ws.hdr + 10);
   e = scan_exclusive_u32(ws.flags, nullptr, ws.pos, n, ws.scratch, n_out_dev, s);
   if (e != cudaSuccess) return e;
-  k_compact<T><<<grid, 256, 0, s>>>(n, K3, in.means, ls, qs, ol, sh, in.birth, ws.flags, ws.pos, partner,
-                                    ws.mmean, ws.mquat, ws.mlogs, out.means, (T*)out.log_scales,
-                                    (T*)out.quats, (T*)out.opacity_logit, (T*)out.sh, out.birth);
+  k_compact<T><<<grid, 256, 0, s>>>(n, K3, in.means, geo, ol, sh, in.birth, ws.flags, ws.pos, partner,
+                                    ws.mmean, ws.mquat, ws.mlogs, out.means, out.log_scales,
+                                    out.quats, (T*)out.opacity_logit, (T*)out.sh, out.birth);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, s);

@@ -16,22 +16,25 @@ struct GaussPre {
   float Rq[9];
   float s[3];
   float S3[6];  // xx xy xz yy yz zz
+  float RS[9];  // Rq diag(s): Sigma = RS RS^T
   float o;
 };
 
 template <typename T>
-__device__ __forceinline__ void load_gauss(int64_t g, const float* means, const T* ls, const T* qs,
-                                           const T* ol, GaussPre& G) {
+__device__ __forceinline__ void load_gauss(int64_t g, const float* means, const Geom& geo, const T* ol,
+                                           GaussPre& G) {
   for (int k = 0; k < 3; ++k) G.mu[k] = __ldg(means + 3 * g + k);
   float q[4];
-  for (int k = 0; k < 4; ++k) q[k] = ld(qs + 4 * g + k);
+  for (int k = 0; k < 4; ++k) q[k] = ld_dt(geo.qs, geo.dt, 4 * g + k);
   G.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   float inv = 1.f / G.qnorm;
   for (int k = 0; k < 4; ++k) G.qn[k] = q[k] * inv;
   quat_rot(G.qn, G.Rq);
-  for (int k = 0; k < 3; ++k) G.s[k] = expf(ld(ls + 3 * g + k));
+  for (int k = 0; k < 3; ++k) G.s[k] = expf(ld_dt(geo.ls, geo.dt, 3 * g + k));
   float s2[3] = {G.s[0] * G.s[0], G.s[1] * G.s[1], G.s[2] * G.s[2]};
   const float* R = G.Rq;
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) G.RS[3 * a + k] = R[3 * a + k] * G.s[k];
   G.S3[0] = R[0] * R[0] * s2[0] + R[1] * R[1] * s2[1] + R[2] * R[2] * s2[2];
   G.S3[1] = R[0] * R[3] * s2[0] + R[1] * R[4] * s2[1] + R[2] * R[5] * s2[2];
   G.S3[2] = R[0] * R[6] * s2[0] + R[1] * R[7] * s2[1] + R[2] * R[8] * s2[2];
@@ -90,18 +93,25 @@ __device__ __forceinline__ void view_geom(const GaussPre& G, const View& V, View
     P.T[c] = J00 * W[c] + J02 * W[6 + c];
     P.T[3 + c] = J11 * W[3 + c] + J12 * W[6 + c];
   }
-  const float* S = G.S3;
-  float M0[3], M1[3];  // T S3
-  M0[0] = P.T[0] * S[0] + P.T[1] * S[1] + P.T[2] * S[2];
-  M0[1] = P.T[0] * S[1] + P.T[1] * S[3] + P.T[2] * S[4];
-  M0[2] = P.T[0] * S[2] + P.T[1] * S[4] + P.T[2] * S[5];
-  M1[0] = P.T[3] * S[0] + P.T[4] * S[1] + P.T[5] * S[2];
-  M1[1] = P.T[3] * S[1] + P.T[4] * S[3] + P.T[5] * S[4];
-  M1[2] = P.T[3] * S[2] + P.T[4] * S[4] + P.T[5] * S[5];
-  P.a = M0[0] * P.T[0] + M0[1] * P.T[1] + M0[2] * P.T[2] + kDilation;
-  P.b = M0[0] * P.T[3] + M0[1] * P.T[4] + M0[2] * P.T[5];
-  P.c = M1[0] * P.T[3] + M1[1] * P.T[4] + M1[2] * P.T[5] + kDilation;
-  float det = P.a * P.c - P.b * P.b;
+  // Sigma_I = T Sigma T^T + 0.3 I with Sigma = RS RS^T, formed as M M^T, M = T RS:
+  // the diagonal entries are sums of squares and det(M M^T) a sum of squared 2x2 minors
+  // (Cauchy-Binet), so neither cancels when the Gaussian is long along the view ray.
+  const float* RS = G.RS;
+  float M0[3], M1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    M0[k] = P.T[0] * RS[k] + P.T[1] * RS[3 + k] + P.T[2] * RS[6 + k];
+    M1[k] = P.T[3] * RS[k] + P.T[4] * RS[3 + k] + P.T[5] * RS[6 + k];
+  }
+  float aa = M0[0] * M0[0] + M0[1] * M0[1] + M0[2] * M0[2];
+  float cc = M1[0] * M1[0] + M1[1] * M1[1] + M1[2] * M1[2];
+  P.b = M0[0] * M1[0] + M0[1] * M1[1] + M0[2] * M1[2];
+  P.a = aa + kDilation;
+  P.c = cc + kDilation;
+  float m01 = M0[0] * M1[1] - M0[1] * M1[0];
+  float m02 = M0[0] * M1[2] - M0[2] * M1[0];
+  float m12 = M0[1] * M1[2] - M0[2] * M1[1];
+  float det = (m01 * m01 + m02 * m02 + m12 * m12) + kDilation * (aa + cc) + kDilation * kDilation;
   P.ok = det > 0.f;
   if (!P.ok) return;
   float idet = 1.f / det;
@@ -116,9 +126,8 @@ __device__ __forceinline__ void view_geom(const GaussPre& G, const View& V, View
 
 // Tile rect of the square of half-width r around the centre (inclusive bounds).
 __device__ __forceinline__ bool tile_rect(const ViewGeom& P, const View& V, int& r, int rc[4]) {
-  float mid = 0.5f * (P.a + P.c);
-  float det = P.a * P.c - P.b * P.b;
-  float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+  float mid = 0.5f * (P.a + P.c), hd = 0.5f * (P.a - P.c);
+  float lam = mid + sqrtf(fmaxf(0.1f, hd * hd + P.b * P.b));  // mid^2 - det, without cancellation
   r = (int)ceilf(3.f * sqrtf(lam));
   float rf = (float)r;
   float fx0 = floorf(__fsub_rn(P.u_hi, rf) * 0.0625f), fx1 = floorf(__fadd_rn(P.u_hi, rf) * 0.0625f);
@@ -146,7 +155,7 @@ __device__ __forceinline__ void colour(const float* c, const float dir[3], float
 
 template <int DEG, typename T>
 __global__ void __launch_bounds__(256) k_preprocess(int64_t N, const float* __restrict__ means,
-                                                    const T* __restrict__ ls, const T* __restrict__ qs,
+                                                    const Geom geo,
                                                     const T* __restrict__ ol, const T* __restrict__ sh,
                                                     const __grid_constant__ ViewTable vt,
                                                     float4* __restrict__ rec, uint2* __restrict__ rects,
@@ -158,7 +167,7 @@ __global__ void __launch_bounds__(256) k_preprocess(int64_t N, const float* __re
   unsigned int my_vis = 0;
   if (g < N) {
     GaussPre G;
-    load_gauss(g, means, ls, qs, ol, G);
+    load_gauss(g, means, geo, ol, G);
     constexpr int K3 = (DEG + 1) * (DEG + 1) * 3;
     float c[K3];
     load_sh<DEG>(g, sh, c);
@@ -201,7 +210,7 @@ __global__ void __launch_bounds__(256) k_preprocess(int64_t N, const float* __re
 
 template <int DEG, typename T>
 __global__ void __launch_bounds__(256) k_project_one(int64_t N, const float* __restrict__ means,
-                                                     const T* __restrict__ ls, const T* __restrict__ qs,
+                                                     const Geom geo,
                                                      const T* __restrict__ ol, const T* __restrict__ sh,
                                                      const __grid_constant__ View V, float* mean2d,
                                                      float* conic, float* rgb, float* depth,
@@ -209,7 +218,7 @@ __global__ void __launch_bounds__(256) k_project_one(int64_t N, const float* __r
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   GaussPre G;
-  load_gauss(g, means, ls, qs, ol, G);
+  load_gauss(g, means, geo, ol, G);
   ViewGeom P;
   view_geom(G, V, P);
   int r = 0, rc[4] = {0, 0, -1, -1};
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(256) k_project_one(int64_t N, const float* __r
 // with gp = dL/dpower, w the blend weight and (dx, dy) = centre - pixel.
 template <int DEG, typename T>
 __global__ void __launch_bounds__(128) k_preprocess_bwd(int64_t N, const float* __restrict__ means,
-                                                        const T* __restrict__ ls, const T* __restrict__ qs,
+                                                        const Geom geo,
                                                         const T* __restrict__ ol, const T* __restrict__ sh,
                                                         const __grid_constant__ ViewTable vt,
                                                         const float4* __restrict__ moments,
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(int64_t N, const float* 
   if (g >= N) return;
   constexpr int K = (DEG + 1) * (DEG + 1);
   GaussPre G;
-  load_gauss(g, means, ls, qs, ol, G);
+  load_gauss(g, means, geo, ol, G);
   float c[3 * K];
   load_sh<DEG>(g, sh, c);
   float dmu[3] = {0.f, 0.f, 0.f}, dS3[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dop = 0.f;
@@ -397,15 +406,14 @@ cudaError_t launch_pre_t(int deg, int64_t N, const mgs_gaussians& g, const ViewT
                          float4* rec, uint2* rects, uint32_t* touched, uint32_t* dkeys,
                          unsigned long long* counters, cudaStream_t s) {
   unsigned grid = (unsigned)div_up(N, 256);
-  const T* ls = (const T*)g.log_scales;
-  const T* qs = (const T*)g.quats;
+  const Geom geo{g.log_scales, g.quats, g.geom_dtype};
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
-    case 0: k_preprocess<0, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
-    case 1: k_preprocess<1, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
-    case 2: k_preprocess<2, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
-    default: k_preprocess<3, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
+    case 0: k_preprocess<0, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
+    case 1: k_preprocess<1, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
+    case 2: k_preprocess<2, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
+    default: k_preprocess<3, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
   }
   count_launch();
   return cudaGetLastError();
@@ -416,15 +424,14 @@ cudaError_t launch_bwd_t(int deg, int64_t N, const mgs_gaussians& g, const ViewT
                          const float4* moments, const uint32_t* touched, const uint2* rects,
                          const mgs_grads& gr, cudaStream_t s) {
   unsigned grid = (unsigned)div_up(N, 128);
-  const T* ls = (const T*)g.log_scales;
-  const T* qs = (const T*)g.quats;
+  const Geom geo{g.log_scales, g.quats, g.geom_dtype};
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
-    case 0: k_preprocess_bwd<0, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, rects, gr); break;
-    case 1: k_preprocess_bwd<1, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, rects, gr); break;
-    case 2: k_preprocess_bwd<2, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, rects, gr); break;
-    default: k_preprocess_bwd<3, T><<<grid, 128, 0, s>>>(N, g.means, ls, qs, ol, sh, vt, moments, touched, rects, gr); break;
+    case 0: k_preprocess_bwd<0, T><<<grid, 128, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, touched, rects, gr); break;
+    case 1: k_preprocess_bwd<1, T><<<grid, 128, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, touched, rects, gr); break;
+    case 2: k_preprocess_bwd<2, T><<<grid, 128, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, touched, rects, gr); break;
+    default: k_preprocess_bwd<3, T><<<grid, 128, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, touched, rects, gr); break;
   }
   count_launch();
   return cudaGetLastError();
@@ -435,15 +442,14 @@ cudaError_t launch_proj_t(int deg, int64_t N, const mgs_gaussians& g, const View
                           float* conic, float* rgb, float* depth, int32_t* radius, int32_t* rect,
                           cudaStream_t s) {
   unsigned grid = (unsigned)div_up(N, 256);
-  const T* ls = (const T*)g.log_scales;
-  const T* qs = (const T*)g.quats;
+  const Geom geo{g.log_scales, g.quats, g.geom_dtype};
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
-    case 0: k_project_one<0, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
-    case 1: k_project_one<1, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
-    case 2: k_project_one<2, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
-    default: k_project_one<3, T><<<grid, 256, 0, s>>>(N, g.means, ls, qs, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
+    case 0: k_project_one<0, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
+    case 1: k_project_one<1, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
+    case 2: k_project_one<2, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
+    default: k_project_one<3, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, V, mean2d, conic, rgb, depth, radius, rect); break;
   }
   count_launch();
   return cudaGetLastError();

@@ -36,7 +36,7 @@ def test_binding_covers_the_header(lib):
 
 def test_struct_sizes_match_header(lib):
     from paper_2509_13536_gb300 import _abi
-    assert C.sizeof(_abi.mgs_gaussians) == 64
+    assert C.sizeof(_abi.mgs_gaussians) == 72
     assert C.sizeof(_abi.mgs_camera) == 80
     assert C.sizeof(_abi.mgs_image) == 24
     assert C.sizeof(_abi.mgs_grads) == 56
@@ -60,7 +60,7 @@ def test_host_only_queries(lib):
 
 def test_invalid_arguments_are_rejected_before_any_launch(lib):
     from paper_2509_13536_gb300 import _abi
-    g = _abi.mgs_gaussians(10, 7, 0, None, None, None, None, None, None)  # bad degree
+    g = _abi.mgs_gaussians(10, 7, 0, 0, 0, None, None, None, None, None, None)  # bad degree
     cam = (_abi.mgs_camera * 1)()
     st = lib.mgs_render(C.byref(g), cam, 1, None, None, 0, None, None)
     assert st == _abi.MGS_ERR_INVALID
@@ -68,7 +68,7 @@ def test_invalid_arguments_are_rejected_before_any_launch(lib):
     st = lib.mgs_sort_pairs(None, None, None, 10, 5, 3, None, 0, None)
     assert st == _abi.MGS_ERR_INVALID
     p = _abi.mgs_merge_params(7.815, 1e-3, 0, 0, None, None, 1, 0)
-    g2 = _abi.mgs_gaussians(10, 0, 0, 1, 1, 1, 1, 1, None)  # no birth
+    g2 = _abi.mgs_gaussians(10, 0, 0, 0, 0, 1, 1, 1, 1, 1, None)  # no birth
     st = lib.mgs_voxel_merge(C.byref(g2), 0.02, C.byref(p), None, None, None, None, None, 0, None)
     assert st == _abi.MGS_ERR_INVALID
 
