@@ -223,6 +223,7 @@ struct Proj {
   bool clampx, clampy;
   double J[6], T[6], cov[3], det, conic[3];
   double u, v, lam, r3;
+  double cond = 1;  // conditioning of the exponent's evaluation (see orc_margins)
   int r = 0;
   int rect[4] = {0, 0, -1, -1};
   double o;
@@ -297,6 +298,15 @@ void project_one(const orc_gaussians* g, const orc_camera* cam, const orc_margin
   P.v = cam->fy * ty / tz + cam->cy;
   double mid = 0.5 * (P.cov[0] + P.cov[2]);
   P.lam = mid + std::sqrt(std::max(0.1, mid * mid - P.det));
+  {
+    double tn = 0, sn = 0;
+    for (int k = 0; k < 6; ++k) tn += P.T[k] * P.T[k];
+    for (int k = 0; k < 9; ++k) sn += P.S3[k] * P.S3[k];
+    double disc = std::sqrt(0.25 * (P.cov[0] - P.cov[2]) * (P.cov[0] - P.cov[2]) + P.cov[1] * P.cov[1]);
+    double lmin = mid - disc, kappa = (mid + disc) / lmin;
+    double gamma = (tn * std::sqrt(sn) + P.cov[0] + P.cov[2]) / lmin;
+    P.cond = std::sqrt(gamma * kappa) + kappa;
+  }
   P.r3 = 3.0 * std::sqrt(P.lam);
   P.r = (int)std::ceil(P.r3);
   rect_of(P.u, P.v, P.r, cam, P.rect);
@@ -449,13 +459,15 @@ void blend_pixel(const std::vector<Proj>& P, const std::vector<Entry>& list, int
                  const orc_margins* mg, bool keep, PixelResult& R) {
   int pos = 0;  // index among the included entries (the CUDA list position)
   double prev_tz = -1;
+  double t_var = 0;  // sum of squared relative alpha margins, weighted by alpha/(1-alpha)
   for (size_t k = 0; k < list.size(); ++k) {
     const Entry& e = list[k];
     const Proj& p = P[e.g];
     double dx, dy, power = power_at(p, px, py, &dx, &dy);
     double a = p.o * std::exp(power);
     double alpha = std::min(kAlphaMax, a);
-    bool potential = power <= 0 && alpha >= kAlphaMin * (1 - (mg ? mg->alpha_rel : 0));
+    double ma = mg ? mg->alpha_rel + mg->cond_rel * p.cond * std::fabs(power) : 0;
+    bool potential = power <= 0 && alpha >= kAlphaMin * (1 - ma);
     if (keep && potential) R.touched.push_back(e.g);
     if (mg && e.uncertain && potential) R.flags |= 8;
     if (!e.included) continue;
@@ -467,8 +479,8 @@ void blend_pixel(const std::vector<Proj>& P, const std::vector<Entry>& list, int
       prev_tz = p.p[2];
     }
     if (power > 0) continue;
-    if (mg && std::fabs(alpha * 255.0 - 1.0) < mg->alpha_rel) R.flags |= 1;
-    if (mg && std::fabs(a - kAlphaMax) < mg->clamp_rel * kAlphaMax) R.flags |= 16;
+    if (mg && std::fabs(alpha * 255.0 - 1.0) < ma) R.flags |= 1;
+    if (mg && std::fabs(a - kAlphaMax) < (mg->clamp_rel + ma) * kAlphaMax) R.flags |= 16;
     if (alpha < kAlphaMin) continue;
     double w = alpha * R.T;
     if (keep) R.contrib.push_back(Contribution{e.g, alpha, a, std::exp(power), R.T, dx, dy});
@@ -476,7 +488,11 @@ void blend_pixel(const std::vector<Proj>& P, const std::vector<Entry>& list, int
     R.depth += p.p[2] * w;
     R.T = R.T * (1 - alpha);
     R.n_contrib = pos;
-    if (mg && std::fabs(R.T / kTStop - 1) < mg->T_rel) R.flags |= 2;
+    if (mg) {
+      double e = alpha / (1 - alpha) * ma;
+      t_var += e * e;
+      if (std::fabs(R.T / kTStop - 1) < mg->T_rel + std::sqrt(t_var)) R.flags |= 2;
+    }
     if (R.T < kTStop) {
       R.n_eval = pos;
       return;

@@ -60,6 +60,14 @@ typedef struct {
   double radius_abs;  /* distance of 3*sqrt(lambda_max) to an integer */
   double near_rel;    /* |tz - near| / near */
   double clamp_rel;   /* |o*G - 0.99| / 0.99 (gradient switch) */
+  double cond_rel;    /* added to alpha_rel per unit of |exponent| x conditioning c of the
+                         projection: c = sqrt(gamma kappa) + kappa, kappa = lambda_max /
+                         lambda_min of Sigma_I, gamma = (||T||_F^2 ||Sigma||_F + tr Sigma_I)
+                         / lambda_min, T = J W.  Rounding the rotation, the scales and T
+                         to float32 moves the exponent by up to ~c units of 2^-24 relative
+                         (most for Gaussians long along the view ray); evaluating it moves
+                         it by ~kappa.  The T margin grows by the root-sum-square of
+                         alpha/(1-alpha) x the alpha margins so far. */
 } orc_margins;
 
 /* Per-Gaussian projection (Eq. 1-2, plus the tiling extent). */

@@ -21,9 +21,15 @@ LIB = os.path.join(BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-# Margins below which a discrete decision counts as a near-tie; see orc_margins.
-DEFAULT_MARGINS = dict(alpha_rel=2e-5, T_rel=2e-5, depth_rel=1e-12, extent_px=2e-3,
-                       radius_abs=2e-4, near_rel=1e-5, clamp_rel=1e-5)
+# Margins below which a discrete decision counts as a near-tie; see orc_margins.  The
+# float32 kernels' exponent is off by up to ~(sqrt(gamma kappa) + kappa) units of 2^-24
+# relative, in the worst direction (measured for the projection: median 0.6, 99.9th
+# percentile 6.9, largest 10.6 x sqrt(gamma kappa)), so cond_rel is 8 x 2^-24; ex2
+# and the opacity add ~1e-6 (alpha_rel); T is a product of float32 factors (T_rel
+# plus the accumulated alpha margins); the extent margins exceed the error of the
+# float32 centre (~1e-4 px) and of 3 sqrt(lambda_max).
+DEFAULT_MARGINS = dict(alpha_rel=2e-6, T_rel=5e-6, depth_rel=1e-12, extent_px=2e-3,
+                       radius_abs=2e-4, near_rel=1e-5, clamp_rel=1e-5, cond_rel=8 * 2.0 ** -24)
 
 
 def build(force: bool = False) -> str:
@@ -55,7 +61,7 @@ class Gaussians(C.Structure):
 
 class Margins(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("alpha_rel", "T_rel", "depth_rel", "extent_px",
-                                          "radius_abs", "near_rel", "clamp_rel")]
+                                          "radius_abs", "near_rel", "clamp_rel", "cond_rel")]
 
 
 class Projection(C.Structure):
