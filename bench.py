@@ -42,11 +42,12 @@ BWD_FLOP_EVAL, BWD_FLOP_CONTRIB = 10, 47
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample", type=float, default=0.5, help="fraction of one view's tiles for the oracle")
+    p.add_argument("--cpu-sample", type=float, default=1.0, help="fraction of each sampled view's tiles for the oracle")
+    p.add_argument("--cpu-views", type=int, default=4, help="keyframes the oracle baseline renders")
     p.add_argument("--views", type=int, default=8, help="keyframes per step (8 = the benchmark workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-precision", action="store_true")
@@ -61,7 +62,7 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -75,7 +76,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.index), "-lms", "100"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -120,25 +121,30 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle leg
-def oracle_sample(frac, seed=0):
-    """Oracle render + backward of one keyframe of the workload on a seeded tile sample;
-    returns (seconds, sampled fraction of the view, threads used)."""
+def oracle_sample(frac, views=1, seed=0):
+    """Oracle render + backward of the first ``views`` keyframes of the workload, each on
+    a seeded sample of ``frac`` of its tiles; returns (seconds, keyframes' worth of
+    tiles processed, threads used)."""
     from oracle import oracle
     from paper_2509_13536_gb300 import scenegen as sg
     scene, cams = sg.workload(WORKLOAD)
-    cam = cams[0]
-    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
-    rng = np.random.default_rng(seed)
-    n_t = max(1, int(round(frac * tx * ty)))
-    tiles = np.sort(rng.choice(tx * ty, n_t, replace=False)).astype(np.int32)
-    gr, gd, ga = (x[0] for x in sg.image_cotangents(1, cam.width, cam.height, seed))
     threads = os.cpu_count() or 1
     oracle.build()
+    rng = np.random.default_rng(seed)
+    jobs, done = [], 0.0
+    for v, cam in enumerate(cams[:views]):
+        tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+        n_t = max(1, int(round(frac * tx * ty)))
+        tiles = np.sort(rng.choice(tx * ty, n_t, replace=False)).astype(np.int32)
+        gr, gd, ga = (x[0] for x in sg.image_cotangents(1, cam.width, cam.height, seed + v))
+        jobs.append((cam, tiles, gr, gd, ga))
+        done += n_t / (tx * ty)
     t0 = time.perf_counter()
-    oracle.render(scene, cam, tiles=tiles, n_threads=threads)
-    oracle.render_backward(scene, cam, gr, gd, ga, tiles=tiles, n_threads=threads)
+    for cam, tiles, gr, gd, ga in jobs:
+        oracle.render(scene, cam, tiles=tiles, n_threads=threads)
+        oracle.render_backward(scene, cam, gr, gd, ga, tiles=tiles, n_threads=threads)
     dt = time.perf_counter() - t0
-    return dt, n_t / (tx * ty), threads
+    return dt, done, threads
 
 
 def run_reference(args):
@@ -147,7 +153,7 @@ def run_reference(args):
         return
     times = []
     for i in range(args.warmup + args.steps):
-        dt, frac, threads = oracle_sample(min(args.cpu_sample, 0.02), seed=i)
+        dt, frac, threads = oracle_sample(min(args.cpu_sample, 0.02), 1, seed=i)
         if i >= args.warmup:
             times.append(dt)
     per_step = sum(times) / len(times)
@@ -472,10 +478,12 @@ def run_ours(args):
     if serving:
         line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, frac, threads = oracle_sample(args.cpu_sample)
+        nv = max(1, min(args.cpu_views, V))
+        dt, frac, threads = oracle_sample(args.cpu_sample, nv)
         line["cpu_baseline"] = {"value": frac / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",
-                                "sample": f"FP64 oracle render+backward of {frac:.1%} of the tiles of keyframe 0 "
-                                          f"(projection and binning of all 1M Gaussians included), {dt:.1f} s"}
+                                "sample": f"FP64 oracle render+backward of keyframes 0-{nv - 1}, "
+                                          f"{args.cpu_sample:.0%} of each one's tiles (projection and binning "
+                                          f"of all 1M Gaussians included per keyframe), {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -94,21 +94,21 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
   }
 }
 
-constexpr int kBwdBatch = 32;
-
+// Backward blend (reverse of Eq. 11).  A batch of kBwdBatch entries is walked back to
+// front by every pixel (pixel phase), which leaves per (pixel, entry) the two scalars
+// the Gaussian needs: gp = dL/dalpha * alpha (zero where the clamp or a cutoff holds)
+// and w = alpha T (the weight of its colour and depth).  They go through shared memory
+// transposed, and in the Gaussian phase each half-warp sums one tile row of them per
+// entry into the ten moments the chain rule of Eq. 1-2 needs.
+constexpr int kBwdBatch = 16;
 constexpr int kBwdStride = kBwdBatch + 1;  // padded row: conflict-free both ways
 constexpr int kBwdWarps = kTilePix / 32;
 constexpr int kMom = 10;
 
 struct BwdSmem {
-  union {
-    struct {
-      float gp[kTilePix][kBwdStride];
-      float w[kTilePix][kBwdStride];
-    } pix;
-    float red[kBwdWarps][kMom][32];
-  } u;
-  float4 g[kTilePix];       // per pixel dL/d(r, g, b, depth)
+  float2 gw[kTilePix][kBwdStride];          // (gp, w) per pixel and entry
+  float red[kBwdWarps][kMom][kBwdBatch];    // per-warp partial moments
+  float4 g[kTilePix];                       // per pixel dL/d(r, g, b, depth)
   float2 xy[kBwdBatch];
   float4 co[kBwdBatch];
   float4 col[kBwdBatch];
@@ -116,11 +116,11 @@ struct BwdSmem {
   int lmax;
 };
 
-__global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ ViewTable vt,
-                                                        const float4* __restrict__ rec,
-                                                        const uint32_t* __restrict__ vals,
-                                                        const uint2* __restrict__ ranges,
-                                                        float4* __restrict__ moments) {
+__global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant__ ViewTable vt,
+                                                           const float4* __restrict__ rec,
+                                                           const uint32_t* __restrict__ vals,
+                                                           const uint2* __restrict__ ranges,
+                                                           float4* __restrict__ moments) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
   const int tile = blockIdx.x;
@@ -152,6 +152,9 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
   const int L = S.lmax;
   const float gAT = gA * Tf;
   float sig = 0.f;
+  // Gaussian-phase lane roles: entry e of the batch, tile row 2 warp + half
+  const int e = lane & (kBwdBatch - 1), half = lane >> 4;
+  const int prow = warp * 32 + half * kTile;
   for (int base = ((L - 1) / kBwdBatch) * kBwdBatch; L > 0 && base >= 0; base -= kBwdBatch) {
     const int cnt = min(kBwdBatch, L - base);
     if (t < cnt) {
@@ -165,7 +168,10 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
     __syncthreads();
     // pixel phase: branch-free back-to-front recursion; sigma = S . g (colour and depth
     // behind, dotted with the pixel's cotangent) is all the recursion needs
+    bool act = false;
     if (__any_sync(0xffffffffu, (uint32_t)base < nc)) {
+      const int lim = (int)nc - base;
+#pragma unroll
       for (int j = kBwdBatch - 1; j >= 0; --j) {
         if (j < cnt) {
           float dx, dy;
@@ -173,7 +179,8 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
           const float p2 = frag_exp2(S.xy[j], co, pxf, pyf, dx, dy);
           const float a = __fmul_rn(co.w, ex2_approx(p2));
           const float al = fminf(kAlphaMax, a);
-          const bool on = (uint32_t)(base + j) < nc && p2 <= 0.f && al >= kAlphaMin;
+          const bool on = j < lim && p2 <= 0.f && al >= kAlphaMin;
+          act |= on;
           const float alc = on ? al : 0.f;
           const float4 c = S.col[j];
           const float rom = __fdividef(1.f, 1.f - alc);
@@ -182,47 +189,55 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
           const float d = cg - sig;
           const float dLda = fmaf(Tb, d, gAT * rom);
           sig = fmaf(alc, d, sig);
-          S.u.pix.gp[t][j] = (on && a <= kAlphaMax) ? dLda * a : 0.f;
-          S.u.pix.w[t][j] = alc * Tb;
+          S.gw[t][j] = make_float2((on && a <= kAlphaMax) ? dLda * a : 0.f, alc * Tb);
           T = Tb;
         }
       }
-    } else {
-      for (int j = 0; j < cnt; ++j) {
-        S.u.pix.gp[t][j] = 0.f;
-        S.u.pix.w[t][j] = 0.f;
-      }
     }
-    __syncthreads();
-    // Gaussian phase: lane = entry, warp = 32 pixels (two tile rows)
+    // Gaussian phase for the 32 pixels this warp just walked (skipped when none of
+    // them took a contribution from the batch): per row sums of gp, k gp, k^2 gp with
+    // k the column offset from the tile centre, then the moments about the centre of
+    // the Gaussian (dx = xy.x - 7.5 - k, dy constant along the row).
+    __syncwarp();  // this warp's gw rows are written by its own lanes
     float m[kMom];
 #pragma unroll
     for (int k = 0; k < kMom; ++k) m[k] = 0.f;
-    if (lane < cnt) {
-      const float2 xy = S.xy[lane];
-#pragma unroll 4
-      for (int k = 0; k < 32; ++k) {
-        const int p = warp * 32 + k;
-        float gp = S.u.pix.gp[p][lane], w = S.u.pix.w[p][lane];
-        float dx = __fsub_rn(xy.x, (float)(p & (kTile - 1)));
-        float dy = __fsub_rn(xy.y, (float)(p / kTile));
-        float4 gg = S.g[p];
-        float gdx = gp * dx, gdy = gp * dy;
-        m[0] += gp;
-        m[1] += gdx;
-        m[2] += gdy;
-        m[3] = fmaf(gdx, dx, m[3]);
-        m[4] = fmaf(gdx, dy, m[4]);
-        m[5] = fmaf(gdy, dy, m[5]);
-        m[6] = fmaf(w, gg.x, m[6]);
-        m[7] = fmaf(w, gg.y, m[7]);
-        m[8] = fmaf(w, gg.z, m[8]);
-        m[9] = fmaf(w, gg.w, m[9]);
-      }
-    }
-    __syncthreads();  // gp / w no longer needed: reuse the space for partial sums
+    if (__any_sync(0xffffffffu, act) && e < cnt) {
+      float s0 = 0.f, k1 = 0.f, k2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
 #pragma unroll
-    for (int k = 0; k < kMom; ++k) S.u.red[warp][k][lane] = m[k];
+      for (int k = 0; k < kTile; ++k) {
+        const float2 gw = S.gw[prow + k][e];
+        const float4 gg = S.g[prow + k];
+        constexpr float c0 = -7.5f;
+        const float kc = c0 + (float)k;
+        s0 += gw.x;
+        k1 = fmaf(kc, gw.x, k1);
+        k2 = fmaf(kc * kc, gw.x, k2);
+        w0 = fmaf(gw.y, gg.x, w0);
+        w1 = fmaf(gw.y, gg.y, w1);
+        w2 = fmaf(gw.y, gg.z, w2);
+        w3 = fmaf(gw.y, gg.w, w3);
+      }
+      const float2 xy = S.xy[e];
+      const float xc = xy.x - 7.5f, dy = xy.y - (float)(prow / kTile);
+      const float m1 = fmaf(xc, s0, -k1);                    // sum gp (xc - kc)
+      m[0] = s0;
+      m[1] = m1;
+      m[2] = dy * s0;
+      m[3] = fmaf(xc, fmaf(xc, s0, -2.f * k1), k2);          // sum gp (xc - kc)^2
+      m[4] = dy * m1;
+      m[5] = dy * dy * s0;
+      m[6] = w0;
+      m[7] = w1;
+      m[8] = w2;
+      m[9] = w3;
+    }
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) m[k] += __shfl_down_sync(0xffffffffu, m[k], kTile);
+    if (half == 0) {
+#pragma unroll
+      for (int k = 0; k < kMom; ++k) S.red[warp][k][e] = m[k];
+    }
     __syncthreads();
     if (t < cnt) {
       float r[kMom];
@@ -230,7 +245,7 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
       for (int k = 0; k < kMom; ++k) {
         float acc = 0.f;
 #pragma unroll
-        for (int ww = 0; ww < kBwdWarps; ++ww) acc += S.u.red[ww][k][t];
+        for (int ww = 0; ww < kBwdWarps; ++ww) acc += S.red[ww][k][t];
         r[k] = acc;
       }
       bool any = false;
@@ -243,7 +258,8 @@ __global__ void __launch_bounds__(kTilePix) k_blend_bwd(const __grid_constant__ 
         atomicAdd(dst + 2, make_float4(r[8], r[9], 0.f, 0.f));
       }
     }
-    __syncthreads();
+    // No barrier here: the next batch's pixel phase writes gw only after the next
+    // load's barrier, and only thread t < cnt reads S.idx[t] / writes it next.
   }
 }
 
