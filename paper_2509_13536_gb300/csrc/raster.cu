@@ -104,17 +104,26 @@ constexpr int kBwdBatch = 16;
 constexpr int kBwdStride = kBwdBatch + 1;  // padded row: conflict-free both ways
 constexpr int kBwdWarps = kTilePix / 32;
 constexpr int kMom = 10;
+constexpr int kRedStride = kMom + 1;     // per-entry row of partial moments (odd: no conflicts)
 
 struct BwdSmem {
-  float2 gw[kTilePix][kBwdStride];          // (gp, w) per pixel and entry
-  float red[kBwdWarps][kMom][kBwdBatch];    // per-warp partial moments
+  float2 gw[kTilePix][kBwdStride];          // (gp, w) per pixel and entry; after the Gaussian
+                                            // phase each warp's rows hold its partial moments
   float4 g[kTilePix];                       // per pixel dL/d(r, g, b, depth)
-  float2 xy[kBwdBatch];
-  float4 co[kBwdBatch];
-  float4 col[kBwdBatch];
-  uint32_t idx[kBwdBatch];
+  float4 raw[2][kBwdBatch][3];              // records of the next batch, landed by cp.async
+  float2 xy[2][kBwdBatch];                  // tile-relative centre
+  float4 co[2][kBwdBatch];                  // scaled conic, opacity
+  float4 col[2][kBwdBatch];                 // colour, depth
+  uint32_t idx[2][kBwdBatch];
   int lmax;
 };
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant__ ViewTable vt,
                                                            const float4* __restrict__ rec,
@@ -155,15 +164,43 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
   // Gaussian-phase lane roles: entry e of the batch, tile row 2 warp + half
   const int e = lane & (kBwdBatch - 1), half = lane >> 4;
   const int prow = warp * 32 + half * kTile;
-  for (int base = ((L - 1) / kBwdBatch) * kBwdBatch; L > 0 && base >= 0; base -= kBwdBatch) {
+  float* const red_own = reinterpret_cast<float*>(&S.gw[warp * 32][0]);
+  // Batches run back to front.  Threads t < kBwdBatch keep the list indices of the next
+  // two batches in registers and land the next batch's records by cp.async, so the
+  // gather overlaps the current batch.
+  int base = L > 0 ? ((L - 1) / kBwdBatch) * kBwdBatch : -1;
+  uint32_t idx_cur = 0, idx_next = 0;
+  if (t < kBwdBatch && base >= 0) {
+    if (base + t < L) {
+      idx_cur = vals[range.x + base + t];
+      const float4* src = rec + 3 * (size_t)idx_cur;
+      cp_async16(&S.raw[0][t][0], src);
+      cp_async16(&S.raw[0][t][1], src + 1);
+      cp_async16(&S.raw[0][t][2], src + 2);
+    }
+    cp_async_commit();
+    if (base >= kBwdBatch) idx_next = vals[range.x + base - kBwdBatch + t];
+  }
+  for (int buf = 0; base >= 0; base -= kBwdBatch, buf ^= 1) {
     const int cnt = min(kBwdBatch, L - base);
-    if (t < cnt) {
-      uint32_t idx = vals[range.x + base + t];
-      float4 r0 = rec[3 * (size_t)idx], r1 = rec[3 * (size_t)idx + 1], r2 = rec[3 * (size_t)idx + 2];
-      S.xy[t] = make_float2(__fadd_rn(__fsub_rn(r0.x, x0f), r0.z), __fadd_rn(__fsub_rn(r0.y, y0f), r0.w));
-      S.co[t] = r1;
-      S.col[t] = r2;
-      S.idx[t] = idx;
+    if (t < kBwdBatch) {
+      cp_async_wait_all();
+      if (t < cnt) {
+        const float4 r0 = S.raw[buf][t][0];
+        S.xy[buf][t] = make_float2(__fadd_rn(__fsub_rn(r0.x, x0f), r0.z), __fadd_rn(__fsub_rn(r0.y, y0f), r0.w));
+        S.co[buf][t] = S.raw[buf][t][1];
+        S.col[buf][t] = S.raw[buf][t][2];
+        S.idx[buf][t] = idx_cur;
+      }
+      if (base >= kBwdBatch) {  // the next batch is full: every t < kBwdBatch has an entry
+        const float4* src = rec + 3 * (size_t)idx_next;
+        cp_async16(&S.raw[buf ^ 1][t][0], src);
+        cp_async16(&S.raw[buf ^ 1][t][1], src + 1);
+        cp_async16(&S.raw[buf ^ 1][t][2], src + 2);
+        cp_async_commit();
+        idx_cur = idx_next;
+        if (base >= 2 * kBwdBatch) idx_next = vals[range.x + base - 2 * kBwdBatch + t];
+      }
     }
     __syncthreads();
     // pixel phase: branch-free back-to-front recursion; sigma = S . g (colour and depth
@@ -175,14 +212,14 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
       for (int j = kBwdBatch - 1; j >= 0; --j) {
         if (j < cnt) {
           float dx, dy;
-          const float4 co = S.co[j];
-          const float p2 = frag_exp2(S.xy[j], co, pxf, pyf, dx, dy);
+          const float4 co = S.co[buf][j];
+          const float p2 = frag_exp2(S.xy[buf][j], co, pxf, pyf, dx, dy);
           const float a = __fmul_rn(co.w, ex2_approx(p2));
           const float al = fminf(kAlphaMax, a);
           const bool on = j < lim && p2 <= 0.f && al >= kAlphaMin;
           act |= on;
           const float alc = on ? al : 0.f;
-          const float4 c = S.col[j];
+          const float4 c = S.col[buf][j];
           const float rom = __fdividef(1.f, 1.f - alc);
           const float Tb = T * rom;
           const float cg = fmaf(c.x, gR, fmaf(c.y, gG, fmaf(c.z, gB, c.w * gD)));
@@ -218,7 +255,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
         w2 = fmaf(gw.y, gg.z, w2);
         w3 = fmaf(gw.y, gg.w, w3);
       }
-      const float2 xy = S.xy[e];
+      const float2 xy = S.xy[buf][e];
       const float xc = xy.x - 7.5f, dy = xy.y - (float)(prow / kTile);
       const float m1 = fmaf(xc, s0, -k1);                    // sum gp (xc - kc)
       m[0] = s0;
@@ -234,32 +271,33 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
     }
 #pragma unroll
     for (int k = 0; k < kMom; ++k) m[k] += __shfl_down_sync(0xffffffffu, m[k], kTile);
+    __syncwarp();  // every lane is done reading this warp's gw rows
     if (half == 0) {
 #pragma unroll
-      for (int k = 0; k < kMom; ++k) S.red[warp][k][e] = m[k];
+      for (int k = 0; k < kMom; ++k) red_own[e * kRedStride + k] = m[k];
     }
     __syncthreads();
-    if (t < cnt) {
-      float r[kMom];
+    // Cross-warp sum, spread over all threads: half-warp q owns entry q, its lane k
+    // moment k; lanes 0, 4, 8 then add four consecutive moments with one vector atomic.
+    {
+      const int q = 2 * warp + half, k = e;
+      float r = 0.f;
+      if (q < cnt && k < kMom) {
 #pragma unroll
-      for (int k = 0; k < kMom; ++k) {
-        float acc = 0.f;
-#pragma unroll
-        for (int ww = 0; ww < kBwdWarps; ++ww) acc += S.red[ww][k][t];
-        r[k] = acc;
+        for (int ww = 0; ww < kBwdWarps; ++ww)
+          r += reinterpret_cast<const float*>(&S.gw[ww * 32][0])[q * kRedStride + k];
       }
-      bool any = false;
-#pragma unroll
-      for (int k = 0; k < kMom; ++k) any |= (r[k] != 0.f);
-      if (any) {
-        float4* dst = moments + 3 * (size_t)S.idx[t];
-        atomicAdd(dst, make_float4(r[0], r[1], r[2], r[3]));
-        atomicAdd(dst + 1, make_float4(r[4], r[5], r[6], r[7]));
-        atomicAdd(dst + 2, make_float4(r[8], r[9], 0.f, 0.f));
+      const float r1 = __shfl_down_sync(0xffffffffu, r, 1);
+      const float r2 = __shfl_down_sync(0xffffffffu, r, 2);
+      const float r3 = __shfl_down_sync(0xffffffffu, r, 3);
+      const uint32_t nz = __ballot_sync(0xffffffffu, r != 0.f) >> (16 * half);
+      if (q < cnt && (k & 3) == 0 && k < kMom && (nz & 0xffffu)) {
+        float4* dst = moments + 3 * (size_t)S.idx[buf][q] + (k >> 2);
+        atomicAdd(dst, make_float4(r, r1, (k < 8) ? r2 : 0.f, (k < 8) ? r3 : 0.f));
       }
     }
-    // No barrier here: the next batch's pixel phase writes gw only after the next
-    // load's barrier, and only thread t < cnt reads S.idx[t] / writes it next.
+    // No barrier here: the next batch's records go to the other buffer, and gw is next
+    // written after the next batch's barrier.
   }
 }
 
