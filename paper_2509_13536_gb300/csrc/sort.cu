@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 // block-wide prefix over the warps' counts then gives every item its position in the
 // block's digit-sorted order; items are staged in shared memory in that order and
 // written out as coalesced runs per digit.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+__global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
     uint32_t mask, int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout) {
@@ -196,12 +196,18 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   __syncthreads();
   const uint32_t lt = lanemask_lt();
   uint32_t key[kRounds], val[kRounds], rank[kRounds];
+  // all 32 loads of the warp's segment in flight before the ranking starts
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const int i = w * kPerWarp + r * 32 + lane;
     const bool valid = i < n_here;
-    key[r] = valid ? kin[base + i] : 0u;
-    val[r] = valid ? (vin ? vin[base + i] : (uint32_t)(base + i)) : 0u;
+    key[r] = valid ? __ldcs(kin + base + i) : 0u;
+    val[r] = valid ? (vin ? __ldcs(vin + base + i) : (uint32_t)(base + i)) : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int i = w * kPerWarp + r * 32 + lane;
+    const bool valid = i < n_here;
     const uint32_t d = valid ? (key[r] >> shift) & mask : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t before = valid ? s_wcnt[w][d] : 0u;
