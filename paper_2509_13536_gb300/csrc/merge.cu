@@ -38,6 +38,7 @@ namespace {
 
 constexpr int kWarpVoxel = 32;
 constexpr int kBlockVoxel = 256;
+constexpr int64_t kPersistBlocks = 152 * 8;  // grid of the grid-stride kernels: 8 blocks per SM
 constexpr uint32_t kNoKey = 0xffffffffu;
 
 __device__ __forceinline__ bool older(uint64_t ba, int64_t a, uint64_t bb, int64_t b) {
@@ -209,12 +210,13 @@ __device__ void merge_pair(const float* means, const Geom& geo, int64_t i, int64
 }
 
 template <typename T>
-__global__ void k_voxel_prep(int64_t n, const float* __restrict__ means, float voxel,
-                             mgs_merge_params p, int32_t* __restrict__ vox, int32_t* hdr) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_voxel_prep(int64_t n, const float* __restrict__ means, float voxel,
+                                                    mgs_merge_params p, int32_t* __restrict__ vox, int32_t* hdr) {
+  // Grid-stride over the Gaussians; the bounding box, the eligible count and the
+  // overflow flag are reduced per block and folded into hdr with one set of atomics.
   int mn[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, mx[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
   int elig = 0, bad = 0;
-  if (i < n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     bool e = true;
     if (p.grad_stat) e = e && p.grad_stat[i] < p.grad_tau;
     if (p.kf_id) e = e && p.kf_id[i] >= p.kf_min && p.kf_id[i] <= p.kf_max;
@@ -224,9 +226,10 @@ __global__ void k_voxel_prep(int64_t n, const float* __restrict__ means, float v
         if (!(q >= -1048576.f && q < 1048576.f)) { bad = 1; q = 0.f; }
         int c = (int)q;
         vox[3 * i + k] = c;
-        mn[k] = c; mx[k] = c;
+        mn[k] = min(mn[k], c);
+        mx[k] = max(mx[k], c);
       }
-      elig = 1;
+      ++elig;
     } else {
       for (int k = 0; k < 3; ++k) vox[3 * i + k] = INT32_MIN;
     }
@@ -239,13 +242,32 @@ __global__ void k_voxel_prep(int64_t n, const float* __restrict__ means, float v
     elig += __shfl_xor_sync(0xffffffffu, elig, o);
     bad |= __shfl_xor_sync(0xffffffffu, bad, o);
   }
-  if ((threadIdx.x & 31) == 0 && elig) {
-    for (int k = 0; k < 3; ++k) {
-      atomicMin(&hdr[k], mn[k]);
-      atomicMax(&hdr[3 + k], mx[k]);
+  __shared__ int s_red[8][8];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    for (int k = 0; k < 3; ++k) { s_red[w][k] = mn[k]; s_red[w][3 + k] = mx[k]; }
+    s_red[w][6] = elig;
+    s_red[w][7] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int ww = 1; ww < nw; ++ww) {
+      for (int k = 0; k < 3; ++k) {
+        s_red[0][k] = min(s_red[0][k], s_red[ww][k]);
+        s_red[0][3 + k] = max(s_red[0][3 + k], s_red[ww][3 + k]);
+      }
+      s_red[0][6] += s_red[ww][6];
+      s_red[0][7] |= s_red[ww][7];
     }
-    atomicAdd(&hdr[6], elig);
-    if (bad) atomicOr(&hdr[7], 1);
+    if (s_red[0][6]) {
+      for (int k = 0; k < 3; ++k) {
+        atomicMin(&hdr[k], s_red[0][k]);
+        atomicMax(&hdr[3 + k], s_red[0][3 + k]);
+      }
+      atomicAdd(&hdr[6], s_red[0][6]);
+      if (s_red[0][7]) atomicOr(&hdr[7], 1);
+    }
   }
 }
 
@@ -290,14 +312,15 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
   __shared__ uint64_t s_birth[4][kWarpVoxel];
   __shared__ int s_pairs[4][kWarpVoxel / 2][2];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t v = (int64_t)blockIdx.x * 4 + wib;
-  if (v >= (int64_t)*n_vox_p) return;
+  const int64_t n_vox = (int64_t)*n_vox_p;
+  // Persistent warps: warp-stride loop over the voxels.
+  for (int64_t v = (int64_t)blockIdx.x * 4 + wib; v < n_vox; v += (int64_t)gridDim.x * 4) {
   const uint32_t st = starts[v], en = starts[v + 1];
   const int nm = (int)(en - st);
-  if (nm < 2) return;
+  if (nm < 2) continue;
   if (nm > kWarpVoxel) {
     if (lane == 0) big[atomicAdd(n_big, 1u)] = (uint32_t)v;
-    return;
+    continue;
   }
   int64_t my = lane < nm ? (int64_t)perm[st + lane] : -1;
   uint64_t mb = lane < nm ? birth[my] : ~0ull;
@@ -369,6 +392,8 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     partner[j] = (int32_t)i;
     pairs[slot + lane] = make_uint2((uint32_t)i, (uint32_t)j);
   }
+  __syncwarp();  // the warp's shared rows are reused by its next voxel
+  }
 }
 
 // Block path: a voxel with 33..256 members; d2 evaluated on the fly each round.
@@ -388,14 +413,17 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
   __shared__ int r_a[kBlockVoxel], r_b[kBlockVoxel];
   __shared__ int s_pairs[kBlockVoxel / 2][2];
   __shared__ int s_np;
-  if (blockIdx.x >= *n_big_p) return;
-  const uint32_t v = big[blockIdx.x];
+  __shared__ uint32_t s_slot;
+  const uint32_t n_big = *n_big_p;
+  const int t = threadIdx.x;
+  // Block-stride loop over the big voxels (every branch below is uniform per block).
+  for (uint32_t bv = blockIdx.x; bv < n_big; bv += gridDim.x) {
+  const uint32_t v = big[bv];
   const uint32_t st = starts[v], en = starts[v + 1];
   const int nm = (int)(en - st);
-  const int t = threadIdx.x;
   if (nm > kBlockVoxel) {
     if (t == 0) atomicOr(err, 2);
-    return;
+    continue;
   }
   int64_t my = t < nm ? (int64_t)perm[st + t] : -1;
   uint64_t mb = t < nm ? birth[my] : ~0ull;
@@ -451,7 +479,6 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
     __syncthreads();
     if (!greedy) break;
   }
-  __shared__ uint32_t s_slot;
   if (t == 0) s_slot = s_np ? atomicAdd(n_pairs, (uint32_t)s_np) : 0u;
   __syncthreads();
   for (int k = t; k < s_np; k += kBlockVoxel) {
@@ -459,6 +486,8 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
     partner[i] = (int32_t)j;
     partner[j] = (int32_t)i;
     pairs[s_slot + k] = make_uint2((uint32_t)i, (uint32_t)j);
+  }
+  __syncthreads();  // shared state is reused by the next voxel
   }
 }
 
@@ -496,6 +525,30 @@ __global__ void k_compact(int64_t n, int K3, const float* __restrict__ means, co
                           const float* __restrict__ mmean, const float* __restrict__ mquat,
                           const float* __restrict__ mlogs, float* omeans, void* ols, void* oqs, T* ool,
                           T* osh, uint64_t* obirth) {
+  // SH rows: the block copies the rows of its kept Gaussians cooperatively, in 16-byte
+  // chunks when both arrays allow it (rows of whole chunks, 16-byte aligned), else
+  // element by element; either way consecutive threads touch consecutive addresses.
+  {
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
+    const int rows = (int)(n - g0 < (int64_t)blockDim.x ? n - g0 : (int64_t)blockDim.x);
+    const int row_bytes = K3 * (int)sizeof(T);
+    if (row_bytes % 16 == 0 && ((uintptr_t)sh & 15u) == 0 && ((uintptr_t)osh & 15u) == 0) {
+      const int Q = row_bytes / 16;
+      const uint4* src = reinterpret_cast<const uint4*>(sh);
+      uint4* dst = reinterpret_cast<uint4*>(osh);
+      for (int c = threadIdx.x; c < rows * Q; c += blockDim.x) {
+        const int r = c / Q, q = c - r * Q;
+        const int64_t gi = g0 + r;
+        if (keep[gi]) dst[(int64_t)pos[gi] * Q + q] = __ldcs(src + gi * Q + q);
+      }
+    } else {
+      for (int c = threadIdx.x; c < rows * K3; c += blockDim.x) {
+        const int r = c / K3, k = c - r * K3;
+        const int64_t gi = g0 + r;
+        if (keep[gi]) osh[(int64_t)pos[gi] * K3 + k] = sh[gi * K3 + k];
+      }
+    }
+  }
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || !keep[i]) return;
   int64_t w = pos[i];
@@ -507,7 +560,6 @@ __global__ void k_compact(int64_t n, int K3, const float* __restrict__ means, co
     for (int k = 0; k < 4; ++k) cp_dt(oqs, geo.qs, geo.dt, 4 * w + k, 4 * i + k);
   }
   ool[w] = ol[i];
-  for (int k = 0; k < K3; ++k) osh[(int64_t)K3 * w + k] = sh[(int64_t)K3 * i + k];
   if (obirth) obirth[w] = birth[i];
 }
 
@@ -528,7 +580,7 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
   e = cudaMemsetAsync(partner, 0xff, sizeof(int32_t) * n, s);
   if (e != cudaSuccess) return e;
   int32_t* vox = vox_out ? vox_out : ws.vox;
-  k_voxel_prep<T><<<grid, 256, 0, s>>>(n, in.means, voxel, p, vox, ws.hdr);
+  k_voxel_prep<T><<<(unsigned)std::min<int64_t>(grid, kPersistBlocks), 256, 0, s>>>(n, in.means, voxel, p, vox, ws.hdr);
   count_launch();
   int32_t h[16];
   e = cudaMemcpyAsync(h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -556,11 +608,11 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
     if (e != cudaSuccess) return e;
     k_starts<<<ge, 256, 0, s>>>(n_elig, ws.flags, ws.pos, ws.starts, n_vox);
     count_launch(3);  // with the two pairing kernels below
-    unsigned gv = (unsigned)div_up(n_elig, 4);
+    unsigned gv = (unsigned)std::min<int64_t>(div_up(n_elig, 4), kPersistBlocks);
     uint32_t* n_pairs = (uint32_t*)(ws.hdr + 11);
     k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, geo, in.birth, perm, ws.starts, n_vox, p.chi2,
                                         p.greedy, partner, ws.pairs, n_pairs, ws.big, n_big);
-    k_voxel_pairs_big<T><<<(unsigned)std::max<int64_t>(1, n_elig / 33), kBlockVoxel, 0, s>>>(
+    k_voxel_pairs_big<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n_elig / 33), 152 * 2), kBlockVoxel, 0, s>>>(
         in.means, geo, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
         ws.pairs, n_pairs, ws.hdr + 7);
     k_merge_pairs<T><<<(unsigned)div_up(n_elig / 2 + 1, 128), 128, 0, s>>>(in.means, geo, ws.pairs, n_pairs,
