@@ -243,9 +243,10 @@ mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_
   cudaError_t e = cudaSuccess;
   int dcur = 0;
   if (L.VN > 0) {
-    // front-to-back order of every (view, Gaussian) item: float32 depth bits, then item index
+    // front-to-back order of the drawn (view, Gaussian) items: float32 depth bits, then item
+    // index; undrawn items (key kSortDrop) leave in the first pass
     ProfScope ps(kProfDepthSort, s);
-    dcur = radix_sort_pairs(dk, dv, L.VN, 0, 32, true, scratch, s, &e);
+    dcur = radix_sort_pairs(dk, dv, L.VN, 0, 32, true, scratch, s, &e, n_vis);
     if (e != cudaSuccess) return cuda_status(e, "depth sort");
     MGS_TRY_CUDA(scan_exclusive_u32(touched, dv[dcur], offsets, n_vis, scratch, nullptr, s));
   }

@@ -50,10 +50,14 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, const uint32_t* gather, uint3
                                cudaStream_t s);
 
 // Stable LSD radix sort of (k[0], v[0]) on bits [begin, end).  When vals_iota the input
-// values are the positions 0..n-1 (v[0] is not read).  Returns the index (0 or 1) of the
-// buffer pair that holds the result.
+// values are the positions 0..n-1 (v[0] is not read).  With n_keep >= 0 the first pass
+// drops every pair whose key is kSortDrop, and n_keep (the number of other keys, known
+// to the caller) pairs remain for the later passes and in the result.  Returns the index
+// (0 or 1) of the buffer pair that holds the result.
+constexpr uint32_t kSortDrop = 0xffffffffu;
 int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, int end_bit,
-                     bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err);
+                     bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err,
+                     int64_t n_keep = -1);
 inline int radix_passes(int begin_bit, int end_bit) {
   return end_bit > begin_bit ? (end_bit - begin_bit + 7) / 8 : 0;
 }

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) k_preprocess(int64_t N, const float* __re
         rects[item] = make_uint2(1u, 0u);  // empty rect: x0 = 1 > x1 = 0
       }
       touched[item] = count;
-      dkeys[item] = count ? __float_as_uint(P.tz) : 0xffffffffu;
+      dkeys[item] = count ? __float_as_uint(P.tz) : kSortDrop;  // undrawn: left out by the depth sort
       my_keys += count;
       my_vis += count ? 1u : 0u;
     }

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* in,
 // come in long runs).
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                              int64_t n, int shift, uint32_t mask, int nb,
-                                                             uint32_t* __restrict__ hist) {
+                                                             uint32_t* __restrict__ hist, bool drop) {
   __shared__ uint32_t h[kWarps][256];
   const int t = threadIdx.x, w = t >> 5;
 #pragma unroll
@@ -147,21 +147,22 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   }
   const int m = (int)(n - i0 < kSortPerThread ? (n - i0 > 0 ? n - i0 : 0) : kSortPerThread);
   if (m > 0) {
-    uint32_t cur = (k[0] >> shift) & mask, cnt = 1;
+    // dropped keys (drop: key == kSortDrop) count under the out-of-range digit 256
+    uint32_t cur = (drop && k[0] == kSortDrop) ? 256u : (k[0] >> shift) & mask, cnt = 1;
 #pragma unroll
     for (int q = 1; q < kSortPerThread; ++q) {
       if (q < m) {
-        const uint32_t d = (k[q] >> shift) & mask;
+        const uint32_t d = (drop && k[q] == kSortDrop) ? 256u : (k[q] >> shift) & mask;
         if (d == cur) {
           ++cnt;
         } else {
-          atomicAdd(&h[w][cur], cnt);
+          if (cur < 256u) atomicAdd(&h[w][cur], cnt);
           cur = d;
           cnt = 1;
         }
       }
     }
-    atomicAdd(&h[w][cur], cnt);
+    if (cur < 256u) atomicAdd(&h[w][cur], cnt);
   }
   __syncthreads();
   uint32_t tot = 0;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
     uint32_t mask, int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout) {
+    uint32_t* __restrict__ vout, bool drop) {
   constexpr int kPerWarp = kSortTile / kWarps;  // 512
   constexpr int kRounds = kPerWarp / 32;        // 16
   __shared__ uint32_t s_wcnt[kWarps][256];      // per-warp digit counts, then exclusive offsets
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
   __shared__ uint32_t s_boff[256];              // start of the digit in the block's sorted order
   __shared__ uint32_t s_key[kSortTile];
   __shared__ uint32_t s_val[kSortTile];
+  __shared__ uint32_t s_nkeep;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   const int n_here = (int)(n - base < kSortTile ? n - base : (int64_t)kSortTile);
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const int i = w * kPerWarp + r * 32 + lane;
-    const bool valid = i < n_here;
+    const bool valid = i < n_here && !(drop && key[r] == kSortDrop);
     const uint32_t d = valid ? (key[r] >> shift) & mask : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t before = valid ? s_wcnt[w][d] : 0u;
@@ -237,12 +239,13 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     uint32_t pre = 0;
     for (int ww = 0; ww < w; ++ww) pre += s_wsum[ww];
     s_boff[t] = pre + inc - run;
+    if (t == kSortThreads - 1) s_nkeep = pre + inc;  // items of this block that are kept
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const int i = w * kPerWarp + r * 32 + lane;
-    if (i < n_here) {
+    if (i < n_here && !(drop && key[r] == kSortDrop)) {
       const uint32_t d = (key[r] >> shift) & mask;
       const uint32_t pos = s_boff[d] + s_wcnt[w][d] + rank[r];
       s_key[pos] = key[r];
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     }
   }
   __syncthreads();
-  for (int i = t; i < n_here; i += kSortThreads) {
+  for (int i = t; i < (int)s_nkeep; i += kSortThreads) {
     const uint32_t k = s_key[i];
     const uint32_t d = (k >> shift) & mask;
     const uint32_t pos = s_goff[d] + (uint32_t)i - s_boff[d];
@@ -294,25 +297,31 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, const uint32_t* gather, uint3
 }
 
 int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, int end_bit,
-                     bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err) {
+                     bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err, int64_t n_keep) {
   *err = cudaSuccess;
   int cur = 0;
   if (n <= 0) return 0;
-  int nb = (int)div_up(n, kSortTile);
+  bool drop = n_keep >= 0;  // first pass drops kSortDrop keys; n_keep of them remain
   uint32_t* hist = scratch;
-  uint32_t* spine = scratch + align_up((size_t)256 * nb, 64);
+  uint32_t* spine = scratch + align_up((size_t)256 * div_up(n, kSortTile), 64);
   bool first = true;
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
+    if (n <= 0) break;
+    const int nb = (int)div_up(n, kSortTile);
     const uint32_t mask = (1u << std::min(8, end_bit - shift)) - 1u;
-    k_radix_hist<<<nb, kSortThreads, 0, s>>>(k[cur], n, shift, mask, nb, hist);
+    k_radix_hist<<<nb, kSortThreads, 0, s>>>(k[cur], n, shift, mask, nb, hist, drop);
     count_launch(2);
     *err = scan_exclusive_u32(hist, nullptr, hist, (int64_t)256 * nb, spine, nullptr, s);
     if (*err != cudaSuccess) return cur;
     const uint32_t* vin = (first && vals_iota) ? nullptr : v[cur];
     k_radix_scatter<<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, mask, nb, hist, k[cur ^ 1],
-                                                v[cur ^ 1]);
+                                                v[cur ^ 1], drop);
     cur ^= 1;
     first = false;
+    if (drop) {
+      n = n_keep;
+      drop = false;
+    }
     *err = cudaGetLastError();
     if (*err != cudaSuccess) return cur;
   }
