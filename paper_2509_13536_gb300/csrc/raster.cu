@@ -5,14 +5,16 @@
 // every thread walks them front to back for its pixel, with transmittance and the
 // colour/depth sums in registers; the CTA leaves as soon as all its pixels stopped.
 //
-// Reverse: the tile's entries are walked back to front in batches of 32.  In the
+// Reverse: the tile's entries are walked back to front in batches of 16.  In the
 // pixel phase each thread runs the back-to-front recursion for its pixel (T recovered
 // by division; of the colour and depth behind each Gaussian only their dot product
 // with the pixel's cotangent is needed, one scalar) and writes two numbers per
 // (pixel, entry) into shared memory: gp = dL/dpower and the blend weight w.  In the
-// Gaussian phase each lane owns one entry and sums, over the 32 pixels of its warp,
-// the ten moments the per-Gaussian chain rule needs; the eight warps' partial sums
-// meet in shared memory and one thread per entry issues three 16-byte vector atomics.
+// Gaussian phase each half-warp owns one tile row and each of its lanes one entry; it
+// sums gp, k gp, k^2 gp (k the column) and w times the cotangent along the row and forms
+// the ten moments the per-Gaussian chain rule needs; the eight warps' partial sums meet
+// in shared memory, are added by all threads (half-warp = entry, lane = moment) and go
+// out as three 16-byte vector atomics per entry.
 // There is no per-fragment shuffle or atomic.
 //
 // Both per-fragment loops are branch-free: a Gaussian that fails the alpha test (or
@@ -301,71 +303,6 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
   }
 }
 
-// Key emission over the items in front-to-back order, one thread per item: the
-// thread writes one (global tile id, item) pair per tile its alpha >= 1/255 ellipse
-// reaches (row by row).  Items with more than 32 keys are written cooperatively by
-// the whole warp afterwards.  An item never writes more than the count the projection
-// pass gave it; any shortfall is padded with the sentinel tile id n_tiles, which sorts
-// last and is ignored by the range build.
-__device__ __forceinline__ void emit_item(uint32_t item, uint32_t off, uint32_t cnt, int lane, int stride,
-                                          const uint2* __restrict__ rects, const float4* __restrict__ rec,
-                                          int64_t N, const ViewTable& vt, uint32_t* __restrict__ tkeys,
-                                          uint32_t* __restrict__ tvals) {
-  const int v = (int)((int64_t)item / N);
-  const View& V = vt.v[v];
-  const uint2 rc = rects[item];
-  const Cull q = make_cull(rec[3 * (size_t)item], rec[3 * (size_t)item + 1]);
-  int y0 = rc.x >> 16, y1 = rc.y >> 16;
-  cull_rows(q, y0, y1);
-  uint32_t w = 0;
-  for (int y = y0; y <= y1 && w < cnt; ++y) {
-    int x0 = rc.x & 0xffff, x1 = rc.y & 0xffff;
-    cull_cols(q, y, x0, x1);
-    const int nx = x1 - x0 + 1;
-    for (int dx = lane; dx < nx; dx += stride) {
-      const uint32_t pos = w + (uint32_t)dx;
-      if (pos < cnt) {
-        tkeys[off + pos] = (uint32_t)(V.tile_base + y * V.tiles_x + x0 + dx);
-        tvals[off + pos] = item;
-      }
-    }
-    if (nx > 0) w += (uint32_t)nx;
-  }
-  for (uint32_t pos = w + lane; pos < cnt; pos += stride) {
-    tkeys[off + pos] = (uint32_t)vt.n_tiles;
-    tvals[off + pos] = item;
-  }
-}
-
-constexpr uint32_t kEmitCoop = 32;
-
-__global__ void __launch_bounds__(256) k_emit(int64_t n_vis, int64_t N, const uint32_t* __restrict__ dvals,
-                                              const uint32_t* __restrict__ offsets,
-                                              const uint32_t* __restrict__ touched,
-                                              const uint2* __restrict__ rects, const float4* __restrict__ rec,
-                                              const __grid_constant__ ViewTable vt,
-                                              uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals) {
-  const int lane = threadIdx.x & 31;
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if ((k & ~int64_t(31)) >= n_vis) return;  // whole warp beyond the end
-  uint32_t item = 0, off = 0, cnt = 0;
-  if (k < n_vis) {
-    item = dvals[k];
-    off = offsets[k];
-    cnt = touched[item];
-  }
-  if (cnt > 0 && cnt <= kEmitCoop) emit_item(item, off, cnt, 0, 1, rects, rec, N, vt, tkeys, tvals);
-  uint32_t big = __ballot_sync(0xffffffffu, cnt > kEmitCoop);
-  while (big) {
-    const int src = __ffs(big) - 1;
-    big &= big - 1;
-    const uint32_t it = __shfl_sync(0xffffffffu, item, src);
-    const uint32_t of = __shfl_sync(0xffffffffu, off, src);
-    const uint32_t cn = __shfl_sync(0xffffffffu, cnt, src);
-    emit_item(it, of, cn, lane, 32, rects, rec, N, vt, tkeys, tvals);
-  }
-}
-
 // Counting pass over the saved forward state: per pixel, entries evaluated by the
 // forward pass (up to its stop, else the whole range), how many of them contributed,
 // and how many the backward pass walks (up to the last contributor).
@@ -439,15 +376,6 @@ cudaError_t launch_frag_stats(const ViewTable& vt, const float4* rec, const uint
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const uint32_t* offsets,
-                        const uint32_t* touched, const uint2* rects, const float4* rec, const ViewTable& vt,
-                        uint32_t* tkeys, uint32_t* tvals, cudaStream_t s) {
-  if (n_vis <= 0) return cudaSuccess;
-  k_emit<<<(unsigned)div_up(n_vis, 256), 256, 0, s>>>(n_vis, N, dvals, offsets, touched, rects, rec, vt, tkeys,
-                                                       tvals);
-  count_launch();
-  return cudaGetLastError();
-}
 
 size_t blend_bwd_smem() { return sizeof(BwdSmem); }
 
