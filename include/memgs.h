@@ -156,8 +156,9 @@ mgs_status mgs_project(const mgs_gaussians* g, const mgs_camera* cam_host, float
                        void* stream);
 
 /* ------------------------------------------------------------------------------
- * Voxel merge, Sec. II-D.  Eq. 3 mask: eligible iff grad_stat < grad_tau and
- * kf_min <= kf_id <= kf_max (a NULL array makes its test pass).  Eligible Gaussians
+ * Voxel merge, Sec. II-D.  Eq. 3 mask: eligible iff the mean gradient norm (grad_stat,
+ * or grad_stat / vis_count) < grad_tau and kf_min <= kf_id <= kf_max (a NULL array
+ * makes its test pass).  Eligible Gaussians
  * are grouped by voxel floor(mu / voxel_size) (float32 quotient, origin at 0).  In a
  * voxel every pair (i older than j) gets Eq. 4's d^2 = (mu_j-mu_i)^T Sigma_i^-1
  * (mu_j-mu_i); pairs with d^2 < chi2 (7.815, chi-square 0.05 with 3 dof) are similar.
@@ -174,6 +175,12 @@ typedef struct {
   int32_t kf_min, kf_max;
   const float* grad_stat;  /* [n] or NULL */
   const int32_t* kf_id;    /* [n] or NULL */
+  const float* vis_count;  /* [n] or NULL.  Non-NULL: grad_stat holds sums of |dL/dmu| over
+                              the views that drew each Gaussian and vis_count the number of
+                              those views (both as mgs_render_backward accumulates them over
+                              a keyframe window); the mask tests the mean, the float32
+                              quotient grad_stat / vis_count (0 for a Gaussian drawn in no
+                              view), against grad_tau.  NULL: grad_stat is the mean itself. */
   int32_t greedy;          /* 1 or 0 */
   int32_t reserved;
 } mgs_merge_params;

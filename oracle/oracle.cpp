@@ -1075,7 +1075,11 @@ int orc_voxel_merge(const orc_gaussians* g, const uint64_t* birth, double voxel,
   std::vector<char> elig(n, 1);
   for (int64_t i = 0; i < n; ++i) {
     bool ok = true;
-    if (p->grad_stat) ok = ok && p->grad_stat[i] < p->grad_tau;
+    if (p->grad_stat) {
+      double gs = p->grad_stat[i];  // Eq. 3: mean gradient norm over the views that drew it
+      if (p->vis_count) gs = p->vis_count[i] > 0 ? (double)(float)(gs / p->vis_count[i]) : 0.0;
+      ok = ok && gs < p->grad_tau;
+    }
     if (p->kf_id) ok = ok && p->kf_id[i] >= p->kf_min && p->kf_id[i] <= p->kf_max;
     elig[i] = ok;
   }

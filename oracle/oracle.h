@@ -130,6 +130,10 @@ typedef struct {
   int32_t kf_min, kf_max;    /* Eq. 3 keyframe window */
   const double* grad_stat;   /* [n] mean |dL/dmu| or NULL (all pass) */
   const int32_t* kf_id;      /* [n] keyframe index or NULL (all pass) */
+  const double* vis_count;   /* [n] or NULL; non-NULL: grad_stat holds sums over the views
+                                that drew each Gaussian and the mask tests the mean, taken
+                                as the float32 quotient grad_stat / vis_count (0 when no view
+                                drew it), the precision the kernel decides in */
   int32_t greedy;            /* 1: greedy disjoint pairs, 0: single minimum pair per voxel */
 } orc_merge_params;
 

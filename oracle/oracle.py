@@ -77,7 +77,7 @@ class Grads(C.Structure):
 class MergeParams(C.Structure):
     _fields_ = [("chi2", C.c_double), ("grad_tau", C.c_double), ("kf_min", C.c_int32),
                 ("kf_max", C.c_int32), ("grad_stat", C.c_void_p), ("kf_id", C.c_void_p),
-                ("greedy", C.c_int32)]
+                ("vis_count", C.c_void_p), ("greedy", C.c_int32)]
 
 
 def lib():
@@ -227,14 +227,15 @@ def voxel_keys(means, voxel):
 
 
 def voxel_merge(scene, voxel, *, chi2=7.815, greedy=True, grad_stat=None, grad_tau=1e-3,
-                kf_id=None, kf_min=0, kf_max=0, tie_rel=1e-4, **over):
+                kf_id=None, kf_min=0, kf_max=0, vis_count=None, tie_rel=1e-4, **over):
     P = _Params(scene, **over)
     n, K = P.n, (P.deg + 1) ** 2
     birth = np.ascontiguousarray(scene.birth, np.uint64)
     gs = None if grad_stat is None else _f64(grad_stat)
     kf = None if kf_id is None else np.ascontiguousarray(kf_id, np.int32)
+    vc = None if vis_count is None else _f64(vis_count)
     prm = MergeParams(float(np.float32(chi2)), float(np.float32(grad_tau)), kf_min, kf_max,
-                      _p(gs), _p(kf), 1 if greedy else 0)
+                      _p(gs), _p(kf), _p(vc), 1 if greedy else 0)
     out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
                opacity_logit=np.zeros(n), sh=np.zeros((n, K, 3)), birth=np.zeros(n, np.uint64),
                cov=np.zeros((n, 6)), partner=np.zeros(n, np.int32), tie=np.zeros(n, np.uint8))

@@ -58,7 +58,7 @@ class mgs_server_config(C.Structure):
 class mgs_merge_params(C.Structure):
     _fields_ = [("chi2", C.c_float), ("grad_tau", C.c_float), ("kf_min", C.c_int32),
                 ("kf_max", C.c_int32), ("grad_stat", C.c_void_p), ("kf_id", C.c_void_p),
-                ("greedy", C.c_int32), ("reserved", C.c_int32)]
+                ("vis_count", C.c_void_p), ("greedy", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lock = threading.Lock()

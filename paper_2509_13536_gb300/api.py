@@ -248,10 +248,12 @@ def mgs_voxel_merge(g: Gaussians, voxel_size: float, chi2: float = 7.815, greedy
                     kf_id: Optional[torch.Tensor] = None, kf_min: int = 0, kf_max: int = 0,
                     workspace: Optional[torch.Tensor] = None, out: Optional[Gaussians] = None,
                     partner: Optional[torch.Tensor] = None, vox: Optional[torch.Tensor] = None,
-                    stream=None):
+                    vis_count: Optional[torch.Tensor] = None, stream=None):
     """voxel_merge(gaussians, voxel_size, thresholds) -> (gaussians, partner, voxel coords).
 
-    ``workspace``, ``out``, ``partner`` and ``vox`` may be passed preallocated."""
+    ``grad_stat`` with ``vis_count``: the sums the backward pass accumulates (Grads.grad_stat,
+    Grads.vis_count); the Eq. 3 mask then tests their quotient.  ``workspace``, ``out``,
+    ``partner`` and ``vox`` may be passed preallocated."""
     if g.birth is None:
         raise ValueError("voxel merge needs birth stamps")
     L = load()
@@ -263,7 +265,7 @@ def mgs_voxel_merge(g: Gaussians, voxel_size: float, chi2: float = 7.815, greedy
     partner = partner if partner is not None else torch.empty(n, dtype=torch.int32, device=dev)
     vox = vox if vox is not None else torch.empty(n, 3, dtype=torch.int32, device=dev)
     p = _abi.mgs_merge_params(chi2, grad_tau, kf_min, kf_max, _ptr(grad_stat), _ptr(kf_id),
-                              1 if greedy else 0, 0)
+                              _ptr(vis_count), 1 if greedy else 0, 0)
     n_out = C.c_int64(0)
     check(L.mgs_voxel_merge(C.byref(g.struct()), float(voxel_size), C.byref(p), C.byref(out.struct()),
                             _ptr(partner), _ptr(vox), C.byref(n_out), _ptr(workspace),

@@ -218,7 +218,11 @@ __global__ void __launch_bounds__(256) k_voxel_prep(int64_t n, const float* __re
   int elig = 0, bad = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     bool e = true;
-    if (p.grad_stat) e = e && p.grad_stat[i] < p.grad_tau;
+    if (p.grad_stat) {
+      float gs = p.grad_stat[i];
+      if (p.vis_count) gs = p.vis_count[i] > 0.f ? __fdiv_rn(gs, p.vis_count[i]) : 0.f;  // Eq. 3 mean
+      e = e && gs < p.grad_tau;
+    }
     if (p.kf_id) e = e && p.kf_id[i] >= p.kf_min && p.kf_id[i] <= p.kf_max;
     if (e) {
       for (int k = 0; k < 3; ++k) {

@@ -40,7 +40,7 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(_abi.mgs_camera) == 80
     assert C.sizeof(_abi.mgs_image) == 24
     assert C.sizeof(_abi.mgs_grads) == 56
-    assert C.sizeof(_abi.mgs_merge_params) == 40
+    assert C.sizeof(_abi.mgs_merge_params) == 48
 
 
 def test_host_only_queries(lib):
@@ -67,7 +67,7 @@ def test_invalid_arguments_are_rejected_before_any_launch(lib):
     assert b"sh_degree" in lib.mgs_last_error()
     st = lib.mgs_sort_pairs(None, None, None, 10, 5, 3, None, 0, None)
     assert st == _abi.MGS_ERR_INVALID
-    p = _abi.mgs_merge_params(7.815, 1e-3, 0, 0, None, None, 1, 0)
+    p = _abi.mgs_merge_params(7.815, 1e-3, 0, 0, None, None, None, 1, 0)
     g2 = _abi.mgs_gaussians(10, 0, 0, 0, 0, 1, 1, 1, 1, 1, None)  # no birth
     st = lib.mgs_voxel_merge(C.byref(g2), 0.02, C.byref(p), None, None, None, None, None, 0, None)
     assert st == _abi.MGS_ERR_INVALID

@@ -18,16 +18,25 @@ def _built():
     build.build()
 
 
-def scrub(orc, scene, voxel, rounds=6, **kw):
+def scrub_kw(orc, scene, voxel, rounds=6, **kw):
     """Drop Gaussians that take part in a near-tie (|d2 - chi2| or two competing
-    candidates within 1e-4 relative), until none is left."""
+    candidates within 1e-4 relative), until none is left; per-Gaussian arrays in kw
+    are subset with the scene."""
     for _ in range(rounds):
         out = orc.voxel_merge(scene, voxel, tie_rel=1e-4, **kw)
         bad = out["tie"] != 0
         if not bad.any():
-            return scene, out
-        scene = scene.subset(np.nonzero(~bad)[0])
+            return scene, out, kw
+        keep = np.nonzero(~bad)[0]
+        kw = {k: (v[keep] if isinstance(v, np.ndarray) and v.shape[:1] == (scene.n,) else v)
+              for k, v in kw.items()}
+        scene = scene.subset(keep)
     raise AssertionError("tie scrub did not converge")
+
+
+def scrub(orc, scene, voxel, rounds=6, **kw):
+    scene, out, _ = scrub_kw(orc, scene, voxel, rounds, **kw)
+    return scene, out
 
 
 def cov_of(q, ls):
@@ -42,7 +51,8 @@ def cov_of(q, ls):
 
 
 def compare_merge(orc, scene, voxel, greedy=True, **kw):
-    scene, ref = scrub(orc, scene, voxel, greedy=greedy, **kw)
+    scene, ref, kw = scrub_kw(orc, scene, voxel, greedy=greedy, **kw)
+    kw.pop("greedy", None)
     g = api.Gaussians.from_scene(scene, "cuda")
     dev_kw = {k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) else v)
               for k, v in kw.items()}
@@ -88,6 +98,37 @@ def test_merge_mask_eq3(orc):
     gs = rng.uniform(0, 2e-3, sc.n).astype(np.float32)
     kf = rng.integers(0, 10, sc.n).astype(np.int32)
     compare_merge(orc, sc, 0.02, grad_stat=gs, grad_tau=1e-3, kf_id=kf, kf_min=2, kf_max=7)
+
+
+def test_merge_mask_eq3_from_sums(orc):
+    """Eq. 3 from per-view sums: the merge forms the mean grad_stat / vis_count itself."""
+    rng = np.random.default_rng(15)
+    sc = _voxel_scene(rng, 100, 5)
+    cnt = rng.integers(0, 6, sc.n).astype(np.float32)
+    sums = (rng.uniform(0, 2e-3, sc.n) * cnt).astype(np.float32)
+    compare_merge(orc, sc, 0.02, grad_stat=sums, vis_count=cnt, grad_tau=1e-3)
+
+
+def test_eq3_statistics_from_the_backward_pass_drive_the_merge(orc):
+    """The Eq. 3 loop on device: two backward passes accumulate sum |dL/dmu| and the view
+    count per Gaussian; the merge tests their quotient.  The oracle merge, fed the same
+    (read back) sums, picks the same clusters."""
+    scene = sg.room_scene(20_000, 17, sh_degree=0)
+    cams = sg.room_poses(2, 18, 320, 240)
+    g = api.Gaussians.from_scene(scene, "cuda")
+    grads = api.Grads.zeros_like(g)
+    for seed in (1, 2):
+        imgs, ws = api.render(g, cams)
+        _, dL = _gpu.cotangents(cams, seed)
+        api.render_backward(g, cams, dL, ws, grads)
+    torch.cuda.synchronize()
+    gs = grads.grad_stat.cpu().numpy()
+    vc = grads.vis_count.cpu().numpy()
+    assert vc.max() == 4 and (vc == 0).any()
+    mean = np.where(vc > 0, gs / np.maximum(vc, 1), 0)
+    tau = float(np.median(mean[vc > 0]))
+    pairs, n = compare_merge(orc, scene, 0.02, grad_stat=gs, vis_count=vc, grad_tau=tau)
+    assert pairs > 50
 
 
 def test_merge_room300k_bit_exact_clusters(orc):

@@ -210,6 +210,24 @@ def test_merge_mask_eq3(orc):
     assert (out["partner"][elig] >= 0).any()
 
 
+def test_merge_mask_eq3_from_sums(orc):
+    """Eq. 3 with the statistic given as sums over the drawing views: the mask tests the
+    mean (float32 quotient); a Gaussian drawn in no view has mean 0.  Same mask as the
+    precomputed mean."""
+    rng = np.random.default_rng(19)
+    sc = _voxel_scene(rng, 40, 4)
+    cnt = rng.integers(0, 6, sc.n).astype(np.float32)
+    mean = rng.uniform(0, 2e-3, sc.n).astype(np.float32)
+    sums = (mean * cnt).astype(np.float32)
+    ref_mean = np.where(cnt > 0, (sums.astype(np.float64) / np.maximum(cnt, 1)).astype(np.float32), 0)
+    a = orc.voxel_merge(sc, 0.02, grad_stat=sums, vis_count=cnt, grad_tau=1e-3)
+    b = orc.voxel_merge(sc, 0.02, grad_stat=ref_mean, grad_tau=1e-3)
+    np.testing.assert_array_equal(a["partner"], b["partner"])
+    elig = ref_mean < np.float32(1e-3)
+    assert np.all(a["partner"][~elig] == -1) and (a["partner"][elig] >= 0).any()
+    assert (cnt == 0).any() and np.all(a["partner"][(cnt == 0)] >= -1)
+
+
 def test_adam_step_one_closed_form(orc):
     rng = np.random.default_rng(10)
     p0 = rng.normal(size=100)
