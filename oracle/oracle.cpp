@@ -1179,3 +1179,128 @@ int orc_adam(int64_t n, double* param, const double* grad, double* m, double* v,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Mapping loss, Eq. 12.  SSIM (Wang et al.) with an 11x11 Gaussian window of standard
+// deviation 1.5 (normalised to sum 1), constants (0.01)^2 and (0.03)^2 for values in
+// [0, 1], evaluated at every pixel with the window cut by the image border (zero
+// padding).  Written as plain windowed sums; the gradient goes through the three window
+// moments of x (mean, mean of x^2, mean of x*y) that SSIM depends on.
+namespace {
+constexpr int kWin = 11, kHalf = 5;
+constexpr double kSigma = 1.5, kC1 = 0.01 * 0.01, kC2 = 0.03 * 0.03;
+
+void ssim_window(double w[kWin]) {
+  double sum = 0;
+  for (int i = 0; i < kWin; ++i) {
+    double t = i - kHalf;
+    w[i] = std::exp(-t * t / (2 * kSigma * kSigma));
+    sum += w[i];
+  }
+  for (int i = 0; i < kWin; ++i) w[i] /= sum;
+}
+}  // namespace
+
+int orc_mapping_loss(int32_t n_views, int32_t H, int32_t W, const double* x, const double* y,
+                     const double* d, const double* dt, double lambda, double w_depth,
+                     double* loss, double* g_rgb, double* g_depth) {
+  if (n_views < 0 || H <= 0 || W <= 0 || !x || !y || !loss) return -1;
+  double w1[kWin];
+  ssim_window(w1);
+  const int64_t HW = (int64_t)H * W;
+  std::vector<double> d1(HW), d2(HW), d3(HW);  // dS/dm1, dS/dm2, dS/dm3 per pixel
+  for (int v = 0; v < n_views; ++v) {
+    double l1 = 0, ssim_sum = 0, ld = 0;
+    for (int c = 0; c < 3; ++c) {
+      const double* X = x + ((int64_t)v * 3 + c) * HW;
+      const double* Y = y + ((int64_t)v * 3 + c) * HW;
+      double* G = g_rgb ? g_rgb + ((int64_t)v * 3 + c) * HW : nullptr;
+      for (int64_t p = 0; p < HW; ++p) l1 += std::fabs(X[p] - Y[p]);
+      for (int qy = 0; qy < H; ++qy)
+        for (int qx = 0; qx < W; ++qx) {
+          double mx = 0, my = 0, mxx = 0, myy = 0, mxy = 0;
+          for (int a = -kHalf; a <= kHalf; ++a)
+            for (int b = -kHalf; b <= kHalf; ++b) {
+              int py = qy + a, px = qx + b;
+              if (py < 0 || py >= H || px < 0 || px >= W) continue;  // zero padding
+              double wt = w1[a + kHalf] * w1[b + kHalf];
+              double xv = X[(int64_t)py * W + px], yv = Y[(int64_t)py * W + px];
+              mx += wt * xv; my += wt * yv;
+              mxx += wt * xv * xv; myy += wt * yv * yv; mxy += wt * xv * yv;
+            }
+          double sx = mxx - mx * mx, sy = myy - my * my, sxy = mxy - mx * my;
+          double A1 = 2 * mx * my + kC1, A2 = 2 * sxy + kC2;
+          double B1 = mx * mx + my * my + kC1, B2 = sx + sy + kC2;
+          double S = A1 * A2 / (B1 * B2);
+          ssim_sum += S;
+          // dS w.r.t. mu_x, sigma_x^2, sigma_xy, then to the moments m1 = E[x], m2 = E[x^2], m3 = E[xy]
+          double dmu = 2 * my * A2 / (B1 * B2) - S * 2 * mx / B1;
+          double dsx = -S / B2;
+          double dsxy = 2 * A1 / (B1 * B2);
+          int64_t q = (int64_t)qy * W + qx;
+          d1[q] = dmu + dsx * (-2 * mx) + dsxy * (-my);
+          d2[q] = dsx;
+          d3[q] = dsxy;
+        }
+      if (G) {
+        const double n = 3.0 * (double)HW;
+        for (int py = 0; py < H; ++py)
+          for (int px = 0; px < W; ++px) {
+            double a1 = 0, a2 = 0, a3 = 0;
+            for (int a = -kHalf; a <= kHalf; ++a)
+              for (int b = -kHalf; b <= kHalf; ++b) {
+                int qy = py + a, qx = px + b;
+                if (qy < 0 || qy >= H || qx < 0 || qx >= W) continue;  // windows exist at image pixels only
+                double wt = w1[a + kHalf] * w1[b + kHalf];
+                int64_t q = (int64_t)qy * W + qx;
+                a1 += wt * d1[q]; a2 += wt * d2[q]; a3 += wt * d3[q];
+              }
+            int64_t p = (int64_t)py * W + px;
+            double dssim = (a1 + 2 * X[p] * a2 + Y[p] * a3) / n;
+            double diff = X[p] - Y[p];
+            double sgn = diff > 0 ? 1.0 : (diff < 0 ? -1.0 : 0.0);
+            G[p] = (1 - lambda) * sgn / n - lambda * dssim;
+          }
+      }
+    }
+    if (dt && d) {
+      const double* D = d + (int64_t)v * HW;
+      const double* Dt = dt + (int64_t)v * HW;
+      double* GD = g_depth ? g_depth + (int64_t)v * HW : nullptr;
+      for (int64_t p = 0; p < HW; ++p) {
+        bool valid = Dt[p] > 0;
+        double diff = D[p] - Dt[p];
+        if (valid) ld += std::fabs(diff);
+        if (GD) GD[p] = valid ? w_depth * (diff > 0 ? 1.0 : (diff < 0 ? -1.0 : 0.0)) / (double)HW : 0.0;
+      }
+    } else if (g_depth) {
+      for (int64_t p = 0; p < HW; ++p) g_depth[(int64_t)v * HW + p] = 0;
+    }
+    loss[3 * v] = (1 - lambda) * l1 / (3.0 * (double)HW);
+    loss[3 * v + 1] = lambda * (1 - ssim_sum / (3.0 * (double)HW));
+    loss[3 * v + 2] = w_depth * ld / (double)HW;
+  }
+  return 0;
+}
+
+int orc_iso_loss(int64_t n, const double* log_scales, double w_iso, double* loss, double* grad_ls) {
+  if (n < 0 || !loss) return -1;
+  double acc = 0;
+  const double scale = n > 0 ? w_iso / (3.0 * (double)n) : 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double s[3], mean = 0;
+    for (int k = 0; k < 3; ++k) { s[k] = std::exp(log_scales[3 * i + k]); mean += s[k] / 3; }
+    double sg[3], sgsum = 0;
+    for (int k = 0; k < 3; ++k) {
+      double dlt = s[k] - mean;
+      acc += std::fabs(dlt);
+      sg[k] = dlt > 0 ? 1.0 : (dlt < 0 ? -1.0 : 0.0);
+      sgsum += sg[k];
+    }
+    if (grad_ls)
+      for (int k = 0; k < 3; ++k)  // d|s_k - mean|/ds_j summed over k, times ds_j/dlog s_j = s_j
+        grad_ls[3 * i + k] += scale * (sg[k] - sgsum / 3) * s[k];
+  }
+  *loss = scale * acc;
+  return 0;
+}

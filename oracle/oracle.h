@@ -169,6 +169,23 @@ int orc_covariance(const double q[4], const double s[3], double S[9]);
 int orc_adam(int64_t n, double* param, const double* grad, double* m, double* v,
              double lr, double b1, double b2, double eps, int32_t step);
 
+/* ---- mapping loss (Sec. II-E, Eq. 12) ----
+ * Per view, rendered x and target y (planar [3][H][W]), depth d and target depth dt
+ * ([H][W], dt NULL = no depth term):
+ *   L = (1-lambda) mean|x-y| + lambda (1 - mean SSIM(x, y)) + w_depth mean_p [dt>0] |d-dt|
+ * mean over the 3HW values (HW for depth).  SSIM per channel and pixel with the 11x11
+ * Gaussian window (sigma 1.5, normalised), C1 = 0.01^2, C2 = 0.03^2, windows cut at the
+ * image border with zero padding (the map has the image's size).  Per view the three
+ * terms go to loss[3*v .. 3*v+2] = (L1 part, SSIM part, depth part), already weighted.
+ * g_rgb / g_depth (optional) receive dL/dx and dL/dd (overwritten). */
+int orc_mapping_loss(int32_t n_views, int32_t H, int32_t W, const double* x, const double* y,
+                     const double* d, const double* dt, double lambda, double w_depth,
+                     double* loss, double* g_rgb, double* g_depth);
+
+/* Isotropic term (after MonoGS): w_iso / (3n) sum_i sum_k |s_ik - mean_k s_ik|, s = exp(log s).
+ * *loss receives the value; grad_ls (optional) receives dL/dlog_scale ADDED to it. */
+int orc_iso_loss(int64_t n, const double* log_scales, double w_iso, double* loss, double* grad_ls);
+
 #ifdef __cplusplus
 }
 #endif

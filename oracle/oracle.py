@@ -291,3 +291,29 @@ def adam(param, grad, m, v, lr, b1, b2, eps, step):
     rc = lib().orc_adam(C.c_int64(param.size), _p(param), _p(g), _p(m), _p(v), C.c_double(lr),
                         C.c_double(b1), C.c_double(b2), C.c_double(eps), C.c_int32(step))
     assert rc == 0
+
+
+def mapping_loss(x, y, d=None, dt=None, lam=0.2, w_depth=1.0, grads=True):
+    """Eq. 12 per view: x, y [V,3,H,W]; d, dt [V,H,W] (optional).  Returns dict with
+    loss [V,3] (weighted L1, SSIM and depth parts) and g_rgb / g_depth."""
+    x64, y64 = _f64(x), _f64(y)
+    V, _, H, W = x64.shape
+    loss = np.zeros((V, 3))
+    g_rgb = np.zeros_like(x64) if grads else None
+    d64 = None if d is None else _f64(d)
+    dt64 = None if dt is None else _f64(dt)
+    g_depth = np.zeros((V, H, W)) if grads else None
+    rc = lib().orc_mapping_loss(C.c_int32(V), C.c_int32(H), C.c_int32(W), _p(x64), _p(y64), _p(d64),
+                                _p(dt64), C.c_double(lam), C.c_double(w_depth), _p(loss), _p(g_rgb),
+                                _p(g_depth))
+    assert rc == 0
+    return dict(loss=loss, g_rgb=g_rgb, g_depth=g_depth)
+
+
+def iso_loss(log_scales, w_iso=1.0):
+    ls = _f64(log_scales)
+    grad = np.zeros_like(ls)
+    val = C.c_double(0)
+    rc = lib().orc_iso_loss(C.c_int64(ls.shape[0]), _p(ls), C.c_double(w_iso), C.byref(val), _p(grad))
+    assert rc == 0
+    return val.value, grad
