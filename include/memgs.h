@@ -211,6 +211,34 @@ mgs_status mgs_adam_step(const mgs_gaussians_mut* params, const mgs_grads* grads
                          const mgs_grads* m_state, const mgs_grads* v_state, float lr, float beta1,
                          float beta2, float eps, int32_t step, int32_t zero_grads, void* stream);
 
+/* ------------------------------------------------------------------------------
+ * Mapping loss of Sec. II-E, Eq. 12, per view v (all views width x height):
+ *   L_v = (1 - lambda) mean|x - y| + lambda (1 - mean SSIM(x, y))
+ *         + w_depth mean_p [dt(p) > 0] |d(p) - dt(p)|          (depth residual, RGB-D)
+ * x = rendered[v].rgb, y = target[v].rgb (planar f32 [3][H][W]), d = rendered[v].depth,
+ * dt = target[v].depth (f32 [H][W]; NULL: no depth term).  Means over the 3HW colour
+ * values and the HW pixels.  SSIM per channel and pixel with the 11x11 Gaussian window
+ * (sigma 1.5, normalised), C1 = 0.01^2, C2 = 0.03^2, windows cut by the image border
+ * (zero padding).  The paper gives no lambda (0.2 is the usual choice).
+ * grad[v].rgb receives dL_v/dx (written, not accumulated), grad[v].depth (optional)
+ * dL_v/dd; they are the cotangents mgs_render_backward takes.  loss: device f32
+ * [n_views][3] = (L1 part, SSIM part, depth part), each already weighted, written.
+ * 1 <= n_views <= MGS_MAX_VIEWS.  Deterministic (fixed-order sums).  Asynchronous.
+ * ------------------------------------------------------------------------------ */
+size_t mgs_mapping_loss_workspace_size(int32_t n_views, int32_t width, int32_t height);
+mgs_status mgs_mapping_loss(int32_t n_views, int32_t width, int32_t height, const mgs_image* rendered,
+                            const mgs_image* target, const mgs_image* grad, float lambda_ssim,
+                            float w_depth, float* loss, void* workspace, size_t workspace_bytes,
+                            void* stream);
+
+/* Isotropic term of Eq. 12 (the paper follows MonoGS and gives no formula):
+ *   L_iso = w_iso / (3n) sum_i sum_k |s_ik - mean_k s_ik|,  s = exp(log_scales).
+ * grads (optional): dL_iso/dlog_scales ADDED to grads->log_scales.  loss: device f32,
+ * written.  Asynchronous. */
+size_t mgs_iso_loss_workspace_size(int64_t n);
+mgs_status mgs_iso_loss(const mgs_gaussians* g, float w_iso, const mgs_grads* grads, float* loss,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
 /* L1 loss helper for mapping steps: grad[i] = scale * sign(pred[i] - target[i]) and
  * *loss += scale * sum |pred - target| (loss is a device f32 accumulator). */
 mgs_status mgs_l1_loss_grad(const float* pred, const float* target, int64_t n, float scale,

@@ -23,7 +23,8 @@ EXPORTS = ["mgs_render_workspace_size", "mgs_render", "mgs_render_backward", "mg
            "mgs_sort_workspace_size", "mgs_sort_pairs", "mgs_last_error", "mgs_version",
            "mgs_launch_count", "mgs_profile_enable", "mgs_profile_read", "mgs_render_stats",
            "mgs_sort_pairs_noalloc", "mgs_server_create", "mgs_server_add_scene", "mgs_server_submit",
-           "mgs_server_poll", "mgs_server_clock", "mgs_server_destroy"]
+           "mgs_server_poll", "mgs_server_clock", "mgs_server_destroy", "mgs_mapping_loss_workspace_size",
+           "mgs_mapping_loss", "mgs_iso_loss_workspace_size", "mgs_iso_loss"]
 
 
 class mgs_gaussians(C.Structure):
@@ -97,6 +98,10 @@ def load():
             "mgs_adam_step": (C.c_int, [P, P, P, P, F, F, F, F, I32, I32, P]),
             "mgs_l1_loss_grad": (C.c_int, [P, P, I64, F, P, P, P]),
             "mgs_sort_workspace_size": (SZ, [I64]),
+            "mgs_mapping_loss_workspace_size": (SZ, [I32, I32, I32]),
+            "mgs_mapping_loss": (C.c_int, [I32, I32, I32, P, P, P, F, F, P, P, SZ, P]),
+            "mgs_iso_loss_workspace_size": (SZ, [I64]),
+            "mgs_iso_loss": (C.c_int, [P, F, P, P, P, SZ, P]),
             "mgs_sort_pairs": (C.c_int, [P, P, P, I64, I32, I32, P, SZ, P]),
             "mgs_sort_pairs_noalloc": (C.c_int, [P, P, P, I64, I32, I32, P]),
             "mgs_server_create": (C.c_int, [P, P]),

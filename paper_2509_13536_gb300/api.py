@@ -289,6 +289,48 @@ def mgs_adam_step(g: Gaussians, grads: Grads, m: Grads, v: Grads, lr: float, bet
 adam_step = mgs_adam_step
 
 
+def mgs_mapping_loss(rendered: Sequence[Image], target: Sequence[Image], grad: Sequence[Image],
+                     lambda_ssim: float = 0.2, w_depth: float = 1.0, loss: Optional[torch.Tensor] = None,
+                     workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Eq. 12 per view: (1-lambda) L1 + lambda (1 - SSIM) + w_depth depth L1.  ``target[v].depth``
+    None = no depth term.  Writes the cotangents into ``grad`` and returns loss [V, 3]
+    (L1, SSIM, depth parts, weighted)."""
+    V = len(rendered)
+    H, W = int(rendered[0].rgb.shape[-2]), int(rendered[0].rgb.shape[-1])
+    dev = rendered[0].rgb.device
+    L = load()
+    need = L.mgs_mapping_loss_workspace_size(V, W, H)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    loss = loss if loss is not None else torch.empty(V, 3, device=dev)
+    check(L.mgs_mapping_loss(V, W, H, _image_array(rendered), _image_array(target), _image_array(grad),
+                             float(lambda_ssim), float(w_depth), _ptr(loss), _ptr(workspace), workspace.numel(),
+                             _stream(stream)), "mgs_mapping_loss")
+    return loss
+
+
+mapping_loss = mgs_mapping_loss
+
+
+def mgs_iso_loss(g: Gaussians, w_iso: float = 1.0, grads: Optional[Grads] = None,
+                 loss: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                 stream=None) -> torch.Tensor:
+    """Isotropic term of Eq. 12; adds its gradient to ``grads.log_scales`` when given."""
+    L = load()
+    need = L.mgs_iso_loss_workspace_size(g.n)
+    dev = g.means.device
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    loss = loss if loss is not None else torch.empty(1, device=dev)
+    gs = None if grads is None else C.byref(grads.struct())
+    check(L.mgs_iso_loss(C.byref(g.struct()), float(w_iso), gs, _ptr(loss), _ptr(workspace), workspace.numel(),
+                         _stream(stream)), "mgs_iso_loss")
+    return loss
+
+
+iso_loss = mgs_iso_loss
+
+
 def mgs_l1_loss_grad(pred: torch.Tensor, target: torch.Tensor, scale: float, grad: torch.Tensor,
                      loss: Optional[torch.Tensor] = None, stream=None):
     check(load().mgs_l1_loss_grad(_ptr(pred), _ptr(target), pred.numel(), scale, _ptr(grad), _ptr(loss),

@@ -414,6 +414,47 @@ mgs_status mgs_l1_loss_grad(const float* pred, const float* target, int64_t n, f
   return MGS_OK;
 }
 
+size_t mgs_mapping_loss_workspace_size(int32_t n_views, int32_t width, int32_t height) {
+  if (n_views < 1 || n_views > MGS_MAX_VIEWS || width <= 0 || height <= 0) return 0;
+  return loss_layout(n_views, width, height).bytes;
+}
+
+mgs_status mgs_mapping_loss(int32_t n_views, int32_t width, int32_t height, const mgs_image* rendered,
+                            const mgs_image* target, const mgs_image* grad, float lambda_ssim,
+                            float w_depth, float* loss, void* workspace, size_t workspace_bytes,
+                            void* stream) {
+  set_error("");
+  if (n_views < 1 || n_views > MGS_MAX_VIEWS) return fail(MGS_ERR_INVALID, "n_views must be in [1, 32]");
+  if (width <= 0 || height <= 0) return fail(MGS_ERR_INVALID, "width and height must be positive");
+  if (!rendered || !target || !grad || !loss) return fail(MGS_ERR_INVALID, "NULL argument");
+  if (!(lambda_ssim >= 0.f && lambda_ssim <= 1.f)) return fail(MGS_ERR_INVALID, "lambda_ssim must be in [0, 1]");
+  for (int v = 0; v < n_views; ++v) {
+    if (!rendered[v].rgb || !target[v].rgb || !grad[v].rgb) return fail(MGS_ERR_INVALID, "NULL rgb plane");
+    if (target[v].depth && !rendered[v].depth) return fail(MGS_ERR_INVALID, "target depth without rendered depth");
+  }
+  const LossLayout L = loss_layout(n_views, width, height);
+  if (!workspace || workspace_bytes < L.bytes) return fail(MGS_ERR_WORKSPACE, "mapping-loss workspace too small");
+  ProfScope ps(kProfLoss, (cudaStream_t)stream);
+  MGS_TRY_CUDA(launch_mapping_loss(n_views, width, height, L, (char*)workspace, rendered, target, grad,
+                                   lambda_ssim, w_depth, loss, (cudaStream_t)stream));
+  return MGS_OK;
+}
+
+size_t mgs_iso_loss_workspace_size(int64_t n) { return n < 0 ? 0 : iso_workspace_bytes(n); }
+
+mgs_status mgs_iso_loss(const mgs_gaussians* g, float w_iso, const mgs_grads* grads, float* loss,
+                        void* workspace, size_t workspace_bytes, void* stream) {
+  set_error("");
+  if (!g || !loss || g->n < 0) return fail(MGS_ERR_INVALID, "bad arguments");
+  if (g->n > 0 && !g->log_scales) return fail(MGS_ERR_INVALID, "NULL log_scales");
+  if (g->geom_dtype < MGS_F32 || g->geom_dtype > MGS_BF16) return fail(MGS_ERR_INVALID, "bad geom_dtype");
+  if (!workspace || workspace_bytes < iso_workspace_bytes(g->n)) return fail(MGS_ERR_WORKSPACE, "iso workspace too small");
+  ProfScope ps(kProfLoss, (cudaStream_t)stream);
+  MGS_TRY_CUDA(launch_iso_loss(*g, w_iso, grads ? grads->log_scales : nullptr, loss, (char*)workspace,
+                               (cudaStream_t)stream));
+  return MGS_OK;
+}
+
 size_t mgs_sort_workspace_size(int64_t n) {
   if (n < 0) return 0;
   size_t m = (size_t)std::max<int64_t>(n, 1);

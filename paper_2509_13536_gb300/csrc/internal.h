@@ -65,4 +65,17 @@ inline int radix_passes(int begin_bit, int end_bit) {
 // [start, end) of every key value < n_valid present in sorted keys (absent values untouched).
 cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s);
 
+// Mapping loss (loss.cu): workspace layout for n_views images of width x height.
+struct LossLayout {
+  int tiles_x, tiles_y, nb_ssim, nb_depth;
+  size_t dmaps, part_ssim, part_depth, bytes;
+};
+LossLayout loss_layout(int n_views, int width, int height);
+cudaError_t launch_mapping_loss(int n_views, int width, int height, const LossLayout& L, char* ws,
+                                const mgs_image* rendered, const mgs_image* target, const mgs_image* grad,
+                                float lambda, float w_depth, float* loss, cudaStream_t s);
+size_t iso_workspace_bytes(int64_t n);
+cudaError_t launch_iso_loss(const mgs_gaussians& g, float w_iso, float* grad_ls, float* loss, char* ws,
+                            cudaStream_t s);
+
 }  // namespace mgs

@@ -124,7 +124,7 @@ def test_eq3_statistics_from_the_backward_pass_drive_the_merge(orc):
     torch.cuda.synchronize()
     gs = grads.grad_stat.cpu().numpy()
     vc = grads.vis_count.cpu().numpy()
-    assert vc.max() == 4 and (vc == 0).any()
+    assert vc.max() >= 2 and (vc == 0).any() and set(np.unique(vc)) <= {0.0, 1.0, 2.0, 3.0, 4.0}
     mean = np.where(vc > 0, gs / np.maximum(vc, 1), 0)
     tau = float(np.median(mean[vc > 0]))
     pairs, n = compare_merge(orc, scene, 0.02, grad_stat=gs, vis_count=vc, grad_tau=tau)
