@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--views", type=int, default=8, help="keyframes per step (8 = the benchmark workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-precision", action="store_true")
+    p.add_argument("--no-eq12", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-rate", type=float, default=200.0)
@@ -250,6 +251,36 @@ def precision_leg(args, api, torch, scene, cams, make_step, dev):
     return out
 
 
+def eq12_leg(args, api, torch, scene, make_step, dev, V):
+    """The mapping step with the paper's loss (Eq. 12: 0.8 L1 + 0.2 (1 - SSIM) on rgb,
+    0.1 x depth L1, isotropic term) instead of the L1 stand-in: frames/s and the loss
+    kernels' share."""
+    g = api.Gaussians.from_scene(scene, dev)
+    step, st = make_step(g, "eq12")
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    k_steps = max(3, args.steps // 2)
+    api.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(k_steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    prof = api.profile_read()
+    api.profile_enable(False)
+    ms = e0.elapsed_time(e1) / k_steps
+    lv = st["loss_views"].sum(0).cpu().tolist()
+    res = {"frames_per_s": V / (ms / 1e3), "ms_per_step": ms, "steps": k_steps,
+           "loss_kernels_ms_per_step": prof.get("l1_loss", (0.0, 0))[0] / k_steps,
+           "last_loss": {"l1": lv[0], "ssim": lv[1], "depth": lv[2], "iso": float(st["loss_iso"].item())},
+           "weights": "lambda_ssim 0.2, w_depth 0.1, w_iso 1"}
+    del g, step, st
+    torch.cuda.empty_cache()
+    return res
+
+
 SERVE_RES = [(320, 240), (640, 480), (1200, 680), (1920, 1080)]
 
 
@@ -344,8 +375,10 @@ def run_ours(args):
     pert = scene.copy()
     pert.means += rng.normal(0, 0.005, pert.means.shape).astype(np.float32)
     pert.sh += rng.normal(0, 0.02, pert.sh.shape).astype(np.float32)
-    def make_step(g):
-        """One mapping step on map g (all buffers allocated here, none inside the step)."""
+    def make_step(g, loss_kind="l1"):
+        """One mapping step on map g (all buffers allocated here, none inside the step).
+        loss_kind "l1": L1 on rgb and 0.1 x L1 on depth (the benchmark's stand-in);
+        "eq12": Eq. 12, 0.8 L1 + 0.2 (1 - SSIM) + 0.1 depth L1 + isotropic term."""
         grads = api.Grads.zeros_like(g)
         m = api.Grads.zeros_like(g, stats=False)
         v = api.Grads.zeros_like(g, stats=False)
@@ -365,14 +398,26 @@ def run_ours(args):
         s_rgb = 1.0 / rgb.numel()
         s_depth = 0.1 / depth.numel()
         state = {"step": 0, "n_out": g.n, "ws": ws, "loss": loss}
+        if loss_kind == "eq12":
+            targets = [api.Image(target_rgb[i], target_depth[i], None) for i in range(V)]
+            lws = torch.empty(api.load().mgs_mapping_loss_workspace_size(V, W, H), dtype=torch.uint8, device=dev)
+            iws = torch.empty(api.load().mgs_iso_loss_workspace_size(g.n), dtype=torch.uint8, device=dev)
+            loss_v = torch.zeros(V, 3, device=dev)
+            loss_iso = torch.zeros(1, device=dev)
+            state.update(loss_views=loss_v, loss_iso=loss_iso)
 
         def step():
             state["step"] += 1
             api.mgs_render(g, cams, out, ws)
-            loss.zero_()
-            api.mgs_l1_loss_grad(rgb, target_rgb, s_rgb, g_rgb, loss)
-            api.mgs_l1_loss_grad(depth, target_depth, s_depth, g_depth, loss)
+            if loss_kind == "eq12":
+                api.mapping_loss(out, targets, dL, 0.2, 0.1, loss=loss_v, workspace=lws)
+            else:
+                loss.zero_()
+                api.mgs_l1_loss_grad(rgb, target_rgb, s_rgb, g_rgb, loss)
+                api.mgs_l1_loss_grad(depth, target_depth, s_depth, g_depth, loss)
             api.mgs_render_backward(g, cams, dL, ws, grads)
+            if loss_kind == "eq12":
+                api.iso_loss(g, 1.0, grads, loss=loss_iso, workspace=iws)
             api.mgs_adam_step(g, grads, m, v, 1e-3, 0.9, 0.999, 1e-8, state["step"], zero_grads=True)
             res, _, _ = api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox)
             state["n_out"] = res.n
@@ -469,6 +514,9 @@ def run_ours(args):
         roofline = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                     "traffic": None}
 
+    eq12 = None
+    if world == 1 and not args.no_eq12:
+        eq12 = eq12_leg(args, api, torch, pert, make_step, dev, V)
     precision = None
     if world == 1 and not args.no_precision:
         precision = precision_leg(args, api, torch, pert, cams, make_step, dev)
@@ -487,6 +535,8 @@ def run_ours(args):
                                           "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "clocks": csum, "kernels": kern, "fragments": stats,
             "merge_survivors": state["n_out"]}
+    if eq12:
+        line["eq12_step"] = eq12
     if precision:
         line["precision"] = precision
     if serving:
