@@ -251,6 +251,34 @@ def precision_leg(args, api, torch, scene, cams, make_step, dev):
     return out
 
 
+def merge_solver_leg(api, torch, scene, dev):
+    """The voxel merge of the 1M-Gaussian map with each Eq. 9 solver: the closed form and
+    the paper's L-BFGS (merged pairs, mean iterations per pair, ms per call)."""
+    g = api.Gaussians.from_scene(scene, dev)
+    ws = torch.empty(api.load().mgs_voxel_merge_workspace_size(g.n), dtype=torch.uint8, device=dev)
+    out, partner = g.empty_like(), torch.empty(g.n, dtype=torch.int32, device=dev)
+    vox = torch.empty(g.n, 3, dtype=torch.int32, device=dev)
+    res = {}
+    for solver in ("closed_form", "lbfgs"):
+        call = lambda: api.mgs_voxel_merge(g, 0.02, workspace=ws, out=out, partner=partner, vox=vox, solver=solver)
+        call()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            call()
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        pairs, iters = api.merge_stats()
+        res[solver] = {"ms_per_call": float(np.median(t)), "pairs": pairs,
+                       "iterations_per_pair": (iters / pairs) if pairs and solver == "lbfgs" else None}
+    del g, ws, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def eq12_leg(args, api, torch, scene, make_step, dev, V):
     """The mapping step with the paper's loss (Eq. 12: 0.8 L1 + 0.2 (1 - SSIM) on rgb,
     0.1 x depth L1, isotropic term) instead of the L1 stand-in: frames/s and the loss
@@ -517,6 +545,7 @@ def run_ours(args):
     eq12 = None
     if world == 1 and not args.no_eq12:
         eq12 = eq12_leg(args, api, torch, pert, make_step, dev, V)
+        eq12["merge_solvers"] = merge_solver_leg(api, torch, pert, dev)
     precision = None
     if world == 1 and not args.no_precision:
         precision = precision_leg(args, api, torch, pert, cams, make_step, dev)

@@ -165,7 +165,8 @@ mgs_status mgs_project(const mgs_gaussians* g, const mgs_camera* cam_host, float
  * greedy=1: repeatedly merge the unmatched pair of smallest (d^2, birth_i, birth_j);
  * greedy=0: only the smallest pair of each voxel.  A merged pair keeps G_i's slot:
  * mean by Eq. 6, covariance the equal-weight 2-Wasserstein barycentre (the minimiser
- * of Eq. 9, in closed form), stored as (quaternion with w >= 0, scales descending),
+ * of Eq. 9: in closed form, or by L-BFGS with solver = 1), stored as (quaternion with
+ * w >= 0, scales descending),
  * opacity, SH and birth copied from the older G_i; G_j is dropped.  Survivors keep
  * the input order.
  * ------------------------------------------------------------------------------ */
@@ -182,8 +183,17 @@ typedef struct {
                               quotient grad_stat / vis_count (0 for a Gaussian drawn in no
                               view), against grad_tau.  NULL: grad_stat is the mean itself. */
   int32_t greedy;          /* 1 or 0 */
-  int32_t reserved;
+  int32_t solver;          /* merged covariance: 0 = the closed-form minimiser of Eq. 9;
+                              1 = the paper's route, L-BFGS over (q, s) from the Eq. 10
+                              start (slerp t = 0.5, mean scale + (0.001, 0.002, 0.003)),
+                              float32, memory 6, line search on the directional
+                              derivative, at most 200 iterations */
 } mgs_merge_params;
+
+/* Counters of the calling thread's last successful mgs_voxel_merge: out[0] = merged
+ * pairs, out[1] = L-BFGS iterations summed over the pairs (0 with solver 0).  Not part
+ * of the paper. */
+void mgs_merge_stats(int64_t out[2]);
 
 size_t mgs_voxel_merge_workspace_size(int64_t n);
 

@@ -24,7 +24,7 @@ EXPORTS = ["mgs_render_workspace_size", "mgs_render", "mgs_render_backward", "mg
            "mgs_launch_count", "mgs_profile_enable", "mgs_profile_read", "mgs_render_stats",
            "mgs_sort_pairs_noalloc", "mgs_server_create", "mgs_server_add_scene", "mgs_server_submit",
            "mgs_server_poll", "mgs_server_clock", "mgs_server_destroy", "mgs_mapping_loss_workspace_size",
-           "mgs_mapping_loss", "mgs_iso_loss_workspace_size", "mgs_iso_loss"]
+           "mgs_mapping_loss", "mgs_iso_loss_workspace_size", "mgs_iso_loss", "mgs_merge_stats"]
 
 
 class mgs_gaussians(C.Structure):
@@ -59,7 +59,7 @@ class mgs_server_config(C.Structure):
 class mgs_merge_params(C.Structure):
     _fields_ = [("chi2", C.c_float), ("grad_tau", C.c_float), ("kf_min", C.c_int32),
                 ("kf_max", C.c_int32), ("grad_stat", C.c_void_p), ("kf_id", C.c_void_p),
-                ("vis_count", C.c_void_p), ("greedy", C.c_int32), ("reserved", C.c_int32)]
+                ("vis_count", C.c_void_p), ("greedy", C.c_int32), ("solver", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -102,6 +102,7 @@ def load():
             "mgs_mapping_loss": (C.c_int, [I32, I32, I32, P, P, P, F, F, P, P, SZ, P]),
             "mgs_iso_loss_workspace_size": (SZ, [I64]),
             "mgs_iso_loss": (C.c_int, [P, F, P, P, P, SZ, P]),
+            "mgs_merge_stats": (None, [P]),
             "mgs_sort_pairs": (C.c_int, [P, P, P, I64, I32, I32, P, SZ, P]),
             "mgs_sort_pairs_noalloc": (C.c_int, [P, P, P, I64, I32, I32, P]),
             "mgs_server_create": (C.c_int, [P, P]),

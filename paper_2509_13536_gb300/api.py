@@ -248,7 +248,7 @@ def mgs_voxel_merge(g: Gaussians, voxel_size: float, chi2: float = 7.815, greedy
                     kf_id: Optional[torch.Tensor] = None, kf_min: int = 0, kf_max: int = 0,
                     workspace: Optional[torch.Tensor] = None, out: Optional[Gaussians] = None,
                     partner: Optional[torch.Tensor] = None, vox: Optional[torch.Tensor] = None,
-                    vis_count: Optional[torch.Tensor] = None, stream=None):
+                    vis_count: Optional[torch.Tensor] = None, solver: str = "closed_form", stream=None):
     """voxel_merge(gaussians, voxel_size, thresholds) -> (gaussians, partner, voxel coords).
 
     ``grad_stat`` with ``vis_count``: the sums the backward pass accumulates (Grads.grad_stat,
@@ -264,8 +264,10 @@ def mgs_voxel_merge(g: Gaussians, voxel_size: float, chi2: float = 7.815, greedy
     out = out if out is not None else g.empty_like()
     partner = partner if partner is not None else torch.empty(n, dtype=torch.int32, device=dev)
     vox = vox if vox is not None else torch.empty(n, 3, dtype=torch.int32, device=dev)
+    if solver not in ("closed_form", "lbfgs"):
+        raise ValueError("solver is 'closed_form' or 'lbfgs'")
     p = _abi.mgs_merge_params(chi2, grad_tau, kf_min, kf_max, _ptr(grad_stat), _ptr(kf_id),
-                              _ptr(vis_count), 1 if greedy else 0, 0)
+                              _ptr(vis_count), 1 if greedy else 0, 1 if solver == "lbfgs" else 0)
     n_out = C.c_int64(0)
     check(L.mgs_voxel_merge(C.byref(g.struct()), float(voxel_size), C.byref(p), C.byref(out.struct()),
                             _ptr(partner), _ptr(vox), C.byref(n_out), _ptr(workspace),
@@ -277,6 +279,13 @@ def mgs_voxel_merge(g: Gaussians, voxel_size: float, chi2: float = 7.815, greedy
 
 
 voxel_merge = mgs_voxel_merge
+
+
+def merge_stats():
+    """(merged pairs, L-BFGS iterations) of this thread's last mgs_voxel_merge."""
+    out = (C.c_int64 * 2)()
+    load().mgs_merge_stats(out)
+    return int(out[0]), int(out[1])
 
 
 def mgs_adam_step(g: Gaussians, grads: Grads, m: Grads, v: Grads, lr: float, beta1=0.9,

@@ -364,6 +364,7 @@ mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_
   if (!p || !out || !n_out_host) return fail(MGS_ERR_INVALID, "params, out or n_out_host is NULL");
   if (!(voxel_size > 0) || !std::isfinite(voxel_size)) return fail(MGS_ERR_INVALID, "voxel_size must be > 0");
   if (!(p->chi2 > 0)) return fail(MGS_ERR_INVALID, "chi2 must be > 0");
+  if (p->solver != 0 && p->solver != 1) return fail(MGS_ERR_INVALID, "solver must be 0 (closed form) or 1 (L-BFGS)");
   if (out->n < in->n || out->sh_degree != in->sh_degree || out->attr_dtype != in->attr_dtype ||
       out->geom_dtype != in->geom_dtype)
     return fail(MGS_ERR_INVALID, "out must have capacity >= n and the same sh_degree / attr_dtype / geom_dtype");
@@ -412,6 +413,12 @@ mgs_status mgs_l1_loss_grad(const float* pred, const float* target, int64_t n, f
   ProfScope ps(kProfLoss, (cudaStream_t)stream);
   MGS_TRY_CUDA(launch_l1(pred, target, n, scale, grad, loss, (cudaStream_t)stream));
   return MGS_OK;
+}
+
+void mgs_merge_stats(int64_t out[2]) {
+  if (!out) return;
+  out[0] = last_merge_stats().pairs;
+  out[1] = last_merge_stats().lbfgs_iterations;
 }
 
 size_t mgs_mapping_loss_workspace_size(int32_t n_views, int32_t width, int32_t height) {

@@ -65,6 +65,12 @@ inline int radix_passes(int begin_bit, int end_bit) {
 // [start, end) of every key value < n_valid present in sorted keys (absent values untouched).
 cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s);
 
+// Counters of the calling thread's last mgs_voxel_merge (merge.cu).
+struct MergeStats {
+  int64_t pairs = 0, lbfgs_iterations = 0;
+};
+MergeStats& last_merge_stats();
+
 // Mapping loss (loss.cu): workspace layout for n_views images of width x height.
 struct LossLayout {
   int tiles_x, tiles_y, nb_ssim, nb_depth;

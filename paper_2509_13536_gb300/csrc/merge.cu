@@ -13,6 +13,8 @@
 //                    equal-weight 2-Wasserstein barycentre (minimiser of Eq. 9) in
 //                    closed form, eigen-decomposition back to (quaternion, scales).
 //  5. ordered compaction: survivors keep input order, merged values in G_i's slot.
+#include <cstring>
+
 #include "internal.h"
 
 namespace mgs {
@@ -131,10 +133,201 @@ __device__ void rot_quat(const float R[9], float q[4]) {
   for (int k = 0; k < 4; ++k) q[k] *= n;
 }
 
+// ---- Eq. 9 by the paper's solver: L-BFGS over (q, s) from the Eq. 10 start ----------
+// Objective W2^2(Sk, A) + W2^2(Sk, B) with Sk = R(q/|q|) diag(s^2) R^T, all in the
+// frame of Sigma_i.  W2^2(Sk, X) = tr Sk + tr X - 2 tr (Sk^1/2 X Sk^1/2)^1/2 (Eq. 8) and
+// dW2^2/dSk = I - T, T = Sk^-1/2 (Sk^1/2 X Sk^1/2)^1/2 Sk^-1/2 (the transport map).
+constexpr int kLbfgsMem = 6, kLbfgsIters = 200;
+
+// C = H X H for symmetric H, X (row-major 3x3), result symmetrised
+__device__ __forceinline__ void sandwich(const float H[9], const float X[9], float C[9]) {
+  float t[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) t[3 * a + b] = H[3 * a] * X[b] + H[3 * a + 1] * X[3 + b] + H[3 * a + 2] * X[6 + b];
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b) {
+      const float x = t[3 * a] * H[b] + t[3 * a + 1] * H[3 + b] + t[3 * a + 2] * H[6 + b];
+      C[3 * a + b] = x;
+      C[3 * b + a] = x;
+    }
+}
+
+__device__ __forceinline__ void rdrt9(const float R[9], const float d[3], float o[9]) {
+  float u[6];
+  rdrt(R, d, u);
+  o[0] = u[0]; o[1] = u[1]; o[2] = u[2]; o[3] = u[1]; o[4] = u[3]; o[5] = u[4]; o[6] = u[2]; o[7] = u[4]; o[8] = u[5];
+}
+
+// f(th) and its gradient; th = (q[4], s[3]).  *gsig (optional): Frobenius norm of the
+// gradient with respect to Sk itself, 2I - T_A - T_B, which vanishes only at the minimum.
+__device__ float w2_objective(const float th[7], const float A[9], const float B[9], float g[7],
+                              float* gsig = nullptr) {
+  const float qn2 = th[0] * th[0] + th[1] * th[1] + th[2] * th[2] + th[3] * th[3];
+  const float iq = rsqrtf(qn2);
+  const float qn[4] = {th[0] * iq, th[1] * iq, th[2] * iq, th[3] * iq};
+  float R[9];
+  quat_rot(qn, R);
+  const float s[3] = {th[4], th[5], th[6]};
+  const float as[3] = {fabsf(s[0]), fabsf(s[1]), fabsf(s[2])};
+  const float ias[3] = {1.f / as[0], 1.f / as[1], 1.f / as[2]};
+  float Hh[9], Hi[9];  // Sk^1/2, Sk^-1/2
+  rdrt9(R, as, Hh);
+  rdrt9(R, ias, Hi);
+  float f = 2.f * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) + (A[0] + A[4] + A[8]) + (B[0] + B[4] + B[8]);
+  float G[9];
+  for (int k = 0; k < 9; ++k) G[k] = (k % 4 == 0) ? 2.f : 0.f;
+  for (int w = 0; w < 2; ++w) {
+    float C[9], V[9];
+    sandwich(Hh, w == 0 ? A : B, C);
+    jacobi3(C, V);
+    const float r[3] = {sqrtf(fmaxf(C[0], 0.f)), sqrtf(fmaxf(C[4], 0.f)), sqrtf(fmaxf(C[8], 0.f))};
+    f -= 2.f * (r[0] + r[1] + r[2]);
+    float Ch[9], T[9];
+    rdrt9(V, r, Ch);
+    sandwich(Hi, Ch, T);
+    for (int k = 0; k < 9; ++k) G[k] -= T[k];
+  }
+  if (gsig) {
+    float n2 = 0.f;
+    for (int k = 0; k < 9; ++k) n2 += G[k] * G[k];
+    *gsig = sqrtf(n2);
+  }
+  // dSk = G  ->  s: 2 s_k (R^T G R)_kk ;  R: 2 G R diag(s^2)  ->  q (through the normalisation)
+  float GR[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) GR[3 * a + b] = G[3 * a] * R[b] + G[3 * a + 1] * R[3 + b] + G[3 * a + 2] * R[6 + b];
+  float dR[9];
+  for (int k = 0; k < 3; ++k) {
+    g[4 + k] = 2.f * s[k] * (R[k] * GR[k] + R[3 + k] * GR[3 + k] + R[6 + k] * GR[6 + k]);
+    for (int a = 0; a < 3; ++a) dR[3 * a + k] = 2.f * GR[3 * a + k] * s[k] * s[k];
+  }
+  float dq[4];
+  quat_rot_vjp(qn, dR, dq);
+  const float dot = dq[0] * qn[0] + dq[1] * qn[1] + dq[2] * qn[2] + dq[3] * qn[3];
+  for (int k = 0; k < 4; ++k) g[k] = (dq[k] - qn[k] * dot) * iq;
+  return f;
+}
+
+// Minimise from th (Eq. 10 start); returns the iterations taken.  Stops when the
+// gradient has dropped by 1e6 or after kLbfgsIters iterations.  The objective is convex
+// in Sk, but the (q, s) parametrisation loses rank where two scales are equal (a
+// rotation mixing those axes leaves Sk unchanged), so the (q, s) gradient can vanish
+// away from the minimum; when it does while the gradient in Sk has not dropped by 1e3,
+// the scales are offset again by the Eq. 10 deltas and the memory is cleared (at most
+// three times).  The line search looks
+// only at the directional derivative g(x + a d).d (bisection until it is within half of
+// the initial slope): near the minimum the objective is a difference of terms ~1e3
+// times larger, so float32 values of f can no longer rank two nearby points while the
+// gradient still can.
+__device__ int lbfgs_w2(float th[7], const float A[9], const float B[9]) {
+  float S[kLbfgsMem][7], Y[kLbfgsMem][7], rho[kLbfgsMem];
+  int nm = 0, head = 0, it = 0;
+  float g[7], gn[7], xn[7], dir[7], gsig0 = 0.f, gsig = 0.f;
+  w2_objective(th, A, B, g, &gsig0);
+  float g0 = 0.f;
+  for (int c = 0; c < 7; ++c) g0 += g[c] * g[c];
+  g0 = sqrtf(g0);
+  int restarts = 0;
+  for (; it < kLbfgsIters; ++it) {
+    float gnorm = 0.f;
+    for (int c = 0; c < 7; ++c) gnorm += g[c] * g[c];
+    gnorm = sqrtf(gnorm);
+    if (!(gnorm > 1e-6f * g0) || gnorm == 0.f) {
+      w2_objective(th, A, B, g, &gsig);
+      if (!(gsig > 1e-3f * gsig0) || restarts == 3) break;
+      ++restarts;  // a rank-deficient point of (q, s), not the minimum
+      const float delta[3] = {0.001f, 0.002f, 0.003f};
+      for (int k = 0; k < 3; ++k) th[4 + k] += delta[k];
+      nm = 0;
+      w2_objective(th, A, B, g);
+      continue;
+    }
+    // two-loop recursion over the stored pairs, newest first
+    float q[7], al[kLbfgsMem];
+    for (int c = 0; c < 7; ++c) q[c] = g[c];
+    for (int k = 0; k < nm; ++k) {
+      const int m = (head - 1 - k + kLbfgsMem) % kLbfgsMem;
+      float d = 0.f;
+      for (int c = 0; c < 7; ++c) d += S[m][c] * q[c];
+      al[m] = rho[m] * d;
+      for (int c = 0; c < 7; ++c) q[c] -= al[m] * Y[m][c];
+    }
+    float gamma;
+    if (nm > 0) {
+      const int m = (head - 1 + kLbfgsMem) % kLbfgsMem;
+      float sy = 0.f, yy = 0.f;
+      for (int c = 0; c < 7; ++c) { sy += S[m][c] * Y[m][c]; yy += Y[m][c] * Y[m][c]; }
+      gamma = sy / yy;
+    } else {
+      gamma = 1e-3f / gnorm;
+    }
+    for (int c = 0; c < 7; ++c) q[c] *= gamma;
+    for (int k = nm - 1; k >= 0; --k) {
+      const int m = (head - 1 - k + kLbfgsMem) % kLbfgsMem;
+      float d = 0.f;
+      for (int c = 0; c < 7; ++c) d += Y[m][c] * q[c];
+      const float beta = rho[m] * d;
+      for (int c = 0; c < 7; ++c) q[c] += S[m][c] * (al[m] - beta);
+    }
+    float slope = 0.f;
+    for (int c = 0; c < 7; ++c) { dir[c] = -q[c]; slope += dir[c] * g[c]; }
+    if (!(slope < 0.f)) {  // not a descent direction: drop the memory, steepest descent
+      nm = 0;
+      slope = 0.f;
+      for (int c = 0; c < 7; ++c) { dir[c] = -g[c] * (1e-3f / gnorm); slope += dir[c] * g[c]; }
+    }
+    // largest step that keeps every scale above a tenth of its magnitude: Sk is singular
+    // at s_k = 0, and an iterate that crosses it does not come back
+    float amax = 1024.f;
+    for (int k = 0; k < 3; ++k) {
+      const float sk = th[4 + k], dk = dir[4 + k];
+      if (sk * dk < 0.f) amax = fminf(amax, 0.9f * fabsf(sk) / fabsf(dk));
+    }
+    float step = fminf(1.f, amax), lo = 0.f, hi = -1.f;
+    bool ok = false;
+    for (int ls = 0; ls < 40; ++ls) {
+      for (int c = 0; c < 7; ++c) xn[c] = th[c] + step * dir[c];
+      w2_objective(xn, A, B, gn);
+      float dd = 0.f;
+      for (int c = 0; c < 7; ++c) dd += gn[c] * dir[c];
+      if (fabsf(dd) <= 0.5f * fabsf(slope)) { ok = true; break; }
+      if (dd < 0.f) {  // still descending: move out, up to amax
+        lo = step;
+        step = hi < 0.f ? fminf(2.f * step, amax) : 0.5f * (lo + hi);
+        if (step == lo) { ok = true; break; }
+      } else {  // past the minimum along dir, or not finite: move in
+        hi = step;
+        step = 0.5f * (lo + hi);
+      }
+    }
+    if (!ok) {
+      if (lo == 0.f) break;  // no step along dir lowers the slope: stalled
+      for (int c = 0; c < 7; ++c) xn[c] = th[c] + lo * dir[c];  // last point that still descended
+      w2_objective(xn, A, B, gn);
+    }
+    float sv[7], yv[7], sy = 0.f;
+    for (int c = 0; c < 7; ++c) {
+      sv[c] = xn[c] - th[c];
+      yv[c] = gn[c] - g[c];
+      sy += sv[c] * yv[c];
+    }
+    if (sy > 0.f) {  // store the pair (over the oldest one when the memory is full)
+      for (int c = 0; c < 7; ++c) { S[head][c] = sv[c]; Y[head][c] = yv[c]; }
+      rho[head] = 1.f / sy;
+      head = (head + 1) % kLbfgsMem;
+      nm = min(nm + 1, kLbfgsMem);
+    }
+    for (int c = 0; c < 7; ++c) { th[c] = xn[c]; g[c] = gn[c]; }
+  }
+  return it;
+}
+
 // Merge of G_i (older) and G_j: Eq. 6 mean and the closed-form minimiser of Eq. 9,
-// computed in the eigenbasis of Sigma_i where Sigma_i = diag(si^2).
+// computed in the eigenbasis of Sigma_i where Sigma_i = diag(si^2).  solver = 1 takes
+// the minimiser of Eq. 9 from the paper's L-BFGS instead (same frame, Eq. 10 start).
+// *iters (optional) receives the L-BFGS iterations.
 __device__ void merge_pair(const float* means, const Geom& geo, int64_t i, int64_t j,
-                           float mk[3], float qk[4], float lk[3]) {
+                           float mk[3], float qk[4], float lk[3], int solver = 0, int* iters = nullptr) {
   float qi[4], si[3], qj[4], sj[3], Ri[9], Rj[9];
   load_qs(geo, i, qi, si);
   load_qs(geo, j, qj, sj);
@@ -171,8 +364,36 @@ __device__ void merge_pair(const float* means, const Geom& geo, int64_t i, int64
                  (c02 * rhs[0] + c12 * rhs[1] + c22 * rhs[2]) * id};
   for (int k = 0; k < 3; ++k)
     mk[k] = means[3 * i + k] + (Ri[3 * k] * xr[0] + Ri[3 * k + 1] * xr[1] + Ri[3 * k + 2] * xr[2]);
+  float Sk[9];  // merged covariance in the R_i basis
+  float V[9];
+  if (solver == 1) {
+    // Eq. 10 start in this frame: q_i is the identity, q_j the quaternion of R_i^T R_j
+    float qr[4];
+    rot_quat(Mr, qr);
+    const float t = 0.5f;
+    const float dq = qr[0];  // <(1,0,0,0), qr>, >= 0: already the shorter arc
+    float th[7];
+    if (dq > 1.f - 1e-6f) {
+      for (int k = 0; k < 4; ++k) th[k] = (1.f - t) * (k == 0 ? 1.f : 0.f) + t * qr[k];
+    } else {
+      const float om = acosf(fminf(1.f, dq)), so = sinf(om);
+      const float ca = sinf((1.f - t) * om) / so, cb = sinf(t * om) / so;
+      for (int k = 0; k < 4; ++k) th[k] = ca * (k == 0 ? 1.f : 0.f) + cb * qr[k];
+    }
+    const float delta[3] = {0.001f, 0.002f, 0.003f};
+    for (int k = 0; k < 3; ++k) th[4 + k] = 0.5f * (si[k] + sj[k]) + delta[k];
+    float Ai[9] = {si[0] * si[0], 0.f, 0.f, 0.f, si[1] * si[1], 0.f, 0.f, 0.f, si[2] * si[2]};
+    const int n_it = lbfgs_w2(th, Ai, Bj);
+    if (iters) *iters = n_it;
+    const float iq = rsqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2] + th[3] * th[3]);
+    const float qn[4] = {th[0] * iq, th[1] * iq, th[2] * iq, th[3] * iq};
+    float Rk[9];
+    quat_rot(qn, Rk);
+    const float s2[3] = {th[4] * th[4], th[5] * th[5], th[6] * th[6]};
+    rdrt9(Rk, s2, Sk);
+  } else {
   // X = (D Bj D)^(1/2), D = diag(si); Tm = D^-1 X D^-1; Mk = (I + Tm)/2; Sk = Mk D^2 Mk.
-  float A[9], V[9];
+  float A[9];
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) A[3 * a + b] = si[a] * Bj[3 * a + b] * si[b];
   jacobi3(A, V);
@@ -183,13 +404,13 @@ __device__ void merge_pair(const float* means, const Geom& geo, int64_t i, int64
       float x = V[3 * a] * V[3 * b] * ev[0] + V[3 * a + 1] * V[3 * b + 1] * ev[1] + V[3 * a + 2] * V[3 * b + 2] * ev[2];
       Mk[3 * a + b] = 0.5f * ((a == b ? 1.f : 0.f) + x / (si[a] * si[b]));
     }
-  float Sk[9];  // Mk diag(si^2) Mk, still in the R_i basis
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 3; ++a)  // Mk diag(si^2) Mk, still in the R_i basis
     for (int b = a; b < 3; ++b) {
       float x = 0.f;
       for (int k = 0; k < 3; ++k) x += Mk[3 * a + k] * si[k] * si[k] * Mk[3 * k + b];
       Sk[3 * a + b] = Sk[3 * b + a] = x;
     }
+  }
   // eigen-decomposition of Sk -> (quaternion, scales), scales descending, det +1
   jacobi3(Sk, V);
   float lam[3] = {Sk[0], Sk[4], Sk[8]};
@@ -502,13 +723,16 @@ __global__ void __launch_bounds__(128) k_merge_pairs(const float* __restrict__ m
                                                      const uint2* __restrict__ pairs,
                                                      const uint32_t* __restrict__ n_pairs_p,
                                                      float* __restrict__ mmean, float* __restrict__ mquat,
-                                                     float* __restrict__ mlogs) {
+                                                     float* __restrict__ mlogs, int solver,
+                                                     unsigned long long* __restrict__ iters) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= (int64_t)*n_pairs_p) return;
   const uint2 pr = pairs[k];
   const int64_t i = pr.x, j = pr.y;
   float mk[3], qk[4], lk[3];
-  merge_pair(means, geo, i, j, mk, qk, lk);
+  int it = 0;
+  merge_pair(means, geo, i, j, mk, qk, lk, solver, &it);
+  if (solver == 1 && iters) atomicAdd(iters, (unsigned long long)it);
   for (int c = 0; c < 3; ++c) { mmean[3 * i + c] = mk[c]; mlogs[3 * i + c] = lk[c]; }
   for (int c = 0; c < 4; ++c) mquat[4 * i + c] = qk[c];
 }
@@ -619,8 +843,9 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
     k_voxel_pairs_big<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n_elig / 33), 152 * 2), kBlockVoxel, 0, s>>>(
         in.means, geo, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
         ws.pairs, n_pairs, ws.hdr + 7);
-    k_merge_pairs<T><<<(unsigned)div_up(n_elig / 2 + 1, 128), 128, 0, s>>>(in.means, geo, ws.pairs, n_pairs,
-                                                                          ws.mmean, ws.mquat, ws.mlogs);
+    k_merge_pairs<T><<<(unsigned)div_up(n_elig / 2 + 1, 128), 128, 0, s>>>(
+        in.means, geo, ws.pairs, n_pairs, ws.mmean, ws.mquat, ws.mlogs, p.solver,
+        reinterpret_cast<unsigned long long*>(ws.hdr + 12));
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -641,10 +866,19 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
   if (e != cudaSuccess) return e;
   if (h[7] & 2) { *unsupported = 2; return cudaSuccess; }
   *n_out_host = (int64_t)(uint32_t)h[10];
+  unsigned long long it = 0;
+  std::memcpy(&it, h + 12, sizeof(it));
+  last_merge_stats().pairs = (int64_t)(uint32_t)h[11];
+  last_merge_stats().lbfgs_iterations = (int64_t)it;
   return cudaSuccess;
 }
 
 }  // namespace
+
+MergeStats& last_merge_stats() {
+  static thread_local MergeStats st;
+  return st;
+}
 
 size_t merge_workspace_bytes(int64_t n, MergeWs* ws, char* base) {
   size_t off = 0;

@@ -71,6 +71,11 @@ def test_invalid_arguments_are_rejected_before_any_launch(lib):
     g2 = _abi.mgs_gaussians(10, 0, 0, 0, 0, 1, 1, 1, 1, 1, None)  # no birth
     st = lib.mgs_voxel_merge(C.byref(g2), 0.02, C.byref(p), None, None, None, None, None, 0, None)
     assert st == _abi.MGS_ERR_INVALID
+    bad = _abi.mgs_merge_params(7.815, 1e-3, 0, 0, None, None, None, 1, 3)  # unknown solver
+    g3 = _abi.mgs_gaussians(10, 0, 0, 0, 0, 16, 16, 16, 16, 16, 16)
+    n_out = C.c_int64(0)
+    st = lib.mgs_voxel_merge(C.byref(g3), 0.02, C.byref(bad), C.byref(g3), None, None, C.byref(n_out), None, 0, None)
+    assert st == _abi.MGS_ERR_INVALID and b"solver" in lib.mgs_last_error()
 
 
 def test_product_path_does_not_import_the_oracle():
