@@ -1304,3 +1304,60 @@ int orc_iso_loss(int64_t n, const double* log_scales, double w_iso, double* loss
   *loss = scale * acc;
   return 0;
 }
+
+// ---------------------------------------------------------------------------
+// Patch-Grid sampling (Sec. II-B): densify patches with too few keypoints.
+int orc_patch_grid(const orc_camera* cam, int32_t n_kp, const float* kp_uv, const float* kp_depth,
+                   const float* depth_image, int32_t patch, int32_t min_keypoints, int32_t grid,
+                   double* out, int32_t* source, int64_t* n_out) {
+  if (!cam || !out || !n_out || n_kp < 0 || (n_kp > 0 && !kp_uv) || patch <= 0 || grid <= 0) return -1;
+  const int W = cam->width, H = cam->height;
+  const int PX = (W + patch - 1) / patch, PY = (H + patch - 1) / patch;
+  std::vector<int> count((size_t)PX * PY, 0);
+  for (int k = 0; k < n_kp; ++k) {
+    float u = kp_uv[2 * k], v = kp_uv[2 * k + 1];
+    if (!(u >= 0 && u < W && v >= 0 && v < H)) continue;
+    count[(size_t)((int)v / patch) * PX + (int)u / patch] += 1;
+  }
+  int64_t n = 0;
+  for (int py = 0; py < PY; ++py)
+    for (int px = 0; px < PX; ++px) {
+      if (count[(size_t)py * PX + px] >= min_keypoints) continue;
+      // the patch as clipped by the image
+      const double x0 = (double)px * patch, y0 = (double)py * patch;
+      const double pw = std::min<double>(patch, W - x0), ph = std::min<double>(patch, H - y0);
+      for (int a = 0; a < grid; ++a)
+        for (int b = 0; b < grid; ++b) {
+          const float u = (float)(x0 + (b + 0.5) * pw / grid), v = (float)(y0 + (a + 0.5) * ph / grid);
+          double d = -1;
+          int src = 0;
+          if (depth_image) {
+            float di = depth_image[(size_t)(int)v * W + (int)u];
+            if (di > 0) d = di;
+          }
+          if (!(d > 0) && kp_depth) {
+            int best = -1;
+            float bd = 0;
+            for (int k = 0; k < n_kp; ++k) {
+              if (!(kp_depth[k] > 0)) continue;
+              float du = kp_uv[2 * k] - u, dv = kp_uv[2 * k + 1] - v;
+              float du2 = du * du, dv2 = dv * dv;
+              float d2 = du2 + dv2;  // float32, as written (built without contraction)
+              if (best < 0 || d2 < bd) { best = k; bd = d2; }
+            }
+            if (best >= 0) { d = kp_depth[best]; src = 1; }
+          }
+          if (!(d > 0)) continue;
+          const double xc = ((double)u - cam->cx) / cam->fx * d, yc = ((double)v - cam->cy) / cam->fy * d;
+          const double pc[3] = {xc - cam->t[0], yc - cam->t[1], d - cam->t[2]};
+          double* o = out + 6 * n;
+          o[0] = u; o[1] = v; o[2] = d;
+          for (int r = 0; r < 3; ++r)
+            o[3 + r] = cam->R[0 * 3 + r] * pc[0] + cam->R[1 * 3 + r] * pc[1] + cam->R[2 * 3 + r] * pc[2];
+          if (source) source[n] = src;
+          ++n;
+        }
+    }
+  *n_out = n;
+  return 0;
+}

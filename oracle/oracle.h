@@ -186,6 +186,22 @@ int orc_mapping_loss(int32_t n_views, int32_t H, int32_t W, const double* x, con
  * *loss receives the value; grad_ls (optional) receives dL/dlog_scale ADDED to it. */
 int orc_iso_loss(int64_t n, const double* log_scales, double w_iso, double* loss, double* grad_ls);
 
+/* ---- Patch-Grid sampling (Sec. II-B) ----
+ * The image is cut into patch x patch pixel patches (the last row / column of patches
+ * clipped to the image).  A patch holding fewer than min_keypoints keypoints (of the
+ * keypoints inside the image) receives grid x grid samples at the centres of an even
+ * grid x grid split of the patch.  A sample's depth is the depth image's value at
+ * (floor u, floor v) when that is > 0; otherwise the depth of the nearest keypoint
+ * with a known depth (kp_depth > 0), nearest by the float32 value of
+ * (ku - u)^2 + (kv - v)^2 evaluated as written (ties: smaller index); a sample with
+ * neither is dropped.  Samples are back-projected (pinhole) and taken to the world
+ * frame: x_w = R^T (x_c - t).  Output in patch order (row-major), then sample order.
+ * kp_uv, kp_depth and depth_image are float32 (the precision the decisions use).
+ * out [n][6] = (u, v, depth, xw, yw, zw); source [n] = 0 (depth image) / 1 (keypoint). */
+int orc_patch_grid(const orc_camera* cam, int32_t n_kp, const float* kp_uv, const float* kp_depth,
+                   const float* depth_image, int32_t patch, int32_t min_keypoints, int32_t grid,
+                   double* out, int32_t* source, int64_t* n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(LIB) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-pthread",
                            src, "-o", tmp])
     os.replace(tmp, LIB)
     return LIB
@@ -317,3 +317,24 @@ def iso_loss(log_scales, w_iso=1.0):
     rc = lib().orc_iso_loss(C.c_int64(ls.shape[0]), _p(ls), C.c_double(w_iso), C.byref(val), _p(grad))
     assert rc == 0
     return val.value, grad
+
+
+def patch_grid(cam, kp_uv, kp_depth=None, depth_image=None, patch=32, min_keypoints=4, grid=2):
+    """Patch-Grid sampling (Sec. II-B) for one keyframe.  Returns dict with samples
+    [n, 6] = (u, v, depth, x, y, z world) and source [n] (0 depth image, 1 keypoint)."""
+    kp = np.ascontiguousarray(kp_uv, np.float32).reshape(-1, 2)
+    K = kp.shape[0]
+    kd = None if kp_depth is None else np.ascontiguousarray(kp_depth, np.float32)
+    di = None if depth_image is None else np.ascontiguousarray(depth_image, np.float32)
+    W, H = int(cam.width), int(cam.height)
+    cap = ((W + patch - 1) // patch) * ((H + patch - 1) // patch) * grid * grid
+    out = np.zeros((max(cap, 1), 6))
+    src = np.zeros(max(cap, 1), np.int32)
+    n = C.c_int64(0)
+    rc = lib().orc_patch_grid(C.byref(camera_struct(cam)), C.c_int32(K), kp.ctypes.data_as(C.c_void_p),
+                              None if kd is None else kd.ctypes.data_as(C.c_void_p),
+                              None if di is None else di.ctypes.data_as(C.c_void_p),
+                              C.c_int32(patch), C.c_int32(min_keypoints), C.c_int32(grid),
+                              _p(out), src.ctypes.data_as(C.c_void_p), C.byref(n))
+    assert rc == 0
+    return dict(samples=out[:n.value], source=src[:n.value])
