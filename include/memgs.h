@@ -249,6 +249,37 @@ size_t mgs_iso_loss_workspace_size(int64_t n);
 mgs_status mgs_iso_loss(const mgs_gaussians* g, float w_iso, const mgs_grads* grads, float* loss,
                         void* workspace, size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------------------------
+ * Patch-Grid sampling, Sec. II-B: initial points for new Gaussians in the patches of a
+ * keyframe that hold too few keypoints.  The image is cut into patch x patch pixel
+ * patches (the last row / column clipped to the image).  A patch holding fewer than
+ * min_keypoints of the keypoints that lie inside the image receives grid x grid samples
+ * at the centres of an even grid x grid split of the patch.  A sample's depth is
+ * depth_image[floor v][floor u] when that is > 0, else the depth of the nearest
+ * keypoint with kp_depth > 0 (float32 squared pixel distance, ties: smaller index); a
+ * sample with neither is dropped.  Samples are back-projected with the pinhole camera
+ * and taken to the world frame (x_w = R^T (x_c - t)).
+ * kp_uv: device f32 [n_keypoints][2]; kp_depth: device f32 [n_keypoints] or NULL;
+ * depth_image: device f32 [height][width] or NULL.  out: device f32 [capacity][6] =
+ * (u, v, depth, x, y, z world), in patch order then sample order; source (optional,
+ * i32 [capacity]): 0 depth image, 1 keypoint.  Synchronises `stream` and writes the
+ * sample count to *n_out_host; MGS_ERR_WORKSPACE when it exceeds capacity (nothing
+ * beyond capacity is written).  mgs_patch_grid_capacity gives the largest count.
+ * ------------------------------------------------------------------------------ */
+typedef struct {
+  int32_t patch;          /* patch edge, px */
+  int32_t min_keypoints;  /* patches with fewer keypoints are sampled */
+  int32_t grid;           /* grid x grid samples per sampled patch */
+  int32_t reserved;
+} mgs_pg_params;
+
+size_t mgs_patch_grid_workspace_size(int32_t width, int32_t height, const mgs_pg_params* p);
+int64_t mgs_patch_grid_capacity(int32_t width, int32_t height, const mgs_pg_params* p);
+mgs_status mgs_patch_grid_sample(const mgs_camera* cam, int32_t n_keypoints, const float* kp_uv,
+                                 const float* kp_depth, const float* depth_image, const mgs_pg_params* p,
+                                 float* out, int32_t* source, int64_t capacity, int64_t* n_out_host,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
 /* L1 loss helper for mapping steps: grad[i] = scale * sign(pred[i] - target[i]) and
  * *loss += scale * sum |pred - target| (loss is a device f32 accumulator). */
 mgs_status mgs_l1_loss_grad(const float* pred, const float* target, int64_t n, float scale,

@@ -24,7 +24,8 @@ EXPORTS = ["mgs_render_workspace_size", "mgs_render", "mgs_render_backward", "mg
            "mgs_launch_count", "mgs_profile_enable", "mgs_profile_read", "mgs_render_stats",
            "mgs_sort_pairs_noalloc", "mgs_server_create", "mgs_server_add_scene", "mgs_server_submit",
            "mgs_server_poll", "mgs_server_clock", "mgs_server_destroy", "mgs_mapping_loss_workspace_size",
-           "mgs_mapping_loss", "mgs_iso_loss_workspace_size", "mgs_iso_loss", "mgs_merge_stats"]
+           "mgs_mapping_loss", "mgs_iso_loss_workspace_size", "mgs_iso_loss", "mgs_merge_stats",
+           "mgs_patch_grid_workspace_size", "mgs_patch_grid_capacity", "mgs_patch_grid_sample"]
 
 
 class mgs_gaussians(C.Structure):
@@ -60,6 +61,11 @@ class mgs_merge_params(C.Structure):
     _fields_ = [("chi2", C.c_float), ("grad_tau", C.c_float), ("kf_min", C.c_int32),
                 ("kf_max", C.c_int32), ("grad_stat", C.c_void_p), ("kf_id", C.c_void_p),
                 ("vis_count", C.c_void_p), ("greedy", C.c_int32), ("solver", C.c_int32)]
+
+
+class mgs_pg_params(C.Structure):
+    _fields_ = [("patch", C.c_int32), ("min_keypoints", C.c_int32), ("grid", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -103,6 +109,9 @@ def load():
             "mgs_iso_loss_workspace_size": (SZ, [I64]),
             "mgs_iso_loss": (C.c_int, [P, F, P, P, P, SZ, P]),
             "mgs_merge_stats": (None, [P]),
+            "mgs_patch_grid_workspace_size": (SZ, [I32, I32, P]),
+            "mgs_patch_grid_capacity": (I64, [I32, I32, P]),
+            "mgs_patch_grid_sample": (C.c_int, [P, I32, P, P, P, P, P, P, I64, P, P, SZ, P]),
             "mgs_sort_pairs": (C.c_int, [P, P, P, I64, I32, I32, P, SZ, P]),
             "mgs_sort_pairs_noalloc": (C.c_int, [P, P, P, I64, I32, I32, P]),
             "mgs_server_create": (C.c_int, [P, P]),

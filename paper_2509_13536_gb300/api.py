@@ -340,6 +340,34 @@ def mgs_iso_loss(g: Gaussians, w_iso: float = 1.0, grads: Optional[Grads] = None
 iso_loss = mgs_iso_loss
 
 
+def mgs_patch_grid_sample(cam, kp_uv: torch.Tensor, kp_depth: Optional[torch.Tensor] = None,
+                          depth_image: Optional[torch.Tensor] = None, patch: int = 32,
+                          min_keypoints: int = 4, grid: int = 2, stream=None):
+    """Patch-Grid sampling (Sec. II-B) for one keyframe -> (samples [n, 6] = u, v, depth,
+    world xyz; source [n]: 0 depth image, 1 nearest keypoint)."""
+    L = load()
+    dev = kp_uv.device
+    p = _abi.mgs_pg_params(int(patch), int(min_keypoints), int(grid), 0)
+    c = camera_struct(cam)
+    W, H = int(cam.width), int(cam.height)
+    cap = L.mgs_patch_grid_capacity(W, H, C.byref(p))
+    need = L.mgs_patch_grid_workspace_size(W, H, C.byref(p))
+    if need == 0:
+        raise ValueError("invalid patch-grid parameters")
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    out = torch.empty(max(cap, 1), 6, device=dev)
+    src = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    n = C.c_int64(0)
+    kp = kp_uv.contiguous()
+    check(L.mgs_patch_grid_sample(C.byref(c), int(kp.shape[0]), _ptr(kp) if kp.numel() else None, _ptr(kp_depth),
+                                  _ptr(depth_image), C.byref(p), _ptr(out), _ptr(src), cap, C.byref(n),
+                                  _ptr(ws), ws.numel(), _stream(stream)), "mgs_patch_grid_sample")
+    return out[:n.value], src[:n.value]
+
+
+patch_grid_sample = mgs_patch_grid_sample
+
+
 def mgs_l1_loss_grad(pred: torch.Tensor, target: torch.Tensor, scale: float, grad: torch.Tensor,
                      loss: Optional[torch.Tensor] = None, stream=None):
     check(load().mgs_l1_loss_grad(_ptr(pred), _ptr(target), pred.numel(), scale, _ptr(grad), _ptr(loss),

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libmemgs.so")
-SOURCES = ["api.cu", "project.cu", "raster.cu", "emit.cu", "sort.cu", "merge.cu", "adam.cu", "loss.cu", "diag.cu", "sort_static.cu", "serve.cu"]
+SOURCES = ["api.cu", "project.cu", "raster.cu", "emit.cu", "sort.cu", "merge.cu", "adam.cu", "loss.cu", "pg.cu", "diag.cu", "sort_static.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

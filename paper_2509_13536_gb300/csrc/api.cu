@@ -415,6 +415,46 @@ mgs_status mgs_l1_loss_grad(const float* pred, const float* target, int64_t n, f
   return MGS_OK;
 }
 
+static std::string pg_check(int32_t width, int32_t height, const mgs_pg_params* p) {
+  if (!p) return "params is NULL";
+  if (width <= 0 || height <= 0) return "width and height must be positive";
+  if (p->patch <= 0 || p->grid <= 0 || p->grid > p->patch) return "need 0 < grid <= patch";
+  if (p->min_keypoints < 0) return "min_keypoints must be >= 0";
+  return "";
+}
+
+size_t mgs_patch_grid_workspace_size(int32_t width, int32_t height, const mgs_pg_params* p) {
+  if (!pg_check(width, height, p).empty()) return 0;
+  return pg_layout(width, height, p->patch, p->grid).bytes;
+}
+
+int64_t mgs_patch_grid_capacity(int32_t width, int32_t height, const mgs_pg_params* p) {
+  if (!pg_check(width, height, p).empty()) return 0;
+  return pg_layout(width, height, p->patch, p->grid).max_cand;
+}
+
+mgs_status mgs_patch_grid_sample(const mgs_camera* cam, int32_t n_keypoints, const float* kp_uv,
+                                 const float* kp_depth, const float* depth_image, const mgs_pg_params* p,
+                                 float* out, int32_t* source, int64_t capacity, int64_t* n_out_host,
+                                 void* workspace, size_t workspace_bytes, void* stream) {
+  set_error("");
+  if (!cam || !n_out_host) return fail(MGS_ERR_INVALID, "camera or n_out_host is NULL");
+  std::string why = pg_check(cam->width, cam->height, p);
+  if (!why.empty()) return fail(MGS_ERR_INVALID, why);
+  if (n_keypoints < 0 || (n_keypoints > 0 && !kp_uv)) return fail(MGS_ERR_INVALID, "bad keypoints");
+  if (capacity < 0 || (capacity > 0 && !out)) return fail(MGS_ERR_INVALID, "bad output");
+  if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(MGS_ERR_INVALID, "focal lengths must be > 0");
+  const PgLayout L = pg_layout(cam->width, cam->height, p->patch, p->grid);
+  if (L.max_cand >= (int64_t)UINT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "too many patches");
+  if (!workspace || workspace_bytes < L.bytes) return fail(MGS_ERR_WORKSPACE, "patch-grid workspace too small");
+  uint32_t n = 0;
+  MGS_TRY_CUDA(launch_patch_grid(*cam, n_keypoints, kp_uv, kp_depth, depth_image, p->patch, p->min_keypoints,
+                                 p->grid, L, (char*)workspace, out, source, capacity, &n, (cudaStream_t)stream));
+  *n_out_host = (int64_t)n;
+  if ((int64_t)n > capacity) return fail(MGS_ERR_WORKSPACE, "output capacity too small");
+  return MGS_OK;
+}
+
 void mgs_merge_stats(int64_t out[2]) {
   if (!out) return;
   out[0] = last_merge_stats().pairs;

@@ -65,6 +65,18 @@ inline int radix_passes(int begin_bit, int end_bit) {
 // [start, end) of every key value < n_valid present in sorted keys (absent values untouched).
 cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s);
 
+// Patch-Grid sampling (pg.cu): workspace layout for one keyframe.
+struct PgLayout {
+  int PX, PY;
+  int64_t n_patch, max_cand;
+  size_t hdr, count, flags, cand_off, cand, keep, pos, scratch, bytes;
+};
+PgLayout pg_layout(int width, int height, int patch, int grid);
+cudaError_t launch_patch_grid(const mgs_camera& c, int n_kp, const float* kp, const float* kd,
+                              const float* depth_image, int patch, int min_kp, int grid, const PgLayout& L,
+                              char* ws, float* out, int32_t* source, int64_t capacity, uint32_t* n_host,
+                              cudaStream_t s);
+
 // Counters of the calling thread's last mgs_voxel_merge (merge.cu).
 struct MergeStats {
   int64_t pairs = 0, lbfgs_iterations = 0;
