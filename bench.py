@@ -279,6 +279,32 @@ def merge_solver_leg(api, torch, scene, dev):
     return res
 
 
+def patch_grid_leg(api, torch, cams, dev, target_depth):
+    """Patch-Grid sampling of each benchmark keyframe: 600 clustered keypoints (8 spots of
+    60 plus 120 scattered, a quarter without depth) and the keyframe's rendered depth
+    as the depth image; 32 px patches, fewer than 5 keypoints -> 2 x 2 samples."""
+    rng = np.random.default_rng(55)
+    jobs = []
+    for v, cam in enumerate(cams):
+        W, H = cam.width, cam.height
+        centres = rng.uniform([0, 0], [W, H], (8, 2))
+        kp = np.concatenate([c + rng.normal(0, 0.03 * W, (60, 2)) for c in centres] +
+                            [rng.uniform([0, 0], [W, H], (120, 2))]).astype(np.float32)
+        kd = rng.uniform(0.5, 4.0, len(kp)).astype(np.float32)
+        kd[rng.random(len(kp)) < 0.25] = 0
+        jobs.append((cam, torch.from_numpy(kp).to(dev), torch.from_numpy(kd).to(dev), target_depth[v]))
+    run = lambda: [api.patch_grid_sample(c, k, d, di, 32, 5, 2)[0].shape[0] for c, k, d, di in jobs]
+    run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        counts = run()
+    dt = (time.perf_counter() - t0) / (reps * len(jobs))
+    return {"ms_per_keyframe": dt * 1e3, "samples_per_keyframe": float(np.mean(counts)),
+            "note": "host-timed, includes the call's two synchronisations"}
+
+
 def eq12_leg(args, api, torch, scene, make_step, dev, V):
     """The mapping step with the paper's loss (Eq. 12: 0.8 L1 + 0.2 (1 - SSIM) on rgb,
     0.1 x depth L1, isotropic term) instead of the L1 stand-in: frames/s and the loss
@@ -546,6 +572,7 @@ def run_ours(args):
     if world == 1 and not args.no_eq12:
         eq12 = eq12_leg(args, api, torch, pert, make_step, dev, V)
         eq12["merge_solvers"] = merge_solver_leg(api, torch, pert, dev)
+        eq12["patch_grid"] = patch_grid_leg(api, torch, cams, dev, target_depth)
     precision = None
     if world == 1 and not args.no_precision:
         precision = precision_leg(args, api, torch, pert, cams, make_step, dev)
