@@ -76,6 +76,28 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_seed(rank):
+    """Seed of the perturbed map each rank optimises: replicas are independent maps."""
+    return 1234 + rank
+
+
+def max_over_ranks(ms, world, device):
+    """Slowest rank's time (all ranks take part when world > 1): the whole job is as
+    fast as its slowest replica."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second (weak scaling: each rank has its own)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
 
@@ -425,7 +447,7 @@ def run_ours(args):
     target_depth = torch.stack([t.depth for t in tgt]).contiguous()
     del g_true, tgt
     # the map being optimised: perturbed copy
-    rng = np.random.default_rng(1234 + rank)
+    rng = np.random.default_rng(replica_seed(rank))
     pert = scene.copy()
     pert.means += rng.normal(0, 0.005, pert.means.shape).astype(np.float32)
     pert.sh += rng.normal(0, 0.02, pert.sh.shape).astype(np.float32)
@@ -505,12 +527,8 @@ def run_ours(args):
         prof = api.profile_read()
         api.profile_enable(False)
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
-    value = world * V / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    value = whole_job_rate(V, world, ms)
 
     # end to end: keyframe images arrive from pinned host memory, the loss goes back
     if args.no_e2e:
@@ -531,12 +549,8 @@ def run_ours(args):
         torch.cuda.current_stream().synchronize()
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3) / max(1, getattr(args, "steps_e2e", args.steps))
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t)
-    e2e_value = world * V / (ms_e2e / 1e3)
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3) / max(1, getattr(args, "steps_e2e", args.steps)), world, dev)
+    e2e_value = whole_job_rate(V, world, ms_e2e)
     h2d = host_rgb.numel() * 4 + host_depth.numel() * 4
 
     # roofline of the dominant kernel group, from a counting pass over the saved state
