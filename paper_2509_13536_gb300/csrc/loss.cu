@@ -9,15 +9,17 @@
 // the same window applied to those three maps:
 //   dL/dx(p) = -lambda/n sum_q w(q-p) (dS/dm1(q) + 2 x(p) dS/dm2(q) + y(p) dS/dm3(q))
 //              + (1-lambda)/n sign(x(p) - y(p)),   n = 3HW.
-// Both passes stage a 32x16 output tile with a 5-pixel halo in shared memory and run
-// the window as two separable 11-tap passes.  Sums go through per-block partials that
+// Both passes stage a 32x32 output tile with a 5-pixel halo in shared memory and run
+// the window as two separable 11-tap passes; a thread computes 4 neighbouring outputs
+// of a pass from one 14-value strip, so each shared value is loaded once per 4 outputs.  Sums go through per-block partials that
 // one block per view adds in a fixed order, so the loss is deterministic.
 #include "internal.h"
 
 namespace mgs {
 namespace {
 
-constexpr int kTX = 32, kTY = 16, kH = 5, kIX = kTX + 2 * kH, kIY = kTY + 2 * kH, kTaps = 11;
+constexpr int kTX = 32, kTY = 32, kH = 5, kIX = kTX + 2 * kH, kIY = kTY + 2 * kH, kTaps = 11;
+constexpr int kRB = 4;  // outputs per thread along the pass direction (register blocking)
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
 struct Window {
@@ -59,54 +61,69 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(int W, int H, const Window win
   load_tile(sx, X, W, H, x0, y0);
   load_tile(sy, Y, W, H, x0, y0);
   __syncthreads();
-  // horizontal pass: rows of the input tile, columns of the output tile
-  for (int i = threadIdx.x; i < kIY * kTX; i += blockDim.x) {
-    const int r = i / kTX, col = i - r * kTX;
-    float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+  // horizontal pass: input row r, output columns c0 .. c0+3
+  for (int i = threadIdx.x; i < kIY * (kTX / kRB); i += blockDim.x) {
+    const int r = i / (kTX / kRB), c0 = (i - r * (kTX / kRB)) * kRB;
+    float xv[kTaps + kRB - 1], yv[kTaps + kRB - 1];
 #pragma unroll
-    for (int k = 0; k < kTaps; ++k) {
-      const float xv = sx[r][col + k], yv = sy[r][col + k], wk = win.w[k];
-      a = fmaf(wk, xv, a);
-      b = fmaf(wk, yv, b);
-      aa = fmaf(wk, xv * xv, aa);
-      bb = fmaf(wk, yv * yv, bb);
-      ab = fmaf(wk, xv * yv, ab);
+    for (int k = 0; k < kTaps + kRB - 1; ++k) { xv[k] = sx[r][c0 + k]; yv[k] = sy[r][c0 + k]; }
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) {
+      float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+#pragma unroll
+      for (int k = 0; k < kTaps; ++k) {
+        const float x = xv[o + k], y = yv[o + k], wk = win.w[k];
+        a = fmaf(wk, x, a);
+        b = fmaf(wk, y, b);
+        aa = fmaf(wk, x * x, aa);
+        bb = fmaf(wk, y * y, bb);
+        ab = fmaf(wk, x * y, ab);
+      }
+      h[0][r][c0 + o] = a; h[1][r][c0 + o] = b; h[2][r][c0 + o] = aa; h[3][r][c0 + o] = bb; h[4][r][c0 + o] = ab;
     }
-    h[0][r][col] = a; h[1][r][col] = b; h[2][r][col] = aa; h[3][r][col] = bb; h[4][r][col] = ab;
   }
   __syncthreads();
   float ssum = 0.f, l1 = 0.f;
   float* D1 = dmaps + ((size_t)blockIdx.z * 3 + 0) * HW;
   float* D2 = dmaps + ((size_t)blockIdx.z * 3 + 1) * HW;
   float* D3 = dmaps + ((size_t)blockIdx.z * 3 + 2) * HW;
-  for (int i = threadIdx.x; i < kTX * kTY; i += blockDim.x) {
-    const int r = i / kTX, col = i - r * kTX;
-    const int gx = x0 + col, gy = y0 + r;
-    if (gx >= W || gy >= H) continue;
-    float mx = 0.f, my = 0.f, mxx = 0.f, myy = 0.f, mxy = 0.f;
+  // vertical pass: output column col, output rows r0 .. r0+3
+  for (int i = threadIdx.x; i < kTX * (kTY / kRB); i += blockDim.x) {
+    const int col = i % kTX, r0 = (i / kTX) * kRB;
+    float m[5][kRB];
 #pragma unroll
-    for (int k = 0; k < kTaps; ++k) {
-      const float wk = win.w[k];
-      mx = fmaf(wk, h[0][r + k][col], mx);
-      my = fmaf(wk, h[1][r + k][col], my);
-      mxx = fmaf(wk, h[2][r + k][col], mxx);
-      myy = fmaf(wk, h[3][r + k][col], myy);
-      mxy = fmaf(wk, h[4][r + k][col], mxy);
+    for (int q = 0; q < 5; ++q) {
+      float hv[kTaps + kRB - 1];
+#pragma unroll
+      for (int k = 0; k < kTaps + kRB - 1; ++k) hv[k] = h[q][r0 + k][col];
+#pragma unroll
+      for (int o = 0; o < kRB; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < kTaps; ++k) acc = fmaf(win.w[k], hv[o + k], acc);
+        m[q][o] = acc;
+      }
     }
-    const float vx = mxx - mx * mx, vy = myy - my * my, cxy = mxy - mx * my;
-    const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
-    const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-    const float iB = 1.f / (B1 * B2);
-    const float S = A1 * A2 * iB;
-    ssum += S;
-    const float dmu = 2.f * my * A2 * iB - S * 2.f * mx / B1;  // dS/dmu_x at fixed variances
-    const float dvx = -S / B2;                                  // dS/dsigma_x^2
-    const float dcxy = 2.f * A1 * iB;                           // dS/dsigma_xy
-    const size_t q = (size_t)gy * W + gx;
-    D1[q] = dmu - 2.f * mx * dvx - my * dcxy;
-    D2[q] = dvx;
-    D3[q] = dcxy;
-    l1 += fabsf(sx[r + kH][col + kH] - sy[r + kH][col + kH]);
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) {
+      const int r = r0 + o, gx = x0 + col, gy = y0 + r;
+      if (gx >= W || gy >= H) continue;
+      const float mx = m[0][o], my = m[1][o], mxx = m[2][o], myy = m[3][o], mxy = m[4][o];
+      const float vx = mxx - mx * mx, vy = myy - my * my, cxy = mxy - mx * my;
+      const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+      const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+      const float iB = 1.f / (B1 * B2);
+      const float S = A1 * A2 * iB;
+      ssum += S;
+      const float dmu = 2.f * my * A2 * iB - S * 2.f * mx / B1;  // dS/dmu_x at fixed variances
+      const float dvx = -S / B2;                                  // dS/dsigma_x^2
+      const float dcxy = 2.f * A1 * iB;                           // dS/dsigma_xy
+      const size_t q = (size_t)gy * W + gx;
+      D1[q] = dmu - 2.f * mx * dvx - my * dcxy;
+      D2[q] = dvx;
+      D3[q] = dcxy;
+      l1 += fabsf(sx[r + kH][col + kH] - sy[r + kH][col + kH]);
+    }
   }
   // block partials (SSIM sum, L1 sum) in a fixed order
   for (int o = 16; o; o >>= 1) {
@@ -135,41 +152,54 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(int W, int H, const Window win
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   for (int m = 0; m < 3; ++m) load_tile(t[m], dmaps + ((size_t)blockIdx.z * 3 + m) * HW, W, H, x0, y0);
   __syncthreads();
-  for (int i = threadIdx.x; i < kIY * kTX; i += blockDim.x) {
-    const int r = i / kTX, col = i - r * kTX;
-    float a = 0.f, b = 0.f, e = 0.f;
+  for (int i = threadIdx.x; i < kIY * (kTX / kRB); i += blockDim.x) {
+    const int r = i / (kTX / kRB), c0 = (i - r * (kTX / kRB)) * kRB;
 #pragma unroll
-    for (int k = 0; k < kTaps; ++k) {
-      const float wk = win.w[k];
-      a = fmaf(wk, t[0][r][col + k], a);
-      b = fmaf(wk, t[1][r][col + k], b);
-      e = fmaf(wk, t[2][r][col + k], e);
+    for (int q = 0; q < 3; ++q) {
+      float tv[kTaps + kRB - 1];
+#pragma unroll
+      for (int k = 0; k < kTaps + kRB - 1; ++k) tv[k] = t[q][r][c0 + k];
+#pragma unroll
+      for (int o = 0; o < kRB; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < kTaps; ++k) acc = fmaf(win.w[k], tv[o + k], acc);
+        h[q][r][c0 + o] = acc;
+      }
     }
-    h[0][r][col] = a; h[1][r][col] = b; h[2][r][col] = e;
   }
   __syncthreads();
   const float* X = P.x[v] + c * HW;
   const float* Y = P.y[v] + c * HW;
   float* G = P.grgb[v] + c * HW;
   const float inv_n = 1.f / (3.f * (float)HW);
-  for (int i = threadIdx.x; i < kTX * kTY; i += blockDim.x) {
-    const int r = i / kTX, col = i - r * kTX;
-    const int gx = x0 + col, gy = y0 + r;
-    if (gx >= W || gy >= H) continue;
-    float a = 0.f, b = 0.f, e = 0.f;
+  for (int i = threadIdx.x; i < kTX * (kTY / kRB); i += blockDim.x) {
+    const int col = i % kTX, r0 = (i / kTX) * kRB;
+    float a3[3][kRB];
 #pragma unroll
-    for (int k = 0; k < kTaps; ++k) {
-      const float wk = win.w[k];
-      a = fmaf(wk, h[0][r + k][col], a);
-      b = fmaf(wk, h[1][r + k][col], b);
-      e = fmaf(wk, h[2][r + k][col], e);
+    for (int q = 0; q < 3; ++q) {
+      float hv[kTaps + kRB - 1];
+#pragma unroll
+      for (int k = 0; k < kTaps + kRB - 1; ++k) hv[k] = h[q][r0 + k][col];
+#pragma unroll
+      for (int o = 0; o < kRB; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < kTaps; ++k) acc = fmaf(win.w[k], hv[o + k], acc);
+        a3[q][o] = acc;
+      }
     }
-    const size_t p = (size_t)gy * W + gx;
-    const float xv = X[p], yv = Y[p];
-    const float dssim = a + 2.f * xv * b + yv * e;
-    const float diff = xv - yv;
-    const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-    G[p] = ((1.f - lambda) * sgn - lambda * dssim) * inv_n;
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) {
+      const int gx = x0 + col, gy = y0 + r0 + o;
+      if (gx >= W || gy >= H) continue;
+      const size_t p = (size_t)gy * W + gx;
+      const float xv = X[p], yv = Y[p];
+      const float dssim = a3[0][o] + 2.f * xv * a3[1][o] + yv * a3[2][o];
+      const float diff = xv - yv;
+      const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+      G[p] = ((1.f - lambda) * sgn - lambda * dssim) * inv_n;
+    }
   }
 }
 

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) k_project_one(int64_t N, const float* __r
 //   m5 = sum gp dy^2, m6..8 = sum w dL/drgb, m9 = sum w dL/ddepth,
 // with gp = dL/dpower, w the blend weight and (dx, dy) = centre - pixel.
 template <int DEG, typename T>
-__global__ void __launch_bounds__(128) k_preprocess_bwd(int64_t N, const float* __restrict__ means,
+__global__ void __launch_bounds__(128, 3) k_preprocess_bwd(int64_t N, const float* __restrict__ means,
                                                         const Geom geo,
                                                         const T* __restrict__ ol, const T* __restrict__ sh,
                                                         const __grid_constant__ ViewTable vt,
