@@ -326,8 +326,9 @@ __device__ int lbfgs_w2(float th[7], const float A[9], const float B[9]) {
 // computed in the eigenbasis of Sigma_i where Sigma_i = diag(si^2).  solver = 1 takes
 // the minimiser of Eq. 9 from the paper's L-BFGS instead (same frame, Eq. 10 start).
 // *iters (optional) receives the L-BFGS iterations.
+template <int SOLVER>
 __device__ void merge_pair(const float* means, const Geom& geo, int64_t i, int64_t j,
-                           float mk[3], float qk[4], float lk[3], int solver = 0, int* iters = nullptr) {
+                           float mk[3], float qk[4], float lk[3], int* iters = nullptr) {
   float qi[4], si[3], qj[4], sj[3], Ri[9], Rj[9];
   load_qs(geo, i, qi, si);
   load_qs(geo, j, qj, sj);
@@ -366,7 +367,7 @@ __device__ void merge_pair(const float* means, const Geom& geo, int64_t i, int64
     mk[k] = means[3 * i + k] + (Ri[3 * k] * xr[0] + Ri[3 * k + 1] * xr[1] + Ri[3 * k + 2] * xr[2]);
   float Sk[9];  // merged covariance in the R_i basis
   float V[9];
-  if (solver == 1) {
+  if constexpr (SOLVER == 1) {
     // Eq. 10 start in this frame: q_i is the identity, q_j the quaternion of R_i^T R_j
     float qr[4];
     rot_quat(Mr, qr);
@@ -718,12 +719,12 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
 
 // One thread per accepted pair: Eq. 6 mean and the Eq. 9 barycentre, written in the
 // older Gaussian's slot of the merged-value arrays.
-template <typename T>
+template <typename T, int SOLVER>
 __global__ void __launch_bounds__(128) k_merge_pairs(const float* __restrict__ means, const Geom geo,
                                                      const uint2* __restrict__ pairs,
                                                      const uint32_t* __restrict__ n_pairs_p,
                                                      float* __restrict__ mmean, float* __restrict__ mquat,
-                                                     float* __restrict__ mlogs, int solver,
+                                                     float* __restrict__ mlogs,
                                                      unsigned long long* __restrict__ iters) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= (int64_t)*n_pairs_p) return;
@@ -731,8 +732,8 @@ __global__ void __launch_bounds__(128) k_merge_pairs(const float* __restrict__ m
   const int64_t i = pr.x, j = pr.y;
   float mk[3], qk[4], lk[3];
   int it = 0;
-  merge_pair(means, geo, i, j, mk, qk, lk, solver, &it);
-  if (solver == 1 && iters) atomicAdd(iters, (unsigned long long)it);
+  merge_pair<SOLVER>(means, geo, i, j, mk, qk, lk, &it);
+  if (SOLVER == 1 && iters) atomicAdd(iters, (unsigned long long)it);
   for (int c = 0; c < 3; ++c) { mmean[3 * i + c] = mk[c]; mlogs[3 * i + c] = lk[c]; }
   for (int c = 0; c < 4; ++c) mquat[4 * i + c] = qk[c];
 }
@@ -843,9 +844,12 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
     k_voxel_pairs_big<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n_elig / 33), 152 * 2), kBlockVoxel, 0, s>>>(
         in.means, geo, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
         ws.pairs, n_pairs, ws.hdr + 7);
-    k_merge_pairs<T><<<(unsigned)div_up(n_elig / 2 + 1, 128), 128, 0, s>>>(
-        in.means, geo, ws.pairs, n_pairs, ws.mmean, ws.mquat, ws.mlogs, p.solver,
-        reinterpret_cast<unsigned long long*>(ws.hdr + 12));
+    const unsigned gp = (unsigned)div_up(n_elig / 2 + 1, 128);
+    unsigned long long* iters = reinterpret_cast<unsigned long long*>(ws.hdr + 12);
+    if (p.solver == 1)
+      k_merge_pairs<T, 1><<<gp, 128, 0, s>>>(in.means, geo, ws.pairs, n_pairs, ws.mmean, ws.mquat, ws.mlogs, iters);
+    else
+      k_merge_pairs<T, 0><<<gp, 128, 0, s>>>(in.means, geo, ws.pairs, n_pairs, ws.mmean, ws.mquat, ws.mlogs, iters);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -154,7 +154,7 @@ __device__ __forceinline__ void colour(const float* c, const float dir[3], float
 }
 
 template <int DEG, typename T>
-__global__ void __launch_bounds__(256) k_preprocess(int64_t N, const float* __restrict__ means,
+__global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* __restrict__ means,
                                                     const Geom geo,
                                                     const T* __restrict__ ol, const T* __restrict__ sh,
                                                     const __grid_constant__ ViewTable vt,
@@ -169,8 +169,6 @@ __global__ void __launch_bounds__(256) k_preprocess(int64_t N, const float* __re
     GaussPre G;
     load_gauss(g, means, geo, ol, G);
     constexpr int K3 = (DEG + 1) * (DEG + 1) * 3;
-    float c[K3];
-    load_sh<DEG>(g, sh, c);
     for (int v = 0; v < vt.n_views; ++v) {
       const View& V = vt.v[v];
       int64_t item = (int64_t)v * N + g;
@@ -181,6 +179,8 @@ __global__ void __launch_bounds__(256) k_preprocess(int64_t N, const float* __re
       uint32_t count = 0;
       if (vis) {
         float raw[3];
+        float c[K3];
+        load_sh<DEG>(g, sh, c);  // per drawn view: the coefficients come from L1 after the first
         colour<DEG>(c, P.dir, raw);
         float4 r0 = make_float4(P.u_hi, P.v_hi, P.u_lo, P.v_lo);
         float4 r1 = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, G.o);
