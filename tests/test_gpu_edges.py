@@ -1,0 +1,115 @@
+"""GPU edge cases against the oracle: the hand-built scenes at the alpha cutoff, the 0.99
+clamp, the transmittance stop and the depth tie-break; the maximum number of views in
+one launch; degenerate merge inputs."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_13536_gb300 import api, scenegen as sg
+from tests import _gpu
+from tests._scenes import camera, make_scene, random_scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_13536_gb300 import build
+    build.build()
+
+
+def _render(sc, cams):
+    g = api.Gaussians.from_scene(sc, "cuda")
+    imgs, ws = api.render(g, cams)
+    torch.cuda.synchronize()
+    return g, imgs, ws
+
+
+def _same_as_oracle(orc, sc, cam, tol=_gpu.IMG_TOL):
+    _, imgs, _ = _render(sc, [cam])
+    ref = orc.render(sc, cam)
+    assert not ref["flags"].any()
+    for name in ("rgb", "depth", "alpha"):
+        np.testing.assert_allclose(_gpu.to_np(getattr(imgs[0], name)), ref[name], atol=tol, rtol=0)
+    return imgs[0], ref
+
+
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_alpha_cutoff_scene(orc, sign):
+    """alpha = 1/255 (1 +- 1e-3) at pixel (19, 16): blended above, skipped below, as in the oracle."""
+    f, z, s = 100.0, 2.0, 0.04
+    sig2 = (f * math.exp(float(np.float32(math.log(s)))) / z) ** 2 + 0.3
+    o = (1 / 255) * (1 + sign * 1e-3) * math.exp(0.5 * 9.0 / sig2)
+    sc = make_scene([[0, 0, z]], [[s, s, s]], [[1, 0, 0, 0]], [o], [[1, 1, 1]])
+    img, ref = _same_as_oracle(orc, sc, camera(32, 32, f, f, 16, 16))
+    a = float(_gpu.to_np(img.alpha)[16, 19])
+    assert (a > 0) == (sign > 0) and (ref["alpha"][16, 19] > 0) == (sign > 0)
+
+
+def test_opacity_clamp_scene(orc):
+    sc = make_scene([[0, 0, 2.0]], [[0.1, 0.1, 0.1]], [[1, 0, 0, 0]], [0.9999], [[1, 1, 1]])
+    img, _ = _same_as_oracle(orc, sc, camera(32, 32, 100, 100, 16, 16))
+    assert abs(float(_gpu.to_np(img.alpha)[16, 16]) - 0.99) < 1e-6
+
+
+def test_transmittance_stop_scene_and_its_gradient(orc):
+    """Six alpha-0.95 layers: at the centre pixel the 4th takes T below 1e-4 and is
+    blended, the 5th and 6th are not (off-centre pixels, with smaller alpha, reach them).
+    Image and gradients as in the oracle."""
+    cols = [[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [0, 1, 1], [1, 0, 1]]
+    z = [2.0, 2.5, 3.0, 3.5, 4.0, 4.5]
+    n = len(z)
+    sc = make_scene([[0, 0, zz] for zz in z], [[0.5, 0.5, 0.5]] * n, [[1, 0, 0, 0]] * n, [0.95] * n, cols)
+    cam = camera(32, 32, 100, 100, 16, 16)
+    g, imgs, ws = _render(sc, [cam])
+    ref = orc.render(sc, cam)
+    np.testing.assert_allclose(_gpu.to_np(imgs[0].rgb), ref["rgb"], atol=_gpu.IMG_TOL)
+    cot_np, dL = _gpu.cotangents([cam], 3)
+    grads = api.render_backward(g, [cam], dL, ws)
+    torch.cuda.synchronize()
+    refg = _gpu.oracle_backward(orc, sc, [cam], cot_np)
+    o = 1 / (1 + math.exp(-float(sc.opacity_logit[0])))
+    assert abs(float(_gpu.to_np(imgs[0].alpha)[16, 16]) - (1 - (1 - o) ** 4)) < 1e-6
+    _gpu.check_grads(grads, refg, refg["taint"])
+
+
+def test_depth_tie_keeps_index_order(orc):
+    cols = [[1, 0, 0], [0, 1, 0]]
+    sc = make_scene([[0, 0, 2.0], [0, 0, 2.0]], [[0.3] * 3] * 2, [[1, 0, 0, 0]] * 2, [0.6, 0.5], cols)
+    img, ref = _same_as_oracle(orc, sc, camera(32, 32, 100, 100, 16, 16))
+    assert abs(float(_gpu.to_np(img.rgb)[0, 16, 16]) - ref["rgb"][0, 16, 16]) < 1e-6
+
+
+def test_maximum_views_in_one_launch(orc):
+    """MGS_MAX_VIEWS = 32 keyframes of mixed sizes in one call; each matches the oracle."""
+    rng = np.random.default_rng(32)
+    sc = random_scene(rng, 3000, sh_degree=1)
+    cams = []
+    for v in range(32):
+        W, H = [(48, 40), (64, 48), (37, 29)][v % 3]
+        t = np.float32([rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2), rng.uniform(-0.5, 0.5)])
+        cams.append(camera(W, H, 60.0, 60.0, W / 2, H / 2, t=t))
+    _, imgs, _ = _render(sc, cams)
+    for v, c in enumerate(cams):
+        _gpu.check_image(imgs[v], orc.render(sc, c), what=f"view {v}")
+    with pytest.raises(Exception):
+        api.render(api.Gaussians.from_scene(sc, "cuda"), cams + cams[:1])  # 33 views: rejected
+
+
+def test_merge_degenerate_inputs(orc):
+    from tests.test_oracle_merge import _voxel_scene
+    rng = np.random.default_rng(8)
+    sc = _voxel_scene(rng, 20, 4)
+    for sub in (sc.subset(np.arange(0)), sc.subset(np.arange(1))):
+        g = api.Gaussians.from_scene(sub, "cuda")
+        out, partner, _ = api.mgs_voxel_merge(g, 0.02)
+        torch.cuda.synchronize()
+        assert out.n == sub.n and np.all(partner.cpu().numpy() == -1)
+    g = api.Gaussians.from_scene(sc, "cuda")
+    high = torch.full((sc.n,), 1.0, device="cuda")  # nothing passes the Eq. 3 mask
+    out, partner, vox = api.mgs_voxel_merge(g, 0.02, grad_stat=high)
+    torch.cuda.synchronize()
+    assert out.n == sc.n and np.all(partner.cpu().numpy() == -1)
+    assert np.all(vox.cpu().numpy() == np.iinfo(np.int32).min)
