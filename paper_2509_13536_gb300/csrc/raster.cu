@@ -61,9 +61,7 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
     for (int j0 = 0; j0 < cnt; j0 += 8) {
       if (__all_sync(0xffffffffu, done)) break;
       const int jn = min(8, cnt - j0);
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        if (jj < jn) {
+      auto entry = [&](int jj) {
           const int j = j0 + jj;
           float dx, dy;
           const float4 co = s_co[j];
@@ -80,7 +78,14 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
           T = __fsub_rn(T, w);
           last = on ? (uint32_t)(b + j + 1) : last;
           done = done || (on && T < kTStop);
-        }
+      };
+      if (jn == 8) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) entry(jj);
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          if (jj < jn) entry(jj);
       }
     }
   }
@@ -210,9 +215,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
     bool act = false;
     if (__any_sync(0xffffffffu, (uint32_t)base < nc)) {
       const int lim = (int)nc - base;
-#pragma unroll
-      for (int j = kBwdBatch - 1; j >= 0; --j) {
-        if (j < cnt) {
+      auto entry = [&](int j) {
           float dx, dy;
           const float4 co = S.co[buf][j];
           const float p2 = frag_exp2(S.xy[buf][j], co, pxf, pyf, dx, dy);
@@ -230,7 +233,14 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
           sig = fmaf(alc, d, sig);
           S.gw[t][j] = make_float2((on && a <= kAlphaMax) ? dLda * a : 0.f, alc * Tb);
           T = Tb;
-        }
+      };
+      if (cnt == kBwdBatch) {  // full batch: no per-entry guard
+#pragma unroll
+        for (int j = kBwdBatch - 1; j >= 0; --j) entry(j);
+      } else {
+#pragma unroll
+        for (int j = kBwdBatch - 1; j >= 0; --j)
+          if (j < cnt) entry(j);
       }
     }
     // Gaussian phase for the 32 pixels this warp just walked (skipped when none of
