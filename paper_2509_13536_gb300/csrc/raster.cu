@@ -21,6 +21,8 @@
 // comes after the pixel stopped) enters with alpha = 0, which leaves every running
 // quantity unchanged.  A warp then issues one path instead of the union of the
 // contributing and skipping paths of its 32 pixels.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace mgs {
@@ -43,11 +45,13 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
   const float pxf = (float)lx, pyf = (float)ly, x0f = (float)x0, y0f = (float)y0;
   const uint2 range = ranges[tile];
   const int n = (int)(range.y - range.x);
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+  // A pixel blends an entry while T (before it) is still >= kTStop: the Gaussian that
+  // takes T below the threshold is the last one blended.  Pixels outside the image
+  // start at T = 0 and take nothing.
+  float T = inside ? 1.f : 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
   uint32_t last = 0;
-  bool done = !inside;
   for (int b = 0; b < n; b += kTilePix) {
-    if (__syncthreads_count(!done) == 0) break;
+    if (__syncthreads_count(T >= kTStop) == 0) break;
     int e = b + threadIdx.x;
     if (e < n) {
       uint32_t idx = vals[range.x + e];
@@ -59,7 +63,7 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
     __syncthreads();
     const int cnt = min(kTilePix, n - b);
     for (int j0 = 0; j0 < cnt; j0 += 8) {
-      if (__all_sync(0xffffffffu, done)) break;
+      if (__all_sync(0xffffffffu, T < kTStop)) break;
       const int jn = min(8, cnt - j0);
       auto entry = [&](int jj) {
           const int j = j0 + jj;
@@ -68,7 +72,7 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
           const float p2 = frag_exp2(s_xy[j], co, pxf, pyf, dx, dy);
           const float a = __fmul_rn(co.w, ex2_approx(p2));
           const float al = fminf(kAlphaMax, a);
-          const bool on = !done && p2 <= 0.f && al >= kAlphaMin;
+          const bool on = T >= kTStop && p2 <= 0.f && al >= kAlphaMin;
           const float4 c = s_col[j];
           const float w = on ? __fmul_rn(al, T) : 0.f;
           C0 = __fmaf_rn(c.x, w, C0);
@@ -77,7 +81,6 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
           D = __fmaf_rn(c.w, w, D);
           T = __fsub_rn(T, w);
           last = on ? (uint32_t)(b + j + 1) : last;
-          done = done || (on && T < kTStop);
       };
       if (jn == 8) {
 #pragma unroll
@@ -215,13 +218,15 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
     bool act = false;
     if (__any_sync(0xffffffffu, (uint32_t)base < nc)) {
       const int lim = (int)nc - base;
-      auto entry = [&](int j) {
+      // chk: whether some pixel of the warp ends inside the batch (then j < lim matters)
+      auto entry = [&](int j, auto chk) {
           float dx, dy;
           const float4 co = S.co[buf][j];
           const float p2 = frag_exp2(S.xy[buf][j], co, pxf, pyf, dx, dy);
           const float a = __fmul_rn(co.w, ex2_approx(p2));
           const float al = fminf(kAlphaMax, a);
-          const bool on = j < lim && p2 <= 0.f && al >= kAlphaMin;
+          bool on = p2 <= 0.f && al >= kAlphaMin;
+          if constexpr (decltype(chk)::value) on = on && j < lim;
           act |= on;
           const float alc = on ? al : 0.f;
           const float4 c = S.col[buf][j];
@@ -234,13 +239,18 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
           S.gw[t][j] = make_float2((on && a <= kAlphaMax) ? dLda * a : 0.f, alc * Tb);
           T = Tb;
       };
-      if (cnt == kBwdBatch) {  // full batch: no per-entry guard
+      using Yes = std::true_type;
+      using No = std::false_type;
+      if (cnt == kBwdBatch && __all_sync(0xffffffffu, lim >= kBwdBatch)) {  // every pixel walks it all
 #pragma unroll
-        for (int j = kBwdBatch - 1; j >= 0; --j) entry(j);
+        for (int j = kBwdBatch - 1; j >= 0; --j) entry(j, No{});
+      } else if (cnt == kBwdBatch) {  // full batch: no per-entry guard
+#pragma unroll
+        for (int j = kBwdBatch - 1; j >= 0; --j) entry(j, Yes{});
       } else {
 #pragma unroll
         for (int j = kBwdBatch - 1; j >= 0; --j)
-          if (j < cnt) entry(j);
+          if (j < cnt) entry(j, Yes{});
       }
     }
     // Gaussian phase for the 32 pixels this warp just walked (skipped when none of
