@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
     __syncthreads();
     // pixel phase: branch-free back-to-front recursion; sigma = S . g (colour and depth
     // behind, dotted with the pixel's cotangent) is all the recursion needs
-    bool act = false;
-    if (__any_sync(0xffffffffu, (uint32_t)base < nc)) {
+    const bool wrun = __any_sync(0xffffffffu, (uint32_t)base < nc);
+    if (wrun) {
       const int lim = (int)nc - base;
       // chk: whether some pixel of the warp ends inside the batch (then j < lim matters)
       auto entry = [&](int j, auto chk) {
@@ -227,7 +227,6 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
           const float al = fminf(kAlphaMax, a);
           bool on = p2 <= 0.f && al >= kAlphaMin;
           if constexpr (decltype(chk)::value) on = on && j < lim;
-          act |= on;
           const float alc = on ? al : 0.f;
           const float4 c = S.col[buf][j];
           const float rom = __fdividef(1.f, 1.f - alc);
@@ -253,15 +252,16 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
           if (j < cnt) entry(j, Yes{});
       }
     }
-    // Gaussian phase for the 32 pixels this warp just walked (skipped when none of
-    // them took a contribution from the batch): per row sums of gp, k gp, k^2 gp with
+    // Gaussian phase for the 32 pixels this warp just walked (skipped when all of them
+    // ended before the batch; tracking per-pixel contributions costs more than it
+    // saves): per row sums of gp, k gp, k^2 gp with
     // k the column offset from the tile centre, then the moments about the centre of
     // the Gaussian (dx = xy.x - 7.5 - k, dy constant along the row).
     __syncwarp();  // this warp's gw rows are written by its own lanes
     float m[kMom];
 #pragma unroll
     for (int k = 0; k < kMom; ++k) m[k] = 0.f;
-    if (__any_sync(0xffffffffu, act) && e < cnt) {
+    if (wrun && e < cnt) {
       float s0 = 0.f, k1 = 0.f, k2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
 #pragma unroll
       for (int k = 0; k < kTile; ++k) {
