@@ -1,15 +1,18 @@
 // Tile blend kernels (Sec. II-E, Eq. 11), forward and reverse, sm_103a.
 //
-// One CTA of 256 threads owns one 16x16 tile of one view.  Forward: batches of
-// 256 sorted entries are gathered into shared memory (one entry per thread) and
-// every thread walks them front to back for its pixel, with transmittance and the
-// colour/depth sums in registers; the CTA leaves as soon as all its pixels stopped.
+// One CTA owns one 16x16 tile of one view.  Forward (128 threads, two pixels of one
+// column each): batches of 256 sorted entries are gathered into shared memory and
+// every thread walks them front to back for its two pixels, with transmittance and
+// the colour/depth sums in registers as packed f32 pairs; the CTA leaves as soon as
+// all its pixels stopped.
 //
-// Reverse: the tile's entries are walked back to front in batches of 16.  In the
-// pixel phase each thread runs the back-to-front recursion for its pixel (T recovered
-// by division; of the colour and depth behind each Gaussian only their dot product
-// with the pixel's cotangent is needed, one scalar) and writes two numbers per
-// (pixel, entry) into shared memory: gp = dL/dpower and the blend weight w.  In the
+// Reverse (256 threads, one pixel each): the tile's entries are walked back to front
+// in batches of 16.  In the pixel phase each thread runs the back-to-front recursion
+// for its pixel (T recovered by division; of the colour and depth behind each
+// Gaussian only their dot product with the pixel's cotangent is needed, one scalar),
+// two entries at a time so that what does not depend on the running T goes through
+// packed f32 pairs, and writes two numbers per (pixel, entry) into shared memory:
+// gp = dL/dpower and the blend weight w.  In the
 // Gaussian phase each half-warp owns one tile row and each of its lanes one entry; it
 // sums gp, k gp, k^2 gp (k the column) and w times the cotangent along the row and forms
 // the ten moments the per-Gaussian chain rule needs; the eight warps' partial sums meet
@@ -28,59 +31,80 @@
 namespace mgs {
 namespace {
 
-__global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ ViewTable vt,
-                                                        const float4* __restrict__ rec,
-                                                        const uint32_t* __restrict__ vals,
-                                                        const uint2* __restrict__ ranges) {
-  __shared__ float2 s_xy[kTilePix];
-  __shared__ float4 s_co[kTilePix];
-  __shared__ float4 s_col[kTilePix];
+// Forward: each thread blends two pixels of one column (rows 2 r and 2 r + 1), so the
+// per-entry arithmetic runs on packed f32 pairs (each element rounds exactly as the
+// scalar operation would).  Shared memory holds every entry with its values
+// duplicated, (v, v), so one 16-byte load yields two operand pairs.
+constexpr int kFwdThreads = kTilePix / 2;
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant__ ViewTable vt,
+                                                          const float4* __restrict__ rec,
+                                                          const uint32_t* __restrict__ vals,
+                                                          const uint2* __restrict__ ranges) {
+  __shared__ float4 s_xy[kTilePix];   // (x, x, y, y) tile-relative centre
+  __shared__ float4 s_ab[kTilePix];   // (A, A, B, B) scaled conic
+  __shared__ float4 s_co[kTilePix];   // (C, C, o, o)
+  __shared__ float4 s_rg[kTilePix];   // (r, r, g, g)
+  __shared__ float4 s_bd[kTilePix];   // (b, b, depth, depth)
   const int tile = blockIdx.x;
   const View& V = vt.v[view_of_tile(vt, tile)];
   const int local = tile - V.tile_base;
   const int x0 = (local % V.tiles_x) * kTile, y0 = (local / V.tiles_x) * kTile;
-  const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+  const int t = threadIdx.x;
+  const int lx = t & (kTile - 1), ly = 2 * (t / kTile);
   const int px = x0 + lx, py = y0 + ly;
-  const bool inside = px < V.width && py < V.height;
-  const float pxf = (float)lx, pyf = (float)ly, x0f = (float)x0, y0f = (float)y0;
+  const bool in0 = px < V.width && py < V.height, in1 = px < V.width && py + 1 < V.height;
+  const float x0f = (float)x0, y0f = (float)y0;
+  const float2 npx = f2(-(float)lx, -(float)lx), npy = f2(-(float)ly, -(float)(ly + 1));
   const uint2 range = ranges[tile];
   const int n = (int)(range.y - range.x);
-  // A pixel blends an entry while T (before it) is still >= kTStop: the Gaussian that
-  // takes T below the threshold is the last one blended.  Pixels outside the image
-  // start at T = 0 and take nothing.
-  float T = inside ? 1.f : 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-  uint32_t last = 0;
+  float2 T = f2(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f);
+  float2 C0 = f2(0.f, 0.f), C1 = C0, C2 = C0, D = C0;
+  uint32_t last0 = 0, last1 = 0;
   for (int b = 0; b < n; b += kTilePix) {
-    if (__syncthreads_count(T >= kTStop) == 0) break;
-    int e = b + threadIdx.x;
-    if (e < n) {
-      uint32_t idx = vals[range.x + e];
-      float4 r0 = rec[3 * (size_t)idx], r1 = rec[3 * (size_t)idx + 1], r2 = rec[3 * (size_t)idx + 2];
-      s_xy[threadIdx.x] = make_float2(__fadd_rn(__fsub_rn(r0.x, x0f), r0.z), __fadd_rn(__fsub_rn(r0.y, y0f), r0.w));
-      s_co[threadIdx.x] = r1;
-      s_col[threadIdx.x] = r2;
+    if (__syncthreads_count(T.x >= kTStop || T.y >= kTStop) == 0) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = t + h * kFwdThreads, e = b + k;
+      if (e < n) {
+        const uint32_t idx = vals[range.x + e];
+        const float4 r0 = rec[3 * (size_t)idx], r1 = rec[3 * (size_t)idx + 1], r2 = rec[3 * (size_t)idx + 2];
+        const float x = __fadd_rn(__fsub_rn(r0.x, x0f), r0.z), y = __fadd_rn(__fsub_rn(r0.y, y0f), r0.w);
+        s_xy[k] = make_float4(x, x, y, y);
+        s_ab[k] = make_float4(r1.x, r1.x, r1.y, r1.y);
+        s_co[k] = make_float4(r1.z, r1.z, r1.w, r1.w);
+        s_rg[k] = make_float4(r2.x, r2.x, r2.y, r2.y);
+        s_bd[k] = make_float4(r2.z, r2.z, r2.w, r2.w);
+      }
     }
     __syncthreads();
     const int cnt = min(kTilePix, n - b);
     for (int j0 = 0; j0 < cnt; j0 += 8) {
-      if (__all_sync(0xffffffffu, T < kTStop)) break;
+      if (__all_sync(0xffffffffu, T.x < kTStop && T.y < kTStop)) break;
       const int jn = min(8, cnt - j0);
       auto entry = [&](int jj) {
           const int j = j0 + jj;
-          float dx, dy;
-          const float4 co = s_co[j];
-          const float p2 = frag_exp2(s_xy[j], co, pxf, pyf, dx, dy);
-          const float a = __fmul_rn(co.w, ex2_approx(p2));
-          const float al = fminf(kAlphaMax, a);
-          const bool on = T >= kTStop && p2 <= 0.f && al >= kAlphaMin;
-          const float4 c = s_col[j];
-          const float w = on ? __fmul_rn(al, T) : 0.f;
-          C0 = __fmaf_rn(c.x, w, C0);
-          C1 = __fmaf_rn(c.y, w, C1);
-          C2 = __fmaf_rn(c.z, w, C2);
-          D = __fmaf_rn(c.w, w, D);
-          T = __fsub_rn(T, w);
-          last = on ? (uint32_t)(b + j + 1) : last;
+          const float4 xy = s_xy[j], ab = s_ab[j], co = s_co[j];
+          const float2 dx = __fadd2_rn(f2(xy.x, xy.y), npx);
+          const float2 dy = __fadd2_rn(f2(xy.z, xy.w), npy);
+          const float2 tt = __ffma2_rn(f2(ab.x, ab.y), dx, __fmul2_rn(f2(ab.z, ab.w), dy));
+          const float2 p2 = __ffma2_rn(tt, dx, __fmul2_rn(__fmul2_rn(f2(co.x, co.y), dy), dy));
+          const float2 a = __fmul2_rn(f2(co.z, co.w), f2(ex2_approx(p2.x), ex2_approx(p2.y)));
+          const float2 al = f2(fminf(kAlphaMax, a.x), fminf(kAlphaMax, a.y));
+          const bool on0 = T.x >= kTStop && p2.x <= 0.f && al.x >= kAlphaMin;
+          const bool on1 = T.y >= kTStop && p2.y <= 0.f && al.y >= kAlphaMin;
+          const float2 wt = __fmul2_rn(al, T);
+          const float2 w = f2(on0 ? wt.x : 0.f, on1 ? wt.y : 0.f);
+          const float4 rg = s_rg[j], bd = s_bd[j];
+          C0 = __ffma2_rn(f2(rg.x, rg.y), w, C0);
+          C1 = __ffma2_rn(f2(rg.z, rg.w), w, C1);
+          C2 = __ffma2_rn(f2(bd.x, bd.y), w, C2);
+          D = __ffma2_rn(f2(bd.z, bd.w), w, D);
+          T = __fadd2_rn(T, f2(-w.x, -w.y));
+          last0 = on0 ? (uint32_t)(b + j + 1) : last0;
+          last1 = on1 ? (uint32_t)(b + j + 1) : last1;
       };
       if (jn == 8) {
 #pragma unroll
@@ -92,15 +116,16 @@ __global__ void __launch_bounds__(kTilePix) k_blend_fwd(const __grid_constant__ 
       }
     }
   }
-  if (inside) {
-    size_t o = (size_t)py * V.width + px, HW = (size_t)V.width * V.height;
-    V.rgb[o] = C0;
-    V.rgb[HW + o] = C1;
-    V.rgb[2 * HW + o] = C2;
-    V.depth[o] = D;
-    V.alpha[o] = 1.f - T;
-    V.T_final[o] = T;
-    V.n_contrib[o] = last;
+  const size_t HW = (size_t)V.width * V.height;
+  if (in0) {
+    const size_t o = (size_t)py * V.width + px;
+    V.rgb[o] = C0.x; V.rgb[HW + o] = C1.x; V.rgb[2 * HW + o] = C2.x;
+    V.depth[o] = D.x; V.alpha[o] = 1.f - T.x; V.T_final[o] = T.x; V.n_contrib[o] = last0;
+  }
+  if (in1) {
+    const size_t o = (size_t)(py + 1) * V.width + px;
+    V.rgb[o] = C0.y; V.rgb[HW + o] = C1.y; V.rgb[2 * HW + o] = C2.y;
+    V.depth[o] = D.y; V.alpha[o] = 1.f - T.y; V.T_final[o] = T.y; V.n_contrib[o] = last1;
   }
 }
 
@@ -121,9 +146,12 @@ struct BwdSmem {
                                             // phase each warp's rows hold its partial moments
   float4 g[kTilePix];                       // per pixel dL/d(r, g, b, depth)
   float4 raw[2][kBwdBatch][3];              // records of the next batch, landed by cp.async
-  float2 xy[2][kBwdBatch];                  // tile-relative centre
-  float4 co[2][kBwdBatch];                  // scaled conic, opacity
-  float4 col[2][kBwdBatch];                 // colour, depth
+  // entries 2p and 2p+1 side by side, so one 16-byte load gives two operand pairs
+  float4 q_xy[2][kBwdBatch / 2];            // (x, x', y, y') tile-relative centre
+  float4 q_ab[2][kBwdBatch / 2];            // (A, A', B, B') scaled conic
+  float4 q_co[2][kBwdBatch / 2];            // (C, C', o, o')
+  float4 q_rg[2][kBwdBatch / 2];            // (r, r', g, g')
+  float4 q_bd[2][kBwdBatch / 2];            // (b, b', depth, depth')
   uint32_t idx[2][kBwdBatch];
   int lmax;
 };
@@ -195,13 +223,29 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
     const int cnt = min(kBwdBatch, L - base);
     if (t < kBwdBatch) {
       cp_async_wait_all();
+      // entries past the end of a partial batch are zeroed: their pair partner then
+      // reads finite values (they enter with alpha = 0)
+      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+      float x = 0.f, y = 0.f;
       if (t < cnt) {
-        const float4 r0 = S.raw[buf][t][0];
-        S.xy[buf][t] = make_float2(__fadd_rn(__fsub_rn(r0.x, x0f), r0.z), __fadd_rn(__fsub_rn(r0.y, y0f), r0.w));
-        S.co[buf][t] = S.raw[buf][t][1];
-        S.col[buf][t] = S.raw[buf][t][2];
+        r0 = S.raw[buf][t][0];
+        r1 = S.raw[buf][t][1];
+        r2 = S.raw[buf][t][2];
+        x = __fadd_rn(__fsub_rn(r0.x, x0f), r0.z);
+        y = __fadd_rn(__fsub_rn(r0.y, y0f), r0.w);
         S.idx[buf][t] = idx_cur;
       }
+      const int pp = t >> 1, sl = t & 1;
+      float* const qxy = reinterpret_cast<float*>(&S.q_xy[buf][pp]);
+      float* const qab = reinterpret_cast<float*>(&S.q_ab[buf][pp]);
+      float* const qco = reinterpret_cast<float*>(&S.q_co[buf][pp]);
+      float* const qrg = reinterpret_cast<float*>(&S.q_rg[buf][pp]);
+      float* const qbd = reinterpret_cast<float*>(&S.q_bd[buf][pp]);
+      qxy[sl] = x; qxy[2 + sl] = y;
+      qab[sl] = r1.x; qab[2 + sl] = r1.y;
+      qco[sl] = r1.z; qco[2 + sl] = r1.w;
+      qrg[sl] = r2.x; qrg[2 + sl] = r2.y;
+      qbd[sl] = r2.z; qbd[2 + sl] = r2.w;
       if (base >= kBwdBatch) {  // the next batch is full: every t < kBwdBatch has an entry
         const float4* src = rec + 3 * (size_t)idx_next;
         cp_async16(&S.raw[buf ^ 1][t][0], src);
@@ -218,38 +262,60 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
     const bool wrun = __any_sync(0xffffffffu, (uint32_t)base < nc);
     if (wrun) {
       const int lim = (int)nc - base;
-      // chk: whether some pixel of the warp ends inside the batch (then j < lim matters)
-      auto entry = [&](int j, auto chk) {
-          float dx, dy;
-          const float4 co = S.co[buf][j];
-          const float p2 = frag_exp2(S.xy[buf][j], co, pxf, pyf, dx, dy);
-          const float a = __fmul_rn(co.w, ex2_approx(p2));
-          const float al = fminf(kAlphaMax, a);
-          bool on = p2 <= 0.f && al >= kAlphaMin;
-          if constexpr (decltype(chk)::value) on = on && j < lim;
-          const float alc = on ? al : 0.f;
-          const float4 c = S.col[buf][j];
-          const float rom = __fdividef(1.f, 1.f - alc);
-          const float Tb = T * rom;
-          const float cg = fmaf(c.x, gR, fmaf(c.y, gG, fmaf(c.z, gB, c.w * gD)));
-          const float d = cg - sig;
-          const float dLda = fmaf(Tb, d, gAT * rom);
-          sig = fmaf(alc, d, sig);
-          S.gw[t][j] = make_float2((on && a <= kAlphaMax) ? dLda * a : 0.f, alc * Tb);
-          T = Tb;
+      // chk: whether some pixel of the warp ends inside the batch (then j < lim matters).
+      // Entries go in pairs (2p+1 first, then 2p): what does not depend on the running
+      // T and sigma is computed for both at once on packed f32 pairs.
+      const float2 npx = make_float2(-pxf, -pxf), npy = make_float2(-pyf, -pyf);
+      const float2 gR2 = make_float2(gR, gR), gG2 = make_float2(gG, gG), gB2 = make_float2(gB, gB),
+                   gD2 = make_float2(gD, gD), gAT2 = make_float2(gAT, gAT);
+      auto pair = [&](int p, auto chk) {
+          const float4 xy = S.q_xy[buf][p], ab = S.q_ab[buf][p], co = S.q_co[buf][p];
+          const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), npx);
+          const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), npy);
+          const float2 tt = __ffma2_rn(make_float2(ab.x, ab.y), dx, __fmul2_rn(make_float2(ab.z, ab.w), dy));
+          const float2 p2 = __ffma2_rn(tt, dx, __fmul2_rn(__fmul2_rn(make_float2(co.x, co.y), dy), dy));
+          const float2 a = __fmul2_rn(make_float2(co.z, co.w), make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
+          const float al0 = fminf(kAlphaMax, a.x), al1 = fminf(kAlphaMax, a.y);
+          bool on0 = p2.x <= 0.f && al0 >= kAlphaMin, on1 = p2.y <= 0.f && al1 >= kAlphaMin;
+          if constexpr (decltype(chk)::value) {
+            on0 = on0 && 2 * p < lim;
+            on1 = on1 && 2 * p + 1 < lim;
+          }
+          const float2 alc = make_float2(on0 ? al0 : 0.f, on1 ? al1 : 0.f);
+          const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-alc.x, -alc.y));
+          const float2 rom = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
+          const float4 rg = S.q_rg[buf][p], bd = S.q_bd[buf][p];
+          const float2 cg = __ffma2_rn(make_float2(rg.x, rg.y), gR2,
+                                       __ffma2_rn(make_float2(rg.z, rg.w), gG2,
+                                                  __ffma2_rn(make_float2(bd.x, bd.y), gB2,
+                                                             __fmul2_rn(make_float2(bd.z, bd.w), gD2))));
+          const float2 gar = __fmul2_rn(gAT2, rom);
+          const float Tb1 = T * rom.y;
+          const float d1 = cg.y - sig;
+          const float dLda1 = fmaf(Tb1, d1, gar.y);
+          sig = fmaf(alc.y, d1, sig);
+          const float Tb0 = Tb1 * rom.x;
+          const float d0 = cg.x - sig;
+          const float dLda0 = fmaf(Tb0, d0, gar.x);
+          sig = fmaf(alc.x, d0, sig);
+          T = Tb0;
+          const float2 gp = __fmul2_rn(make_float2(dLda0, dLda1), a);
+          const float2 w = __fmul2_rn(alc, make_float2(Tb0, Tb1));
+          S.gw[t][2 * p + 1] = make_float2((on1 && a.y <= kAlphaMax) ? gp.y : 0.f, w.y);
+          S.gw[t][2 * p] = make_float2((on0 && a.x <= kAlphaMax) ? gp.x : 0.f, w.x);
       };
       using Yes = std::true_type;
       using No = std::false_type;
       if (cnt == kBwdBatch && __all_sync(0xffffffffu, lim >= kBwdBatch)) {  // every pixel walks it all
 #pragma unroll
-        for (int j = kBwdBatch - 1; j >= 0; --j) entry(j, No{});
+        for (int p = kBwdBatch / 2 - 1; p >= 0; --p) pair(p, No{});
       } else if (cnt == kBwdBatch) {  // full batch: no per-entry guard
 #pragma unroll
-        for (int j = kBwdBatch - 1; j >= 0; --j) entry(j, Yes{});
+        for (int p = kBwdBatch / 2 - 1; p >= 0; --p) pair(p, Yes{});
       } else {
 #pragma unroll
-        for (int j = kBwdBatch - 1; j >= 0; --j)
-          if (j < cnt) entry(j, Yes{});
+        for (int p = kBwdBatch / 2 - 1; p >= 0; --p)
+          if (2 * p < cnt) pair(p, Yes{});
       }
     }
     // Gaussian phase for the 32 pixels this warp just walked (skipped when all of them
@@ -277,8 +343,8 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
         w2 = fmaf(gw.y, gg.z, w2);
         w3 = fmaf(gw.y, gg.w, w3);
       }
-      const float2 xy = S.xy[buf][e];
-      const float xc = xy.x - 7.5f, dy = xy.y - (float)(prow / kTile);
+      const float* const qxy = reinterpret_cast<const float*>(&S.q_xy[buf][e >> 1]);
+      const float xc = qxy[e & 1] - 7.5f, dy = qxy[2 + (e & 1)] - (float)(prow / kTile);
       const float m1 = fmaf(xc, s0, -k1);                    // sum gp (xc - kc)
       m[0] = s0;
       m[1] = m1;
@@ -402,7 +468,7 @@ size_t blend_bwd_smem() { return sizeof(BwdSmem); }
 cudaError_t launch_blend_fwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
                              const uint2* ranges, cudaStream_t s) {
   if (vt.n_tiles <= 0) return cudaSuccess;
-  k_blend_fwd<<<vt.n_tiles, kTilePix, 0, s>>>(vt, rec, vals, ranges);
+  k_blend_fwd<<<vt.n_tiles, kFwdThreads, 0, s>>>(vt, rec, vals, ranges);
   count_launch();
   return cudaGetLastError();
 }
