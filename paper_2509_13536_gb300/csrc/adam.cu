@@ -18,12 +18,28 @@ __device__ __forceinline__ float adam_update(float p, float& g, float& m, float&
   return p - h.lr * (m / h.c1) / (sqrtf(v / h.c2) + h.eps);
 }
 
-// One parameter array; each thread owns 4 consecutive elements (16-byte vector
-// accesses on the f32 gradient and moment arrays).
+// The parameter arrays of one step: block b works on the segment whose block range
+// holds b; each thread owns 4 consecutive elements (16-byte vector accesses on the f32
+// gradient and moment arrays).
+struct AdamSeg {
+  void* p;
+  float* g;
+  float* m;
+  float* v;
+  int64_t n;
+  int dt;          // storage type of p
+  int block_end;   // one past the last block of this segment
+};
+struct AdamTable {
+  AdamSeg seg[5];
+  int n_seg;
+};
+constexpr int kAdamThreads = 256;
+constexpr int kAdamPerBlock = 4 * kAdamThreads;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_adam(T* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
-                                              float* __restrict__ v, int64_t n, const AdamHyper h) {
-  int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+__device__ __forceinline__ void adam_seg(T* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
+                                         float* __restrict__ v, int64_t n, int64_t i, const AdamHyper& h) {
   if (i >= n) return;
   if (i + 4 <= n) {
     float4 gg = *reinterpret_cast<float4*>(g + i), mm = *reinterpret_cast<float4*>(m + i),
@@ -56,6 +72,19 @@ __global__ void __launch_bounds__(256) k_adam(T* __restrict__ p, float* __restri
       if (h.zero_grads) g[k] = gk;
       st(p + k, x);
     }
+  }
+}
+
+__global__ void __launch_bounds__(kAdamThreads) k_adam(const __grid_constant__ AdamTable tab, const AdamHyper h) {
+  int s = 0;
+  while (s + 1 < tab.n_seg && (int)blockIdx.x >= tab.seg[s].block_end) ++s;
+  const AdamSeg& q = tab.seg[s];
+  const int b0 = s ? tab.seg[s - 1].block_end : 0;
+  const int64_t i = ((int64_t)((int)blockIdx.x - b0) * kAdamThreads + threadIdx.x) * 4;
+  switch (q.dt) {  // uniform per block
+    case MGS_F16: adam_seg((__half*)q.p, q.g, q.m, q.v, q.n, i, h); break;
+    case MGS_BF16: adam_seg((__nv_bfloat16*)q.p, q.g, q.m, q.v, q.n, i, h); break;
+    default: adam_seg((float*)q.p, q.g, q.m, q.v, q.n, i, h); break;
   }
 }
 
@@ -97,16 +126,17 @@ cudaError_t launch_adam(const mgs_gaussians_mut& p, const mgs_grads& g, const mg
       {p.quats, p.geom_dtype, g.quats, m.quats, v.quats, 4 * n},
       {p.opacity_logit, p.attr_dtype, g.opacity_logit, m.opacity_logit, v.opacity_logit, n},
       {p.sh, p.attr_dtype, g.sh, m.sh, v.sh, K3 * n}};
+  AdamTable tab{};
+  int64_t blocks = 0;
   for (const Seg& q : list) {
     if (q.n <= 0) continue;
-    unsigned grid = (unsigned)div_up(q.n, 1024);
-    switch (q.dt) {
-      case MGS_F16: k_adam<__half><<<grid, 256, 0, s>>>((__half*)q.p, q.g, q.m, q.v, q.n, h); break;
-      case MGS_BF16: k_adam<__nv_bfloat16><<<grid, 256, 0, s>>>((__nv_bfloat16*)q.p, q.g, q.m, q.v, q.n, h); break;
-      default: k_adam<float><<<grid, 256, 0, s>>>((float*)q.p, q.g, q.m, q.v, q.n, h); break;
-    }
-    count_launch();
+    blocks += div_up(q.n, kAdamPerBlock);
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+    tab.seg[tab.n_seg++] = AdamSeg{q.p, q.g, q.m, q.v, q.n, q.dt, (int)blocks};
   }
+  if (blocks == 0) return cudaSuccess;
+  k_adam<<<(unsigned)blocks, kAdamThreads, 0, s>>>(tab, h);
+  count_launch();
   return cudaGetLastError();
 }
 

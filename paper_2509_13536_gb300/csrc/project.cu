@@ -262,9 +262,30 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(int64_t N, const floa
                                                         const uint32_t* __restrict__ touched,
                                                         const uint2* __restrict__ rects,
                                                         mgs_grads grads) {
+  // Lanes of a warp hold different Gaussians, drawn in different views: each thread
+  // first lists its own views with a gradient, then walks only those (in view order),
+  // so the lanes of a warp run the per-view body together on different views.  The
+  // view constants are read from a shared-memory copy (the index differs per lane).
+  __shared__ View s_view[MGS_MAX_VIEWS];
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&vt.v[0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&s_view[0]);
+    const int words = vt.n_views * (int)(sizeof(View) / 4);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+  }
+  __syncthreads();
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   constexpr int K = (DEG + 1) * (DEG + 1);
+  uint32_t drawn = 0, todo = 0;
+  for (int v = 0; v < vt.n_views; ++v) {
+    const uint2 rc = rects[(int64_t)v * N + g];
+    if ((rc.x & 0xffff) <= (rc.y & 0xffff)) drawn |= 1u << v;
+  }
+  for (int v = 0; v < vt.n_views; ++v)  // drawn, but reaching no pixel: zero gradient
+    if (((drawn >> v) & 1u) && touched[(int64_t)v * N + g] != 0) todo |= 1u << v;
+  const float vis = (float)__popc(drawn);
+  if (drawn == 0) return;
   GaussPre G;
   load_gauss(g, means, geo, ol, G);
   float c[3 * K];
@@ -273,14 +294,12 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(int64_t N, const floa
   float dsh[3 * K];
 #pragma unroll
   for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
-  float stat = 0.f, vis = 0.f;
-  for (int v = 0; v < vt.n_views; ++v) {
-    int64_t item = (int64_t)v * N + g;
-    uint2 rc = rects[item];
-    if ((rc.x & 0xffff) > (rc.y & 0xffff)) continue;  // not drawn in this view
-    vis += 1.f;
-    if (touched[item] == 0) continue;  // drawn, but reaches no pixel: zero gradient
-    const View& V = vt.v[v];
+  float stat = 0.f;
+  while (todo) {
+    const int v = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int64_t item = (int64_t)v * N + g;
+    const View& V = s_view[v];
     float4 q0 = moments[3 * item], q1 = moments[3 * item + 1], q2 = moments[3 * item + 2];
     ViewGeom P;
     view_geom(G, V, P);
@@ -372,7 +391,6 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(int64_t N, const floa
     for (int k = 0; k < 3; ++k) dmu[k] += dm[k];
     stat += sqrtf(dm[0] * dm[0] + dm[1] * dm[1] + dm[2] * dm[2]);
   }
-  if (vis == 0.f) return;
   // S3 = Rq diag(s^2) Rq^T  ->  log-scales and quaternion
   const float* R = G.Rq;
   float H[9] = {dS3[0], dS3[1], dS3[2], dS3[1], dS3[3], dS3[4], dS3[2], dS3[4], dS3[5]};
