@@ -262,14 +262,32 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
   }
 }
 
+// Tile ranges of the sorted keys: four keys per thread (one vector load), neighbours
+// at the ends from the adjacent threads' keys.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, int64_t n, uint32_t n_valid,
                          uint2* __restrict__ ranges) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  uint32_t key = keys[k];
-  if (key >= n_valid) return;  // sentinel keys
-  if (k == 0 || keys[k - 1] != key) ranges[key].x = (uint32_t)k;
-  if (k == n - 1 || keys[k + 1] != key) ranges[key].y = (uint32_t)(k + 1);
+  const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (k0 >= n) return;
+  uint32_t kk[4];
+  if (k0 + 4 <= n && (reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
+    const uint4 q = *reinterpret_cast<const uint4*>(keys + k0);
+    kk[0] = q.x; kk[1] = q.y; kk[2] = q.z; kk[3] = q.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) kk[q] = k0 + q < n ? keys[k0 + q] : 0xffffffffu;
+  }
+  const uint32_t prev = k0 > 0 ? keys[k0 - 1] : 0xffffffffu;
+  const uint32_t next = k0 + 4 < n ? keys[k0 + 4] : 0xffffffffu;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t k = k0 + q;
+    const uint32_t key = kk[q];
+    if (k >= n || key >= n_valid) continue;  // past the end, or sentinel keys
+    const uint32_t left = q ? kk[q - 1] : prev;
+    const uint32_t right = q < 3 ? kk[q + 1] : next;
+    if (k == 0 || left != key) ranges[key].x = (uint32_t)k;
+    if (k == n - 1 || right != key) ranges[key].y = (uint32_t)(k + 1);
+  }
 }
 
 }  // namespace
@@ -334,7 +352,7 @@ int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, i
 
 cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_ranges<<<(unsigned)div_up(n, 256), 256, 0, s>>>(keys, n, n_valid, ranges);
+  k_ranges<<<(unsigned)div_up(div_up(n, 4), 256), 256, 0, s>>>(keys, n, n_valid, ranges);
   count_launch();
   return cudaGetLastError();
 }
