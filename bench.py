@@ -625,8 +625,9 @@ def run_ours(args):
                        "resolution": f"{W}x{H}", "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (236 MB parameters, 384 MB projected records, "
                              f"{stats['keys']} tile keys per step)"},
-            "roofline": roofline, "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d,
-                                          "d2h_bytes_per_step": 4},
+            "roofline": roofline,
+            "e2e": ({"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+                    if n_e2e > 0 else None),
             "gpu_launches": launches, "clocks": csum, "kernels": kern, "fragments": stats,
             "merge_survivors": state["n_out"]}
     if eq12:
