@@ -3,8 +3,8 @@
 // Reduce-then-scan structure, no inter-block waiting: every pass is a histogram
 // kernel, a scan of the digit-major histogram table, and a stable scatter.  Blocks
 // own 4096 consecutive items; inside a block, items are ranked round by round (256
-// at a time) with warp match masks and per-warp digit counters in shared memory,
-// which keeps equal keys in input order.
+// at a time) with warp peer masks (match instruction, or one ballot per digit bit) and
+// per-warp digit counters in shared memory, which keeps equal keys in input order.
 #include "internal.h"
 
 namespace mgs {
@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 // block-wide prefix over the warps' counts then gives every item its position in the
 // block's digit-sorted order; items are staged in shared memory in that order and
 // written out as coalesced runs per digit.
+template <bool kBallot>
 __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
     uint32_t mask, int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
@@ -197,6 +198,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
   s_goff[t] = hist[(int64_t)t * nb + blockIdx.x];
   __syncthreads();
   const uint32_t lt = lanemask_lt();
+  const int nbits = __popc(mask);
   uint32_t key[kRounds], val[kRounds], rank[kRounds];
   // all 32 loads of the warp's segment in flight before the ranking starts
 #pragma unroll
@@ -211,7 +213,23 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const int i = w * kPerWarp + r * 32 + lane;
     const bool valid = i < n_here && !(drop && key[r] == kSortDrop);
     const uint32_t d = valid ? (key[r] >> shift) & mask : 256u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // lanes holding the same digit: the match instruction costs more the more distinct
+    // digits a round holds, the ballot form (one ballot per digit bit) costs the same
+    // for any round
+    uint32_t peers;
+    if (kBallot) {
+      peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        if (b < nbits) {
+          const bool bit = (d >> b) & 1u;
+          const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+          peers &= bit ? bal : ~bal;
+        }
+      }
+    } else {
+      peers = __match_any_sync(0xffffffffu, d);
+    }
     const uint32_t before = valid ? s_wcnt[w][d] : 0u;
     rank[r] = before + __popc(peers & lt);
     __syncwarp();
@@ -332,8 +350,16 @@ int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, i
     *err = scan_exclusive_u32(hist, nullptr, hist, (int64_t)256 * nb, spine, nullptr, s);
     if (*err != cudaSuccess) return cur;
     const uint32_t* vin = (first && vals_iota) ? nullptr : v[cur];
-    k_radix_scatter<<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, mask, nb, hist, k[cur ^ 1],
-                                                v[cur ^ 1], drop);
+    // Full 8-bit digits below the top byte take the ballot form: there (low bytes of tile
+    // ids, middle bytes of depths) a warp's 32 keys hold nearly 32 distinct digits.  The
+    // top byte and the first, dropping pass of the depth sort hold few distinct digits
+    // per round and keep the match instruction.
+    if (mask == 0xffu && !drop && shift < 24)
+      k_radix_scatter<true><<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, mask, nb, hist, k[cur ^ 1],
+                                                        v[cur ^ 1], drop);
+    else
+      k_radix_scatter<false><<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, mask, nb, hist, k[cur ^ 1],
+                                                         v[cur ^ 1], drop);
     cur ^= 1;
     first = false;
     if (drop) {
