@@ -5,8 +5,9 @@
 //  2. k_voxel_pack   voxel coordinates packed relative to the box into one u32 key
 //                    (ineligible Gaussians get the all-ones key and sort last).
 //  3. radix sort of (key, index); segment heads -> one (start, end) per voxel.
-//  4. k_voxel_pairs  one warp per voxel (<= 32 members; larger voxels go to a
-//                    block-per-voxel kernel, <= 256 members): members ranked by
+//  4. k_voxel_pairs  8 lanes per voxel of <= 8 members, a whole warp per voxel of
+//                    9..32 (larger voxels go to a block-per-voxel kernel, <= 256
+//                    members): members ranked by
 //                    (birth, index), Eq. 4 for every older/younger pair, greedy
 //                    disjoint pairing on (d2, birth_i, birth_j, i, j) below chi2,
 //                    then the merge of each accepted pair: Eq. 6 mean, the
@@ -525,7 +526,15 @@ struct PairCand {
   int a, b;  // member ranks (a older)
 };
 
-// Warp path: a voxel with 2..32 members.
+// Pairing of the voxels with 2..32 members (larger ones go to the block path).
+// Members are ranked by (birth, index), Eq. 4 is evaluated for every older/younger
+// pair, and pairs below chi2 are taken greedily on (d2, birth_i, birth_j, i, j).
+// A warp takes four consecutive voxels at a time: voxels with at most 8 members are
+// paired by 8-lane groups side by side (all shuffles run on the whole warp with fixed
+// trip counts; a group's lanes reduce among themselves), larger ones by the whole warp
+// one after the other.
+constexpr int kGroupVoxel = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_voxel_pairs(
     const float* __restrict__ means, const Geom geo,
@@ -539,14 +548,14 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
   __shared__ int s_pairs[4][kWarpVoxel / 2][2];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_vox = (int64_t)*n_vox_p;
-  // Persistent warps: warp-stride loop over the voxels.
-  for (int64_t v = (int64_t)blockIdx.x * 4 + wib; v < n_vox; v += (int64_t)gridDim.x * 4) {
+  // whole-warp pairing of voxel v (2..32 members; more go to the big list)
+  auto warp_voxel = [&](int64_t v) {
   const uint32_t st = starts[v], en = starts[v + 1];
   const int nm = (int)(en - st);
-  if (nm < 2) continue;
+  if (nm < 2) return;
   if (nm > kWarpVoxel) {
     if (lane == 0) big[atomicAdd(n_big, 1u)] = (uint32_t)v;
-    continue;
+    return;
   }
   int64_t my = lane < nm ? (int64_t)perm[st + lane] : -1;
   uint64_t mb = lane < nm ? birth[my] : ~0ull;
@@ -619,6 +628,110 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     pairs[slot + lane] = make_uint2((uint32_t)i, (uint32_t)j);
   }
   __syncwarp();  // the warp's shared rows are reused by its next voxel
+  };
+  const int grp = lane >> 3, gl = lane & (kGroupVoxel - 1), gbase = grp * kGroupVoxel;
+  // Persistent warps: warp-stride loop over groups of four voxels.
+  for (int64_t vg = ((int64_t)blockIdx.x * 4 + wib) * 4; vg < n_vox; vg += (int64_t)gridDim.x * 16) {
+    const int64_t v = vg + grp;
+    uint32_t st = 0;
+    int nm = 0;
+    if (v < n_vox) {
+      st = starts[v];
+      nm = (int)(starts[v + 1] - st);
+    }
+    const bool small = nm >= 2 && nm <= kGroupVoxel;
+    const bool mine = small && gl < nm;
+    const int64_t my = mine ? (int64_t)perm[st + gl] : -1;
+    const uint64_t mb = mine ? birth[my] : ~0ull;
+    int rank = 0;
+#pragma unroll
+    for (int m = 0; m < kGroupVoxel; ++m) {
+      const int64_t oi = __shfl_sync(0xffffffffu, my, gbase + m);
+      const uint64_t ob = __shfl_sync(0xffffffffu, mb, gbase + m);
+      if (mine && m < nm && older(ob, oi, mb, my)) ++rank;
+    }
+    if (mine) {
+      s_idx[wib][gbase + rank] = my;
+      s_birth[wib][gbase + rank] = mb;
+    }
+    __syncwarp();
+    if (mine) {  // Eq. 4 row: rank gl (older) against every younger rank
+      const int64_t ia = s_idx[wib][gbase + gl];
+      float P[6];
+      precision_of(geo, ia, P);
+      const float* ma = means + 3 * ia;
+      const float mav[3] = {ma[0], ma[1], ma[2]};
+      for (int b = gl + 1; b < nm; ++b) {
+        const float* mb3 = means + 3 * s_idx[wib][gbase + b];
+        const float mbv[3] = {mb3[0], mb3[1], mb3[2]};
+        s_d2[wib][gbase + gl][b] = mahalanobis2(P, mav, mbv);
+      }
+    }
+    __syncwarp();
+    uint32_t matched = 0;
+    int np = 0;
+    bool done = !small;
+    for (int round = 0; round < kGroupVoxel / 2; ++round) {
+      PairCand best{INFINITY, -1, -1};
+      if (!done && gl < nm && !((matched >> gl) & 1u)) {
+        for (int b = gl + 1; b < nm; ++b) {
+          if ((matched >> b) & 1u) continue;
+          const float d2 = s_d2[wib][gbase + gl][b];
+          if (d2 < chi2 && d2 < best.d2) best = PairCand{d2, gl, b};
+        }
+      }
+      for (int o = kGroupVoxel / 2; o; o >>= 1) {  // stays inside the 8-lane group
+        PairCand oc{__shfl_xor_sync(0xffffffffu, best.d2, o), __shfl_xor_sync(0xffffffffu, best.a, o),
+                    __shfl_xor_sync(0xffffffffu, best.b, o)};
+        bool take;
+        if (oc.a < 0) take = false;
+        else if (best.a < 0) take = true;
+        else if (oc.d2 != best.d2) take = oc.d2 < best.d2;
+        else {
+          const uint64_t b1 = s_birth[wib][gbase + best.a], b2 = s_birth[wib][gbase + best.b];
+          const uint64_t c1 = s_birth[wib][gbase + oc.a], c2 = s_birth[wib][gbase + oc.b];
+          const int64_t i1 = s_idx[wib][gbase + best.a], i2 = s_idx[wib][gbase + best.b];
+          const int64_t j1 = s_idx[wib][gbase + oc.a], j2 = s_idx[wib][gbase + oc.b];
+          if (c1 != b1) take = c1 < b1;
+          else if (c2 != b2) take = c2 < b2;
+          else if (j1 != i1) take = j1 < i1;
+          else take = j2 < i2;
+        }
+        if (take) best = oc;
+      }
+      if (!done) {
+        if (best.a < 0) {
+          done = true;
+        } else {
+          matched |= (1u << best.a) | (1u << best.b);
+          if (gl == 0) {
+            s_pairs[wib][grp * (kGroupVoxel / 2) + np][0] = best.a;
+            s_pairs[wib][grp * (kGroupVoxel / 2) + np][1] = best.b;
+          }
+          ++np;
+          if (!greedy || np == nm / 2) done = true;
+        }
+      }
+      if (__all_sync(0xffffffffu, done)) break;
+    }
+    __syncwarp();
+    uint32_t slot = 0;
+    if (gl == 0 && np > 0) slot = atomicAdd(n_pairs, (uint32_t)np);
+    slot = __shfl_sync(0xffffffffu, slot, gbase);
+    if (gl < np) {
+      const int64_t i = s_idx[wib][gbase + s_pairs[wib][grp * (kGroupVoxel / 2) + gl][0]];
+      const int64_t j = s_idx[wib][gbase + s_pairs[wib][grp * (kGroupVoxel / 2) + gl][1]];
+      partner[i] = (int32_t)j;
+      partner[j] = (int32_t)i;
+      pairs[slot + gl] = make_uint2((uint32_t)i, (uint32_t)j);
+    }
+    __syncwarp();  // the groups' shared rows are reused below and by the next voxels
+    uint32_t large = __ballot_sync(0xffffffffu, gl == 0 && nm > kGroupVoxel);
+    while (large) {
+      const int src = __ffs(large) - 1;
+      large &= large - 1;
+      warp_voxel(vg + (src >> 3));
+    }
   }
 }
 

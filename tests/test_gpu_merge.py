@@ -7,6 +7,7 @@ import torch
 
 from paper_2509_13536_gb300 import api, scenegen as sg
 from tests import _gpu
+from tests._scenes import make_scene
 from tests.test_oracle_merge import _voxel_scene
 
 pytestmark = pytest.mark.gpu
@@ -85,6 +86,30 @@ def test_merge_small_voxels(orc, greedy):
     sc = _voxel_scene(rng, 200, 6)
     pairs, n = compare_merge(orc, sc, 0.02, greedy=greedy)
     assert pairs > 50
+
+
+def _mixed_voxel_scene(rng, sizes, v=0.02):
+    """One voxel per entry of ``sizes`` (member count), each on its own grid cell."""
+    means, scales, quats = [], [], []
+    for k, per in enumerate(sizes):
+        base = (np.array([k % 7, (k // 7) % 5, k // 35]) + 0.5) * v
+        for _ in range(per):
+            means.append(base + rng.uniform(-0.3, 0.3, 3) * v)
+            scales.append(np.exp(rng.uniform(np.log(0.004), np.log(0.02), 3)))
+            quats.append(rng.normal(size=4))
+    n = len(means)
+    return make_scene(means, scales, quats, rng.uniform(0.1, 0.9, n), rng.random((n, 3)), 0,
+                      birth=rng.permutation(n))
+
+
+@pytest.mark.parametrize("greedy", [True, False])
+def test_merge_mixed_voxel_sizes(orc, greedy):
+    """Voxels of 1..33 members side by side: the 8-lane group path (<= 8 members), the
+    whole-warp path (9..32) and the block path (> 32) within the same groups of four."""
+    rng = np.random.default_rng(11)
+    sizes = [2, 9, 3, 8, 1, 16, 7, 32, 33, 4, 12, 2, 8, 8, 9, 5] * 4
+    pairs, n = compare_merge(orc, _mixed_voxel_scene(rng, sizes), 0.02, greedy=greedy)
+    assert pairs > 40
 
 
 def test_merge_crowded_voxels_use_block_path(orc):
