@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant
 // transposed, and in the Gaussian phase each half-warp sums one tile row of them per
 // entry into the ten moments the chain rule of Eq. 1-2 needs.
 constexpr int kBwdBatch = 16;
-constexpr int kBwdStride = kBwdBatch + 1;  // padded row: conflict-free both ways
+constexpr int kBwdStride = kBwdBatch + 2;  // padded row: 16-byte aligned, conflict-free both ways
 constexpr int kBwdWarps = kTilePix / 32;
 constexpr int kMom = 10;
 constexpr int kRedStride = kMom + 1;     // per-entry row of partial moments (odd: no conflicts)
@@ -301,8 +301,8 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
           T = Tb0;
           const float2 gp = __fmul2_rn(make_float2(dLda0, dLda1), a);
           const float2 w = __fmul2_rn(alc, make_float2(Tb0, Tb1));
-          S.gw[t][2 * p + 1] = make_float2((on1 && a.y <= kAlphaMax) ? gp.y : 0.f, w.y);
-          S.gw[t][2 * p] = make_float2((on0 && a.x <= kAlphaMax) ? gp.x : 0.f, w.x);
+          *reinterpret_cast<float4*>(&S.gw[t][2 * p]) =
+              make_float4((on0 && a.x <= kAlphaMax) ? gp.x : 0.f, w.x, (on1 && a.y <= kAlphaMax) ? gp.y : 0.f, w.y);
       };
       using Yes = std::true_type;
       using No = std::false_type;
