@@ -17,6 +17,7 @@ workload (there is no runnable reference implementation of the paper).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -393,8 +394,13 @@ def serving_leg(args, api, torch, sg, dev):
                     break
 
         th = threading.Thread(target=collect, daemon=True)
+        # no cyclic garbage collection while requests are timed: a full pass over this
+        # process's objects stalls the submitting thread for ~0.1 s
+        gc.collect()
+        gc.disable()
         th.start()
         t0 = server.clock() + 0.2
+        late = np.zeros(n_req)
         for i, (sid, cam) in enumerate(reqs):
             target = t0 + float(arrivals[i])
             d = target - server.clock()
@@ -402,13 +408,22 @@ def serving_leg(args, api, torch, sg, dev):
                 time.sleep(d)
             key = (cam.width, cam.height)
             server.submit(ids[sid], cam, ring[key][i % 16], i, target)
+            late[i] = server.clock() - target  # the client's own delay in submitting
         stop[0] = True
         th.join(timeout=600)
+        gc.enable()
         server.close()
         lat = np.array([got[i][2] - got[i][0] for i in range(warm, n_req) if i in got and got[i][3] == 0])
         t_first = t0 + float(arrivals[warm])
         t_last = max(got[i][2] for i in range(warm, n_req) if i in got)
+        ok = [i for i in range(warm, n_req) if i in got and got[i][3] == 0]
+        queue = np.array([got[i][1] - got[i][0] for i in ok])
+        service = np.array([got[i][2] - got[i][1] for i in ok])
+        pct = lambda a, q: float(np.percentile(a, q) * 1e3) if len(a) else None
         res = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+               "max_ms": float(lat.max() * 1e3),
+               "p99_client_late_ms": pct(late[warm:], 99), "max_client_late_ms": float(late[warm:].max() * 1e3),
+               "p99_queue_ms": pct(queue, 99), "p99_service_ms": pct(service, 99),
                "frames_per_s": len(lat) / (t_last - t_first), "completed": int(len(lat)),
                "failed": int(sum(1 for i in range(warm, n_req) if i in got and got[i][3] != 0))}
         del maps
