@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 }
 
 // Stable scatter of one pass.  Warp w owns the contiguous items [512 w, 512 w + 512) of
-// the block's 4096 and ranks them round by round (32 at a time) with match masks and
+// the block's 4096 and ranks them round by round (32 at a time) with peer masks and
 // warp-local digit counters, so stability needs no block barrier per round.  One
 // block-wide prefix over the warps' counts then gives every item its position in the
 // block's digit-sorted order; items are staged in shared memory in that order and
