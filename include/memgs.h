@@ -209,7 +209,7 @@ mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_
 
 /* ------------------------------------------------------------------------------
  * Optimiser: Adam with bias correction over every parameter array of `params`
- * (one streaming launch per array; the optimiser is not named in the paper, Sec. II-E; Adam is this
+ * (one streaming launch over all arrays; the optimiser is not named in the paper, Sec. II-E; Adam is this
  * library's choice).  m and v are f32 state arrays shaped like the parameters
  * (same mgs_gaussians_mut layout, f32 pointers in m_state / v_state), 16-byte
  * aligned like the parameter and gradient arrays.  Parameters
