@@ -212,7 +212,8 @@ mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_
  * (one streaming launch over all arrays; the optimiser is not named in the paper, Sec. II-E; Adam is this
  * library's choice).  m and v are f32 state arrays shaped like the parameters
  * (same mgs_gaussians_mut layout, f32 pointers in m_state / v_state), 16-byte
- * aligned like the parameter and gradient arrays.  Parameters
+ * aligned like the parameter and gradient arrays (every f32 array: a misaligned
+ * one returns MGS_ERR_INVALID before anything runs).  Parameters
  * stored in f16/bf16 (either group) are updated in f32 and rounded back.  step >= 1.  zero_grads = 1
  * clears each gradient element after it is consumed (the next backward pass
  * accumulates from zero without a separate clearing pass).  Asynchronous.
@@ -233,6 +234,7 @@ mgs_status mgs_adam_step(const mgs_gaussians_mut* params, const mgs_grads* grads
  * grad[v].rgb receives dL_v/dx (written, not accumulated), grad[v].depth (optional)
  * dL_v/dd; they are the cotangents mgs_render_backward takes.  loss: device f32
  * [n_views][3] = (L1 part, SSIM part, depth part), each already weighted, written.
+ * lambda = 0 skips the SSIM windows altogether (the plain L1 form; SSIM part 0).
  * 1 <= n_views <= MGS_MAX_VIEWS.  Deterministic (fixed-order sums).  Asynchronous.
  * ------------------------------------------------------------------------------ */
 size_t mgs_mapping_loss_workspace_size(int32_t n_views, int32_t width, int32_t height);

@@ -455,11 +455,25 @@ double power_at(const Proj& P, double px, double py, double* dx, double* dy) {
   return -0.5 * (P.conic[0] * (*dx) * (*dx) + P.conic[2] * (*dy) * (*dy)) - P.conic[1] * (*dx) * (*dy);
 }
 
+// A near-tie decision of one pixel's pass: kind 1 alpha cutoff, 2 T stop, 4 depth order
+// (entries k and kp may swap), 8 extent / near plane (entry k may be in or out of the
+// tile list).  The opacity clamp (flag 16) is continuous in the image and is not one.
+struct Tie {
+  uint8_t kind;
+  int32_t k, kp;
+};
+
 void blend_pixel(const std::vector<Proj>& P, const std::vector<Entry>& list, int px, int py,
-                 const orc_margins* mg, bool keep, PixelResult& R) {
+                 const orc_margins* mg, bool keep, PixelResult& R, const Tie* flip = nullptr,
+                 std::vector<Tie>* ties = nullptr) {
   int pos = 0;  // index among the included entries (the CUDA list position)
   double prev_tz = -1;
+  int32_t prev_k = -1;
   double t_var = 0;  // sum of squared relative alpha margins, weighted by alpha/(1-alpha)
+  auto flipped = [&](uint8_t kind, size_t k) { return flip && flip->kind == kind && flip->k == (int32_t)k; };
+  auto tie = [&](uint8_t kind, size_t k, int32_t kp) {
+    if (ties) ties->push_back(Tie{kind, (int32_t)k, kp});
+  };
   for (size_t k = 0; k < list.size(); ++k) {
     const Entry& e = list[k];
     const Proj& p = P[e.g];
@@ -469,19 +483,29 @@ void blend_pixel(const std::vector<Proj>& P, const std::vector<Entry>& list, int
     double ma = mg ? mg->alpha_rel + mg->cond_rel * p.cond * std::fabs(power) : 0;
     bool potential = power <= 0 && alpha >= kAlphaMin * (1 - ma);
     if (keep && potential) R.touched.push_back(e.g);
-    if (mg && e.uncertain && potential) R.flags |= 8;
-    if (!e.included) continue;
+    if (mg && e.uncertain && potential) {
+      R.flags |= 8;
+      tie(8, k, -1);
+    }
+    if (e.included == flipped(8, k)) continue;
     ++pos;
     if (mg && potential) {
       // The order is decided on float32 depth keys; a pair can swap only when the
       // keys are within one ulp and a depth sits next to a float32 rounding midpoint.
-      if (prev_tz >= 0 && near_key_tie(prev_tz, p.p[2], mg->depth_rel)) R.flags |= 4;
+      if (prev_tz >= 0 && near_key_tie(prev_tz, p.p[2], mg->depth_rel)) {
+        R.flags |= 4;
+        tie(4, k, prev_k);
+      }
       prev_tz = p.p[2];
+      prev_k = (int32_t)k;
     }
     if (power > 0) continue;
-    if (mg && std::fabs(alpha * 255.0 - 1.0) < ma) R.flags |= 1;
+    if (mg && std::fabs(alpha * 255.0 - 1.0) < ma) {
+      R.flags |= 1;
+      tie(1, k, -1);
+    }
     if (mg && std::fabs(a - kAlphaMax) < (mg->clamp_rel + ma) * kAlphaMax) R.flags |= 16;
-    if (alpha < kAlphaMin) continue;
+    if ((alpha < kAlphaMin) != flipped(1, k)) continue;
     double w = alpha * R.T;
     if (keep) R.contrib.push_back(Contribution{e.g, alpha, a, std::exp(power), R.T, dx, dy});
     for (int c = 0; c < 3; ++c) R.rgb[c] += p.rgb[c] * w;
@@ -491,14 +515,29 @@ void blend_pixel(const std::vector<Proj>& P, const std::vector<Entry>& list, int
     if (mg) {
       double e = alpha / (1 - alpha) * ma;
       t_var += e * e;
-      if (std::fabs(R.T / kTStop - 1) < mg->T_rel + std::sqrt(t_var)) R.flags |= 2;
+      if (std::fabs(R.T / kTStop - 1) < mg->T_rel + std::sqrt(t_var)) {
+        R.flags |= 2;
+        tie(2, k, -1);
+      }
     }
-    if (R.T < kTStop) {
+    if ((R.T < kTStop) != flipped(2, k)) {
       R.n_eval = pos;
       return;
     }
   }
   R.n_eval = pos;
+}
+
+// The pixel's image with its one near-tie decision taken the other way.
+void blend_pixel_flipped(const std::vector<Proj>& P, const std::vector<Entry>& list, int px, int py,
+                         const orc_margins* mg, const Tie& t, PixelResult& R) {
+  if (t.kind != 4) {
+    blend_pixel(P, list, px, py, mg, false, R, &t, nullptr);
+    return;
+  }
+  std::vector<Entry> swapped(list);  // the two neighbouring contributors in the other order
+  std::swap(swapped[t.k], swapped[t.kp]);
+  blend_pixel(P, swapped, px, py, mg, false, R, nullptr, nullptr);
 }
 
 uint64_t mix(uint64_t h, uint64_t v) {
@@ -750,25 +789,29 @@ int orc_project(const orc_gaussians* g, const orc_camera* cam, orc_projection* o
   return 0;
 }
 
-int orc_render(const orc_gaussians* g, const orc_camera* cam, const orc_margins* mg,
-               const int32_t* tiles, int32_t n_tiles, double* rgb, double* depth, double* alpha,
-               double* T_final, int32_t* n_contrib, int32_t* n_eval, uint8_t* flags,
-               uint64_t* decision_hash, int32_t n_threads) {
+static int render_impl(const orc_gaussians* g, const orc_camera* cam, const orc_margins* mg,
+                       const int32_t* tiles, int32_t n_tiles, double* rgb, double* depth, double* alpha,
+                       double* T_final, int32_t* n_contrib, int32_t* n_eval, uint8_t* flags,
+                       uint64_t* decision_hash, double* alt_rgb, double* alt_depth, double* alt_alpha,
+                       int32_t* n_ties, int32_t n_threads) {
   if (!g || !cam || g->n < 0 || cam->width <= 0 || cam->height <= 0) return -1;
   std::vector<Proj> P = project_all(g, cam, mg, n_threads);
   std::vector<char> want = tile_mask(cam, tiles, n_tiles);
   auto bins = bin_tiles(P, cam, want, n_threads);
   int TX = tiles_x(cam), W = cam->width, H = cam->height;
   size_t HW = (size_t)W * H;
+  const bool alt = alt_rgb || alt_depth || alt_alpha || n_ties;
   std::vector<uint64_t> tile_hash(bins.size(), 0);
   parallel_for((int64_t)bins.size(), n_threads, [&](int64_t t) {
     if (!want[t]) return;
     int x0 = (int)(t % TX) * kTile, y0 = (int)(t / TX) * kTile;
     uint64_t h = 0;
+    std::vector<Tie> ties;
     for (int py = y0; py < std::min(H, y0 + kTile); ++py)
       for (int px = x0; px < std::min(W, x0 + kTile); ++px) {
         PixelResult R;
-        blend_pixel(P, bins[t], px, py, mg, decision_hash != nullptr, R);
+        ties.clear();
+        blend_pixel(P, bins[t], px, py, mg, decision_hash != nullptr, R, nullptr, alt ? &ties : nullptr);
         size_t o = (size_t)py * W + px;
         for (int c = 0; c < 3; ++c) if (rgb) rgb[c * HW + o] = R.rgb[c];
         if (depth) depth[o] = R.depth;
@@ -777,6 +820,20 @@ int orc_render(const orc_gaussians* g, const orc_camera* cam, const orc_margins*
         if (n_contrib) n_contrib[o] = R.n_contrib;
         if (n_eval) n_eval[o] = R.n_eval;
         if (flags) flags[o] = R.flags;
+        if (alt) {
+          // the other outcome of a single near-tie decision; none for two or more
+          PixelResult A = R;
+          if (ties.size() == 1) {
+            A = PixelResult();
+            blend_pixel_flipped(P, bins[t], px, py, mg, ties[0], A);
+          }
+          const double nan = std::nan("");
+          const bool many = ties.size() > 1;
+          for (int c = 0; c < 3; ++c) if (alt_rgb) alt_rgb[c * HW + o] = many ? nan : A.rgb[c];
+          if (alt_depth) alt_depth[o] = many ? nan : A.depth;
+          if (alt_alpha) alt_alpha[o] = many ? nan : 1 - A.T;
+          if (n_ties) n_ties[o] = (int32_t)ties.size();
+        }
         if (decision_hash) {
           h = mix(h, o);
           for (auto& c : R.contrib) h = mix(h, (uint64_t)c.g + 1);
@@ -791,6 +848,23 @@ int orc_render(const orc_gaussians* g, const orc_camera* cam, const orc_margins*
     *decision_hash = h;
   }
   return 0;
+}
+
+int orc_render(const orc_gaussians* g, const orc_camera* cam, const orc_margins* mg,
+               const int32_t* tiles, int32_t n_tiles, double* rgb, double* depth, double* alpha,
+               double* T_final, int32_t* n_contrib, int32_t* n_eval, uint8_t* flags,
+               uint64_t* decision_hash, int32_t n_threads) {
+  return render_impl(g, cam, mg, tiles, n_tiles, rgb, depth, alpha, T_final, n_contrib, n_eval, flags,
+                     decision_hash, nullptr, nullptr, nullptr, nullptr, n_threads);
+}
+
+int orc_render_outcomes(const orc_gaussians* g, const orc_camera* cam, const orc_margins* mg,
+                        const int32_t* tiles, int32_t n_tiles, double* rgb, double* depth, double* alpha,
+                        double* T_final, int32_t* n_contrib, uint8_t* flags, double* alt_rgb,
+                        double* alt_depth, double* alt_alpha, int32_t* n_ties, int32_t n_threads) {
+  if (!mg) return -1;
+  return render_impl(g, cam, mg, tiles, n_tiles, rgb, depth, alpha, T_final, n_contrib, nullptr, flags,
+                     nullptr, alt_rgb, alt_depth, alt_alpha, n_ties, n_threads);
 }
 
 int orc_render_bruteforce(const orc_gaussians* g, const orc_camera* cam, double* rgb, double* depth,

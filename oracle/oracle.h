@@ -102,6 +102,20 @@ int orc_render(const orc_gaussians* g, const orc_camera* cam, const orc_margins*
                int32_t* n_contrib, int32_t* n_eval, uint8_t* flags,
                uint64_t* decision_hash, int32_t n_threads);
 
+/* Both outcomes of the near-tie decisions (needs margins).  Besides the image of
+ * orc_render, per pixel: n_ties = the number of near-tie decisions that can change the
+ * image (alpha cutoff, T stop, order of two neighbouring contributors, extent / near
+ * plane; the opacity clamp is continuous in the image and is not counted), and alt_*
+ * = the image with that decision taken the other way when n_ties == 1 (the same image
+ * when n_ties == 0, NaN when n_ties >= 2).  A float32 renderer that takes the
+ * decision either way matches one of the two. */
+int orc_render_outcomes(const orc_gaussians* g, const orc_camera* cam, const orc_margins* m,
+                        const int32_t* tiles, int32_t n_tiles,
+                        double* rgb, double* depth, double* alpha, double* T_final,
+                        int32_t* n_contrib, uint8_t* flags,
+                        double* alt_rgb, double* alt_depth, double* alt_alpha, int32_t* n_ties,
+                        int32_t n_threads);
+
 /* Same image, computed pixel by pixel over all n Gaussians with the tile-rect
  * predicate and an explicit (depth, index) ordering; no binning. */
 int orc_render_bruteforce(const orc_gaussians* g, const orc_camera* cam,

@@ -177,6 +177,27 @@ def render(scene, cam, *, tiles=None, margin=None, n_threads=None, hash_decision
     return out
 
 
+def render_outcomes(scene, cam, *, tiles=None, margin=None, n_threads=None, **over):
+    """Forward render of one view plus, per pixel, the number of near-tie decisions that
+    can change the image (``n_ties``) and the image with a single such decision taken
+    the other way (``alt_rgb``, ``alt_depth``, ``alt_alpha``; NaN where n_ties >= 2)."""
+    P = _Params(scene, **over)
+    W, H = cam.width, cam.height
+    out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), alpha=np.zeros((H, W)),
+               T_final=np.ones((H, W)), n_contrib=np.zeros((H, W), np.int32),
+               flags=np.zeros((H, W), np.uint8), alt_rgb=np.zeros((3, H, W)),
+               alt_depth=np.zeros((H, W)), alt_alpha=np.zeros((H, W)), n_ties=np.zeros((H, W), np.int32))
+    t = None if tiles is None else np.ascontiguousarray(tiles, np.int32)
+    m = margin if margin is not None else margins()
+    rc = lib().orc_render_outcomes(C.byref(P.struct), C.byref(camera_struct(cam)), C.byref(m), _p(t),
+                                   C.c_int32(-1 if t is None else t.size), _p(out["rgb"]), _p(out["depth"]),
+                                   _p(out["alpha"]), _p(out["T_final"]), _p(out["n_contrib"]),
+                                   _p(out["flags"]), _p(out["alt_rgb"]), _p(out["alt_depth"]),
+                                   _p(out["alt_alpha"]), _p(out["n_ties"]), C.c_int32(_threads(n_threads)))
+    assert rc == 0
+    return out
+
+
 def render_bruteforce(scene, cam, **over):
     P = _Params(scene, **over)
     W, H = cam.width, cam.height

@@ -161,13 +161,19 @@ class Grads:
 
 
 class RenderWorkspace:
-    """Caller-owned scratch of mgs_render / mgs_render_backward, grown on demand."""
+    """Caller-owned scratch of mgs_render / mgs_render_backward, grown on demand.
+
+    It holds the saved state of the last render (projected records, sorted lists,
+    per-pixel T and contributor counts) that the backward pass reads.  ``generation``
+    counts renders into it and regrowths of it, so that a backward pass can tell that
+    the state it needs was overwritten."""
 
     def __init__(self, device="cuda", key_headroom: float = 1.25):
         self.device = torch.device(device)
         self.buf: Optional[torch.Tensor] = None
         self.headroom = key_headroom
         self.n_keys = 0
+        self.generation = 0
 
     def ensure(self, n, cams, key_capacity) -> torch.Tensor:
         arr = _cam_array(cams)
@@ -177,6 +183,7 @@ class RenderWorkspace:
         if self.buf is None or self.buf.numel() < need:
             self.buf = None
             self.buf = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self.generation += 1
         return self.buf
 
 
@@ -197,6 +204,7 @@ def mgs_render(g: Gaussians, cams, out: List[Image], ws: RenderWorkspace, stream
             continue
         check(st, "mgs_render")
         ws.n_keys = nk.value
+        ws.generation += 1
         return nk.value
     check(st, "mgs_render")
     return 0
@@ -429,51 +437,127 @@ def render_stats(g: Gaussians, cams, ws: RenderWorkspace, stream=None):
 class RenderFn(torch.autograd.Function):
     """Differentiable multi-view render through libmemgs.
 
-    apply(means, log_scales, quats, opacity_logit, sh, cams, ws) -> (rgb [V,3,H,W],
-    depth [V,H,W], alpha [V,H,W]) for views of one resolution.  The backward pass is
-    mgs_render_backward on the same workspace; parameter gradients are f32.
+    apply(means, log_scales, quats, opacity_logit, sh, cams, ws, grads=None) ->
+    (rgb [V,3,H,W], depth [V,H,W], alpha [V,H,W]) for views of one resolution.  The
+    backward pass is mgs_render_backward on the saved state in ``ws``; it refuses to run
+    if ``ws`` was rendered into or regrown after this forward pass.
+
+    ``grads`` None: the backward pass returns new f32 gradient tensors (plain autograd).
+    ``grads`` a Grads: the library accumulates the gradients into those buffers in place
+    (with the Eq. 3 statistics when the Grads has them) and the backward pass returns
+    None for the parameters: no allocation and no copy in the step; whoever owns the
+    buffers (MappingStep's Adam) consumes and clears them.
     """
 
     @staticmethod
-    def forward(ctx, means, log_scales, quats, opacity_logit, sh, cams, ws):
+    def forward(ctx, means, log_scales, quats, opacity_logit, sh, cams, ws, grads=None):
         g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), opacity_logit.detach(),
                       sh.detach())
         V = len(cams)
         H, W = int(cams[0].height), int(cams[0].width)
+        if any(int(c.height) != H or int(c.width) != W for c in cams):
+            raise ValueError("RenderFn renders views of one resolution")
         rgb = torch.empty(V, 3, H, W, device=means.device)
         depth = torch.empty(V, H, W, device=means.device)
         alpha = torch.empty(V, H, W, device=means.device)
         out = [Image(rgb[v], depth[v], alpha[v]) for v in range(V)]
         mgs_render(g, cams, out, ws)
-        ctx.cams, ctx.ws = cams, ws
+        ctx.set_materialize_grads(False)  # an unused output's cotangent stays None: no zero-filled tensor
+        ctx.cams, ctx.ws, ctx.grads = cams, ws, grads
+        ctx.generation, ctx.buf = ws.generation, ws.buf
         ctx.save_for_backward(means, log_scales, quats, opacity_logit, sh)
         return rgb, depth, alpha
 
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_alpha):
+        ws = ctx.ws
+        if ws.generation != ctx.generation or ws.buf is not ctx.buf:
+            raise RuntimeError("RenderFn.backward: the render workspace was reused or regrown after this "
+                               "forward pass; give each pending render its own RenderWorkspace")
         means, log_scales, quats, opacity_logit, sh = ctx.saved_tensors
         g = Gaussians(means, log_scales, quats, opacity_logit, sh)
         V = len(ctx.cams)
         c = lambda t: None if t is None else t.contiguous()
         g_rgb, g_depth, g_alpha = c(g_rgb), c(g_depth), c(g_alpha)
-        dL = [Image(None if g_rgb is None else g_rgb[v], None if g_depth is None else g_depth[v],
-                    None if g_alpha is None else g_alpha[v]) for v in range(V)]
         arr = (_abi.mgs_image * V)()
-        for v, im in enumerate(dL):
-            arr[v] = _abi.mgs_image(_ptr(im.rgb), _ptr(im.depth), _ptr(im.alpha))
-        grads = Grads.zeros_like(g, stats=False)
+        for v in range(V):
+            arr[v] = _abi.mgs_image(None if g_rgb is None else _ptr(g_rgb[v]),
+                                    None if g_depth is None else _ptr(g_depth[v]),
+                                    None if g_alpha is None else _ptr(g_alpha[v]))
+        grads = ctx.grads if ctx.grads is not None else Grads.zeros_like(g, stats=False)
         check(load().mgs_render_backward(C.byref(g.struct()), _cam_array(ctx.cams), V, arr,
-                                         _ptr(ctx.ws.buf), ctx.ws.buf.numel(), C.byref(grads.struct()),
+                                         _ptr(ws.buf), ws.buf.numel(), C.byref(grads.struct()),
                                          _stream()), "mgs_render_backward")
+        if ctx.grads is not None:
+            return None, None, None, None, None, None, None, None
         cast = lambda gr, p: gr if p.dtype == torch.float32 else gr.to(p.dtype)
         return (grads.means, cast(grads.log_scales, log_scales), cast(grads.quats, quats),
-                cast(grads.opacity_logit, opacity_logit), cast(grads.sh, sh), None, None)
+                cast(grads.opacity_logit, opacity_logit), cast(grads.sh, sh), None, None, None)
 
 
 def render_views(g: Gaussians, cams, ws: Optional[RenderWorkspace] = None):
     """Differentiable render of same-resolution views: returns (rgb, depth, alpha) tensors."""
     ws = ws or RenderWorkspace(g.means.device)
     return RenderFn.apply(g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, cams, ws)
+
+
+class MappingStep:
+    """The batched mapping step of Sec. II-E driven through torch.autograd.
+
+    Each call: render every keyframe of the batch in one multi-view launch through
+    RenderFn (forward A1-A4), the mapping loss against the keyframe images
+    (mgs_mapping_loss: Eq. 12, lambda = 0 gives its plain L1 form, plus the
+    isotropic term when w_iso > 0), torch.autograd.backward from the rendered images
+    with the loss kernel's cotangents (RenderFn.backward: A5-A6 into the gradient
+    buffers, in place), then the in-kernel Adam step, which also clears the
+    gradients.  Every kernel of the step is the library's; the parameter tensors are
+    updated in place.  Returns the device loss tensor [V, 3] (weighted L1, SSIM and
+    depth parts per view); ``loss_iso`` holds the isotropic term.
+    """
+
+    def __init__(self, g: Gaussians, cams, lr=1e-3, lambda_ssim=0.0, w_depth=0.1, w_iso=0.0,
+                 betas=(0.9, 0.999), eps=1e-8, stats=True):
+        self.g = g
+        self.cams = list(cams)
+        self.lr, self.betas, self.eps = float(lr), betas, float(eps)
+        self.lambda_ssim, self.w_depth, self.w_iso = float(lambda_ssim), float(w_depth), float(w_iso)
+        self.params = [p.requires_grad_(True) for p in g.params()]
+        self.grads = Grads.zeros_like(g, stats=stats)
+        self.m = Grads.zeros_like(g, stats=False)
+        self.v = Grads.zeros_like(g, stats=False)
+        self.ws = RenderWorkspace(g.means.device)
+        V = len(self.cams)
+        H, W = int(self.cams[0].height), int(self.cams[0].width)
+        dev = g.means.device
+        self.g_rgb = torch.empty(V, 3, H, W, device=dev)
+        self.g_depth = torch.empty(V, H, W, device=dev)
+        self.loss = torch.zeros(V, 3, device=dev)
+        self.loss_iso = torch.zeros(1, device=dev)
+        L = load()
+        self.loss_ws = torch.empty(max(1, L.mgs_mapping_loss_workspace_size(V, W, H)), dtype=torch.uint8,
+                                   device=dev)
+        self.iso_ws = torch.empty(max(1, L.mgs_iso_loss_workspace_size(g.n)), dtype=torch.uint8, device=dev)
+        self.step_count = 0
+        self._dL = [Image(self.g_rgb[v], self.g_depth[v], None) for v in range(V)]
+
+    def __call__(self, target_rgb: torch.Tensor, target_depth: Optional[torch.Tensor] = None):
+        """One step against keyframe images target_rgb [V,3,H,W] (and target_depth [V,H,W])."""
+        self.step_count += 1
+        rgb, depth, alpha = RenderFn.apply(*self.params, self.cams, self.ws, self.grads)
+        V = len(self.cams)
+        rendered = [Image(rgb[v].detach(), depth[v].detach(), alpha[v].detach()) for v in range(V)]
+        targets = [Image(target_rgb[v], None if target_depth is None else target_depth[v], None)
+                   for v in range(V)]
+        mgs_mapping_loss(rendered, targets, self._dL, self.lambda_ssim, self.w_depth, loss=self.loss,
+                         workspace=self.loss_ws)
+        torch.autograd.backward((rgb, depth), (self.g_rgb, self.g_depth))
+        g = self.g
+        if self.w_iso > 0:
+            mgs_iso_loss(g, self.w_iso, self.grads, loss=self.loss_iso, workspace=self.iso_ws)
+        with torch.no_grad():
+            mgs_adam_step(g, self.grads, self.m, self.v, self.lr, self.betas[0], self.betas[1], self.eps,
+                          self.step_count, zero_grads=True)
+        return self.loss
 
 
 class Server:

@@ -400,6 +400,20 @@ mgs_status mgs_adam_step(const mgs_gaussians_mut* params, const mgs_grads* grads
     return fail(MGS_ERR_INVALID, "bad attr_dtype / geom_dtype");
   if (!(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
     return fail(MGS_ERR_INVALID, "need 0 <= beta < 1 and eps > 0");
+  {
+    // the kernel moves f32 arrays in 16-byte vectors: a misaligned view is an error here,
+    // not a fault on the device
+    auto mis = [](const void* q) { return q && (reinterpret_cast<uintptr_t>(q) & 15) != 0; };
+    const void* f32s[] = {grads->means, grads->log_scales, grads->quats, grads->opacity_logit, grads->sh,
+                          m->means, m->log_scales, m->quats, m->opacity_logit, m->sh,
+                          v->means, v->log_scales, v->quats, v->opacity_logit, v->sh, params->means,
+                          params->geom_dtype == MGS_F32 ? params->log_scales : nullptr,
+                          params->geom_dtype == MGS_F32 ? params->quats : nullptr,
+                          params->attr_dtype == MGS_F32 ? params->opacity_logit : nullptr,
+                          params->attr_dtype == MGS_F32 ? params->sh : nullptr};
+    for (const void* q : f32s)
+      if (mis(q)) return fail(MGS_ERR_INVALID, "f32 parameter, gradient and moment arrays must be 16-byte aligned");
+  }
   ProfScope ps(kProfAdam, (cudaStream_t)stream);
   MGS_TRY_CUDA(launch_adam(*params, *grads, *m, *v, lr, beta1, beta2, eps, step, zero_grads ? 1 : 0,
                            (cudaStream_t)stream));

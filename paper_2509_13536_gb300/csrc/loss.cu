@@ -203,6 +203,40 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(int W, int H, const Window win
   }
 }
 
+// lambda = 0 (the L1 form of Eq. 12): no SSIM term.  Same grid and partial layout as
+// k_ssim_fwd (the SSIM slot of each partial is 0, which lambda = 0 ignores), and the
+// cotangent k_ssim_bwd would write: sign(x - y) / n.
+__global__ void __launch_bounds__(256) k_l1_rgb(int W, int H, const __grid_constant__ Planes P,
+                                                float* __restrict__ part) {
+  __shared__ float red[8];
+  const int v = blockIdx.z / 3, c = blockIdx.z % 3;
+  const size_t HW = (size_t)W * H;
+  const float* X = P.x[v] + c * HW;
+  const float* Y = P.y[v] + c * HW;
+  float* G = P.grgb[v] + c * HW;
+  const float inv_n = 1.f / (3.f * (float)HW);
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  float l1 = 0.f;
+  for (int i = threadIdx.x; i < kTX * kTY; i += blockDim.x) {
+    const int gx = x0 + (i % kTX), gy = y0 + i / kTX;
+    if (gx >= W || gy >= H) continue;
+    const size_t q = (size_t)gy * W + gx;
+    const float diff = X[q] - Y[q];
+    l1 += fabsf(diff);
+    G[q] = (diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f)) * inv_n;
+  }
+  for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    for (int k = 0; k < 8; ++k) b += red[k];
+    const size_t bi = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    part[2 * bi] = 0.f;
+    part[2 * bi + 1] = b;
+  }
+}
+
 // Depth residual: one thread per pixel of every view; block partials of |d - dt|.
 __global__ void __launch_bounds__(256) k_depth_l1(int W, int H, float w_depth,
                                                   const __grid_constant__ Planes P, float* __restrict__ part) {
@@ -352,13 +386,18 @@ cudaError_t launch_mapping_loss(int n_views, int width, int height, const LossLa
   float* part_depth = reinterpret_cast<float*>(ws + L.part_depth);
   const Window win = make_window();
   const dim3 grid(L.tiles_x, L.tiles_y, 3 * n_views);
-  k_ssim_fwd<<<grid, 256, 0, s>>>(width, height, win, P, dmaps, part_ssim);
-  k_ssim_bwd<<<grid, 256, 0, s>>>(width, height, win, lambda, P, dmaps);
+  if (lambda == 0.f) {
+    k_l1_rgb<<<grid, 256, 0, s>>>(width, height, P, part_ssim);
+  } else {
+    k_ssim_fwd<<<grid, 256, 0, s>>>(width, height, win, P, dmaps, part_ssim);
+    k_ssim_bwd<<<grid, 256, 0, s>>>(width, height, win, lambda, P, dmaps);
+    count_launch();
+  }
   k_depth_l1<<<dim3(L.nb_depth, n_views), 256, 0, s>>>(width, height, w_depth, P, part_depth);
   const double HW = (double)width * height;
   k_loss_reduce<<<n_views, 256, 0, s>>>(n_views, L.nb_ssim, L.nb_depth, part_ssim, part_depth, lambda, w_depth,
                                         3.0 * HW, HW, loss);
-  count_launch(4);
+  count_launch(3);
   return cudaGetLastError();
 }
 

@@ -134,7 +134,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   __syncthreads();
   const int64_t i0 = (int64_t)blockIdx.x * kSortTile + (int64_t)t * kSortPerThread;
   uint32_t k[kSortPerThread];
-  if (i0 + kSortPerThread <= n) {
+  // i0 is a multiple of 16 keys, so keys + i0 is 16-byte aligned exactly when keys is;
+  // a caller's 4-byte aligned array (an offset view) takes the scalar path
+  if (i0 + kSortPerThread <= n && (reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
     const uint4* p = reinterpret_cast<const uint4*>(keys + i0);
 #pragma unroll
     for (int q = 0; q < kSortPerThread / 4; ++q) {

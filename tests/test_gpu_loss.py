@@ -62,6 +62,21 @@ def test_mapping_loss_matches_oracle(orc, V, H, W):
     np.testing.assert_allclose(g_d, ref["g_depth"], rtol=1e-6, atol=0)
 
 
+@pytest.mark.parametrize("V,H,W", [(2, 45, 67), (3, 7, 5)])
+def test_mapping_loss_l1_form_matches_oracle(orc, V, H, W):
+    """lambda = 0 (the L1 form of Eq. 12, no SSIM windows): loss parts and cotangents
+    as the oracle's, with exact ties giving a zero cotangent."""
+    rng = np.random.default_rng(V * 31 + W)
+    x, y, d, dt = _case(rng, V, H, W)
+    loss, g_rgb, g_d = _run(x, y, d, dt, 0.0, 0.1)
+    ref = orc.mapping_loss(x, y, d, dt, lam=0.0, w_depth=0.1)
+    np.testing.assert_allclose(loss, ref["loss"], rtol=2e-5, atol=1e-7)
+    assert np.all(loss[:, 1] == 0)
+    np.testing.assert_array_equal(np.sign(g_rgb), np.sign(ref["g_rgb"]))
+    np.testing.assert_allclose(g_rgb, ref["g_rgb"], rtol=1e-6, atol=0)
+    np.testing.assert_allclose(g_d, ref["g_depth"], rtol=1e-6, atol=0)
+
+
 def test_mapping_loss_without_depth_and_identical_images(orc):
     rng = np.random.default_rng(7)
     x, _, _, _ = _case(rng, 2, 33, 40)

@@ -1,0 +1,182 @@
+"""The mapping step driven through torch.autograd (RenderFn + MappingStep) against the
+FP64 oracle's own steps: render (Eq. 11), the Eq. 12 loss with its isotropic term,
+the reverse pass, Adam.  Sec. II-E."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_13536_gb300 import api, scenegen as sg
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = _gpu.FIELDS
+LR, B1, B2, EPS = 1e-3, 0.9, 0.999, 1e-8
+LAM, W_DEPTH, W_ISO = 0.2, 0.5, 0.1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_13536_gb300 import build
+    build.build()
+
+
+def _scene_with(scene, params):
+    s = scene.copy()
+    for k in FIELDS:
+        setattr(s, k, params[k])
+    return s
+
+
+def _oracle_steps(orc, scene, cams, y, dt, n_steps=2):
+    """The oracle's own steps from the FP64 copy of the map: per step the per-view images,
+    flags and loss, the summed gradient and the parameters after Adam."""
+    P = {k: getattr(scene, k).astype(np.float64).copy() for k in FIELDS}
+    M = {k: np.zeros_like(v) for k, v in P.items()}
+    Vs = {k: np.zeros_like(v) for k, v in P.items()}
+    hist = []
+    for t in range(1, n_steps + 1):
+        sc = _scene_with(scene, P)
+        outs = [orc.render_outcomes(sc, c) for c in cams]
+        x = np.stack([o["rgb"] for o in outs])
+        d = np.stack([o["depth"] for o in outs])
+        lo = orc.mapping_loss(x, y, d, dt, lam=LAM, w_depth=W_DEPTH)
+        grads = orc.new_grads(scene.n, scene.sh_degree)
+        for v, c in enumerate(cams):
+            orc.render_backward(sc, c, lo["g_rgb"][v], lo["g_depth"][v], None, grads=grads)
+        iso, g_ls = orc.iso_loss(P["log_scales"], W_ISO)
+        grads["log_scales"] += g_ls
+        hist.append(dict(x=x, d=d, flags=np.stack([o["flags"] for o in outs]), loss=lo["loss"], iso=iso,
+                         grads={k: grads[k].copy() for k in FIELDS}, taint=grads["taint"].copy()))
+        for k in FIELDS:
+            orc.adam(P[k], grads[k], M[k], Vs[k], LR, B1, B2, EPS, t)
+    return hist, P
+
+
+def _adam_np(g_list):
+    """Parameter change after len(g_list) Adam steps (bias-corrected), in float64."""
+    m = v = 0.0
+    delta = 0.0
+    for t, g in enumerate(g_list, 1):
+        m = B1 * m + (1 - B1) * g
+        v = B2 * v + (1 - B2) * g * g
+        delta = delta - LR * (m / (1 - B1 ** t)) / (np.sqrt(v / (1 - B2 ** t)) + EPS)
+    return delta
+
+
+@pytest.fixture(scope="module")
+def mapping_case(orc):
+    """A small room map, 2 keyframes, random keyframe images; Gaussians that reach a pixel
+    with a near-tie decision in either step are dropped, and target values within 1e-4
+    of the oracle's rendered value are moved, until the oracle's two steps take no
+    near-tie decision and no L1 sign is in doubt (all on the CPU, oracle only)."""
+    scene = sg.room_scene(6000, 17, sh_degree=1)
+    cams = sg.room_poses(2, 18, 96, 72)
+    rng = np.random.default_rng(19)
+    V, H, W = len(cams), cams[0].height, cams[0].width
+    y = rng.uniform(0, 1, (V, 3, H, W))
+    dt = rng.uniform(0.5, 4.0, (V, H, W))
+    dt[:, ::5, ::3] = 0
+    for _ in range(8):
+        hist, P = _oracle_steps(orc, scene, cams, y, dt)
+        flagged = any(h["flags"].any() for h in hist)
+        taint = np.zeros(scene.n, bool)
+        for h in hist:
+            taint |= h["taint"] > 0
+        moved = False
+        for h in hist:
+            close = np.abs(h["x"] - y) < 1e-4
+            if close.any():
+                y = np.where(close, np.where(y > 0.5, y - 0.01, y + 0.01), y)
+                moved = True
+            dclose = (np.abs(h["d"] - dt) < 1e-4) & (dt > 0)
+            if dclose.any():
+                dt = np.where(dclose, dt + 0.01, dt)
+                moved = True
+        if not flagged and not moved:
+            break
+        if flagged:
+            scene = scene.subset(np.nonzero(~taint)[0])
+    else:
+        pytest.fail("could not scrub the mapping case")
+    return dict(scene=scene, cams=cams, y=y.astype(np.float32), dt=dt.astype(np.float32), hist=hist, P=P)
+
+
+def test_two_mapping_steps_match_the_oracle(mapping_case):
+    """Two MappingStep calls (RenderFn forward, Eq. 12 loss with lambda 0.2 and the depth
+    and isotropic terms, autograd backward, in-kernel Adam) against the oracle's own two
+    steps from the same map: per-view loss parts, and every parameter element within
+    the gradient tolerance propagated through Adam (the largest change of the Adam
+    update over g_t +- 1e-3 (|g_t| + 1e-3 rms), t = 1, 2) plus float32 rounding."""
+    c = mapping_case
+    scene, cams, hist = c["scene"], c["cams"], c["hist"]
+    g = api.Gaussians.from_scene(scene, "cuda")
+    step = api.MappingStep(g, cams, lr=LR, lambda_ssim=LAM, w_depth=W_DEPTH, w_iso=W_ISO)
+    y, dt = torch.from_numpy(c["y"]).cuda(), torch.from_numpy(c["dt"]).cuda()
+    for t in range(2):
+        loss = step(y, dt)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(loss.cpu().numpy(), hist[t]["loss"], rtol=1e-4, atol=1e-7)
+        np.testing.assert_allclose(float(step.loss_iso.item()), hist[t]["iso"], rtol=1e-5)
+    worst = 0.0
+    for k in FIELDS:
+        ref = c["P"][k]
+        gpu = _gpu.to_np(getattr(g, k))
+        g1, g2 = hist[0]["grads"][k], hist[1]["grads"][k]
+        e1 = 1e-3 * (np.abs(g1) + 1e-3 * np.sqrt(np.mean(g1 ** 2)))
+        e2 = 1e-3 * (np.abs(g2) + 1e-3 * np.sqrt(np.mean(g2 ** 2)))
+        nominal = _adam_np([g1, g2])
+        spread = np.zeros_like(ref)
+        for s1 in (-1, 1):
+            for s2 in (-1, 1):
+                spread = np.maximum(spread, np.abs(_adam_np([g1 + s1 * e1, g2 + s2 * e2]) - nominal))
+        bound = spread + 4 * np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64) + 1e-12
+        r = np.abs(gpu - ref) / bound
+        i = int(np.argmax(r))
+        worst = max(worst, float(r.flat[i]))
+        assert r.flat[i] <= 1.0, (k, np.unravel_index(i, ref.shape), gpu.flat[i], ref.flat[i], bound.flat[i])
+        assert np.abs(gpu - getattr(scene, k)).max() > 0  # the step really moved the map
+    print("two mapping steps: worst |gpu - oracle| / bound", worst, "Gaussians", scene.n)
+
+
+def test_render_fn_gradients_match_the_oracle(orc):
+    """RenderFn's backward (plain autograd, new gradient tensors) and its in-place form
+    (gradients accumulated into a Grads) against the oracle's gradient, element-wise,
+    with the cotangent on unflagged pixels."""
+    scene, cams = sg.workload("box10k")
+    refs = [orc.render_outcomes(scene, cams[0])]
+    cot_np, dL = _gpu.masked_cotangents(cams, refs, 11)
+    ref = _gpu.oracle_backward(orc, scene, cams, cot_np)
+    g = api.Gaussians.from_scene(scene, "cuda")
+    params = [p.clone().requires_grad_(True) for p in g.params()]
+    ws = api.RenderWorkspace("cuda")
+    rgb, depth, alpha = api.RenderFn.apply(*params, cams, ws)
+    torch.autograd.backward((rgb, depth, alpha), (dL[0].rgb[None], dL[0].depth[None], dL[0].alpha[None]))
+    torch.cuda.synchronize()
+    got = api.Grads(*(p.grad for p in params))
+    _gpu.check_grads(got, ref, what="RenderFn")
+    into = api.Grads.zeros_like(g, stats=False)
+    ws2 = api.RenderWorkspace("cuda")
+    params2 = [p.detach().clone().requires_grad_(True) for p in g.params()]
+    rgb, depth, alpha = api.RenderFn.apply(*params2, cams, ws2, into)
+    torch.autograd.backward((rgb, depth, alpha), (dL[0].rgb[None], dL[0].depth[None], dL[0].alpha[None]))
+    torch.cuda.synchronize()
+    assert all(p.grad is None for p in params2)
+    _gpu.check_grads(into, ref, what="RenderFn in place")
+
+
+def test_render_fn_refuses_a_reused_workspace():
+    """A second render into the same workspace before the first one's backward pass
+    overwrites the saved state that backward pass needs: it raises instead of returning
+    wrong gradients."""
+    scene, cams = sg.workload("box10k")
+    g = api.Gaussians.from_scene(scene, "cuda")
+    params = [p.clone().requires_grad_(True) for p in g.params()]
+    ws = api.RenderWorkspace("cuda")
+    rgb1, _, _ = api.RenderFn.apply(*params, cams, ws)
+    rgb2, _, _ = api.RenderFn.apply(*params, cams, ws)
+    with pytest.raises(RuntimeError, match="reused or regrown"):
+        rgb1.backward(torch.ones_like(rgb1))
+    rgb2.backward(torch.ones_like(rgb2))  # the latest render's state is intact
+    torch.cuda.synchronize()
+    assert params[0].grad is not None and torch.isfinite(params[0].grad).all()

@@ -50,6 +50,32 @@ def test_radix_sort_with_values():
     np.testing.assert_array_equal(v.cpu().numpy(), vals[want])
 
 
+def test_radix_sort_of_an_offset_view():
+    """keys[1:] (4-byte aligned, not 16) sorts like an aligned copy of the same keys."""
+    rng = np.random.default_rng(9)
+    n = 70_001
+    keys = rng.integers(0, 2 ** 32, n + 1, dtype=np.uint64).astype(np.uint32)
+    base = torch.from_numpy(keys.view(np.int32).copy()).cuda()
+    view = base[1:]
+    assert view.data_ptr() % 16 != 0
+    perm = api.mgs_sort_pairs(view, None, 0, 32)
+    torch.cuda.synchronize()
+    want = np.argsort(keys[1:], kind="stable")
+    np.testing.assert_array_equal(perm.cpu().numpy(), want.astype(np.int32))
+    np.testing.assert_array_equal(view.cpu().numpy().view(np.uint32), keys[1:][want])
+
+
+def test_adam_rejects_misaligned_arrays():
+    """The optimiser's 16-byte vector accesses need aligned f32 arrays: an offset view is
+    refused on the host with an error, before anything is launched."""
+    scene, _ = sg.workload("box10k")
+    g = api.Gaussians.from_scene(scene, "cuda")
+    grads, m, v = (api.Grads.zeros_like(g, stats=False) for _ in range(3))
+    m.opacity_logit = torch.zeros(g.n + 1, device="cuda")[1:]
+    with pytest.raises(Exception, match="16-byte aligned"):
+        api.mgs_adam_step(g, grads, m, v, 1e-3)
+
+
 # ------------------------------------------------------------------ projection
 def test_projection_matches_oracle(orc):
     scene, cams = sg.workload("box10k")
@@ -80,26 +106,27 @@ def test_projection_matches_oracle(orc):
 def test_render_box10k_matches_oracle(orc):
     scene, cams = sg.workload("box10k")
     g, imgs, ws = _gpu.render_gpu(scene, cams)
-    ref = orc.render(scene, cams[0])
-    errs, frac = _gpu.check_image(imgs[0], ref, what="box10k")
-    print("box10k", errs, "flagged", frac, "keys", ws.n_keys)
+    ref = orc.render_outcomes(scene, cams[0])
+    rep = _gpu.check_image(imgs[0], ref, what="box10k")
+    print("box10k", rep, "keys", ws.n_keys)
 
 
 def test_backward_box10k_matches_oracle(orc):
+    """Every Gaussian's gradient, element by element, with the cotangent U[-1, 1] on the
+    pixels the oracle does not flag (zero on the flagged ones, which then add nothing)."""
     scene, cams = sg.workload("box10k")
     g, imgs, ws = _gpu.render_gpu(scene, cams)
-    cot = sg.image_cotangents(1, 320, 240, 0)
-    cot_np = [(cot[0][0], cot[1][0], cot[2][0])]
-    dL = [api.Image(*(torch.from_numpy(x).cuda() for x in cot_np[0]))]
+    refs = [orc.render_outcomes(scene, cams[0])]
+    cot_np, dL = _gpu.masked_cotangents(cams, refs, 0)
     grads = api.render_backward(g, cams, dL, ws)
     torch.cuda.synchronize()
     ref = _gpu.oracle_backward(orc, scene, cams, cot_np)
-    errs = _gpu.check_grads(grads, ref, ref["taint"], what="box10k")
-    print("box10k grads", errs, "tainted", int(ref["taint"].sum()))
+    errs = _gpu.check_grads(grads, ref, what="box10k")
+    print("box10k grads", errs)
     np.testing.assert_allclose(_gpu.to_np(grads.vis_count), ref["vis_count"])
-    m = ref["taint"] == 0
-    e = np.linalg.norm(_gpu.to_np(grads.grad_stat)[m] - ref["grad_stat"][m]) / np.linalg.norm(ref["grad_stat"][m])
-    assert e < 1e-3
+    gs, rs = _gpu.to_np(grads.grad_stat), ref["grad_stat"]
+    assert np.linalg.norm(gs - rs) / np.linalg.norm(rs) < 1e-3
+    assert (np.abs(gs - rs) <= 1e-3 * (rs + 1e-3 * np.sqrt(np.mean(rs ** 2)))).all()
 
 
 @pytest.mark.parametrize("deg", [1, 3])
@@ -108,13 +135,14 @@ def test_multiview_mixed_resolution_sh(orc, deg):
     scene = sg.room_scene(20_000, 5 + deg, sh_degree=deg)
     cams = sg.room_poses(2, 7, 160, 120) + sg.room_poses(1, 8, 97, 61)
     g, imgs, ws = _gpu.render_gpu(scene, cams)
+    refs = [orc.render_outcomes(scene, c) for c in cams]
     for v, c in enumerate(cams):
-        _gpu.check_image(imgs[v], orc.render(scene, c), what=f"view {v}")
-    cot_np, dL = _gpu.cotangents(cams, 3)
+        _gpu.check_image(imgs[v], refs[v], what=f"view {v}")
+    cot_np, dL = _gpu.masked_cotangents(cams, refs, 3)
     grads = api.render_backward(g, cams, dL, ws)
     torch.cuda.synchronize()
     ref = _gpu.oracle_backward(orc, scene, cams, cot_np)
-    _gpu.check_grads(grads, ref, ref["taint"], what=f"multiview deg {deg}")
+    _gpu.check_grads(grads, ref, what=f"multiview deg {deg}")
 
 
 def test_empty_and_culled_scenes(orc):
@@ -141,13 +169,13 @@ def test_ragged_tiny_scenes(orc, seed):
     sc.log_scales[4] = np.log(np.float32(2.0))
     cam = camera(53, 37, 30, 31, 26.1, 17.7)
     g, imgs, ws = _gpu.render_gpu(sc, [cam])
-    ref = orc.render(sc, cam)
+    ref = orc.render_outcomes(sc, cam)
     _gpu.check_image(imgs[0], ref, what=f"ragged {seed}")
-    cot_np, dL = _gpu.cotangents([cam], seed)
+    cot_np, dL = _gpu.masked_cotangents([cam], [ref], seed)
     grads = api.render_backward(g, [cam], dL, ws)
     torch.cuda.synchronize()
     ref_g = _gpu.oracle_backward(orc, sc, [cam], cot_np)
-    _gpu.check_grads(grads, ref_g, ref_g["taint"], what=f"ragged {seed}")
+    _gpu.check_grads(grads, ref_g, what=f"ragged {seed}")
 
 
 def test_workspace_regrowth_and_determinism(orc):
@@ -161,20 +189,3 @@ def test_workspace_regrowth_and_determinism(orc):
     api.mgs_render(g, cams, b, ws)
     torch.cuda.synchronize()
     assert torch.equal(a[0].rgb, b[0].rgb) and torch.equal(a[0].alpha, b[0].alpha)
-
-
-def test_autograd_function_matches_direct_backward(orc):
-    scene, cams = sg.workload("box10k")
-    g = api.Gaussians.from_scene(scene, "cuda")
-    params = [p.clone().requires_grad_(True) for p in g.params()]
-    ws = api.RenderWorkspace("cuda")
-    rgb, depth, alpha = api.RenderFn.apply(*params, cams, ws)
-    cot_np, dL = _gpu.cotangents(cams, 11)
-    loss = (rgb[0] * dL[0].rgb).sum() + (depth[0] * dL[0].depth).sum() + (alpha[0] * dL[0].alpha).sum()
-    loss.backward()
-    g2, imgs, ws2 = _gpu.render_gpu(scene, cams)
-    direct = api.render_backward(g2, cams, dL, ws2)
-    torch.cuda.synchronize()
-    for p, d in zip(params, direct.tensors()):
-        # both paths run the same kernels; only the order of float atomics differs
-        assert torch.allclose(p.grad, d, rtol=1e-4, atol=1e-6 * float(d.abs().max()))

@@ -248,3 +248,152 @@ def test_tile_subset_matches_full_render(orc):
         sl = (slice(ty * 16, ty * 16 + 16), slice(tx * 16, tx * 16 + 16))
         np.testing.assert_array_equal(part["alpha"][sl], full["alpha"][sl])
         np.testing.assert_array_equal(part["rgb"][(slice(None),) + sl], full["rgb"][(slice(None),) + sl])
+
+
+def test_sh_basis_matches_cartesian_forms(orc):
+    """The basis at fixed directions equals the textbook Cartesian forms of the real
+    orthonormal harmonics, index l^2 + l + m, without the Condon-Shortley phase
+    (Y_1,-1 ~ y, Y_1,0 ~ z, Y_1,1 ~ x, ...).  A swapped index or a flipped sign keeps
+    the basis orthonormal, so the quadrature pin alone would not see it."""
+    pi = math.pi
+    forms = {
+        0: lambda x, y, z: 0.5 * math.sqrt(1 / pi),
+        1: lambda x, y, z: math.sqrt(3 / (4 * pi)) * y,
+        2: lambda x, y, z: math.sqrt(3 / (4 * pi)) * z,
+        3: lambda x, y, z: math.sqrt(3 / (4 * pi)) * x,
+        4: lambda x, y, z: 0.5 * math.sqrt(15 / pi) * x * y,
+        5: lambda x, y, z: 0.5 * math.sqrt(15 / pi) * y * z,
+        6: lambda x, y, z: 0.25 * math.sqrt(5 / pi) * (3 * z * z - 1),
+        7: lambda x, y, z: 0.5 * math.sqrt(15 / pi) * x * z,
+        8: lambda x, y, z: 0.25 * math.sqrt(15 / pi) * (x * x - y * y),
+        9: lambda x, y, z: 0.25 * math.sqrt(35 / (2 * pi)) * y * (3 * x * x - y * y),
+        10: lambda x, y, z: 0.5 * math.sqrt(105 / pi) * x * y * z,
+        11: lambda x, y, z: 0.25 * math.sqrt(21 / (2 * pi)) * y * (5 * z * z - 1),
+        12: lambda x, y, z: 0.25 * math.sqrt(7 / pi) * z * (5 * z * z - 3),
+        13: lambda x, y, z: 0.25 * math.sqrt(21 / (2 * pi)) * x * (5 * z * z - 1),
+        14: lambda x, y, z: 0.25 * math.sqrt(105 / pi) * z * (x * x - y * y),
+        15: lambda x, y, z: 0.25 * math.sqrt(35 / (2 * pi)) * x * (x * x - 3 * y * y),
+    }
+    dirs = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (0.48, -0.6, 0.64), (-0.36, 0.48, -0.8)]
+    for d in dirs:
+        d = np.asarray(d, float) / np.linalg.norm(d)
+        Y, _ = orc.sh_basis(3, d)
+        want = np.array([forms[k](*d) for k in range(16)])
+        np.testing.assert_allclose(Y, want, atol=1e-14)
+    # on the axes: Y_1,-1 = Y_1,0 = 0 at +x and only Y_1,1 carries the sign of x
+    Yx, _ = orc.sh_basis(1, [1, 0, 0])
+    assert Yx[1] == 0 and Yx[2] == 0 and Yx[3] > 0
+
+
+# ---------------------------------------------------------------- near-tie outcomes
+def _o32(sc, i=0):
+    return 1 / (1 + math.exp(-float(sc.opacity_logit[i])))
+
+
+def _c32(sc):
+    return np.maximum(0, sc.sh[:, 0, :].astype(np.float64) * Y00 + 0.5)
+
+
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_outcomes_alpha_cutoff_tie(orc, sign):
+    """alpha = 1/255 (1 +- 1e-7) at pixel (19, 16), inside the alpha margin: one tie; the
+    image takes the FP64 decision and the other outcome the opposite one."""
+    f, z, s, W, H = 100.0, 2.0, 0.04, 32, 32
+    sig2 = _iso_sigma2(f, math.exp(float(np.float32(math.log(s)))), z)
+    o = (1 / 255) * (1 + sign * 1e-7) * math.exp(0.5 * 9.0 / sig2)
+    sc = make_scene([[0, 0, z]], [[s, s, s]], [[1, 0, 0, 0]], [o], [[0.2, 0.5, 0.9]])
+    out = orc.render_outcomes(sc, camera(W, H, f, f, 16, 16))
+    expect = _o32(sc) * math.exp(-0.5 * 9.0 / sig2)
+    assert abs(expect * 255 - 1) < 1e-6
+    assert out["n_ties"][16, 19] == 1 and out["flags"][16, 19] & 1
+    blended, other = (out["alpha"], out["alt_alpha"]) if expect >= 1 / 255 else (out["alt_alpha"], out["alpha"])
+    assert abs(blended[16, 19] - expect) < 1e-15 and other[16, 19] == 0.0
+    c = _c32(sc)[0]
+    alt_rgb = out["alt_rgb"][:, 16, 19]
+    np.testing.assert_allclose(alt_rgb, c * out["alt_alpha"][16, 19], atol=1e-15)
+    np.testing.assert_allclose(out["alt_depth"][16, 19], z * out["alt_alpha"][16, 19], atol=1e-15)
+    # pixels with no tie: the other outcome is the image itself
+    free = out["n_ties"] == 0
+    np.testing.assert_array_equal(out["alt_alpha"][free], out["alpha"][free])
+
+
+def test_outcomes_transmittance_stop_tie(orc):
+    """Centre-pixel alpha o with (1 - o)^4 = 1e-4 (1 + 1e-7): the FP64 pass does not stop
+    after the 4th layer and blends the 5th; the other outcome stops after the 4th."""
+    cols = [[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [0, 1, 1], [1, 0, 1]]
+    z = [2.0, 2.5, 3.0, 3.5, 4.0, 4.5]
+    n = len(z)
+    o = 1 - (1e-4 * (1 + 1e-7)) ** 0.25
+    sc = make_scene([[0, 0, zz] for zz in z], [[0.5] * 3] * n, [[1, 0, 0, 0]] * n, [o] * n, cols)
+    out = orc.render_outcomes(sc, camera(32, 32, 100, 100, 16, 16))
+    o32 = _o32(sc)
+    assert abs((1 - o32) ** 4 / 1e-4 - 1) < 5e-6
+    c = _c32(sc)
+    four = sum(c[k] * o32 * (1 - o32) ** k for k in range(4))
+    five = four + c[4] * o32 * (1 - o32) ** 4
+    assert out["n_ties"][16, 16] == 1 and out["flags"][16, 16] & 2
+    got, alt = out["rgb"][:, 16, 16], out["alt_rgb"][:, 16, 16]
+    if (1 - o32) ** 4 >= 1e-4:
+        np.testing.assert_allclose(got, five, atol=1e-14)
+        np.testing.assert_allclose(alt, four, atol=1e-14)
+        assert abs(out["alt_alpha"][16, 16] - (1 - (1 - o32) ** 4)) < 1e-15
+    else:
+        np.testing.assert_allclose(got, four, atol=1e-14)
+        np.testing.assert_allclose(alt, five, atol=1e-14)
+
+
+def test_outcomes_depth_order_tie(orc):
+    """Two Gaussians whose camera depth 2 + 2^-23 is a float32 rounding midpoint: equal
+    keys, index order in the image, the swapped order as the other outcome."""
+    cols = [[1, 0, 0], [0, 1, 0]]
+    sc = make_scene([[0, 0, 2.0], [0, 0, 2.0]], [[0.3] * 3] * 2, [[1, 0, 0, 0]] * 2, [0.6, 0.5], cols)
+    cam = camera(32, 32, 100, 100, 16, 16, t=[0, 0, 2.0 ** -23])
+    out = orc.render_outcomes(sc, cam)
+    o = [_o32(sc, 0), _o32(sc, 1)]
+    c = _c32(sc)
+    assert out["n_ties"][16, 16] == 1 and out["flags"][16, 16] & 4
+    np.testing.assert_allclose(out["rgb"][:, 16, 16], c[0] * o[0] + c[1] * o[1] * (1 - o[0]), atol=1e-14)
+    np.testing.assert_allclose(out["alt_rgb"][:, 16, 16], c[1] * o[1] + c[0] * o[0] * (1 - o[1]), atol=1e-14)
+    np.testing.assert_allclose(out["alt_alpha"][16, 16], out["alpha"][16, 16], atol=1e-15)
+
+
+def test_outcomes_extent_tie(orc):
+    """A Gaussian whose rect edge u + r sits 1e-3 px short of the tile boundary x = 32:
+    pixel (32, 16) is outside its rect in the image and inside it in the other outcome,
+    where it takes the Gaussian's alpha o exp(-d^2 / (2 lambda))."""
+    f, z, s = 100.0, 2.0, 0.1
+    s32 = math.exp(float(np.float32(math.log(s))))
+    lam = (f * s32 / z) ** 2 + 0.3
+    r = math.ceil(3 * math.sqrt(lam))
+    u = 32.0 - r - 1e-3  # on the optical axis: principal point at u
+    sc = make_scene([[0, 0, z]], [[s, s, s]], [[1, 0, 0, 0]], [0.9], [[1, 1, 1]])
+    cam = camera(64, 32, f, f, u, 16.0)
+    p = orc.project(sc, cam)
+    edge = p["mean2d"][0, 0] + p["radius"][0]
+    assert abs(edge - (32 - 1e-3)) < 1e-5 and p["rect"][0, 2] == 1
+    out = orc.render_outcomes(sc, cam)
+    assert out["n_ties"][16, 32] == 1 and out["flags"][16, 32] & 8
+    assert out["alpha"][16, 32] == 0.0
+    d = 32.0 - p["mean2d"][0, 0]
+    want = _o32(sc) * math.exp(-0.5 * d * d / lam)
+    assert abs(out["alt_alpha"][16, 32] - want) < 1e-12 and want > 1 / 255
+    assert out["n_ties"][16, 31] == 0 and out["alpha"][16, 31] > 0
+
+
+def test_outcomes_agree_with_render_on_a_random_scene(orc):
+    """The image of render_outcomes is orc_render's; two or more ties leave NaN."""
+    rng = np.random.default_rng(11)
+    sc = random_scene(rng, 200, sh_degree=2, spread=1.2, depth=2.5)
+    cam = camera(80, 48, 40, 40, 40.3, 23.9)
+    wide = orc.margins(alpha_rel=0.05, T_rel=0.05)  # wide margins: many ties, some pixels with two
+    a = orc.render(sc, cam, margin=wide)
+    b = orc.render_outcomes(sc, cam, margin=wide)
+    for k in ("rgb", "depth", "alpha", "flags", "n_contrib"):
+        np.testing.assert_array_equal(a[k], b[k])
+    many = b["n_ties"] >= 2
+    assert np.isnan(b["alt_alpha"][many]).all() and not np.isnan(b["alt_alpha"][~many]).any()
+    # every flag but the opacity clamp's marks a tie, and every tie sets a flag
+    np.testing.assert_array_equal((b["flags"] & 15) != 0, b["n_ties"] > 0)
+    one = b["n_ties"] == 1
+    assert one.any() and many.any()
+    assert (np.abs(b["alt_alpha"] - b["alpha"])[one] > 0).mean() > 0.5

@@ -66,3 +66,23 @@ def test_noalloc_sort_rejects_sizes_beyond_its_maximum():
                                     C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == _abi.MGS_ERR_UNSUPPORTED
     assert b"MGS_SORT_NOALLOC_MAX" in lib.mgs_last_error()
+
+
+def test_noalloc_sort_of_an_offset_view():
+    """Keys that start 4 bytes into an allocation (keys[1:], not 16-byte aligned) sort
+    exactly as an aligned copy of them does."""
+    from paper_2509_13536_gb300 import _abi
+    lib = _abi.load()
+    rng = np.random.default_rng(7)
+    n = 200_003
+    raw = rng.integers(0, 2 ** 32, n + 1, dtype=np.uint64).astype(np.uint32)
+    base = torch.from_numpy(raw.view(np.int32)).cuda()
+    view = base[1:]
+    assert view.data_ptr() % 16 != 0
+    k_ref, v_ref = _sort_with_workspace(lib, view.clone(), False, (0, 32))
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = lib.mgs_sort_pairs_noalloc(_p(view), None, _p(out), n, 0, 32,
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, lib.mgs_last_error()
+    torch.cuda.synchronize()
+    assert torch.equal(view, k_ref) and torch.equal(out, v_ref)
