@@ -546,8 +546,13 @@ uint64_t mix(uint64_t h, uint64_t v) {
 }
 
 // Chain rule from the screen-space gradient of one Gaussian to its parameters.
-void gaussian_backward(const orc_gaussians* g, const orc_camera* cam, const Proj& P, int64_t i,
-                       const double* g2, orc_grads* out) {
+// Parameter gradient of one Gaussian from its screen-space gradient (linear in g2).
+struct ParamGrad {
+  double mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {0, 0, 0, 0}, op = 0, sh[48] = {}, stat = 0;
+};
+
+void gaussian_backward_local(const orc_gaussians* g, const orc_camera* cam, const Proj& P, int64_t i,
+                             const double* g2, ParamGrad& o) {
   double du = g2[0], dv = g2[1], dA = g2[2], dB = g2[3], dC = g2[4], dop = g2[5];
   const double* dcol = g2 + 6;
   double dd = g2[9];
@@ -556,18 +561,17 @@ void gaussian_backward(const orc_gaussians* g, const orc_camera* cam, const Proj
   double dp[3] = {0, 0, 0};
   double dmu[3] = {0, 0, 0};
   // opacity = sigmoid(logit)
-  out->opacity_logit[i] += dop * P.o * (1 - P.o);
+  o.op += dop * P.o * (1 - P.o);
   // colour
   int K = (g->sh_degree + 1) * (g->sh_degree + 1);
   double Y[16], dY[48];
   sh_eval(g->sh_degree, P.dir, Y, dY);
   const double* sh = g->sh + (size_t)i * K * 3;
-  double* gsh = out->sh + (size_t)i * K * 3;
   double ddir[3] = {0, 0, 0};
   for (int ch = 0; ch < 3; ++ch) {
     if (P.raw[ch] < 0) continue;
     for (int k = 0; k < K; ++k) {
-      gsh[k * 3 + ch] += dcol[ch] * Y[k];
+      o.sh[k * 3 + ch] += dcol[ch] * Y[k];
       for (int a = 0; a < 3; ++a) ddir[a] += dcol[ch] * sh[k * 3 + ch] * dY[k * 3 + a];
     }
   }
@@ -614,13 +618,13 @@ void gaussian_backward(const orc_gaussians* g, const orc_camera* cam, const Proj
   }
   // p = W mu + t
   for (int a = 0; a < 3; ++a) dmu[a] += cam->R[0 * 3 + a] * dp[0] + cam->R[1 * 3 + a] * dp[1] + cam->R[2 * 3 + a] * dp[2];
-  for (int a = 0; a < 3; ++a) out->means[3 * i + a] += dmu[a];
+  for (int a = 0; a < 3; ++a) o.mu[a] += dmu[a];
   // S3 = Rq diag(s^2) Rq^T
   double RtH[9], RtHR[9], Rqt[9];
   transpose(P.Rq, Rqt, 3, 3);
   matmul(Rqt, H, RtH, 3, 3, 3);
   matmul(RtH, P.Rq, RtHR, 3, 3, 3);
-  for (int k = 0; k < 3; ++k) out->log_scales[3 * i + k] += 2 * P.s[k] * RtHR[k * 4] * P.s[k];
+  for (int k = 0; k < 3; ++k) o.ls[k] += 2 * P.s[k] * RtHR[k * 4] * P.s[k];
   double dR[9], HR[9];
   matmul(H, P.Rq, HR, 3, 3, 3);
   for (int a = 0; a < 3; ++a)
@@ -628,8 +632,40 @@ void gaussian_backward(const orc_gaussians* g, const orc_camera* cam, const Proj
   double dqn[4];
   rot_backward(P.qn, dR, dqn);
   double dot = dqn[0] * P.qn[0] + dqn[1] * P.qn[1] + dqn[2] * P.qn[2] + dqn[3] * P.qn[3];
-  for (int k = 0; k < 4; ++k) out->quats[4 * i + k] += (dqn[k] - P.qn[k] * dot) / P.qnorm;
-  if (out->grad_stat) out->grad_stat[i] += std::sqrt(dmu[0] * dmu[0] + dmu[1] * dmu[1] + dmu[2] * dmu[2]);
+  for (int k = 0; k < 4; ++k) o.q[k] += (dqn[k] - P.qn[k] * dot) / P.qnorm;
+  o.stat = std::sqrt(dmu[0] * dmu[0] + dmu[1] * dmu[1] + dmu[2] * dmu[2]);
+}
+
+void gaussian_backward(const orc_gaussians* g, const orc_camera* cam, const Proj& P, int64_t i,
+                       const double* g2, const double* g2abs, orc_grads* out) {
+  ParamGrad o;
+  gaussian_backward_local(g, cam, P, i, g2, o);
+  const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
+  for (int a = 0; a < 3; ++a) out->means[3 * i + a] += o.mu[a];
+  for (int k = 0; k < 3; ++k) out->log_scales[3 * i + k] += o.ls[k];
+  for (int k = 0; k < 4; ++k) out->quats[4 * i + k] += o.q[k];
+  out->opacity_logit[i] += o.op;
+  for (int k = 0; k < K * 3; ++k) out->sh[(size_t)i * K * 3 + k] += o.sh[k];
+  if (out->grad_stat) out->grad_stat[i] += o.stat;
+  if (!g2abs || !out->scale_means) return;
+  // Scale of each parameter element: sum over the screen-space components j of
+  // |d element / d s_j| times the sum of the absolute values of the per-pixel terms
+  // that made s_j (the chain rule is linear in s, so its columns are the images of the
+  // unit vectors).  A float32 evaluation of the same sums errs by a few units of
+  // 2^-24 times this, however much the terms cancel.
+  for (int j = 0; j < 10; ++j) {
+    if (g2abs[j] == 0) continue;
+    double e[10] = {};
+    e[j] = 1;
+    ParamGrad c;
+    gaussian_backward_local(g, cam, P, i, e, c);
+    const double s = g2abs[j];
+    for (int a = 0; a < 3; ++a) out->scale_means[3 * i + a] += std::fabs(c.mu[a]) * s;
+    for (int k = 0; k < 3; ++k) out->scale_log_scales[3 * i + k] += std::fabs(c.ls[k]) * s;
+    for (int k = 0; k < 4; ++k) out->scale_quats[4 * i + k] += std::fabs(c.q[k]) * s;
+    out->scale_opacity_logit[i] += std::fabs(c.op) * s;
+    for (int k = 0; k < K * 3; ++k) out->scale_sh[(size_t)i * K * 3 + k] += std::fabs(c.sh[k]) * s;
+  }
 }
 
 // ---------- 2-Wasserstein helpers (Eq. 7-9) ----------
@@ -924,7 +960,8 @@ int orc_render_backward(const orc_gaussians* g, const orc_camera* cam, const orc
   int TX = tiles_x(cam), W = cam->width, H = cam->height;
   size_t HW = (size_t)W * H;
   // Per (tile, list entry) screen-space gradients, reduced afterwards in tile order.
-  std::vector<std::vector<double>> acc(bins.size());
+  std::vector<std::vector<double>> acc(bins.size()), accabs(bins.size());
+  const bool scale = out->scale_means != nullptr;
   std::vector<std::vector<int32_t>> taint_lists(bins.size());
   parallel_for((int64_t)bins.size(), n_threads, [&](int64_t t) {
     if (!want[t] || bins[t].empty()) return;
@@ -940,6 +977,7 @@ int orc_render_backward(const orc_gaussians* g, const orc_camera* cam, const orc
       return it->second;
     };
     acc[t].assign(list.size() * 10, 0.0);
+    if (scale) accabs[t].assign(list.size() * 10, 0.0);
     int x0 = (int)(t % TX) * kTile, y0 = (int)(t / TX) * kTile;
     for (int py = y0; py < std::min(H, y0 + kTile); ++py)
       for (int px = x0; px < std::min(W, x0 + kTile); ++px) {
@@ -955,9 +993,13 @@ int orc_render_backward(const orc_gaussians* g, const orc_camera* cam, const orc
           const Contribution& c = R.contrib[k];
           const Proj& p = P[c.g];
           double* a = &acc[t][(size_t)slot_of(c.g) * 10];
+          double dummy[10];
+          double* b = scale ? &accabs[t][(size_t)slot_of(c.g) * 10] : dummy;
           double w = c.alpha * c.Tb;
           for (int ch = 0; ch < 3; ++ch) a[6 + ch] += w * gC[ch];
           a[9] += w * gD;
+          for (int ch = 0; ch < 3; ++ch) b[6 + ch] += std::fabs(w * gC[ch]);
+          b[9] += std::fabs(w * gD);
           double dLda = 0;
           for (int ch = 0; ch < 3; ++ch) dLda += (p.rgb[ch] - S[ch]) * gC[ch];
           dLda += (p.p[2] - SD) * gD;
@@ -972,15 +1014,24 @@ int orc_render_backward(const orc_gaussians* g, const orc_camera* cam, const orc
             a[4] += gp * (-0.5 * c.dy * c.dy);
             a[0] += gp * (-p.conic[0] * c.dx - p.conic[1] * c.dy);
             a[1] += gp * (-p.conic[2] * c.dy - p.conic[1] * c.dx);
+            b[5] += std::fabs(dLda * c.G);
+            b[2] += std::fabs(gp * 0.5 * c.dx * c.dx);
+            b[3] += std::fabs(gp * c.dx * c.dy);
+            b[4] += std::fabs(gp * 0.5 * c.dy * c.dy);
+            b[0] += std::fabs(gp) * (std::fabs(p.conic[0] * c.dx) + std::fabs(p.conic[1] * c.dy));
+            b[1] += std::fabs(gp) * (std::fabs(p.conic[2] * c.dy) + std::fabs(p.conic[1] * c.dx));
           }
         }
       }
   });
-  std::vector<double> g2((size_t)g->n * 10, 0.0);
+  std::vector<double> g2((size_t)g->n * 10, 0.0), g2abs(scale ? (size_t)g->n * 10 : 0, 0.0);
   for (size_t t = 0; t < bins.size(); ++t) {
     if (acc[t].empty()) continue;
     for (size_t k = 0; k < bins[t].size(); ++k)
-      for (int c = 0; c < 10; ++c) g2[(size_t)bins[t][k].g * 10 + c] += acc[t][k * 10 + c];
+      for (int c = 0; c < 10; ++c) {
+        g2[(size_t)bins[t][k].g * 10 + c] += acc[t][k * 10 + c];
+        if (scale) g2abs[(size_t)bins[t][k].g * 10 + c] += accabs[t][k * 10 + c];
+      }
     if (out->taint)
       for (int32_t gi : taint_lists[t]) out->taint[gi] = 1;
   }
@@ -990,7 +1041,7 @@ int orc_render_backward(const orc_gaussians* g, const orc_camera* cam, const orc
     for (int64_t i = b * 1024; i < std::min<int64_t>(g->n, (b + 1) * 1024); ++i) {
       if (!P[i].visible) continue;
       if (out->vis_count) out->vis_count[i] += 1;
-      gaussian_backward(g, cam, P[i], i, &g2[(size_t)i * 10], out);
+      gaussian_backward(g, cam, P[i], i, &g2[(size_t)i * 10], scale ? &g2abs[(size_t)i * 10] : nullptr, out);
     }
   });
   return 0;

@@ -130,6 +130,13 @@ int orc_render_bruteforce(const orc_gaussians* g, const orc_camera* cam,
 typedef struct {
   double* means; double* log_scales; double* quats; double* opacity_logit; double* sh;
   double* grad2d; uint8_t* taint; double* grad_stat; double* vis_count;
+  /* optional (all five or none), += like the gradients: the scale of each gradient
+   * element, sum over the screen-space components s_j of |d element / d s_j| times
+   * the sum of the absolute values of the per-pixel terms that make s_j.  An
+   * evaluation in float32 of the same sums is off by a few units of 2^-24 times this,
+   * however much the terms cancel. */
+  double* scale_means; double* scale_log_scales; double* scale_quats; double* scale_opacity_logit;
+  double* scale_sh;
 } orc_grads;
 
 int orc_render_backward(const orc_gaussians* g, const orc_camera* cam, const orc_margins* m,

@@ -69,9 +69,12 @@ class Projection(C.Structure):
                                           "radius", "rect", "visible")]
 
 
+GRAD_KEYS = ("means", "log_scales", "quats", "opacity_logit", "sh", "grad2d", "taint", "grad_stat", "vis_count",
+             "scale_means", "scale_log_scales", "scale_quats", "scale_opacity_logit", "scale_sh")
+
+
 class Grads(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logit", "sh",
-                                          "grad2d", "taint", "grad_stat", "vis_count")]
+    _fields_ = [(k, C.c_void_p) for k in GRAD_KEYS]
 
 
 class MergeParams(C.Structure):
@@ -217,8 +220,7 @@ def render_backward(scene, cam, g_rgb=None, g_depth=None, g_alpha=None, *, tiles
     n, K = P.n, (P.deg + 1) ** 2
     if grads is None:
         grads = new_grads(n, P.deg)
-    gs = Grads(**{k: _p(grads[k]) for k in ("means", "log_scales", "quats", "opacity_logit", "sh",
-                                            "grad2d", "taint", "grad_stat", "vis_count")})
+    gs = Grads(**{k: _p(grads.get(k)) for k in GRAD_KEYS})
     t = None if tiles is None else np.ascontiguousarray(tiles, np.int32)
     m = margin if margin is not None else margins()
     gr = None if g_rgb is None else _f64(g_rgb)
@@ -231,11 +233,17 @@ def render_backward(scene, cam, g_rgb=None, g_depth=None, g_alpha=None, *, tiles
     return grads
 
 
-def new_grads(n, deg):
+def new_grads(n, deg, scale=False):
+    """float64 gradient accumulators; ``scale`` adds the per-element scale arrays
+    (``scale_<field>``, see orc_grads)."""
     K = (deg + 1) ** 2
-    return dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
-                opacity_logit=np.zeros(n), sh=np.zeros((n, K, 3)), grad2d=np.zeros((n, 10)),
-                taint=np.zeros(n, np.uint8), grad_stat=np.zeros(n), vis_count=np.zeros(n))
+    d = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+             opacity_logit=np.zeros(n), sh=np.zeros((n, K, 3)), grad2d=np.zeros((n, 10)),
+             taint=np.zeros(n, np.uint8), grad_stat=np.zeros(n), vis_count=np.zeros(n))
+    if scale:
+        for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+            d["scale_" + k] = np.zeros_like(d[k])
+    return d
 
 
 def voxel_keys(means, voxel):

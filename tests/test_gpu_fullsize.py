@@ -35,6 +35,13 @@ def _built():
     build.build()
 
 
+def _grad_summary(e):
+    f = _gpu.FIELDS
+    return dict(grad_rel_max=max(e[k] for k in f), grad_elem_ratio_max=max(e[k + "_elem"] for k in f),
+                beyond_literal=sum(e.get(k + "_beyond_literal", 0) for k in f),
+                max_ulps_of_scale=max(e.get(k + "_ulps_of_scale", 0.0) for k in f))
+
+
 def _sum_reports(reps):
     out = {}
     for r in reps:
@@ -53,8 +60,7 @@ def test_room300k_full_image_and_gradients(orc):
     torch.cuda.synchronize()
     ref_g = _gpu.oracle_backward(orc, scene, cams, cot_np)
     e = _gpu.check_grads(grads, ref_g, what="room300k")
-    _report("room300k", **rep, grad_rel_max=max(v for k, v in e.items() if not k.endswith("_elem")),
-            grad_elem_ratio_max=max(v for k, v in e.items() if k.endswith("_elem")))
+    _report("room300k", **rep, **_grad_summary(e))
 
 
 def _sampled_tiles(cam, n, rng):
@@ -100,9 +106,7 @@ def test_room1m_whole_keyframes_backward(orc, big):
     e = _gpu.check_grads(big["grads"], ref, what="room1m 8 keyframes")
     np.testing.assert_allclose(_gpu.to_np(big["grads"].vis_count), ref["vis_count"])
     drawn = int((ref["vis_count"] > 0).sum())
-    _report("room1m 8 keyframes gradients", gaussians_drawn=drawn,
-            grad_rel_max=max(v for k, v in e.items() if not k.endswith("_elem")),
-            grad_elem_ratio_max=max(v for k, v in e.items() if k.endswith("_elem")))
+    _report("room1m 8 keyframes gradients", gaussians_drawn=drawn, **_grad_summary(e))
 
 
 def _richardson(f, th, h):
@@ -134,7 +138,7 @@ def test_room1m_finite_differences_64_parameters(orc, big):
         dL.append(api.Image(*(torch.from_numpy(x).cuda() for x in (gr, gd, ga))))
     grads = api.render_backward(big["g"], cams, dL, big["ws"])  # same saved forward state
     torch.cuda.synchronize()
-    ref = orc.new_grads(scene.n, 3)
+    ref = orc.new_grads(scene.n, 3, scale=True)
     for c, t, (gr, gd, ga) in zip(cams, tiles, cot):
         orc.render_backward(scene, c, gr, gd, ga, tiles=t, grads=ref)
     reach = np.zeros(scene.n, bool)
@@ -188,9 +192,10 @@ def test_room1m_finite_differences_64_parameters(orc, big):
             skipped += 1
             continue
         gpu = float(_gpu.to_np(getattr(grads, f))[(idx[gi],) + comp])
-        scale = max(abs(fd), 1e-3 * np.sqrt(np.mean(ref[f][idx] ** 2)))
-        worst = max(worst, abs(gpu - fd) / scale)
-        assert abs(gpu - fd) <= 1e-3 * scale, (f, int(idx[gi]), comp, gpu, fd)
+        lit = 1e-3 * max(abs(fd), 1e-3 * np.sqrt(np.mean(ref[f][idx] ** 2)))
+        bound = max(lit, _gpu.SCALE_ULPS * _gpu.EPS32 * float(ref["scale_" + f][(idx[gi],) + comp]))
+        worst = max(worst, abs(gpu - fd) / bound)
+        assert abs(gpu - fd) <= bound, (f, int(idx[gi]), comp, gpu, fd, lit, bound)
         checked += 1
     _report("room1m finite differences", checked=checked, skipped=skipped, worst_rel=worst)
     assert skipped <= 8
