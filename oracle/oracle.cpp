@@ -15,6 +15,7 @@
 #include <map>
 #include <thread>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -26,6 +27,7 @@ constexpr double kAlphaMax = 0.99;        // alpha is clamped to this
 constexpr double kTStop = 1e-4;           // stop a pixel once T falls below this
 constexpr double kDilation = 0.3;         // px^2 added to the 2D covariance diagonal
 constexpr double kFovClamp = 1.3;         // x/z and y/z clamp factor inside the Jacobian
+constexpr double kEps32 = 1.0 / 16777216; // 2^-24, unit roundoff of float32
 
 template <class F>
 void parallel_for(int64_t n, int nthreads, F f) {
@@ -48,18 +50,38 @@ void parallel_for(int64_t n, int nthreads, F f) {
 }
 
 // ---------- small dense linear algebra (row-major) ----------
-void matmul(const double* A, const double* B, double* C, int n, int k, int m) {
+// Templated on the element types so that the chain rule below also runs on AbsVal.
+template <class TA, class TB, class TC>
+void matmul(const TA* A, const TB* B, TC* C, int n, int k, int m) {
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < m; ++j) {
-      double s = 0;
+      TC s = TC();
       for (int l = 0; l < k; ++l) s += A[i * k + l] * B[l * m + j];
       C[i * m + j] = s;
     }
 }
-void transpose(const double* A, double* At, int n, int m) {
+template <class T>
+void transpose(const T* A, T* At, int n, int m) {
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < m; ++j) At[j * n + i] = A[i * m + j];
 }
+
+// Running-error arithmetic for a computation that is linear in its AbsVal inputs: every
+// sum and difference adds magnitudes, every product takes |constant|.  Run on the sums
+// of |terms| of its inputs, a linear map gives the sum over all its paths of the
+// absolute products: the quantity a floating-point evaluation's rounding error is
+// proportional to, however much the exact result cancels.
+struct AbsVal {
+  double v = 0;
+};
+inline AbsVal operator+(AbsVal a, AbsVal b) { return {a.v + b.v}; }
+inline AbsVal operator-(AbsVal a, AbsVal b) { return {a.v + b.v}; }
+inline AbsVal operator-(AbsVal a) { return a; }
+inline AbsVal operator*(AbsVal a, double c) { return {a.v * std::fabs(c)}; }
+inline AbsVal operator*(double c, AbsVal a) { return {a.v * std::fabs(c)}; }
+inline AbsVal operator/(AbsVal a, double c) { return {a.v / std::fabs(c)}; }
+inline AbsVal& operator+=(AbsVal& a, AbsVal b) { a.v += b.v; return a; }
+inline AbsVal& operator*=(AbsVal& a, double c) { a.v *= std::fabs(c); return a; }
 
 // Rotation matrix of a unit quaternion (w, x, y, z).
 void quat_to_rot(const double* q, double* R) {
@@ -70,7 +92,8 @@ void quat_to_rot(const double* q, double* R) {
 }
 
 // d(sum_ij G_ij R_ij)/dq for the rotation above, q unit (w, x, y, z).
-void rot_backward(const double* q, const double* G, double* dq) {
+template <class T>
+void rot_backward(const double* q, const T* G, T* dq) {
   double w = q[0], x = q[1], y = q[2], z = q[3];
   dq[0] = 2 * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
   dq[1] = 2 * (y * G[1] + z * G[2] + y * G[3] - 2 * x * G[4] - w * G[5] + z * G[6] + w * G[7] -
@@ -428,9 +451,11 @@ std::vector<char> tile_mask(const orc_camera* cam, const int32_t* tiles, int32_t
 struct Contribution {
   int32_t g;
   double alpha, a, G, Tb, dx, dy;
+  double ma;  // relative alpha margin at this pixel (the modelled float32 error of alpha)
 };
 struct PixelResult {
   double rgb[3] = {0, 0, 0}, depth = 0, T = 1;
+  double t_err = 0;  // modelled relative float32 error of T at the end of the pass
   int n_contrib = 0, n_eval = 0;
   uint8_t flags = 0;
   std::vector<Contribution> contrib;  // only filled when requested
@@ -507,7 +532,7 @@ void blend_pixel(const std::vector<Proj>& P, const std::vector<Entry>& list, int
     if (mg && std::fabs(a - kAlphaMax) < (mg->clamp_rel + ma) * kAlphaMax) R.flags |= 16;
     if ((alpha < kAlphaMin) != flipped(1, k)) continue;
     double w = alpha * R.T;
-    if (keep) R.contrib.push_back(Contribution{e.g, alpha, a, std::exp(power), R.T, dx, dy});
+    if (keep) R.contrib.push_back(Contribution{e.g, alpha, a, std::exp(power), R.T, dx, dy, ma});
     for (int c = 0; c < 3; ++c) R.rgb[c] += p.rgb[c] * w;
     R.depth += p.p[2] * w;
     R.T = R.T * (1 - alpha);
@@ -515,6 +540,7 @@ void blend_pixel(const std::vector<Proj>& P, const std::vector<Entry>& list, int
     if (mg) {
       double e = alpha / (1 - alpha) * ma;
       t_var += e * e;
+      R.t_err = std::sqrt(t_var);
       if (std::fabs(R.T / kTStop - 1) < mg->T_rel + std::sqrt(t_var)) {
         R.flags |= 2;
         tie(2, k, -1);
@@ -546,20 +572,24 @@ uint64_t mix(uint64_t h, uint64_t v) {
 }
 
 // Chain rule from the screen-space gradient of one Gaussian to its parameters.
-// Parameter gradient of one Gaussian from its screen-space gradient (linear in g2).
-struct ParamGrad {
-  double mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {0, 0, 0, 0}, op = 0, sh[48] = {}, stat = 0;
+// Parameter gradient of one Gaussian from its screen-space gradient (linear in g2);
+// G = double computes it, G = AbsVal its running-error scale.
+template <class G>
+struct ParamGradT {
+  G mu[3] = {}, ls[3] = {}, q[4] = {}, op = G(), sh[48] = {};
+  double stat = 0;
 };
 
+template <class G>
 void gaussian_backward_local(const orc_gaussians* g, const orc_camera* cam, const Proj& P, int64_t i,
-                             const double* g2, ParamGrad& o) {
-  double du = g2[0], dv = g2[1], dA = g2[2], dB = g2[3], dC = g2[4], dop = g2[5];
-  const double* dcol = g2 + 6;
-  double dd = g2[9];
+                             const G* g2, ParamGradT<G>& o) {
+  G du = g2[0], dv = g2[1], dA = g2[2], dB = g2[3], dC = g2[4], dop = g2[5];
+  const G* dcol = g2 + 6;
+  G dd = g2[9];
   double fx = cam->fx, fy = cam->fy;
   double tx = P.p[0], ty = P.p[1], tz = P.p[2];
-  double dp[3] = {0, 0, 0};
-  double dmu[3] = {0, 0, 0};
+  G dp[3] = {G(), G(), G()};
+  G dmu[3] = {G(), G(), G()};
   // opacity = sigmoid(logit)
   o.op += dop * P.o * (1 - P.o);
   // colour
@@ -567,7 +597,7 @@ void gaussian_backward_local(const orc_gaussians* g, const orc_camera* cam, cons
   double Y[16], dY[48];
   sh_eval(g->sh_degree, P.dir, Y, dY);
   const double* sh = g->sh + (size_t)i * K * 3;
-  double ddir[3] = {0, 0, 0};
+  G ddir[3] = {G(), G(), G()};
   for (int ch = 0; ch < 3; ++ch) {
     if (P.raw[ch] < 0) continue;
     for (int k = 0; k < K; ++k) {
@@ -575,7 +605,7 @@ void gaussian_backward_local(const orc_gaussians* g, const orc_camera* cam, cons
       for (int a = 0; a < 3; ++a) ddir[a] += dcol[ch] * sh[k * 3 + ch] * dY[k * 3 + a];
     }
   }
-  double dd_dot = ddir[0] * P.dir[0] + ddir[1] * P.dir[1] + ddir[2] * P.dir[2];
+  G dd_dot = ddir[0] * P.dir[0] + ddir[1] * P.dir[1] + ddir[2] * P.dir[2];
   for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - P.dir[a] * dd_dot) / P.vnorm;
   // depth and projected centre
   dp[2] += dd;
@@ -585,20 +615,22 @@ void gaussian_backward_local(const orc_gaussians* g, const orc_camera* cam, cons
   dp[2] += -dv * fy * ty / (tz * tz);
   // conic = inverse(cov): dL/dcov = -M Gm M (symmetric trace form)
   double M[4] = {P.conic[0], P.conic[1], P.conic[1], P.conic[2]};
-  double Gm[4] = {dA, 0.5 * dB, 0.5 * dB, dC};
-  double t1[4], Gs[4];
+  G Gm[4] = {dA, 0.5 * dB, 0.5 * dB, dC};
+  G t1[4], Gs[4];
   matmul(M, Gm, t1, 2, 2, 2);
   matmul(t1, M, Gs, 2, 2, 2);
-  for (double& x : Gs) x = -x;
+  for (G& x : Gs) x = -x;
   // cov = T S3 T^T + 0.3 I
-  double GsT[6], H[9], Tt[6];
+  G GsT[6], H[9];
+  double Tt[6];
   matmul(Gs, P.T, GsT, 2, 2, 3);
   transpose(P.T, Tt, 2, 3);
   matmul(Tt, GsT, H, 3, 2, 3);          // dL/dS3 = T^T Gs T
-  double dT[6];
+  G dT[6];
   matmul(GsT, P.S3, dT, 2, 3, 3);       // dL/dT = 2 Gs T S3
-  for (double& x : dT) x *= 2;
-  double Wt[9], dJ[6];
+  for (G& x : dT) x *= 2;
+  double Wt[9];
+  G dJ[6];
   transpose(cam->R, Wt, 3, 3);
   matmul(dT, Wt, dJ, 2, 3, 3);          // T = J W
   dp[2] += dJ[0] * (-fx / (tz * tz)) + dJ[4] * (-fy / (tz * tz));
@@ -620,25 +652,27 @@ void gaussian_backward_local(const orc_gaussians* g, const orc_camera* cam, cons
   for (int a = 0; a < 3; ++a) dmu[a] += cam->R[0 * 3 + a] * dp[0] + cam->R[1 * 3 + a] * dp[1] + cam->R[2 * 3 + a] * dp[2];
   for (int a = 0; a < 3; ++a) o.mu[a] += dmu[a];
   // S3 = Rq diag(s^2) Rq^T
-  double RtH[9], RtHR[9], Rqt[9];
+  G RtH[9], RtHR[9];
+  double Rqt[9];
   transpose(P.Rq, Rqt, 3, 3);
   matmul(Rqt, H, RtH, 3, 3, 3);
   matmul(RtH, P.Rq, RtHR, 3, 3, 3);
   for (int k = 0; k < 3; ++k) o.ls[k] += 2 * P.s[k] * RtHR[k * 4] * P.s[k];
-  double dR[9], HR[9];
+  G dR[9], HR[9];
   matmul(H, P.Rq, HR, 3, 3, 3);
   for (int a = 0; a < 3; ++a)
     for (int k = 0; k < 3; ++k) dR[a * 3 + k] = 2 * HR[a * 3 + k] * P.s[k] * P.s[k];
-  double dqn[4];
+  G dqn[4];
   rot_backward(P.qn, dR, dqn);
-  double dot = dqn[0] * P.qn[0] + dqn[1] * P.qn[1] + dqn[2] * P.qn[2] + dqn[3] * P.qn[3];
+  G dot = dqn[0] * P.qn[0] + dqn[1] * P.qn[1] + dqn[2] * P.qn[2] + dqn[3] * P.qn[3];
   for (int k = 0; k < 4; ++k) o.q[k] += (dqn[k] - P.qn[k] * dot) / P.qnorm;
-  o.stat = std::sqrt(dmu[0] * dmu[0] + dmu[1] * dmu[1] + dmu[2] * dmu[2]);
+  if constexpr (std::is_same<G, double>::value)
+    o.stat = std::sqrt(dmu[0] * dmu[0] + dmu[1] * dmu[1] + dmu[2] * dmu[2]);
 }
 
 void gaussian_backward(const orc_gaussians* g, const orc_camera* cam, const Proj& P, int64_t i,
                        const double* g2, const double* g2abs, orc_grads* out) {
-  ParamGrad o;
+  ParamGradT<double> o;
   gaussian_backward_local(g, cam, P, i, g2, o);
   const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
   for (int a = 0; a < 3; ++a) out->means[3 * i + a] += o.mu[a];
@@ -648,24 +682,19 @@ void gaussian_backward(const orc_gaussians* g, const orc_camera* cam, const Proj
   for (int k = 0; k < K * 3; ++k) out->sh[(size_t)i * K * 3 + k] += o.sh[k];
   if (out->grad_stat) out->grad_stat[i] += o.stat;
   if (!g2abs || !out->scale_means) return;
-  // Scale of each parameter element: sum over the screen-space components j of
-  // |d element / d s_j| times the sum of the absolute values of the per-pixel terms
-  // that made s_j (the chain rule is linear in s, so its columns are the images of the
-  // unit vectors).  A float32 evaluation of the same sums errs by a few units of
-  // 2^-24 times this, however much the terms cancel.
-  for (int j = 0; j < 10; ++j) {
-    if (g2abs[j] == 0) continue;
-    double e[10] = {};
-    e[j] = 1;
-    ParamGrad c;
-    gaussian_backward_local(g, cam, P, i, e, c);
-    const double s = g2abs[j];
-    for (int a = 0; a < 3; ++a) out->scale_means[3 * i + a] += std::fabs(c.mu[a]) * s;
-    for (int k = 0; k < 3; ++k) out->scale_log_scales[3 * i + k] += std::fabs(c.ls[k]) * s;
-    for (int k = 0; k < 4; ++k) out->scale_quats[4 * i + k] += std::fabs(c.q[k]) * s;
-    out->scale_opacity_logit[i] += std::fabs(c.op) * s;
-    for (int k = 0; k < K * 3; ++k) out->scale_sh[(size_t)i * K * 3 + k] += std::fabs(c.sh[k]) * s;
-  }
+  // Error scale of each parameter element: the same chain rule in running-error
+  // arithmetic, fed per screen-space component the sum of |per-pixel term| times the
+  // relative error that term may carry in float32.  Cancellation in the exact sums or
+  // in the chain rule does not shrink it.
+  AbsVal in[10];
+  for (int j = 0; j < 10; ++j) in[j].v = g2abs[j];
+  ParamGradT<AbsVal> c;
+  gaussian_backward_local(g, cam, P, i, in, c);
+  for (int a = 0; a < 3; ++a) out->scale_means[3 * i + a] += c.mu[a].v;
+  for (int k = 0; k < 3; ++k) out->scale_log_scales[3 * i + k] += c.ls[k].v;
+  for (int k = 0; k < 4; ++k) out->scale_quats[4 * i + k] += c.q[k].v;
+  out->scale_opacity_logit[i] += c.op.v;
+  for (int k = 0; k < K * 3; ++k) out->scale_sh[(size_t)i * K * 3 + k] += c.sh[k].v;
 }
 
 // ---------- 2-Wasserstein helpers (Eq. 7-9) ----------
@@ -995,11 +1024,15 @@ int orc_render_backward(const orc_gaussians* g, const orc_camera* cam, const orc
           double* a = &acc[t][(size_t)slot_of(c.g) * 10];
           double dummy[10];
           double* b = scale ? &accabs[t][(size_t)slot_of(c.g) * 10] : dummy;
+          // relative error a float32 evaluation of this pixel's terms may carry: the alpha
+          // margin of this contribution, the accumulated T margin of the pixel, and 32
+          // units of 2^-24 for the rounding of the sums
+          const double u = c.ma + R.t_err + 32.0 * kEps32;
           double w = c.alpha * c.Tb;
           for (int ch = 0; ch < 3; ++ch) a[6 + ch] += w * gC[ch];
           a[9] += w * gD;
-          for (int ch = 0; ch < 3; ++ch) b[6 + ch] += std::fabs(w * gC[ch]);
-          b[9] += std::fabs(w * gD);
+          for (int ch = 0; ch < 3; ++ch) b[6 + ch] += u * std::fabs(w * gC[ch]);
+          b[9] += u * std::fabs(w * gD);
           double dLda = 0;
           for (int ch = 0; ch < 3; ++ch) dLda += (p.rgb[ch] - S[ch]) * gC[ch];
           dLda += (p.p[2] - SD) * gD;
@@ -1014,12 +1047,12 @@ int orc_render_backward(const orc_gaussians* g, const orc_camera* cam, const orc
             a[4] += gp * (-0.5 * c.dy * c.dy);
             a[0] += gp * (-p.conic[0] * c.dx - p.conic[1] * c.dy);
             a[1] += gp * (-p.conic[2] * c.dy - p.conic[1] * c.dx);
-            b[5] += std::fabs(dLda * c.G);
-            b[2] += std::fabs(gp * 0.5 * c.dx * c.dx);
-            b[3] += std::fabs(gp * c.dx * c.dy);
-            b[4] += std::fabs(gp * 0.5 * c.dy * c.dy);
-            b[0] += std::fabs(gp) * (std::fabs(p.conic[0] * c.dx) + std::fabs(p.conic[1] * c.dy));
-            b[1] += std::fabs(gp) * (std::fabs(p.conic[2] * c.dy) + std::fabs(p.conic[1] * c.dx));
+            b[5] += u * std::fabs(dLda * c.G);
+            b[2] += u * std::fabs(gp * 0.5 * c.dx * c.dx);
+            b[3] += u * std::fabs(gp * c.dx * c.dy);
+            b[4] += u * std::fabs(gp * 0.5 * c.dy * c.dy);
+            b[0] += u * std::fabs(gp) * (std::fabs(p.conic[0] * c.dx) + std::fabs(p.conic[1] * c.dy));
+            b[1] += u * std::fabs(gp) * (std::fabs(p.conic[2] * c.dy) + std::fabs(p.conic[1] * c.dx));
           }
         }
       }

@@ -130,11 +130,12 @@ int orc_render_bruteforce(const orc_gaussians* g, const orc_camera* cam,
 typedef struct {
   double* means; double* log_scales; double* quats; double* opacity_logit; double* sh;
   double* grad2d; uint8_t* taint; double* grad_stat; double* vis_count;
-  /* optional (all five or none), += like the gradients: the scale of each gradient
-   * element, sum over the screen-space components s_j of |d element / d s_j| times
-   * the sum of the absolute values of the per-pixel terms that make s_j.  An
-   * evaluation in float32 of the same sums is off by a few units of 2^-24 times this,
-   * however much the terms cancel. */
+  /* optional (all five or none), += like the gradients: the modelled float32 error
+   * of each gradient element.  Each per-pixel term of a screen-space component is
+   * taken in absolute value times the relative error it may carry in float32 (its
+   * alpha margin, the pixel's accumulated T margin, and 32 x 2^-24 for the sums),
+   * and the chain rule to the parameters is run in running-error arithmetic (sums
+   * of absolute products).  It does not shrink where the exact terms cancel. */
   double* scale_means; double* scale_log_scales; double* scale_quats; double* scale_opacity_logit;
   double* scale_sh;
 } orc_grads;

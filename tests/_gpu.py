@@ -69,16 +69,17 @@ def check_image(img, ref, tol=IMG_TOL, mask=None, what=""):
 
 
 EPS32 = 2.0 ** -24
-# Float32 sums of terms that cancel are off by a few units of 2^-24 times the sum of
-# the terms' absolute values, whatever the size of the result.  The oracle reports
-# that sum per element (``scale_<field>``); an element passes when it is within the
-# literal bound 1e-3 (|ref| + 1e-3 rms) or within SCALE_ULPS x 2^-24 x its scale.
-SCALE_ULPS = 32
+# The oracle models the float32 error of each gradient element (``scale_<field>``):
+# every per-pixel term in absolute value times the relative error it may carry (the
+# alpha and T margins of its pixel, plus 32 units of 2^-24 for the sums), carried
+# through the chain rule in running-error arithmetic.  An element passes when it is
+# within the literal bound 1e-3 (|ref| + 1e-3 rms) or within ERR_SAFETY x that model.
+ERR_SAFETY = 2.0
 
 
 def check_grads(grads, ref, taint=None, rel=GRAD_REL, elem=GRAD_REL, what=""):
     """Per parameter group: relative L2 error <= rel and, per element,
-    |gpu - ref| <= max(elem (|ref| + 1e-3 rms(ref)), SCALE_ULPS 2^-24 scale) over the
+    |gpu - ref| <= max(elem (|ref| + 1e-3 rms(ref)), ERR_SAFETY x modelled error) over the
     untainted Gaussians (all of them when ``taint`` is None); the second term only
     when the oracle reported the element scales.  Returns the errors, the largest
     ratio to the bound, and how many elements needed the scale term.  ``elem`` None
@@ -100,13 +101,13 @@ def check_grads(grads, ref, taint=None, rel=GRAD_REL, elem=GRAD_REL, what=""):
             rms = float(np.sqrt(np.mean(b * b)))
             d = np.abs(a - b)
             lit = elem * (np.abs(b) + 1e-3 * rms)
-            bound = lit if sc is None else np.maximum(lit, SCALE_ULPS * EPS32 * sc)
+            bound = lit if sc is None else np.maximum(lit, ERR_SAFETY * sc)
             r = d / np.maximum(bound, 1e-300)
             i = int(np.argmax(r))
             out[k + "_elem"] = float(r.flat[i])
             out[k + "_beyond_literal"] = int((d > lit).sum())
             if sc is not None:
-                out[k + "_ulps_of_scale"] = float((d / np.maximum(EPS32 * sc, 1e-300))[d > lit].max(initial=0))
+                out[k + "_of_model"] = float((d / np.maximum(sc, 1e-300))[d > lit].max(initial=0))
             assert r.flat[i] <= 1.0, (f"{what}: {k} element {np.unravel_index(i, b.shape)} gpu {a.flat[i]:.9e} "
                                       f"ref {b.flat[i]:.9e} (literal bound {lit.flat[i]:.3e}, scale "
                                       f"{(sc.flat[i] if sc is not None else 0):.3e}, rms {rms:.3e})")

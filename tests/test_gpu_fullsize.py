@@ -39,7 +39,7 @@ def _grad_summary(e):
     f = _gpu.FIELDS
     return dict(grad_rel_max=max(e[k] for k in f), grad_elem_ratio_max=max(e[k + "_elem"] for k in f),
                 beyond_literal=sum(e.get(k + "_beyond_literal", 0) for k in f),
-                max_ulps_of_scale=max(e.get(k + "_ulps_of_scale", 0.0) for k in f))
+                max_of_error_model=max(e.get(k + "_of_model", 0.0) for k in f))
 
 
 def _sum_reports(reps):
@@ -193,7 +193,7 @@ def test_room1m_finite_differences_64_parameters(orc, big):
             continue
         gpu = float(_gpu.to_np(getattr(grads, f))[(idx[gi],) + comp])
         lit = 1e-3 * max(abs(fd), 1e-3 * np.sqrt(np.mean(ref[f][idx] ** 2)))
-        bound = max(lit, _gpu.SCALE_ULPS * _gpu.EPS32 * float(ref["scale_" + f][(idx[gi],) + comp]))
+        bound = max(lit, _gpu.ERR_SAFETY * float(ref["scale_" + f][(idx[gi],) + comp]))
         worst = max(worst, abs(gpu - fd) / bound)
         assert abs(gpu - fd) <= bound, (f, int(idx[gi]), comp, gpu, fd, lit, bound)
         checked += 1

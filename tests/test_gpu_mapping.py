@@ -127,7 +127,7 @@ def test_two_mapping_steps_match_the_oracle(mapping_case):
         gpu = _gpu.to_np(getattr(g, k))
         g1, g2 = hist[0]["grads"][k], hist[1]["grads"][k]
         e1, e2 = (np.maximum(1e-3 * (np.abs(gt) + 1e-3 * np.sqrt(np.mean(gt ** 2))),
-                             _gpu.SCALE_ULPS * _gpu.EPS32 * h["scale"][k])
+                             _gpu.ERR_SAFETY * h["scale"][k])
                   for gt, h in ((g1, hist[0]), (g2, hist[1])))
         nominal = _adam_np([g1, g2])
         spread = np.zeros_like(ref)

@@ -109,29 +109,35 @@ def test_tile_subset_backward_equals_masked_cotangent(orc):
 
 
 def test_gradient_scale_bounds_and_single_term_equality(orc):
-    """The per-element scale (sum of |chain-rule column| x sum of |per-pixel terms|) is
-    never below |gradient| (triangle inequality), equals |gradient| for the SH
-    coefficients when one pixel carries the only cotangent (a single term, no
-    cancellation), and stays large where two mirror pixels' terms cancel."""
+    """The per-element error scale (sum over paths of |term| x the term's relative error
+    budget, u = 32 x 2^-24 with zero margins) is never below u |gradient| (triangle
+    inequality), equals u |gradient| for the SH coefficients when one pixel carries the
+    only cotangent (a single term, no cancellation), stays large where two mirror
+    pixels' terms cancel, and grows with the alpha and T margins."""
+    u = 32 * 2.0 ** -24
+    zero = orc.margins(alpha_rel=0, T_rel=0, cond_rel=0)
     rng = np.random.default_rng(5)
     sc = random_scene(rng, 40, sh_degree=2, spread=1.0, depth=2.5)
     cam = camera(48, 32, 30, 30, 23.7, 15.2)
     w = (rng.uniform(-1, 1, (3, 32, 48)), rng.uniform(-1, 1, (32, 48)), rng.uniform(-1, 1, (32, 48)))
-    g = orc.render_backward(sc, cam, *w, margin=None, grads=orc.new_grads(sc.n, 2, scale=True))
+    g = orc.render_backward(sc, cam, *w, margin=zero, grads=orc.new_grads(sc.n, 2, scale=True))
+    gm = orc.render_backward(sc, cam, *w, margin=orc.margins(), grads=orc.new_grads(sc.n, 2, scale=True))
     for k in FIELDS:
-        assert (g["scale_" + k] >= np.abs(g[k]) * (1 - 1e-12)).all(), k
+        assert (g["scale_" + k] >= u * np.abs(g[k]) * (1 - 1e-12)).all(), k
         assert (g["scale_" + k] > 0).any()
+        assert (gm["scale_" + k] >= g["scale_" + k] * (1 - 1e-12)).all(), k
+        assert (gm["scale_" + k] > 1.5 * g["scale_" + k]).any(), k
     # one Gaussian on the axis, one pixel of cotangent on the red channel
     one = make_scene([[0, 0, 2.0]], [[0.05] * 3], [[1, 0, 0, 0]], [0.7], [[0.3, 0.6, 0.9]], sh_degree=1,
                      sh=np.full((1, 4, 3), 0.1))
     cam1 = camera(32, 32, 100, 100, 16, 16)
     gr = np.zeros((3, 32, 32)); gr[0, 18, 19] = 0.7
-    g1 = orc.render_backward(one, cam1, gr, None, None, margin=None, grads=orc.new_grads(1, 1, scale=True))
+    g1 = orc.render_backward(one, cam1, gr, None, None, margin=zero, grads=orc.new_grads(1, 1, scale=True))
     assert np.abs(g1["sh"]).max() > 0
-    np.testing.assert_allclose(g1["scale_sh"], np.abs(g1["sh"]), rtol=1e-12, atol=0)
+    np.testing.assert_allclose(g1["scale_sh"], u * np.abs(g1["sh"]), rtol=1e-12, atol=0)
     # two mirror pixels with equal cotangent: their du terms cancel (screen-space du ~ 0);
     # what is left of the mean's x-gradient comes through the Jacobian, far below its scale
     gr = np.zeros((3, 32, 32)); gr[0, 16, 13] = 1.0; gr[0, 16, 19] = 1.0
-    g2 = orc.render_backward(one, cam1, gr, None, None, margin=None, grads=orc.new_grads(1, 1, scale=True))
+    g2 = orc.render_backward(one, cam1, gr, None, None, margin=zero, grads=orc.new_grads(1, 1, scale=True))
     assert abs(g2["grad2d"][0, 0]) < 1e-9 * np.abs(g2["grad2d"][0]).max()
-    assert g2["scale_means"][0, 0] > 100 * abs(g2["means"][0, 0])
+    assert g2["scale_means"][0, 0] > 100 * u * abs(g2["means"][0, 0])
