@@ -250,6 +250,7 @@ struct Proj {
   int r = 0;
   int rect[4] = {0, 0, -1, -1};
   double o;
+  int64_t index = 0;  // of the Gaussian
   double dir[3], vnorm, raw[3], rgb[3];
   // Near-tie alternatives of the tile rect: union and intersection of the rects
   // any near-tie resolution could give (union empty when nothing could be drawn).
@@ -274,6 +275,7 @@ void project_one(const orc_gaussians* g, const orc_camera* cam, const orc_margin
                  Proj& P) {
   const double* mu = g->means + 3 * i;
   const double* Rw = cam->R;
+  P.index = i;
   for (int r = 0; r < 3; ++r)
     P.p[r] = Rw[r * 3 + 0] * mu[0] + Rw[r * 3 + 1] * mu[1] + Rw[r * 3 + 2] * mu[2] + cam->t[r];
   double tx = P.p[0], ty = P.p[1], tz = P.p[2];
@@ -578,7 +580,57 @@ template <class G>
 struct ParamGradT {
   G mu[3] = {}, ls[3] = {}, q[4] = {}, op = G(), sh[48] = {};
   double stat = 0;
+  // G = double only: modelled float32 error that comes from the SH direction (see below)
+  double xmu[3] = {0, 0, 0}, xsh[48] = {};
 };
+
+// The SH argument is the direction from the camera centre to the mean.  A float32
+// evaluation forms it from rounded coordinates: model its error as
+// dd = 4 x 2^-24 (|mu|_1 + |C|_1) / |mu - C| + 4 x 2^-24 per component, take the change
+// of each basis function and of its gradient over dd along each axis (plus 16 x 2^-24
+// for evaluating the polynomial), and carry it to the SH and mean gradients.  Where the
+// colour clamp max(0, raw) sits within the modelled error of raw, the clamp decision can
+// go either way: the whole channel's terms count as error.
+void sh_direction_error(const orc_gaussians* g, const orc_camera* cam, const Proj& P, const double* sh, int K,
+                        const double* dcol, const double* ddir, const double* Y, const double* dY,
+                        ParamGradT<double>& o) {
+  double C[3], l1 = 0;
+  for (int k = 0; k < 3; ++k) {
+    C[k] = -(cam->R[0 * 3 + k] * cam->t[0] + cam->R[1 * 3 + k] * cam->t[1] + cam->R[2 * 3 + k] * cam->t[2]);
+    l1 += std::fabs(g->means[3 * P.index + k]) + std::fabs(C[k]);
+  }
+  const double dd = 4 * kEps32 * l1 / P.vnorm + 4 * kEps32;
+  double eY[16] = {}, edY[48] = {};
+  for (int a = 0; a < 3; ++a) {
+    double d2[3] = {P.dir[0], P.dir[1], P.dir[2]};
+    d2[a] += dd;
+    double Y2[16], dY2[48];
+    sh_eval(g->sh_degree, d2, Y2, dY2);
+    for (int k = 0; k < K; ++k) {
+      eY[k] += std::fabs(Y2[k] - Y[k]);
+      for (int b = 0; b < 3; ++b) edY[k * 3 + b] += std::fabs(dY2[k * 3 + b] - dY[k * 3 + b]);
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    eY[k] += 16 * kEps32;
+    for (int b = 0; b < 3; ++b) edY[k * 3 + b] += 16 * kEps32 * (1 + std::fabs(dY[k * 3 + b]));
+  }
+  double eddir[3] = {0, 0, 0};
+  for (int ch = 0; ch < 3; ++ch) {
+    double raw_err = 0;
+    for (int k = 0; k < K; ++k) raw_err += std::fabs(sh[k * 3 + ch]) * (eY[k] + 16 * kEps32 * std::fabs(Y[k]));
+    const bool open = std::fabs(P.raw[ch]) <= raw_err;  // the clamp decision is in doubt
+    if (P.raw[ch] < 0 && !open) continue;
+    for (int k = 0; k < K; ++k) {
+      o.xsh[k * 3 + ch] += std::fabs(dcol[ch]) * (eY[k] + (open ? std::fabs(Y[k]) : 0.0));
+      for (int b = 0; b < 3; ++b)
+        eddir[b] += std::fabs(dcol[ch] * sh[k * 3 + ch]) * (edY[k * 3 + b] + (open ? std::fabs(dY[k * 3 + b]) : 0.0));
+    }
+  }
+  double e_sum = eddir[0] + eddir[1] + eddir[2];
+  double dsum = std::fabs(ddir[0]) + std::fabs(ddir[1]) + std::fabs(ddir[2]);
+  for (int a = 0; a < 3; ++a) o.xmu[a] += (eddir[a] + e_sum + 2 * dd * dsum) / P.vnorm;
+}
 
 template <class G>
 void gaussian_backward_local(const orc_gaussians* g, const orc_camera* cam, const Proj& P, int64_t i,
@@ -605,6 +657,7 @@ void gaussian_backward_local(const orc_gaussians* g, const orc_camera* cam, cons
       for (int a = 0; a < 3; ++a) ddir[a] += dcol[ch] * sh[k * 3 + ch] * dY[k * 3 + a];
     }
   }
+  if constexpr (std::is_same<G, double>::value) sh_direction_error(g, cam, P, sh, K, dcol, ddir, Y, dY, o);
   G dd_dot = ddir[0] * P.dir[0] + ddir[1] * P.dir[1] + ddir[2] * P.dir[2];
   for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - P.dir[a] * dd_dot) / P.vnorm;
   // depth and projected centre
@@ -694,7 +747,8 @@ void gaussian_backward(const orc_gaussians* g, const orc_camera* cam, const Proj
   for (int k = 0; k < 3; ++k) out->scale_log_scales[3 * i + k] += c.ls[k].v;
   for (int k = 0; k < 4; ++k) out->scale_quats[4 * i + k] += c.q[k].v;
   out->scale_opacity_logit[i] += c.op.v;
-  for (int k = 0; k < K * 3; ++k) out->scale_sh[(size_t)i * K * 3 + k] += c.sh[k].v;
+  for (int k = 0; k < K * 3; ++k) out->scale_sh[(size_t)i * K * 3 + k] += c.sh[k].v + o.xsh[k];
+  for (int a = 0; a < 3; ++a) out->scale_means[3 * i + a] += o.xmu[a];
 }
 
 // ---------- 2-Wasserstein helpers (Eq. 7-9) ----------

@@ -128,7 +128,13 @@ void fill_view(View& V, const mgs_camera& c) {
   std::memcpy(V.R, c.R, sizeof(V.R));
   std::memcpy(V.t, c.t, sizeof(V.t));
   V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy; V.near_z = c.near_z;
-  for (int k = 0; k < 3; ++k) V.C[k] = -(c.R[k] * c.t[0] + c.R[3 + k] * c.t[1] + c.R[6 + k] * c.t[2]);
+  // camera centre -R^T t in double, kept as a pair of floats: the viewing direction of
+  // a Gaussian (the SH argument) is then as accurate as its mean allows
+  for (int k = 0; k < 3; ++k) {
+    const double Cd = -((double)c.R[k] * c.t[0] + (double)c.R[3 + k] * c.t[1] + (double)c.R[6 + k] * c.t[2]);
+    V.C[k] = (float)Cd;
+    V.C_lo[k] = (float)(Cd - (double)V.C[k]);
+  }
   V.limx = kFovClamp * (0.5f * (float)c.width / c.fx);
   V.limy = kFovClamp * (0.5f * (float)c.height / c.fy);
   V.width = c.width; V.height = c.height;

@@ -35,7 +35,8 @@ constexpr float kSh3e = 1.4453057213202769f;   // sqrt(105/pi)/4
 struct View {
   float R[9], t[3];
   float fx, fy, cx, cy, near_z;
-  float C[3];          // camera centre in world coordinates
+  float C[3];          // camera centre in world coordinates (rounded)
+  float C_lo[3];       // C - (double) C[] rounded: the centre as a double-float pair
   float limx, limy;    // 1.3 * half field of view (tangent)
   int width, height, tiles_x, tiles_y;
   int tile_base;       // first global tile id of this view

@@ -118,7 +118,8 @@ __device__ __forceinline__ void view_geom(const GaussPre& G, const View& V, View
   P.A = P.c * idet;
   P.B = -P.b * idet;
   P.C = P.a * idet;
-  float d[3] = {G.mu[0] - V.C[0], G.mu[1] - V.C[1], G.mu[2] - V.C[2]};
+  float d[3] = {__fsub_rn(__fsub_rn(G.mu[0], V.C[0]), V.C_lo[0]), __fsub_rn(__fsub_rn(G.mu[1], V.C[1]), V.C_lo[1]),
+                __fsub_rn(__fsub_rn(G.mu[2], V.C[2]), V.C_lo[2])};
   P.vnorm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   float iv = 1.f / P.vnorm;
   P.dir[0] = d[0] * iv; P.dir[1] = d[1] * iv; P.dir[2] = d[2] * iv;

@@ -111,8 +111,8 @@ def test_tile_subset_backward_equals_masked_cotangent(orc):
 def test_gradient_scale_bounds_and_single_term_equality(orc):
     """The per-element error scale (sum over paths of |term| x the term's relative error
     budget, u = 32 x 2^-24 with zero margins) is never below u |gradient| (triangle
-    inequality), equals u |gradient| for the SH coefficients when one pixel carries the
-    only cotangent (a single term, no cancellation), stays large where two mirror
+    inequality), equals it (plus the evaluation budget of Y00) for the DC coefficient
+    when one pixel carries the only cotangent (a single term, no cancellation), stays large where two mirror
     pixels' terms cancel, and grows with the alpha and T margins."""
     u = 32 * 2.0 ** -24
     zero = orc.margins(alpha_rel=0, T_rel=0, cond_rel=0)
@@ -134,7 +134,12 @@ def test_gradient_scale_bounds_and_single_term_equality(orc):
     gr = np.zeros((3, 32, 32)); gr[0, 18, 19] = 0.7
     g1 = orc.render_backward(one, cam1, gr, None, None, margin=zero, grads=orc.new_grads(1, 1, scale=True))
     assert np.abs(g1["sh"]).max() > 0
-    np.testing.assert_allclose(g1["scale_sh"], u * np.abs(g1["sh"]), rtol=1e-12, atol=0)
+    # the DC basis function does not depend on the direction: only the 16 x 2^-24 of its
+    # evaluation is added to the single term's budget (d colour = g_sh0 / Y00)
+    Y00 = 0.28209479177387814
+    want = (u + 16 * 2.0 ** -24 / Y00) * abs(g1["sh"][0, 0, 0])
+    np.testing.assert_allclose(g1["scale_sh"][0, 0, 0], want, rtol=1e-12)
+    assert (g1["scale_sh"] >= u * np.abs(g1["sh"])).all()
     # two mirror pixels with equal cotangent: their du terms cancel (screen-space du ~ 0);
     # what is left of the mean's x-gradient comes through the Jacobian, far below its scale
     gr = np.zeros((3, 32, 32)); gr[0, 16, 13] = 1.0; gr[0, 16, 19] = 1.0
