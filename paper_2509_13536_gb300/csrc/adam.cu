@@ -1,5 +1,7 @@
 // Optimiser step and loss helper, sm_103a.  Both are streaming (HBM-bound) kernels:
 // one launch covers every parameter array, each element is read and written once.
+#include <cmath>
+
 #include "internal.h"
 
 namespace mgs {
@@ -117,7 +119,12 @@ int sm_count() {
 cudaError_t launch_adam(const mgs_gaussians_mut& p, const mgs_grads& g, const mgs_grads& m,
                         const mgs_grads& v, float lr, float b1, float b2, float eps, int step,
                         int zero_grads, cudaStream_t s) {
-  AdamHyper h{lr, b1, b2, eps, 1.f - powf(b1, (float)step), 1.f - powf(b2, (float)step), zero_grads};
+  // Bias corrections 1 - beta^t in double: in float32, 1 - powf(0.999, 2) keeps only ~4
+  // significant digits (the rounding of beta^2 is ~1e-5 of the difference), which moved
+  // second-step updates by ~1e-5 relative.  Rounded once to float, they now cancel with
+  // the (1 - beta) factors of the moment updates as in exact arithmetic.
+  AdamHyper h{lr, b1, b2, eps, (float)(1.0 - std::pow((double)b1, (double)step)),
+              (float)(1.0 - std::pow((double)b2, (double)step)), zero_grads};
   const int64_t n = p.n;
   const int64_t K3 = (int64_t)(p.sh_degree + 1) * (p.sh_degree + 1) * 3;
   struct Seg { void* p; int dt; float* g; float* m; float* v; int64_t n; } list[5] = {
