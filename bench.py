@@ -61,8 +61,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample", type=float, default=1.0, help="fraction of each sampled view's tiles for the oracle")
-    p.add_argument("--cpu-views", type=int, default=4, help="keyframes the oracle baseline renders")
+    p.add_argument("--cpu-reps", type=int, default=3, help="times the oracle baseline renders keyframe 0")
+    p.add_argument("--no-configs", action="store_true", help="skip the box10k and room300k legs")
     p.add_argument("--views", type=int, default=8, help="keyframes per step (8 = the benchmark workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-precision", action="store_true")
@@ -159,30 +159,30 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle leg
-def oracle_sample(frac, views=1, seed=0):
-    """Oracle render + backward of the first ``views`` keyframes of the workload, each on
-    a seeded sample of ``frac`` of its tiles; returns (seconds, keyframes' worth of
-    tiles processed, threads used)."""
+def oracle_sample(views=1, reps=1):
+    """The FP64 oracle's render + backward of the first ``views`` keyframes of the
+    workload, whole keyframes (projection and binning of all 1M Gaussians included),
+    ``reps`` times; returns (seconds per keyframe, threads used).  The GPU arm's
+    cpu_baseline and the reference arm time this same sample."""
     from oracle import oracle
     from paper_2509_13536_gb300 import scenegen as sg
     scene, cams = sg.workload(WORKLOAD)
     threads = os.cpu_count() or 1
     oracle.build()
-    rng = np.random.default_rng(seed)
-    jobs, done = [], 0.0
+    jobs = []
     for v, cam in enumerate(cams[:views]):
-        tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
-        n_t = max(1, int(round(frac * tx * ty)))
-        tiles = np.sort(rng.choice(tx * ty, n_t, replace=False)).astype(np.int32)
-        gr, gd, ga = (x[0] for x in sg.image_cotangents(1, cam.width, cam.height, seed + v))
-        jobs.append((cam, tiles, gr, gd, ga))
-        done += n_t / (tx * ty)
+        gr, gd, ga = (x[0] for x in sg.image_cotangents(1, cam.width, cam.height, v))
+        jobs.append((cam, gr, gd, ga))
     t0 = time.perf_counter()
-    for cam, tiles, gr, gd, ga in jobs:
-        oracle.render(scene, cam, tiles=tiles, n_threads=threads)
-        oracle.render_backward(scene, cam, gr, gd, ga, tiles=tiles, n_threads=threads)
+    for _ in range(reps):
+        for cam, gr, gd, ga in jobs:
+            oracle.render(scene, cam, n_threads=threads)
+            oracle.render_backward(scene, cam, gr, gd, ga, n_threads=threads)
     dt = time.perf_counter() - t0
-    return dt, done, threads
+    return dt / (reps * len(jobs)), threads
+
+
+ORACLE_SAMPLE = "FP64 oracle render + backward of keyframe 0, whole 1200x680 frame (projection and binning of all 1M Gaussians included)"
 
 
 def run_reference(args):
@@ -190,20 +190,19 @@ def run_reference(args):
     if rank != 0:
         return
     times = []
+    threads = 1
     for i in range(args.warmup + args.steps):
-        dt, frac, threads = oracle_sample(min(args.cpu_sample, 0.02), 1, seed=i)
+        dt, threads = oracle_sample(1, 1)
         if i >= args.warmup:
             times.append(dt)
     per_step = sum(times) / len(times)
-    value = frac / per_step
-    sample = (f"FP64 oracle render+backward of {frac:.1%} of the tiles of keyframe 0 per step "
-              f"(projection and binning of all 1M Gaussians included)")
+    value = 1.0 / per_step
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC},
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": ORACLE_SAMPLE + ", one keyframe per step"},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -437,6 +436,83 @@ def serving_leg(args, api, torch, sg, dev):
             "continuous_batching_fp16": served, "one_at_a_time_fp32": sequential}
 
 
+def configs_leg(args, api, torch, sg, dev):
+    """The two smaller workloads.  box10k: 10k Gaussians, 320x240, SH0, render + backward
+    with U[-1, 1] image cotangents.  room300k: 300k Gaussians, 640x480, SH0, render +
+    backward + voxel merge (v = 0.02 m).  GPU frames/s over the steps (CUDA events,
+    inputs resident), the merge's ms, the FP64 oracle's frames/s on the same whole
+    frames on the host cores, and on room300k the merge partners against the oracle's
+    (Gaussians the oracle marks as near a tie left out)."""
+    from oracle import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    out = {}
+    for name in ("box10k", "room300k"):
+        scene, cams = sg.workload(name)
+        cam = cams[0]
+        g = api.Gaussians.from_scene(scene, dev)
+        cot = [x[0] for x in sg.image_cotangents(1, cam.width, cam.height, 0)]
+        dL = [api.Image(*(torch.from_numpy(c).to(dev) for c in cot))]
+        ws = api.RenderWorkspace(dev)
+        imgs = api.new_images(cams, dev)
+        grads = api.Grads.zeros_like(g)
+        merge = name == "room300k"
+        if merge:
+            mws = torch.empty(api.load().mgs_voxel_merge_workspace_size(g.n), dtype=torch.uint8, device=dev)
+            merged, partner = g.empty_like(), torch.empty(g.n, dtype=torch.int32, device=dev)
+            vox = torch.empty(g.n, 3, dtype=torch.int32, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        merge_ms = []
+
+        def step(timed=False):
+            api.mgs_render(g, cams, imgs, ws)
+            api.mgs_render_backward(g, cams, dL, ws, grads)
+            if merge:
+                if timed:
+                    ev[2].record()
+                api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox)
+                if timed:
+                    ev[3].record()
+                    ev[3].synchronize()
+                    merge_ms.append(ev[2].elapsed_time(ev[3]))
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        k = max(20, args.steps)
+        ev[0].record()
+        for _ in range(k):
+            step()
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / k
+        for _ in range(5):
+            step(timed=True)
+        res = {"frames_per_s": 1e3 / ms, "ms_per_step": ms, "steps": k, "gaussians": g.n,
+               "resolution": f"{cam.width}x{cam.height}",
+               "step": "render + backward" + (" + voxel_merge v=0.02 m" if merge else "")}
+        if merge:
+            res["merge_ms"] = float(np.median(merge_ms))
+        t0 = time.perf_counter()
+        oracle.render(scene, cam, n_threads=threads)
+        oracle.render_backward(scene, cam, *cot, n_threads=threads)
+        t_orc = time.perf_counter() - t0
+        res["oracle"] = {"frames_per_s": 1.0 / t_orc, "cores": threads, "kind": "FP64 oracle, whole frame"}
+        if merge:
+            t0 = time.perf_counter()
+            ref = oracle.voxel_merge(scene, 0.02)
+            res["oracle"]["merge_s"] = time.perf_counter() - t0
+            got = partner.cpu().numpy()
+            clear = ref["tie"] == 0
+            res["clusters"] = {"gaussians_compared": int(clear.sum()), "near_tie_left_out": int((~clear).sum()),
+                               "partner_mismatches": int((got != ref["partner"])[clear].sum()),
+                               "merged_pairs": int((ref["partner"] >= 0).sum() // 2)}
+        out[name] = res
+        del g, ws, imgs, grads
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -468,10 +544,30 @@ def run_ours(args):
     pert = scene.copy()
     pert.means += rng.normal(0, 0.005, pert.means.shape).astype(np.float32)
     pert.sh += rng.normal(0, 0.02, pert.sh.shape).astype(np.float32)
-    def make_step(g, loss_kind="l1"):
+    def make_step(g, loss_kind="l1", autograd=True):
         """One mapping step on map g (all buffers allocated here, none inside the step).
-        loss_kind "l1": L1 on rgb and 0.1 x L1 on depth (the benchmark's stand-in);
-        "eq12": Eq. 12, 0.8 L1 + 0.2 (1 - SSIM) + 0.1 depth L1 + isotropic term."""
+        loss_kind "l1": Eq. 12 with lambda = 0 (L1 on rgb plus 0.1 x the depth residual),
+        the workload's stand-in; "eq12": Eq. 12 with lambda 0.2, the 0.1 depth residual
+        and the isotropic term.  autograd: the step runs through api.MappingStep
+        (RenderFn forward, loss kernel, torch.autograd.backward into the gradient
+        buffers, in-kernel Adam); otherwise the same kernels are called directly through
+        the C ABI.  Both end with the voxel merge of the updated map into a buffer."""
+        lam, w_iso = (0.2, 1.0) if loss_kind == "eq12" else (0.0, 0.0)
+        merged = g.empty_like()
+        partner = torch.empty(g.n, dtype=torch.int32, device=dev)
+        vox = torch.empty(g.n, 3, dtype=torch.int32, device=dev)
+        mws = torch.empty(api.load().mgs_voxel_merge_workspace_size(g.n), dtype=torch.uint8, device=dev)
+        state = {"step": 0, "n_out": g.n}
+        if autograd:
+            ms = api.MappingStep(g, cams, lr=1e-3, lambda_ssim=lam, w_depth=0.1, w_iso=w_iso)
+            state.update(ws=ms.ws, loss=ms.loss, loss_views=ms.loss, loss_iso=ms.loss_iso, mapping=ms)
+
+            def step():
+                ms(tref["rgb"], tref["depth"])
+                res, _, _ = api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox)
+                state["n_out"] = res.n
+
+            return step, state
         grads = api.Grads.zeros_like(g)
         m = api.Grads.zeros_like(g, stats=False)
         v = api.Grads.zeros_like(g, stats=False)
@@ -482,35 +578,21 @@ def run_ours(args):
         g_rgb = torch.empty_like(rgb)
         g_depth = torch.empty_like(depth)
         dL = [api.Image(g_rgb[i], g_depth[i], None) for i in range(V)]
-        loss = torch.zeros(1, device=dev)
-        merged = g.empty_like()
-        partner = torch.empty(g.n, dtype=torch.int32, device=dev)
-        vox = torch.empty(g.n, 3, dtype=torch.int32, device=dev)
-        mws = torch.empty(api.load().mgs_voxel_merge_workspace_size(g.n), dtype=torch.uint8, device=dev)
         ws = api.RenderWorkspace(dev)
-        s_rgb = 1.0 / rgb.numel()
-        s_depth = 0.1 / depth.numel()
-        state = {"step": 0, "n_out": g.n, "ws": ws, "loss": loss}
-        if loss_kind == "eq12":
-            targets = [api.Image(target_rgb[i], target_depth[i], None) for i in range(V)]
-            lws = torch.empty(api.load().mgs_mapping_loss_workspace_size(V, W, H), dtype=torch.uint8, device=dev)
-            iws = torch.empty(api.load().mgs_iso_loss_workspace_size(g.n), dtype=torch.uint8, device=dev)
-            loss_v = torch.zeros(V, 3, device=dev)
-            loss_iso = torch.zeros(1, device=dev)
-            state.update(loss_views=loss_v, loss_iso=loss_iso)
+        lws = torch.empty(api.load().mgs_mapping_loss_workspace_size(V, W, H), dtype=torch.uint8, device=dev)
+        iws = torch.empty(api.load().mgs_iso_loss_workspace_size(g.n), dtype=torch.uint8, device=dev)
+        loss_v = torch.zeros(V, 3, device=dev)
+        loss_iso = torch.zeros(1, device=dev)
+        state.update(ws=ws, loss=loss_v, loss_views=loss_v, loss_iso=loss_iso)
 
         def step():
             state["step"] += 1
             api.mgs_render(g, cams, out, ws)
-            if loss_kind == "eq12":
-                api.mapping_loss(out, targets, dL, 0.2, 0.1, loss=loss_v, workspace=lws)
-            else:
-                loss.zero_()
-                api.mgs_l1_loss_grad(rgb, tref["rgb"], s_rgb, g_rgb, loss)
-                api.mgs_l1_loss_grad(depth, tref["depth"], s_depth, g_depth, loss)
+            targets = [api.Image(tref["rgb"][i], tref["depth"][i], None) for i in range(V)]
+            api.mapping_loss(out, targets, dL, lam, 0.1, loss=loss_v, workspace=lws)
             api.mgs_render_backward(g, cams, dL, ws, grads)
-            if loss_kind == "eq12":
-                api.iso_loss(g, 1.0, grads, loss=loss_iso, workspace=iws)
+            if w_iso > 0:
+                api.iso_loss(g, w_iso, grads, loss=loss_iso, workspace=iws)
             api.mgs_adam_step(g, grads, m, v, 1e-3, 0.9, 0.999, 1e-8, state["step"], zero_grads=True)
             res, _, _ = api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox)
             state["n_out"] = res.n
@@ -552,7 +634,7 @@ def run_ours(args):
         args.steps_e2e = 0
     host_rgb = target_rgb.cpu().pin_memory()
     host_depth = target_depth.cpu().pin_memory()
-    host_loss = torch.empty(2, pin_memory=True)
+    host_loss = torch.empty(2, V, 3, pin_memory=True)
     # double-buffered keyframe images: a copy stream brings step k+1's images from
     # pinned host memory while step k computes; every step's loss goes back to the host
     dev_rgb = [target_rgb, torch.empty_like(target_rgb)]
@@ -584,7 +666,7 @@ def run_ours(args):
         tref["rgb"], tref["depth"] = dev_rgb[cur], dev_depth[cur]
         step()
         used[cur].record(stream)
-        host_loss[cur:cur + 1].copy_(loss, non_blocking=True)
+        host_loss[cur].copy_(loss, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
     tref["rgb"], tref["depth"] = target_rgb, target_depth
@@ -621,6 +703,29 @@ def run_ours(args):
         roofline = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                     "traffic": None}
 
+    # the same step with the kernels called directly through the C ABI (no autograd)
+    direct = None
+    if world == 1:
+        gd_ = api.Gaussians.from_scene(pert, dev)
+        step_d, _ = make_step(gd_, autograd=False)
+        for _ in range(3):
+            step_d()
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(args.steps):
+            step_d()
+        d1.record(stream)
+        torch.cuda.synchronize()
+        ms_d = d0.elapsed_time(d1) / args.steps
+        direct = {"ms_per_step_direct_cabi": ms_d, "ms_per_step_autograd": ms, "autograd_overhead_ms": ms - ms_d,
+                  "note": "same kernels and loss; the autograd step adds RenderFn, graph construction and "
+                          "torch.autograd.backward on the host"}
+        del gd_, step_d
+        torch.cuda.empty_cache()
+    configs = None
+    if world == 1 and not args.no_configs:
+        configs = configs_leg(args, api, torch, sg, dev)
     eq12 = None
     if world == 1 and not args.no_eq12:
         eq12 = eq12_leg(args, api, torch, pert, make_step, dev, V)
@@ -641,10 +746,14 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (236 MB parameters, 384 MB projected records, "
                              f"{stats['keys']} tile keys per step)"},
             "roofline": roofline,
-            "e2e": ({"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
-                    if n_e2e > 0 else None),
+            "e2e": ({"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                     "d2h_bytes_per_step": host_loss[0].numel() * 4} if n_e2e > 0 else None),
             "gpu_launches": launches, "clocks": csum, "kernels": kern, "fragments": stats,
             "merge_survivors": state["n_out"]}
+    if direct:
+        line["autograd"] = direct
+    if configs:
+        line["configs"] = configs
     if eq12:
         line["eq12_step"] = eq12
     if precision:
@@ -652,12 +761,9 @@ def run_ours(args):
     if serving:
         line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        nv = max(1, min(args.cpu_views, V))
-        dt, frac, threads = oracle_sample(args.cpu_sample, nv)
-        line["cpu_baseline"] = {"value": frac / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",
-                                "sample": f"FP64 oracle render+backward of keyframes 0-{nv - 1}, "
-                                          f"{args.cpu_sample:.0%} of each one's tiles (projection and binning "
-                                          f"of all 1M Gaussians included per keyframe), {dt:.1f} s"}
+        dt, threads = oracle_sample(1, args.cpu_reps)
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",
+                                "sample": ORACLE_SAMPLE + f", {args.cpu_reps} times ({dt:.1f} s each)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
