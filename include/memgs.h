@@ -141,6 +141,23 @@ mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams_host, int32
                       const mgs_image* out_host, void* workspace, size_t workspace_bytes,
                       int64_t* n_keys_host, void* stream);
 
+/* Forward render of views that each name their own map (Sec. II-E rasteriser, serving
+ * several resident maps at once): view v is rendered from maps_host[map_of_view_host[v]]
+ * (0 <= index < n_maps; map_of_view_host is a host array of n_views entries).  One
+ * projection launch per run of consecutive views that share a map, then, for all views
+ * together, one depth sort, one key emission, one tile sort and one blend launch over
+ * every (view, tile).  Each view's image is bit-identical to rendering it alone with
+ * mgs_render.  Together the views' maps may hold fewer than 2^32 Gaussians (counted once
+ * per view).  Workspace, key capacity, *n_keys_host, errors and the synchronisation are
+ * as for mgs_render; the workspace does not support mgs_render_backward (one map only).
+ * Not in the paper: the serving form of its rasteriser. */
+size_t mgs_render_multi_workspace_size(const mgs_gaussians* maps_host, int32_t n_maps,
+                                       const int32_t* map_of_view_host, const mgs_camera* cams_host,
+                                       int32_t n_views, int64_t key_capacity);
+mgs_status mgs_render_multi(const mgs_gaussians* maps_host, int32_t n_maps, const int32_t* map_of_view_host,
+                            const mgs_camera* cams_host, int32_t n_views, const mgs_image* out_host,
+                            void* workspace, size_t workspace_bytes, int64_t* n_keys_host, void* stream);
+
 /* Reverse pass of the last mgs_render on `workspace` (same g, cams, n_views).
  * dL_host[v] gives dL/drgb, dL/ddepth, dL/dalpha planes of view v (any plane may
  * be NULL = zero).  Gradients of all views are ADDED to `grads` (f32).  Asynchronous. */
@@ -301,13 +318,14 @@ mgs_status mgs_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* vals_out, in
 /* ------------------------------------------------------------------------------
  * Render serving with continuous batching (not in the paper: the serving form of the
  * Sec. II-E rasteriser).  Resident scene maps are registered once; requests (scene,
- * camera, output planes) are submitted at any time.  A dispatcher thread admits the
- * oldest pending request when a worker slot is free and its workspace fits in free
- * memory of the caller's device arena (first-fit; the server allocates no device
- * memory), folding every pending request of the same scene into the same multi-view
- * mgs_render launch (up to max_batch_views).  Each slot has its own stream and
- * thread, so batches overlap on the device.  Results are bit-identical to rendering
- * each request alone (the forward pass is deterministic).  The gaussians and output
+ * camera, output planes) are submitted at any time.  When a worker slot is free, a
+ * dispatcher thread admits the oldest pending requests, of any scene and resolution,
+ * up to max_batch_views of them and as many as their workspace fits in free memory of
+ * the caller's device arena (first-fit; the server allocates no device memory), and
+ * renders them with one mgs_render_multi call: one blend launch over the (view, tile)
+ * items of all of them.  Each slot has its own stream and thread, so batches overlap
+ * on the device.  Results are bit-identical to rendering each request alone (the
+ * forward pass is deterministic).  The gaussians and output
  * buffers must stay valid until the request completes; destroying the server drops
  * requests not yet admitted.
  * ------------------------------------------------------------------------------ */
@@ -332,6 +350,10 @@ int32_t mgs_server_poll(mgs_server* s, int32_t max, int64_t* tags_host, double* 
                         double* t_start_host, double* t_done_host, int32_t* status_host,
                         double wait_s);
 double mgs_server_clock(void);
+/* Counters since creation: out[0] render launches, out[1] requests served by them,
+ * out[2] largest number of requests in one launch, out[3] launches holding more than
+ * one scene. */
+mgs_status mgs_server_stats(mgs_server* s, int64_t out_host[4]);
 mgs_status mgs_server_destroy(mgs_server* s);
 
 /* ------------------------------------------------------------------------------

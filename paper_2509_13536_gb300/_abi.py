@@ -25,7 +25,8 @@ EXPORTS = ["mgs_render_workspace_size", "mgs_render", "mgs_render_backward", "mg
            "mgs_sort_pairs_noalloc", "mgs_server_create", "mgs_server_add_scene", "mgs_server_submit",
            "mgs_server_poll", "mgs_server_clock", "mgs_server_destroy", "mgs_mapping_loss_workspace_size",
            "mgs_mapping_loss", "mgs_iso_loss_workspace_size", "mgs_iso_loss", "mgs_merge_stats",
-           "mgs_patch_grid_workspace_size", "mgs_patch_grid_capacity", "mgs_patch_grid_sample"]
+           "mgs_patch_grid_workspace_size", "mgs_patch_grid_capacity", "mgs_patch_grid_sample",
+           "mgs_render_multi_workspace_size", "mgs_render_multi", "mgs_server_stats"]
 
 
 class mgs_gaussians(C.Structure):
@@ -97,6 +98,8 @@ def load():
         sig = {
             "mgs_render_workspace_size": (SZ, [I64, P, I32, I64]),
             "mgs_render": (C.c_int, [P, P, I32, P, P, SZ, P, P]),
+            "mgs_render_multi_workspace_size": (SZ, [P, I32, P, P, I32, I64]),
+            "mgs_render_multi": (C.c_int, [P, I32, P, P, I32, P, P, SZ, P, P]),
             "mgs_render_backward": (C.c_int, [P, P, I32, P, P, SZ, P, P]),
             "mgs_project": (C.c_int, [P, P, P, P, P, P, P, P, P]),
             "mgs_voxel_merge_workspace_size": (SZ, [I64]),
@@ -119,6 +122,7 @@ def load():
             "mgs_server_submit": (C.c_int, [P, I32, P, P, I64, C.c_double]),
             "mgs_server_poll": (I32, [P, I32, P, P, P, P, P, C.c_double]),
             "mgs_server_clock": (C.c_double, []),
+            "mgs_server_stats": (C.c_int, [P, P]),
             "mgs_server_destroy": (C.c_int, [P]),
             "mgs_launch_count": (C.c_uint64, []),
             "mgs_profile_enable": (None, [I32]),

@@ -210,6 +210,44 @@ def mgs_render(g: Gaussians, cams, out: List[Image], ws: RenderWorkspace, stream
     return 0
 
 
+def mgs_render_multi(maps: Sequence[Gaussians], map_of_view: Sequence[int], cams, out: List[Image],
+                     ws: RenderWorkspace, stream=None) -> int:
+    """One call of mgs_render_multi (view v from maps[map_of_view[v]]); grows the
+    workspace and retries when it is too small.  Returns the key count."""
+    L = load()
+    ms = (_abi.mgs_gaussians * len(maps))()
+    for i, g in enumerate(maps):
+        ms[i] = g.struct()
+    mov = (C.c_int32 * len(cams))(*[int(m) for m in map_of_view])
+    arr = _cam_array(cams)
+    imgs = _image_array(out)
+
+    def grow(keys):
+        need = L.mgs_render_multi_workspace_size(ms, len(maps), mov, arr, len(cams), int(keys))
+        if need == 0:
+            raise ValueError("invalid render arguments")
+        if ws.buf is None or ws.buf.numel() < need:
+            ws.buf = None
+            ws.buf = torch.empty(need, dtype=torch.uint8, device=ws.device)
+            ws.generation += 1
+
+    if ws.buf is None:
+        grow(max(1024, 8 * sum(maps[m].n for m in map_of_view)))
+    for _ in range(3):
+        nk = C.c_int64(0)
+        st = L.mgs_render_multi(ms, len(maps), mov, arr, len(cams), imgs, _ptr(ws.buf), ws.buf.numel(),
+                                C.byref(nk), _stream(stream))
+        if st == _abi.MGS_ERR_WORKSPACE and nk.value > 0:
+            grow(int(nk.value * ws.headroom) + 1024)
+            continue
+        check(st, "mgs_render_multi")
+        ws.n_keys = nk.value
+        ws.generation += 1
+        return nk.value
+    check(st, "mgs_render_multi")
+    return 0
+
+
 def mgs_render_backward(g: Gaussians, cams, dL: Sequence[Optional[Image]], ws: RenderWorkspace,
                         grads: Grads, stream=None):
     L = load()
@@ -602,6 +640,13 @@ class Server:
     @staticmethod
     def clock() -> float:
         return float(load().mgs_server_clock())
+
+    def stats(self):
+        """{launches, requests, max_views, mixed_scene_launches} since creation."""
+        out = (C.c_int64 * 4)()
+        check(load().mgs_server_stats(self.h, out), "mgs_server_stats")
+        return dict(launches=int(out[0]), requests=int(out[1]), max_views=int(out[2]),
+                    mixed_scene_launches=int(out[3]))
 
     def close(self):
         if self.h:

@@ -68,10 +68,24 @@ bool cams_valid(const mgs_camera* cams, int nv, std::string* why) {
   return true;
 }
 
-RenderLayout render_layout(int64_t n, const mgs_camera* cams, int nv, int64_t key_cap) {
+// Per-view item counts: the number of Gaussians of each view's map.
+struct ViewItems {
+  int64_t n[MGS_MAX_VIEWS];
+};
+ViewItems uniform_items(int64_t n, int nv) {
+  ViewItems it{};
+  for (int v = 0; v < nv && v < MGS_MAX_VIEWS; ++v) it.n[v] = n;
+  return it;
+}
+
+RenderLayout render_layout(const ViewItems& items, const mgs_camera* cams, int nv, int64_t key_cap) {
   RenderLayout L;
-  L.N = n;
-  L.VN = n * nv;
+  L.N = 0;
+  L.VN = 0;
+  for (int v = 0; v < nv; ++v) {
+    L.N = std::max(L.N, items.n[v]);
+    L.VN += items.n[v];
+  }
   for (int v = 0; v < nv; ++v) {
     L.pixels += (int64_t)cams[v].width * cams[v].height;
     L.tiles += div_up(cams[v].width, MGS_TILE) * div_up(cams[v].height, MGS_TILE);
@@ -103,13 +117,13 @@ RenderLayout render_layout(int64_t n, const mgs_camera* cams, int nv, int64_t ke
 }
 
 // Largest key capacity whose layout fits in `bytes` (-1 if not even zero keys fit).
-int64_t key_capacity_for(int64_t n, const mgs_camera* cams, int nv, size_t bytes) {
-  if (render_layout(n, cams, nv, 0).total > bytes) return -1;
+int64_t key_capacity_for(const ViewItems& items, const mgs_camera* cams, int nv, size_t bytes) {
+  if (render_layout(items, cams, nv, 0).total > bytes) return -1;
   int64_t lo = 0, hi = 1;
-  while (render_layout(n, cams, nv, hi).total <= bytes && hi < (int64_t(1) << 40)) hi *= 2;
+  while (render_layout(items, cams, nv, hi).total <= bytes && hi < (int64_t(1) << 40)) hi *= 2;
   while (hi - lo > 1) {
     int64_t mid = lo + (hi - lo) / 2;
-    if (render_layout(n, cams, nv, mid).total <= bytes) lo = mid; else hi = mid;
+    if (render_layout(items, cams, nv, mid).total <= bytes) lo = mid; else hi = mid;
   }
   return lo;
 }
@@ -142,15 +156,18 @@ void fill_view(View& V, const mgs_camera& c) {
   V.tiles_y = (int)div_up(c.height, MGS_TILE);
 }
 
-ViewTable make_table(const mgs_camera* cams, int nv, const RenderLayout& L, void* ws) {
+ViewTable make_table(const mgs_camera* cams, int nv, const RenderLayout& L, void* ws, const ViewItems& items) {
   ViewTable vt{};
   vt.n_views = nv;
   int tb = 0;
-  int64_t pb = 0;
+  int64_t pb = 0, ib = 0;
   for (int v = 0; v < nv; ++v) {
     View& V = vt.v[v];
     fill_view(V, cams[v]);
     V.tile_base = tb;
+    V.item_base = ib;
+    V.n_items = items.n[v];
+    ib += items.n[v];
     tb += V.tiles_x * V.tiles_y;
     V.T_final = at<float>(ws, L.tfinal) + pb;
     V.n_contrib = at<uint32_t>(ws, L.ncontrib) + pb;
@@ -193,28 +210,32 @@ size_t mgs_render_workspace_size(int64_t n, const mgs_camera* cams, int32_t n_vi
                                  int64_t key_capacity) {
   std::string why;
   if (n < 0 || key_capacity < 0 || !cams_valid(cams, n_views, &why)) return 0;
-  return render_layout(n, cams, n_views, key_capacity).total;
+  return render_layout(uniform_items(n, n_views), cams, n_views, key_capacity).total;
 }
 
-mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_views,
-                      const mgs_image* out, void* workspace, size_t workspace_bytes,
-                      int64_t* n_keys_host, void* stream) {
-  set_error("");
-  cudaStream_t s = (cudaStream_t)stream;
-  std::string why = check_gaussians(g, false);
-  if (!why.empty()) return fail(MGS_ERR_INVALID, why);
+static mgs_status render_impl(const mgs_gaussians* maps, int n_maps, const int32_t* map_of_view,
+                              const mgs_camera* cams, int32_t n_views, const mgs_image* out, void* workspace,
+                              size_t workspace_bytes, int64_t* n_keys_host, cudaStream_t s) {
+  std::string why;
   if (!cams_valid(cams, n_views, &why)) return fail(MGS_ERR_INVALID, why);
   if (!out || !workspace) return fail(MGS_ERR_INVALID, "out or workspace is NULL");
-  for (int v = 0; v < n_views; ++v)
+  ViewItems items{};
+  int64_t total = 0;
+  for (int v = 0; v < n_views; ++v) {
     if (!out[v].rgb || !out[v].depth || !out[v].alpha) return fail(MGS_ERR_INVALID, "image plane is NULL");
-  if (g->n * n_views >= (int64_t)UINT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "n * n_views must be < 2^32");
-  int64_t cap = key_capacity_for(g->n, cams, n_views, workspace_bytes);
+    const int m = map_of_view ? map_of_view[v] : 0;
+    if (m < 0 || m >= n_maps) return fail(MGS_ERR_INVALID, "map_of_view out of range");
+    items.n[v] = maps[m].n;
+    total += maps[m].n;
+  }
+  if (total >= (int64_t)UINT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "the views' maps hold 2^32 or more Gaussians in all");
+  int64_t cap = key_capacity_for(items, cams, n_views, workspace_bytes);
   if (cap < 0) {
     if (n_keys_host) *n_keys_host = 0;
     return fail(MGS_ERR_WORKSPACE, "workspace smaller than the zero-key layout");
   }
-  RenderLayout L = render_layout(g->n, cams, n_views, cap);
-  ViewTable vt = make_table(cams, n_views, L, workspace);
+  RenderLayout L = render_layout(items, cams, n_views, cap);
+  ViewTable vt = make_table(cams, n_views, L, workspace, items);
   for (int v = 0; v < n_views; ++v) {
     vt.v[v].rgb = out[v].rgb;
     vt.v[v].depth = out[v].depth;
@@ -235,7 +256,20 @@ mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_
   {
     ProfScope ps(kProfPreprocess, s);
     MGS_TRY_CUDA(cudaMemsetAsync(counters, 0, 256, s));
-    MGS_TRY_CUDA(launch_preprocess(*g, vt, rec, rects, touched, dk[0], counters, s));
+    // one projection launch per run of consecutive views that share a map: each thread
+    // projects one Gaussian into every view of the run (its items are consecutive)
+    for (int v0 = 0; v0 < n_views;) {
+      const int m = map_of_view ? map_of_view[v0] : 0;
+      int v1 = v0 + 1;
+      while (v1 < n_views && (map_of_view ? map_of_view[v1] : 0) == m) ++v1;
+      ViewTable sub{};
+      sub.n_views = v1 - v0;
+      sub.n_tiles = vt.n_tiles;
+      for (int v = v0; v < v1; ++v) sub.v[v - v0] = vt.v[v];
+      const int64_t ib = vt.v[v0].item_base;
+      MGS_TRY_CUDA(launch_preprocess(maps[m], sub, rec + 3 * ib, rects + ib, touched + ib, dk[0] + ib, counters, s));
+      v0 = v1;
+    }
   }
   unsigned long long cnt[2] = {0, 0};
   MGS_TRY_CUDA(cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
@@ -258,7 +292,7 @@ mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_
   }
   {
     ProfScope ps(kProfEmit, s);
-    MGS_TRY_CUDA(launch_emit(n_vis, g->n, dv[dcur], offsets, touched, rects, rec, vt, tk[0], tv[0], s));
+    MGS_TRY_CUDA(launch_emit(n_vis, L.N, dv[dcur], offsets, touched, rects, rec, vt, tk[0], tv[0], s));
   }
   int tcur = 0;
   {
@@ -275,6 +309,41 @@ mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_
   return MGS_OK;
 }
 
+mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_views,
+                      const mgs_image* out, void* workspace, size_t workspace_bytes,
+                      int64_t* n_keys_host, void* stream) {
+  set_error("");
+  std::string why = check_gaussians(g, false);
+  if (!why.empty()) return fail(MGS_ERR_INVALID, why);
+  return render_impl(g, 1, nullptr, cams, n_views, out, workspace, workspace_bytes, n_keys_host,
+                     (cudaStream_t)stream);
+}
+
+size_t mgs_render_multi_workspace_size(const mgs_gaussians* maps, int32_t n_maps, const int32_t* map_of_view,
+                                       const mgs_camera* cams, int32_t n_views, int64_t key_capacity) {
+  std::string why;
+  if (!maps || !map_of_view || n_maps < 1 || key_capacity < 0 || !cams_valid(cams, n_views, &why)) return 0;
+  ViewItems items{};
+  for (int v = 0; v < n_views; ++v) {
+    if (map_of_view[v] < 0 || map_of_view[v] >= n_maps || maps[map_of_view[v]].n < 0) return 0;
+    items.n[v] = maps[map_of_view[v]].n;
+  }
+  return render_layout(items, cams, n_views, key_capacity).total;
+}
+
+mgs_status mgs_render_multi(const mgs_gaussians* maps, int32_t n_maps, const int32_t* map_of_view,
+                            const mgs_camera* cams, int32_t n_views, const mgs_image* out, void* workspace,
+                            size_t workspace_bytes, int64_t* n_keys_host, void* stream) {
+  set_error("");
+  if (!maps || n_maps < 1 || !map_of_view) return fail(MGS_ERR_INVALID, "need maps, n_maps >= 1 and map_of_view");
+  for (int m = 0; m < n_maps; ++m) {
+    std::string why = check_gaussians(&maps[m], false);
+    if (!why.empty()) return fail(MGS_ERR_INVALID, "map " + std::to_string(m) + ": " + why);
+  }
+  return render_impl(maps, n_maps, map_of_view, cams, n_views, out, workspace, workspace_bytes, n_keys_host,
+                     (cudaStream_t)stream);
+}
+
 mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_views,
                                const mgs_image* dL, void* workspace, size_t workspace_bytes,
                                const mgs_grads* grads, void* stream) {
@@ -286,10 +355,11 @@ mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams, i
   if (!dL || !workspace || !grads) return fail(MGS_ERR_INVALID, "dL, workspace or grads is NULL");
   if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit || !grads->sh))
     return fail(MGS_ERR_INVALID, "gradient pointer is NULL");
-  int64_t cap = key_capacity_for(g->n, cams, n_views, workspace_bytes);
+  const ViewItems items = uniform_items(g->n, n_views);
+  int64_t cap = key_capacity_for(items, cams, n_views, workspace_bytes);
   if (cap < 0) return fail(MGS_ERR_WORKSPACE, "workspace smaller than the zero-key layout");
-  RenderLayout L = render_layout(g->n, cams, n_views, cap);
-  ViewTable vt = make_table(cams, n_views, L, workspace);
+  RenderLayout L = render_layout(items, cams, n_views, cap);
+  ViewTable vt = make_table(cams, n_views, L, workspace, items);
   for (int v = 0; v < n_views; ++v) {
     vt.v[v].g_rgb = dL[v].rgb;
     vt.v[v].g_depth = dL[v].depth;
@@ -320,10 +390,11 @@ mgs_status mgs_render_stats(const mgs_gaussians* g, const mgs_camera* cams, int3
   if (!why.empty()) return fail(MGS_ERR_INVALID, why);
   if (!cams_valid(cams, n_views, &why)) return fail(MGS_ERR_INVALID, why);
   if (!workspace || !stats) return fail(MGS_ERR_INVALID, "workspace or stats is NULL");
-  int64_t cap = key_capacity_for(g->n, cams, n_views, workspace_bytes);
+  const ViewItems items = uniform_items(g->n, n_views);
+  int64_t cap = key_capacity_for(items, cams, n_views, workspace_bytes);
   if (cap < 0) return fail(MGS_ERR_WORKSPACE, "workspace smaller than the zero-key layout");
-  RenderLayout L = render_layout(g->n, cams, n_views, cap);
-  ViewTable vt = make_table(cams, n_views, L, workspace);
+  RenderLayout L = render_layout(items, cams, n_views, cap);
+  ViewTable vt = make_table(cams, n_views, L, workspace, items);
   uint32_t* tv[2] = {at<uint32_t>(workspace, L.tvals[0]), at<uint32_t>(workspace, L.tvals[1])};
   int tcur = radix_passes(0, tile_bits(vt.n_tiles)) & 1;
   auto* hdr = at<unsigned long long>(workspace, L.hdr);

@@ -40,6 +40,9 @@ struct View {
   float limx, limy;    // 1.3 * half field of view (tangent)
   int width, height, tiles_x, tiles_y;
   int tile_base;       // first global tile id of this view
+  int64_t item_base;   // first (view, Gaussian) item of this view: items of view v are
+                       // item_base + i for Gaussian i of the view's map (n_items of them)
+  int64_t n_items;
   float* rgb;          // forward outputs
   float* depth;
   float* alpha;
@@ -55,6 +58,12 @@ struct ViewTable {
   int n_tiles;         // sum over views
   View v[MGS_MAX_VIEWS];
 };
+
+__device__ __forceinline__ int view_of_item(const ViewTable& vt, int64_t item) {
+  int v = 0;
+  while (v + 1 < vt.n_views && vt.v[v + 1].item_base <= item) ++v;
+  return v;
+}
 
 __device__ __forceinline__ int view_of_tile(const ViewTable& vt, int tile) {
   int v = 0;

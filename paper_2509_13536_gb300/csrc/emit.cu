@@ -17,7 +17,7 @@ __device__ __forceinline__ void emit_item(uint32_t item, uint32_t off, uint32_t 
                                           const uint2* __restrict__ rects, const float4* __restrict__ rec,
                                           int64_t N, const ViewTable& vt, uint32_t* __restrict__ tkeys,
                                           uint32_t* __restrict__ tvals) {
-  const int v = (int)((int64_t)item / N);
+  const int v = view_of_item(vt, item);
   const View& V = vt.v[v];
   const uint2 rc = rects[item];
   const Cull q = make_cull(rec[3 * (size_t)item], rec[3 * (size_t)item + 1]);
@@ -51,7 +51,7 @@ __device__ __forceinline__ void emit_item_coop(uint32_t item, uint32_t off, uint
                                                const uint2* __restrict__ rects, const float4* __restrict__ rec,
                                                int64_t N, const ViewTable& vt, uint32_t* __restrict__ tkeys,
                                                uint32_t* __restrict__ tvals) {
-  const int v = (int)((int64_t)item / N);
+  const int v = view_of_item(vt, item);
   const View& V = vt.v[v];
   const uint2 rc = rects[item];
   const Cull q = make_cull(rec[3 * (size_t)item], rec[3 * (size_t)item + 1]);

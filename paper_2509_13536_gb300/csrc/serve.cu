@@ -1,12 +1,12 @@
 // Render-serving loop with continuous batching (host runtime, C++).
 //
 // Resident scene maps; requests (scene, camera, output planes) arrive at any time.  A
-// dispatcher thread admits the oldest pending request as soon as a worker slot is free
-// and the request's workspace fits in free memory of the caller's device arena, and
-// folds every other pending request of the same scene into the same multi-view launch
-// (up to max_batch_views).  Each slot owns a CUDA stream and a worker thread, so
-// admitted batches of different requests run concurrently on the device while new
-// requests keep arriving.  The arena is carved first-fit; nothing is allocated on the
+// dispatcher thread admits the oldest pending requests, of any scene and resolution, as
+// soon as a worker slot is free: up to max_batch_views of them, as many as fit in free
+// memory of the caller's device arena, go into one mgs_render_multi call (one
+// projection launch per map, then one sort, one emission and one blend launch over all
+// their (view, tile) items).  Each slot owns a CUDA stream and a worker thread, so
+// admitted batches run concurrently on the device while new requests keep arriving.  The arena is carved first-fit; nothing is allocated on the
 // device.  Workspace sizes are learnt per (scene, resolution) from the key counts of
 // earlier renders; a render that reports a too-small workspace is retried once with the
 // reported size if the arena has room, and otherwise goes back to the head of the queue.
@@ -84,6 +84,8 @@ struct Arena {
 
 struct Batch {
   std::vector<Request> reqs;
+  std::vector<mgs_gaussians> maps;      // distinct maps of the batch, copied under the lock
+  std::vector<int32_t> map_of_view;     // per request: index into maps
   size_t off = SIZE_MAX, bytes = 0;
 };
 
@@ -106,25 +108,49 @@ struct mgs_server {
   std::vector<Request> done;
   std::vector<Slot> slots;
   Arena arena;
-  std::map<std::pair<int, int64_t>, int64_t> keys_seen;  // (scene, w*65536+h) -> max keys per view
+  std::map<std::pair<int, int64_t>, int64_t> keys_seen;  // (scene, w*65536+h) -> keys per view
   int64_t in_flight = 0;
+  int64_t n_launches = 0, n_served = 0, max_views = 0, mixed_launches = 0;
   bool stop = false;
   std::thread dispatcher;
   std::string last_error;
 
-  int64_t est_keys(int scene, const mgs_camera& c) {
+  // keys of one view: learnt from earlier renders, else 8 per Gaussian
+  int64_t raw_keys(int scene, const mgs_camera& c) {
     auto it = keys_seen.find({scene, (int64_t)c.width * 65536 + c.height});
-    if (it != keys_seen.end()) return it->second + it->second / 4 + 1024;
-    return 8 * scenes[scene].n + 1024;
+    return it != keys_seen.end() ? it->second : 8 * scenes[scene].n;
   }
-  size_t need_bytes(const std::vector<Request>& rs) {
+  int64_t est_keys(int scene, const mgs_camera& c) {
+    const int64_t k = raw_keys(scene, c);
+    return k + k / 4 + 1024;
+  }
+  // the batch's maps and views (call with the lock held)
+  void bind_maps(Batch& b) {
+    b.maps.clear();
+    b.map_of_view.clear();
+    std::vector<int> ids;
+    for (auto& r : b.reqs) {
+      int m = -1;
+      for (size_t k = 0; k < ids.size(); ++k)
+        if (ids[k] == r.scene) m = (int)k;
+      if (m < 0) {
+        m = (int)ids.size();
+        ids.push_back(r.scene);
+        b.maps.push_back(scenes[r.scene]);
+      }
+      b.map_of_view.push_back(m);
+    }
+  }
+  size_t need_bytes(Batch& b) {
+    bind_maps(b);
     std::vector<mgs_camera> cams;
     int64_t keys = 0;
-    for (auto& r : rs) {
+    for (auto& r : b.reqs) {
       cams.push_back(r.cam);
       keys += est_keys(r.scene, r.cam);
     }
-    return mgs_render_workspace_size(scenes[rs[0].scene].n, cams.data(), (int)cams.size(), keys);
+    return mgs_render_multi_workspace_size(b.maps.data(), (int)b.maps.size(), b.map_of_view.data(), cams.data(),
+                                           (int)cams.size(), keys);
   }
 
   void dispatch_loop() {
@@ -137,21 +163,16 @@ struct mgs_server {
         cv_disp.wait(lk);
         continue;
       }
-      // oldest request, plus every pending request of the same scene (up to the batch cap)
+      // the oldest pending requests, any scene and resolution (up to the batch cap)
       Batch b;
-      const int scene = pending.front().scene;
-      for (auto it = pending.begin(); it != pending.end() && (int)b.reqs.size() < cfg.max_batch_views;) {
-        if (it->scene == scene) {
-          b.reqs.push_back(*it);
-          it = pending.erase(it);
-        } else {
-          ++it;
-        }
+      while (!pending.empty() && (int)b.reqs.size() < cfg.max_batch_views) {
+        b.reqs.push_back(pending.front());
+        pending.pop_front();
       }
       // admission by free arena memory: shrink the batch until it fits; if even the
       // oldest request alone does not fit, wait for running work to free memory
       while (true) {
-        size_t need = need_bytes(b.reqs);
+        size_t need = need_bytes(b);
         size_t off = arena.take(need);
         if (off != SIZE_MAX) {
           b.off = off;
@@ -162,6 +183,7 @@ struct mgs_server {
         pending.push_front(b.reqs.back());
         b.reqs.pop_back();
       }
+      bind_maps(b);
       if (b.off == SIZE_MAX) {
         for (auto it = b.reqs.rbegin(); it != b.reqs.rend(); ++it) pending.push_front(*it);
         if (in_flight == 0) {  // nothing will ever free memory: fail the request
@@ -205,13 +227,16 @@ struct mgs_server {
         cams.push_back(r.cam);
         outs.push_back(r.out);
       }
-      const mgs_gaussians g = scenes[b.reqs[0].scene];
+      // the batch's maps were copied by the dispatcher under the lock: no access to
+      // `scenes` here, which add_scene may grow meanwhile
+      const int nm = (int)b.maps.size();
       int64_t nk = 0;
-      mgs_status st = mgs_render(&g, cams.data(), (int)cams.size(), outs.data(), arena.base + b.off, b.bytes,
-                                 &nk, s.stream);
+      mgs_status st = mgs_render_multi(b.maps.data(), nm, b.map_of_view.data(), cams.data(), (int)cams.size(),
+                                       outs.data(), arena.base + b.off, b.bytes, &nk, s.stream);
       if (st == MGS_ERR_WORKSPACE && nk > 0) {
         // learn the true size and retry once with a bigger block if the arena has room
-        size_t need = mgs_render_workspace_size(g.n, cams.data(), (int)cams.size(), nk + nk / 8 + 1024);
+        size_t need = mgs_render_multi_workspace_size(b.maps.data(), nm, b.map_of_view.data(), cams.data(),
+                                                      (int)cams.size(), nk + nk / 8 + 1024);
         std::unique_lock<std::mutex> lk(mu);
         arena.give(b.off, b.bytes);
         size_t off = arena.take(need);
@@ -219,8 +244,8 @@ struct mgs_server {
           b.off = off;
           b.bytes = need;
           lk.unlock();
-          st = mgs_render(&g, cams.data(), (int)cams.size(), outs.data(), arena.base + b.off, b.bytes, &nk,
-                          s.stream);
+          st = mgs_render_multi(b.maps.data(), nm, b.map_of_view.data(), cams.data(), (int)cams.size(),
+                                outs.data(), arena.base + b.off, b.bytes, &nk, s.stream);
         } else {
           b.off = SIZE_MAX;
         }
@@ -229,17 +254,25 @@ struct mgs_server {
       double t1 = now_s();
       std::unique_lock<std::mutex> lk(mu);
       if (b.off != SIZE_MAX) arena.give(b.off, b.bytes);
-      if (st == MGS_OK && nk > 0) {
-        auto key = std::make_pair(b.reqs[0].scene, (int64_t)cams[0].width * 65536 + cams[0].height);
-        int64_t per_view = nk / (int64_t)cams.size() + 1;
-        bool same_res = true;
-        for (auto& c : cams) same_res = same_res && c.width == cams[0].width && c.height == cams[0].height;
-        if (same_res) keys_seen[key] = std::max(keys_seen[key], per_view);
+      if ((st == MGS_OK || st == MGS_ERR_WORKSPACE) && nk > 0) {
+        // the key count of the whole batch, shared out over its views in proportion to
+        // what each view was expected to need
+        double expect = 0;
+        for (auto& r : b.reqs) expect += (double)raw_keys(r.scene, r.cam);
+        const double ratio = expect > 0 ? (double)nk / expect : 1.0;
+        for (auto& r : b.reqs) {
+          const int64_t k = (int64_t)(ratio * (double)raw_keys(r.scene, r.cam)) + 1;
+          keys_seen[{r.scene, (int64_t)r.cam.width * 65536 + r.cam.height}] = k;
+        }
+      }
+      if (st == MGS_OK) {
+        n_launches += 1;
+        n_served += (int64_t)b.reqs.size();
+        max_views = std::max<int64_t>(max_views, (int64_t)b.reqs.size());
+        if (b.maps.size() > 1) mixed_launches += 1;
       }
       if (st == MGS_ERR_WORKSPACE && b.off == SIZE_MAX) {
-        // too big for the arena right now: learn the size and queue the requests again
-        auto key = std::make_pair(b.reqs[0].scene, (int64_t)cams[0].width * 65536 + cams[0].height);
-        keys_seen[key] = std::max(keys_seen[key], nk / (int64_t)cams.size() + 1);
+        // too big for the arena right now: queue the requests again (sizes learnt above)
         for (auto it = b.reqs.rbegin(); it != b.reqs.rend(); ++it) pending.push_front(*it);
       } else {
         for (auto& r : b.reqs) {
@@ -348,6 +381,16 @@ int32_t mgs_server_poll(mgs_server* s, int32_t max, int64_t* tags, double* t_sub
 }
 
 double mgs_server_clock(void) { return now_s(); }
+
+mgs_status mgs_server_stats(mgs_server* s, int64_t out[4]) {
+  if (!s || !out) return MGS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  out[0] = s->n_launches;
+  out[1] = s->n_served;
+  out[2] = s->max_views;
+  out[3] = s->mixed_launches;
+  return MGS_OK;
+}
 
 mgs_status mgs_server_destroy(mgs_server* s) {
   if (!s) return MGS_ERR_INVALID;

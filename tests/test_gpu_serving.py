@@ -1,6 +1,7 @@
 """Render serving with continuous batching: every request's image is bit-identical to
-rendering it alone, whether it was batched with others, overlapped with other scenes,
-or delayed by a small arena (admission by free memory)."""
+rendering it alone, whether it was batched with requests of other scenes and
+resolutions into one launch, overlapped with other batches, or delayed by a small
+arena (admission by free memory)."""
 import numpy as np
 import pytest
 import torch
@@ -51,6 +52,25 @@ def _run(server, scenes, reqs, burst=True):
     return outs, done
 
 
+def test_multi_map_render_matches_each_view_alone(scenes):
+    """Views of three maps (f16, f32 and bf16 storage), interleaved and at mixed
+    resolutions, in one mgs_render_multi call: every image is bit-identical to the same
+    view rendered alone from its own map."""
+    rng = np.random.default_rng(77)
+    mov = [0, 2, 2, 1, 0, 1, 2]
+    cams = [sg.room_poses(1, int(rng.integers(1 << 30)), *RES[k % 3])[0] for k in range(len(mov))]
+    out = [api.new_images([c])[0] for c in cams]
+    ws = api.RenderWorkspace("cuda")
+    ws.ensure(10, cams[:1], 10)  # far too small: the binding grows it and retries
+    api.mgs_render_multi(scenes, mov, cams, out, ws)
+    torch.cuda.synchronize()
+    for v, (m, cam) in enumerate(zip(mov, cams)):
+        alone, _ = api.render(scenes[m], [cam])
+        torch.cuda.synchronize()
+        for plane in ("rgb", "depth", "alpha"):
+            assert torch.equal(getattr(out[v], plane), getattr(alone[0], plane)), (v, plane)
+
+
 @pytest.mark.parametrize("arena_mb,slots,batch", [(6000, 6, 8), (700, 2, 4)])
 def test_each_request_matches_rendering_it_alone(scenes, arena_mb, slots, batch):
     reqs = _requests(40, arena_mb)
@@ -58,7 +78,11 @@ def test_each_request_matches_rendering_it_alone(scenes, arena_mb, slots, batch)
     sids = [server.add_scene(g) for g in scenes]
     assert sids == [0, 1, 2]
     outs, done = _run(server, scenes, reqs)
+    st = server.stats()
     server.close()
+    assert st["requests"] == len(reqs)
+    if batch > 1:
+        assert st["mixed_scene_launches"] > 0, st  # a burst of 40 requests over 3 scenes mixes them
     for tag, (sid, cam) in enumerate(reqs):
         alone, _ = api.render(scenes[sid], [cam])
         torch.cuda.synchronize()
