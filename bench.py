@@ -70,6 +70,9 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-rate", type=float, default=200.0)
+    p.add_argument("--serve-sweep", type=float, nargs="*", default=[1000.0, 3000.0],
+                   help="offered rates (req/s) of the saturation sweep")
+    p.add_argument("--serve-sweep-requests", type=int, default=1000)
     return p.parse_args()
 
 
@@ -361,25 +364,29 @@ SERVE_RES = [(320, 240), (640, 480), (1200, 680), (1920, 1080)]
 
 
 def serving_leg(args, api, torch, sg, dev):
-    """Render serving: 4 resident maps (0.5M, 1M, 2M, 3M Gaussians, SH3, FP16 storage),
-    Poisson arrivals at 200 req/s, each request a random map, pose and resolution.  The
-    continuous-batching server is compared with the same trace served one request at a
-    time from plain FP32 maps.  Latency = arrival -> image ready."""
+    """Render serving: 4 resident maps (0.5M, 1M, 2M, 3M Gaussians, SH3), Poisson arrivals,
+    each request a random map, pose and resolution.  The continuous-batching server (FP16
+    maps, requests of any scene and resolution batched into one launch) against the same
+    trace served one request at a time from plain FP32 maps.  Latency = arrival -> image
+    ready.  The workload's trace (200 req/s) and a sweep of offered rates up to
+    saturation, where the completed frames/s show what batching buys."""
     import threading
     sizes = [500_000, 1_000_000, 2_000_000, 3_000_000]
     scenes = [sg.room_scene(n, 40 + i, sh_degree=3) for i, n in enumerate(sizes)]
-    rng = np.random.default_rng(4)
-    n_req = args.serve_requests
-    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, n_req))
-    reqs = []
-    for i in range(n_req):
-        w, h = SERVE_RES[rng.integers(len(SERVE_RES))]
-        reqs.append((int(rng.integers(len(sizes))), sg.room_poses(1, int(rng.integers(1 << 30)), w, h)[0]))
     ring = {r: [api.new_images([sg.box_camera(*r)], dev)[0] for _ in range(16)] for r in SERVE_RES}
-    warm = min(200, n_req // 10)
 
-    def run(dtype, slots, batch, arena_gb):
-        maps = [api.Gaussians.from_scene(sc, dev, dtype) for sc in scenes]
+    def trace(rate, n_req, seed):
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        reqs = []
+        for i in range(n_req):
+            w, h = SERVE_RES[rng.integers(len(SERVE_RES))]
+            reqs.append((int(rng.integers(len(sizes))), sg.room_poses(1, int(rng.integers(1 << 30)), w, h)[0]))
+        return arrivals, reqs
+
+    def run(maps, slots, batch, arena_gb, arrivals, reqs):
+        n_req = len(reqs)
+        warm = min(200, n_req // 10)
         server = api.Server(int(arena_gb * (1 << 30)), n_slots=slots, max_batch_views=batch, device=dev)
         ids = [server.add_scene(g) for g in maps]
         got = {}
@@ -411,29 +418,42 @@ def serving_leg(args, api, torch, sg, dev):
         stop[0] = True
         th.join(timeout=600)
         gc.enable()
+        st = server.stats()
         server.close()
-        lat = np.array([got[i][2] - got[i][0] for i in range(warm, n_req) if i in got and got[i][3] == 0])
-        t_first = t0 + float(arrivals[warm])
-        t_last = max(got[i][2] for i in range(warm, n_req) if i in got)
         ok = [i for i in range(warm, n_req) if i in got and got[i][3] == 0]
+        lat = np.array([got[i][2] - got[i][0] for i in ok])
+        t_first = t0 + float(arrivals[warm])
+        t_last = max(got[i][2] for i in ok)
         queue = np.array([got[i][1] - got[i][0] for i in ok])
         service = np.array([got[i][2] - got[i][1] for i in ok])
         pct = lambda a, q: float(np.percentile(a, q) * 1e3) if len(a) else None
-        res = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-               "max_ms": float(lat.max() * 1e3),
-               "p99_client_late_ms": pct(late[warm:], 99), "max_client_late_ms": float(late[warm:].max() * 1e3),
-               "p99_queue_ms": pct(queue, 99), "p99_service_ms": pct(service, 99),
-               "frames_per_s": len(lat) / (t_last - t_first), "completed": int(len(lat)),
-               "failed": int(sum(1 for i in range(warm, n_req) if i in got and got[i][3] != 0))}
+        return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "max_ms": float(lat.max() * 1e3),
+                "p50_queue_ms": pct(queue, 50), "p99_queue_ms": pct(queue, 99),
+                "p50_service_ms": pct(service, 50), "p99_service_ms": pct(service, 99),
+                "p99_client_late_ms": pct(late[warm:], 99), "max_client_late_ms": float(late[warm:].max() * 1e3),
+                "frames_per_s": len(lat) / (t_last - t_first), "completed": int(len(lat)),
+                "failed": int(sum(1 for i in range(warm, n_req) if i in got and got[i][3] != 0)),
+                "launches": st["launches"], "requests_per_launch": st["requests"] / max(1, st["launches"]),
+                "mixed_scene_launches": st["mixed_scene_launches"]}
+
+    res = {"maps": "0.5M/1M/2M/3M Gaussians, SH3", "resolutions": [f"{w}x{h}" for w, h in SERVE_RES],
+           "batching": "FP16 maps, 8 slots, up to 8 requests of any scene and resolution per launch",
+           "one_at_a_time": "FP32 maps, 1 slot, 1 request per launch"}
+    for label, dtype, slots, batch, arena in (("continuous_batching_fp16", torch.float16, 8, 8, 24),
+                                              ("one_at_a_time_fp32", torch.float32, 1, 1, 8)):
+        maps = [api.Gaussians.from_scene(sc, dev, dtype) for sc in scenes]
+        arrivals, reqs = trace(args.serve_rate, args.serve_requests, 4)
+        res[label] = run(maps, slots, batch, arena, arrivals, reqs)
+        sweep = {}
+        for rate in args.serve_sweep:
+            arrivals, reqs = trace(rate, args.serve_sweep_requests, 5)
+            sweep[f"{rate:g}_req_per_s"] = run(maps, slots, batch, arena, arrivals, reqs)
+        res[label + "_sweep"] = sweep
         del maps
         torch.cuda.empty_cache()
-        return res
-
-    served = run(torch.float16, 8, 8, 24)
-    sequential = run(torch.float32, 1, 1, 8)
-    return {"requests": n_req, "warmup_requests": warm, "rate_per_s": args.serve_rate,
-            "maps": "0.5M/1M/2M/3M Gaussians, SH3", "resolutions": [f"{w}x{h}" for w, h in SERVE_RES],
-            "continuous_batching_fp16": served, "one_at_a_time_fp32": sequential}
+    res.update({"requests": args.serve_requests, "rate_per_s": args.serve_rate,
+                "sweep_requests": args.serve_sweep_requests})
+    return res
 
 
 def configs_leg(args, api, torch, sg, dev):

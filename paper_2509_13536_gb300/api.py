@@ -237,8 +237,9 @@ def mgs_render_multi(maps: Sequence[Gaussians], map_of_view: Sequence[int], cams
         nk = C.c_int64(0)
         st = L.mgs_render_multi(ms, len(maps), mov, arr, len(cams), imgs, _ptr(ws.buf), ws.buf.numel(),
                                 C.byref(nk), _stream(stream))
-        if st == _abi.MGS_ERR_WORKSPACE and nk.value > 0:
-            grow(int(nk.value * ws.headroom) + 1024)
+        if st == _abi.MGS_ERR_WORKSPACE:
+            # nk = 0: not even the layout without keys fitted; else the keys did not
+            grow(int(nk.value * ws.headroom) + 1024 if nk.value > 0 else 8 * sum(maps[m].n for m in map_of_view))
             continue
         check(st, "mgs_render_multi")
         ws.n_keys = nk.value
