@@ -460,7 +460,6 @@ mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_
                                   static_cast<char*>(workspace), (cudaStream_t)stream, &unsupported);
   if (e != cudaSuccess) return cuda_status(e, "voxel merge");
   if (unsupported == 1) return fail(MGS_ERR_UNSUPPORTED, "voxel coordinate outside +-2^20");
-  if (unsupported == 2) return fail(MGS_ERR_UNSUPPORTED, "a voxel holds more than 256 eligible Gaussians");
   if (unsupported == 3) return fail(MGS_ERR_UNSUPPORTED, "occupied voxel box needs more than 31 key bits");
   return MGS_OK;
 }

@@ -6,8 +6,8 @@
 //                    (ineligible Gaussians get the all-ones key and sort last).
 //  3. radix sort of (key, index); segment heads -> one (start, end) per voxel.
 //  4. k_voxel_pairs  8 lanes per voxel of <= 8 members, a whole warp per voxel of
-//                    9..32 (larger voxels go to a block-per-voxel kernel, <= 256
-//                    members): members ranked by
+//                    9..32, a block per voxel of 33..256 (members in shared
+//                    memory) or of more (members in global scratch): members ranked by
 //                    (birth, index), Eq. 4 for every older/younger pair, greedy
 //                    disjoint pairing on (d2, birth_i, birth_j, i, j) below chi2,
 //                    then the merge of each accepted pair: Eq. 6 mean, the
@@ -32,8 +32,16 @@ struct MergeWs {
   float* mquat;            // [n][4]
   float* mlogs;            // [n][3]
   uint32_t* big;           // [n] voxel ids with more than 32 members
+  uint32_t* huge;          // [n] voxel ids with more than 256 members
+  // members of the huge voxels, ranked by (birth, index), at their voxel's positions of
+  // the sorted order
+  int64_t* h_idx;          // [n]
+  float* h_mu;             // [n][3]
+  float* h_P;              // [n][6] precision (inverse covariance)
+  int32_t* h_match;        // [n]
   uint2* pairs;            // [n/2 + 1] accepted (older, younger) pairs
-  int32_t* hdr;            // 16 ints: bbox min xyz, max xyz, n_elig, err, n_vox, n_big, n_out, n_pairs
+  int32_t* hdr;            // 16 ints: bbox min xyz, max xyz, n_elig, err, n_vox, n_big, n_out, n_pairs,
+                           // L-BFGS iterations (2 ints), n_huge
   uint32_t* scratch;       // sort / scan scratch
 };
 
@@ -742,7 +750,8 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
     const uint64_t* __restrict__ birth, const uint32_t* __restrict__ perm,
     const uint32_t* __restrict__ starts, const uint32_t* __restrict__ big,
     const uint32_t* __restrict__ n_big_p, float chi2, int greedy, int32_t* __restrict__ partner,
-    uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs, int32_t* err) {
+    uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs, uint32_t* __restrict__ huge,
+    uint32_t* __restrict__ n_huge) {
   __shared__ int64_t s_idx[kBlockVoxel];
   __shared__ uint64_t s_birth[kBlockVoxel];
   __shared__ float s_mu[kBlockVoxel][3];
@@ -760,8 +769,8 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
   const uint32_t v = big[bv];
   const uint32_t st = starts[v], en = starts[v + 1];
   const int nm = (int)(en - st);
-  if (nm > kBlockVoxel) {
-    if (t == 0) atomicOr(err, 2);
+  if (nm > kBlockVoxel) {  // left to the global-memory path
+    if (t == 0) huge[atomicAdd(n_huge, 1u)] = v;
     continue;
   }
   int64_t my = t < nm ? (int64_t)perm[st + t] : -1;
@@ -827,6 +836,88 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
     pairs[s_slot + k] = make_uint2((uint32_t)i, (uint32_t)j);
   }
   __syncthreads();  // shared state is reused by the next voxel
+  }
+}
+
+// Global-memory path: a voxel with more than 256 members, one block per voxel.  The
+// members are ranked by (birth, index) into global scratch at the voxel's positions of
+// the sorted order; each greedy round takes the block-wide minimum of (d2, rank a,
+// rank b) over the unmatched pairs below chi2, as the shared-memory path does.
+template <typename T>
+__global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_huge(
+    const float* __restrict__ means, const Geom geo, const uint64_t* __restrict__ birth,
+    const uint32_t* __restrict__ perm, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ huge,
+    const uint32_t* __restrict__ n_huge_p, float chi2, int greedy, int32_t* __restrict__ partner,
+    uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs, int64_t* __restrict__ h_idx,
+    float* __restrict__ h_mu, float* __restrict__ h_P, int32_t* __restrict__ h_match) {
+  __shared__ float r_d2[kBlockVoxel];
+  __shared__ int r_a[kBlockVoxel], r_b[kBlockVoxel];
+  const uint32_t n_huge = *n_huge_p;
+  const int t = threadIdx.x;
+  for (uint32_t hv = blockIdx.x; hv < n_huge; hv += gridDim.x) {
+    const uint32_t v = huge[hv];
+    const uint32_t st = starts[v];
+    const int nm = (int)(starts[v + 1] - st);
+    for (int m = t; m < nm; m += kBlockVoxel) {
+      const int64_t i = perm[st + m];
+      const uint64_t bi = birth[i];
+      int rank = 0;
+      for (int k = 0; k < nm; ++k) {
+        const int64_t j = perm[st + k];
+        if (older(birth[j], j, bi, i)) ++rank;
+      }
+      const uint32_t slot = st + (uint32_t)rank;
+      h_idx[slot] = i;
+      h_match[slot] = 0;
+      for (int k = 0; k < 3; ++k) h_mu[3 * (size_t)slot + k] = means[3 * i + k];
+      precision_of(geo, i, h_P + 6 * (size_t)slot);
+    }
+    __syncthreads();
+    for (int round = 0; round < nm / 2; ++round) {
+      float bd = INFINITY;
+      int ba = -1, bb = -1;
+      for (int a = t; a < nm; a += kBlockVoxel) {
+        if (h_match[st + a]) continue;
+        float P[6], ma[3];
+        for (int k = 0; k < 6; ++k) P[k] = h_P[6 * (size_t)(st + a) + k];
+        for (int k = 0; k < 3; ++k) ma[k] = h_mu[3 * (size_t)(st + a) + k];
+        for (int b = a + 1; b < nm; ++b) {
+          if (h_match[st + b]) continue;
+          const float d2 = mahalanobis2(P, ma, h_mu + 3 * (size_t)(st + b));
+          if (d2 >= chi2) continue;
+          // a rises with the thread's rows, b within a row: (d2, a, b) order per thread
+          if (ba < 0 || d2 < bd || (d2 == bd && (a < ba || (a == ba && b < bb)))) { bd = d2; ba = a; bb = b; }
+        }
+      }
+      r_d2[t] = bd; r_a[t] = ba; r_b[t] = bb;
+      __syncthreads();
+      for (int stp = kBlockVoxel / 2; stp; stp >>= 1) {
+        if (t < stp) {
+          const int oa = r_a[t + stp];
+          bool take;
+          if (oa < 0) take = false;
+          else if (r_a[t] < 0) take = true;
+          else if (r_d2[t + stp] != r_d2[t]) take = r_d2[t + stp] < r_d2[t];
+          else take = oa < r_a[t] || (oa == r_a[t] && r_b[t + stp] < r_b[t]);
+          if (take) { r_d2[t] = r_d2[t + stp]; r_a[t] = oa; r_b[t] = r_b[t + stp]; }
+        }
+        __syncthreads();
+      }
+      const int a = r_a[0], b = r_b[0];
+      __syncthreads();
+      if (a < 0) break;
+      if (t == 0) {
+        h_match[st + a] = 1;
+        h_match[st + b] = 1;
+        const int64_t i = h_idx[st + a], j = h_idx[st + b];
+        partner[i] = (int32_t)j;
+        partner[j] = (int32_t)i;
+        pairs[atomicAdd(n_pairs, 1u)] = make_uint2((uint32_t)i, (uint32_t)j);
+      }
+      __syncthreads();
+      if (!greedy) break;
+    }
+    __syncthreads();  // the next voxel's ranking must not overlap this one's last reads
   }
 }
 
@@ -954,9 +1045,14 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
     uint32_t* n_pairs = (uint32_t*)(ws.hdr + 11);
     k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, geo, in.birth, perm, ws.starts, n_vox, p.chi2,
                                         p.greedy, partner, ws.pairs, n_pairs, ws.big, n_big);
+    uint32_t* n_huge = (uint32_t*)(ws.hdr + 14);
     k_voxel_pairs_big<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n_elig / 33), 152 * 2), kBlockVoxel, 0, s>>>(
         in.means, geo, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
-        ws.pairs, n_pairs, ws.hdr + 7);
+        ws.pairs, n_pairs, ws.huge, n_huge);
+    k_voxel_pairs_huge<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n_elig / 257), 152), kBlockVoxel, 0, s>>>(
+        in.means, geo, in.birth, perm, ws.starts, ws.huge, n_huge, p.chi2, p.greedy, partner, ws.pairs, n_pairs,
+        ws.h_idx, ws.h_mu, ws.h_P, ws.h_match);
+    count_launch();
     const unsigned gp = (unsigned)div_up(n_elig / 2 + 1, 128);
     unsigned long long* iters = reinterpret_cast<unsigned long long*>(ws.hdr + 12);
     if (p.solver == 1)
@@ -981,7 +1077,6 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
   if (e != cudaSuccess) return e;
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
-  if (h[7] & 2) { *unsupported = 2; return cudaSuccess; }
   *n_out_host = (int64_t)(uint32_t)h[10];
   unsigned long long it = 0;
   std::memcpy(&it, h + 12, sizeof(it));
@@ -1016,6 +1111,11 @@ size_t merge_workspace_bytes(int64_t n, MergeWs* ws, char* base) {
   w.mquat = (float*)take(16 * m);
   w.mlogs = (float*)take(12 * m);
   w.big = (uint32_t*)take(4 * m);
+  w.huge = (uint32_t*)take(4 * m);
+  w.h_idx = (int64_t*)take(8 * m);
+  w.h_mu = (float*)take(12 * m);
+  w.h_P = (float*)take(24 * m);
+  w.h_match = (int32_t*)take(4 * m);
   w.pairs = (uint2*)take(8 * (m / 2 + 1));
   w.scratch = (uint32_t*)take(4 * sort_scratch_words(m));
   if (ws) *ws = w;

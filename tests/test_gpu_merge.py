@@ -233,3 +233,33 @@ def test_l1_loss_grad():
     torch.cuda.synchronize()
     assert torch.equal(grad, 0.5 * torch.sign(a - b))
     assert abs(float(loss) - 0.5 * float((a - b).abs().sum())) < 1e-3 * float(loss)
+
+
+def _crowded_scene(rng, sizes, v=0.02, scale=(0.0004, 0.001)):
+    """One voxel per entry of ``sizes`` with that many members (means uniform in the
+    middle 60% of the voxel, small scales so that similarity is sparse), random births."""
+    means, scales, quats = [], [], []
+    for k, m in enumerate(sizes):
+        base = (np.array([3 * k, 1, 1]) + 0.5) * v
+        for _ in range(m):
+            means.append(base + rng.uniform(-0.3, 0.3, 3) * v)
+            scales.append(np.exp(rng.uniform(np.log(scale[0]), np.log(scale[1]), 3)))
+            quats.append(rng.normal(size=4))
+    n = len(means)
+    return make_scene(means, scales, quats, rng.uniform(0.1, 0.9, n), rng.random((n, 3)), 0,
+                      birth=rng.permutation(n))
+
+
+@pytest.mark.parametrize("greedy", [True, False])
+def test_merge_voxels_of_300_and_1000_members(orc, greedy):
+    """Voxels beyond the shared-memory block path (more than 256 members) take the
+    global-memory path: all n (n - 1) / 2 pairs of each voxel (Sec. II-D), clusters bit
+    for bit as the oracle's, next to small voxels."""
+    rng = np.random.default_rng(1000)
+    sc = _crowded_scene(rng, [300, 1000, 5, 40, 3])
+    sc, ref, _ = scrub_kw(orc, sc, 0.02, rounds=30, greedy=greedy)
+    keys = orc.voxel_keys(sc.means, 0.02)
+    _, counts = np.unique(keys, axis=0, return_counts=True)
+    assert sorted(counts)[-2:][0] > 256  # both big voxels are still past the block path
+    pairs, n = compare_merge(orc, sc, 0.02, greedy=greedy)
+    assert pairs > (100 if greedy else 2)
