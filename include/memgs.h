@@ -141,6 +141,18 @@ mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams_host, int32
                       const mgs_image* out_host, void* workspace, size_t workspace_bytes,
                       int64_t* n_keys_host, void* stream);
 
+/* mgs_render without the host synchronisation: the launches are sized for the
+ * workspace's key capacity and read the actual counts from device memory.  If the keys
+ * exceed the capacity, nothing is emitted or blended (the images come out empty) and
+ * the status says so.  status_pinned (optional, page-locked host memory of 2 int64):
+ * receives {number of (Gaussian, tile) keys, 1 if they exceeded the capacity else 0}
+ * once the stream has reached the end of the call; read it after synchronising with
+ * the stream (or an event recorded after the call).  Everything else as mgs_render,
+ * including the state mgs_render_backward reads.  Asynchronous. */
+mgs_status mgs_render_async(const mgs_gaussians* g, const mgs_camera* cams_host, int32_t n_views,
+                            const mgs_image* out_host, void* workspace, size_t workspace_bytes,
+                            int64_t* status_pinned, void* stream);
+
 /* Forward render of views that each name their own map (Sec. II-E rasteriser, serving
  * several resident maps at once): view v is rendered from maps_host[map_of_view_host[v]]
  * (0 <= index < n_maps; map_of_view_host is a host array of n_views entries).  One
@@ -216,13 +228,25 @@ size_t mgs_voxel_merge_workspace_size(int64_t n);
 
 /* out: capacity >= in->n, same sh_degree, attr_dtype and geom_dtype.  partner (optional, [n]):
  * index of the merge partner or -1.  voxel (optional, i32 [n][3]): voxel coordinates
- * of eligible Gaussians (INT32_MIN for ineligible ones).  Synchronises `stream` and
- * writes the survivor count to *n_out_host.  Voxel coordinates must fit in 21 bits
- * signed (|mu / voxel_size| < 2^20), else MGS_ERR_UNSUPPORTED. */
+ * of eligible Gaussians (INT32_MIN for ineligible ones).  Voxels of any number of
+ * members.  Synchronises `stream` and writes the survivor count to *n_out_host.  Voxel
+ * coordinates must fit in 21 bits signed (|mu / voxel_size| < 2^20) and the occupied
+ * voxels' box in 31 key bits, else nothing merges (out is a copy) and the call returns
+ * MGS_ERR_UNSUPPORTED. */
 mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_merge_params* p,
                            const mgs_gaussians_mut* out, int32_t* partner, int32_t* voxel,
                            int64_t* n_out_host, void* workspace, size_t workspace_bytes,
                            void* stream);
+/* mgs_voxel_merge without the host synchronisation (every launch is sized from n and
+ * reads its counts from device memory).  status_pinned (optional, page-locked host
+ * memory of 2 int32): receives {survivor count, flags} once the stream has reached the
+ * end of the call; flags bit 0: a voxel coordinate outside +-2^20, bit 2: nothing
+ * merged because of it or of a box needing more than 31 key bits.  mgs_merge_stats
+ * does not cover this form.  Asynchronous. */
+mgs_status mgs_voxel_merge_async(const mgs_gaussians* in, float voxel_size, const mgs_merge_params* p,
+                                 const mgs_gaussians_mut* out, int32_t* partner, int32_t* voxel,
+                                 int32_t* status_pinned, void* workspace, size_t workspace_bytes,
+                                 void* stream);
 
 /* ------------------------------------------------------------------------------
  * Optimiser: Adam with bias correction over every parameter array of `params`

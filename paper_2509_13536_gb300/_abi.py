@@ -26,7 +26,8 @@ EXPORTS = ["mgs_render_workspace_size", "mgs_render", "mgs_render_backward", "mg
            "mgs_server_poll", "mgs_server_clock", "mgs_server_destroy", "mgs_mapping_loss_workspace_size",
            "mgs_mapping_loss", "mgs_iso_loss_workspace_size", "mgs_iso_loss", "mgs_merge_stats",
            "mgs_patch_grid_workspace_size", "mgs_patch_grid_capacity", "mgs_patch_grid_sample",
-           "mgs_render_multi_workspace_size", "mgs_render_multi", "mgs_server_stats"]
+           "mgs_render_multi_workspace_size", "mgs_render_multi", "mgs_server_stats", "mgs_render_async",
+           "mgs_voxel_merge_async"]
 
 
 class mgs_gaussians(C.Structure):
@@ -100,6 +101,8 @@ def load():
             "mgs_render": (C.c_int, [P, P, I32, P, P, SZ, P, P]),
             "mgs_render_multi_workspace_size": (SZ, [P, I32, P, P, I32, I64]),
             "mgs_render_multi": (C.c_int, [P, I32, P, P, I32, P, P, SZ, P, P]),
+            "mgs_render_async": (C.c_int, [P, P, I32, P, P, SZ, P, P]),
+            "mgs_voxel_merge_async": (C.c_int, [P, F, P, P, P, P, P, P, SZ, P]),
             "mgs_render_backward": (C.c_int, [P, P, I32, P, P, SZ, P, P]),
             "mgs_project": (C.c_int, [P, P, P, P, P, P, P, P, P]),
             "mgs_voxel_merge_workspace_size": (SZ, [I64]),

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import check, load
+from ._abi import MemgsError, check, load
 
 _DTYPES = {torch.float32: _abi.MGS_F32, torch.float16: _abi.MGS_F16, torch.bfloat16: _abi.MGS_BF16}
 
@@ -174,6 +174,30 @@ class RenderWorkspace:
         self.headroom = key_headroom
         self.n_keys = 0
         self.generation = 0
+        self.status: Optional[torch.Tensor] = None  # pinned {keys, overflow} of an asynchronous render
+        self.pending = False
+
+    def status_buffer(self) -> torch.Tensor:
+        if self.status is None:
+            self.status = torch.zeros(2, dtype=torch.int64, pin_memory=True)
+        return self.status
+
+    def check(self, stream=None) -> int:
+        """After asynchronous renders: wait for the stream, then the key count of the
+        last one.  If its keys exceeded the capacity (its images are empty), grow the
+        workspace for them and raise: that render has to be repeated."""
+        if not self.pending:
+            return self.n_keys
+        (stream or torch.cuda.current_stream()).synchronize()
+        self.pending = False
+        keys, over = int(self.status[0]), int(self.status[1])
+        self.n_keys = keys
+        if over:
+            self.buf = None
+            self.generation += 1
+            raise MemgsError(_abi.MGS_ERR_WORKSPACE, "mgs_render_async",
+                             f"{keys} keys exceeded the workspace; it is released, the next render regrows it")
+        return keys
 
     def ensure(self, n, cams, key_capacity) -> torch.Tensor:
         arr = _cam_array(cams)
@@ -187,12 +211,20 @@ class RenderWorkspace:
         return self.buf
 
 
-def mgs_render(g: Gaussians, cams, out: List[Image], ws: RenderWorkspace, stream=None) -> int:
-    """One call of mgs_render; grows the workspace and retries when it is too small."""
+def mgs_render(g: Gaussians, cams, out: List[Image], ws: RenderWorkspace, stream=None, sync=True) -> int:
+    """One call of mgs_render; grows the workspace and retries when it is too small.
+    sync=False (with a workspace sized by an earlier render): mgs_render_async, no host
+    synchronisation; the key count and an overflow are checked by ws.check()."""
     L = load()
     gs = g.struct()
     arr = _cam_array(cams)
     imgs = _image_array(out)
+    if not sync and ws.buf is not None:
+        check(L.mgs_render_async(C.byref(gs), arr, len(cams), imgs, _ptr(ws.buf), ws.buf.numel(),
+                                 C.c_void_p(ws.status_buffer().data_ptr()), _stream(stream)), "mgs_render_async")
+        ws.pending = True
+        ws.generation += 1
+        return -1
     if ws.buf is None:
         ws.ensure(g.n, cams, max(1024, 8 * g.n * len(cams)))
     for _ in range(3):
@@ -295,12 +327,15 @@ def mgs_voxel_merge(g: Gaussians, voxel_size: float, chi2: float = 7.815, greedy
                     kf_id: Optional[torch.Tensor] = None, kf_min: int = 0, kf_max: int = 0,
                     workspace: Optional[torch.Tensor] = None, out: Optional[Gaussians] = None,
                     partner: Optional[torch.Tensor] = None, vox: Optional[torch.Tensor] = None,
-                    vis_count: Optional[torch.Tensor] = None, solver: str = "closed_form", stream=None):
+                    vis_count: Optional[torch.Tensor] = None, solver: str = "closed_form", stream=None,
+                    status: Optional[torch.Tensor] = None):
     """voxel_merge(gaussians, voxel_size, thresholds) -> (gaussians, partner, voxel coords).
 
     ``grad_stat`` with ``vis_count``: the sums the backward pass accumulates (Grads.grad_stat,
     Grads.vis_count); the Eq. 3 mask then tests their quotient.  ``workspace``, ``out``,
-    ``partner`` and ``vox`` may be passed preallocated."""
+    ``partner`` and ``vox`` may be passed preallocated.  ``status`` (a pinned int32 [2]
+    tensor): mgs_voxel_merge_async, no host synchronisation; the returned map then has
+    the input's capacity and status receives {survivors, flags} with the stream."""
     if g.birth is None:
         raise ValueError("voxel merge needs birth stamps")
     L = load()
@@ -315,6 +350,11 @@ def mgs_voxel_merge(g: Gaussians, voxel_size: float, chi2: float = 7.815, greedy
         raise ValueError("solver is 'closed_form' or 'lbfgs'")
     p = _abi.mgs_merge_params(chi2, grad_tau, kf_min, kf_max, _ptr(grad_stat), _ptr(kf_id),
                               _ptr(vis_count), 1 if greedy else 0, 1 if solver == "lbfgs" else 0)
+    if status is not None:
+        check(L.mgs_voxel_merge_async(C.byref(g.struct()), float(voxel_size), C.byref(p), C.byref(out.struct()),
+                                      _ptr(partner), _ptr(vox), C.c_void_p(status.data_ptr()), _ptr(workspace),
+                                      workspace.numel(), _stream(stream)), "mgs_voxel_merge_async")
+        return out, partner, vox
     n_out = C.c_int64(0)
     check(L.mgs_voxel_merge(C.byref(g.struct()), float(voxel_size), C.byref(p), C.byref(out.struct()),
                             _ptr(partner), _ptr(vox), C.byref(n_out), _ptr(workspace),
@@ -476,10 +516,11 @@ def render_stats(g: Gaussians, cams, ws: RenderWorkspace, stream=None):
 class RenderFn(torch.autograd.Function):
     """Differentiable multi-view render through libmemgs.
 
-    apply(means, log_scales, quats, opacity_logit, sh, cams, ws, grads=None) ->
+    apply(means, log_scales, quats, opacity_logit, sh, cams, ws, grads=None, sync=True) ->
     (rgb [V,3,H,W], depth [V,H,W], alpha [V,H,W]) for views of one resolution.  The
     backward pass is mgs_render_backward on the saved state in ``ws``; it refuses to run
-    if ``ws`` was rendered into or regrown after this forward pass.
+    if ``ws`` was rendered into or regrown after this forward pass.  sync=False renders
+    with mgs_render_async (no host synchronisation; ws.check() reports an overflow).
 
     ``grads`` None: the backward pass returns new f32 gradient tensors (plain autograd).
     ``grads`` a Grads: the library accumulates the gradients into those buffers in place
@@ -489,7 +530,7 @@ class RenderFn(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, means, log_scales, quats, opacity_logit, sh, cams, ws, grads=None):
+    def forward(ctx, means, log_scales, quats, opacity_logit, sh, cams, ws, grads=None, sync=True):
         g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), opacity_logit.detach(),
                       sh.detach())
         V = len(cams)
@@ -500,7 +541,7 @@ class RenderFn(torch.autograd.Function):
         depth = torch.empty(V, H, W, device=means.device)
         alpha = torch.empty(V, H, W, device=means.device)
         out = [Image(rgb[v], depth[v], alpha[v]) for v in range(V)]
-        mgs_render(g, cams, out, ws)
+        mgs_render(g, cams, out, ws, sync=sync)
         ctx.set_materialize_grads(False)  # an unused output's cotangent stays None: no zero-filled tensor
         ctx.cams, ctx.ws, ctx.grads = cams, ws, grads
         ctx.generation, ctx.buf = ws.generation, ws.buf
@@ -528,10 +569,10 @@ class RenderFn(torch.autograd.Function):
                                          _ptr(ws.buf), ws.buf.numel(), C.byref(grads.struct()),
                                          _stream()), "mgs_render_backward")
         if ctx.grads is not None:
-            return None, None, None, None, None, None, None, None
+            return None, None, None, None, None, None, None, None, None
         cast = lambda gr, p: gr if p.dtype == torch.float32 else gr.to(p.dtype)
         return (grads.means, cast(grads.log_scales, log_scales), cast(grads.quats, quats),
-                cast(grads.opacity_logit, opacity_logit), cast(grads.sh, sh), None, None, None)
+                cast(grads.opacity_logit, opacity_logit), cast(grads.sh, sh), None, None, None, None)
 
 
 def render_views(g: Gaussians, cams, ws: Optional[RenderWorkspace] = None):
@@ -552,6 +593,11 @@ class MappingStep:
     gradients.  Every kernel of the step is the library's; the parameter tensors are
     updated in place.  Returns the device loss tensor [V, 3] (weighted L1, SSIM and
     depth parts per view); ``loss_iso`` holds the isotropic term.
+
+    The first call renders synchronously (it sizes the render workspace from the key
+    count, with headroom); later calls render with mgs_render_async, so a step makes no
+    host round trip.  check() waits for the stream and raises if a render's keys
+    outgrew the workspace (that step's images were empty; the next step regrows it).
     """
 
     def __init__(self, g: Gaussians, cams, lr=1e-3, lambda_ssim=0.0, w_depth=0.1, w_iso=0.0,
@@ -578,11 +624,12 @@ class MappingStep:
         self.iso_ws = torch.empty(max(1, L.mgs_iso_loss_workspace_size(g.n)), dtype=torch.uint8, device=dev)
         self.step_count = 0
         self._dL = [Image(self.g_rgb[v], self.g_depth[v], None) for v in range(V)]
+        self.ws.headroom = 1.5
 
     def __call__(self, target_rgb: torch.Tensor, target_depth: Optional[torch.Tensor] = None):
         """One step against keyframe images target_rgb [V,3,H,W] (and target_depth [V,H,W])."""
         self.step_count += 1
-        rgb, depth, alpha = RenderFn.apply(*self.params, self.cams, self.ws, self.grads)
+        rgb, depth, alpha = RenderFn.apply(*self.params, self.cams, self.ws, self.grads, self.ws.buf is None)
         V = len(self.cams)
         rendered = [Image(rgb[v].detach(), depth[v].detach(), alpha[v].detach()) for v in range(V)]
         targets = [Image(target_rgb[v], None if target_depth is None else target_depth[v], None)
@@ -597,6 +644,10 @@ class MappingStep:
             mgs_adam_step(g, self.grads, self.m, self.v, self.lr, self.betas[0], self.betas[1], self.eps,
                           self.step_count, zero_grads=True)
         return self.loss
+
+    def check(self) -> int:
+        """Key count of the last render (waits for the stream); raises on an overflow."""
+        return self.ws.check()
 
 
 class Server:

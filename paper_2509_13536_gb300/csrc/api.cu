@@ -19,7 +19,7 @@ cudaError_t launch_project_one(const mgs_gaussians& g, const View& V, float* mea
                                float* rgb, float* depth, int32_t* radius, int32_t* rect, cudaStream_t s);
 cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const uint32_t* offsets,
                         const uint32_t* touched, const uint2* rects, const float4* rec, const ViewTable& vt,
-                        uint32_t* tkeys, uint32_t* tvals, cudaStream_t s);
+                        uint32_t* tkeys, uint32_t* tvals, cudaStream_t s, const uint32_t* n_vis_dev = nullptr);
 cudaError_t launch_blend_fwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
                              const uint2* ranges, cudaStream_t s);
 cudaError_t launch_blend_bwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
@@ -34,8 +34,8 @@ cudaError_t launch_l1(const float* pred, const float* target, int64_t n, float s
 struct MergeWs;
 size_t merge_workspace_bytes(int64_t n, MergeWs* ws, char* base);
 cudaError_t run_voxel_merge(const mgs_gaussians& in, float voxel, const mgs_merge_params& p,
-                            const mgs_gaussians_mut& out, int32_t* partner, int32_t* vox,
-                            int64_t* n_out_host, char* ws_base, cudaStream_t s, int* unsupported);
+                            const mgs_gaussians_mut& out, int32_t* partner, int32_t* vox, char* ws_base,
+                            cudaStream_t s, int32_t** hdr_dev);
 
 namespace {
 thread_local std::string g_error;
@@ -213,9 +213,25 @@ size_t mgs_render_workspace_size(int64_t n, const mgs_camera* cams, int32_t n_vi
   return render_layout(uniform_items(n, n_views), cams, n_views, key_capacity).total;
 }
 
+// Render-plan of the asynchronous form: from the projection's counters, the number of
+// drawn items and of keys the later launches process (both 0 when the keys exceed the
+// workspace's capacity: then nothing is emitted, sorted or blended beyond empty
+// tiles), and the status {keys, overflow} for the caller.
+__global__ void k_render_plan(const unsigned long long* counters, unsigned long long cap, uint32_t* plan,
+                              long long* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned long long nk = counters[0], nv = counters[1];
+  const bool over = nk > cap || nk >= 0xffffffffull;
+  plan[0] = over ? 0u : (uint32_t)nv;
+  plan[1] = over ? 0u : (uint32_t)nk;
+  status[0] = (long long)nk;
+  status[1] = over ? 1 : 0;
+}
+
 static mgs_status render_impl(const mgs_gaussians* maps, int n_maps, const int32_t* map_of_view,
                               const mgs_camera* cams, int32_t n_views, const mgs_image* out, void* workspace,
-                              size_t workspace_bytes, int64_t* n_keys_host, cudaStream_t s) {
+                              size_t workspace_bytes, int64_t* n_keys_host, cudaStream_t s,
+                              bool async = false, int64_t* status_pinned = nullptr) {
   std::string why;
   if (!cams_valid(cams, n_views, &why)) return fail(MGS_ERR_INVALID, why);
   if (!out || !workspace) return fail(MGS_ERR_INVALID, "out or workspace is NULL");
@@ -271,37 +287,56 @@ static mgs_status render_impl(const mgs_gaussians* maps, int n_maps, const int32
       v0 = v1;
     }
   }
-  unsigned long long cnt[2] = {0, 0};
-  MGS_TRY_CUDA(cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
-  MGS_TRY_CUDA(cudaStreamSynchronize(s));
-  const int64_t n_keys = (int64_t)cnt[0], n_vis = (int64_t)cnt[1];
-  if (n_keys_host) *n_keys_host = n_keys;
-  if (n_keys >= (int64_t)UINT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "more than 2^32-1 (Gaussian, tile) pairs");
-  if (n_keys > cap)
-    return fail(MGS_ERR_WORKSPACE, "workspace holds " + std::to_string(cap) + " keys, render needs " +
-                                       std::to_string(n_keys));
+  // Counts for the launches that follow: read on the host (one synchronisation), or
+  // kept on the device (asynchronous form: launches sized for the workspace's capacity
+  // read them from the plan).
+  int64_t n_keys = cap, n_vis = L.VN;
+  const uint32_t* vis_dev = nullptr;
+  const uint32_t* keys_dev = nullptr;
+  auto* plan = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(counters) + 128);
+  auto* status = reinterpret_cast<long long*>(reinterpret_cast<char*>(counters) + 144);
+  if (async) {
+    k_render_plan<<<1, 32, 0, s>>>(counters, (unsigned long long)cap, plan, status);
+    count_launch();
+    MGS_TRY_CUDA(cudaGetLastError());
+    vis_dev = plan;
+    keys_dev = plan + 1;
+  } else {
+    unsigned long long cnt[2] = {0, 0};
+    MGS_TRY_CUDA(cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    MGS_TRY_CUDA(cudaStreamSynchronize(s));
+    n_keys = (int64_t)cnt[0];
+    n_vis = (int64_t)cnt[1];
+    if (n_keys_host) *n_keys_host = n_keys;
+    if (n_keys >= (int64_t)UINT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "more than 2^32-1 (Gaussian, tile) pairs");
+    if (n_keys > cap)
+      return fail(MGS_ERR_WORKSPACE, "workspace holds " + std::to_string(cap) + " keys, render needs " +
+                                         std::to_string(n_keys));
+  }
   cudaError_t e = cudaSuccess;
   int dcur = 0;
   if (L.VN > 0) {
     // front-to-back order of the drawn (view, Gaussian) items: float32 depth bits, then item
     // index; undrawn items (key kSortDrop) leave in the first pass
     ProfScope ps(kProfDepthSort, s);
-    dcur = radix_sort_pairs(dk, dv, L.VN, 0, 32, true, scratch, s, &e, n_vis);
+    dcur = radix_sort_pairs(dk, dv, L.VN, 0, 32, true, scratch, s, &e, n_vis, nullptr, vis_dev);
     if (e != cudaSuccess) return cuda_status(e, "depth sort");
-    MGS_TRY_CUDA(scan_exclusive_u32(touched, dv[dcur], offsets, n_vis, scratch, nullptr, s));
+    MGS_TRY_CUDA(scan_exclusive_u32(touched, dv[dcur], offsets, n_vis, scratch, nullptr, s, vis_dev));
   }
   {
     ProfScope ps(kProfEmit, s);
-    MGS_TRY_CUDA(launch_emit(n_vis, L.N, dv[dcur], offsets, touched, rects, rec, vt, tk[0], tv[0], s));
+    MGS_TRY_CUDA(launch_emit(n_vis, L.N, dv[dcur], offsets, touched, rects, rec, vt, tk[0], tv[0], s, vis_dev));
   }
   int tcur = 0;
   {
     ProfScope ps(kProfTileSort, s);
-    tcur = radix_sort_pairs(tk, tv, n_keys, 0, tile_bits(vt.n_tiles), false, scratch, s, &e);
+    tcur = radix_sort_pairs(tk, tv, n_keys, 0, tile_bits(vt.n_tiles), false, scratch, s, &e, -1, keys_dev);
     if (e != cudaSuccess) return cuda_status(e, "tile sort");
     MGS_TRY_CUDA(cudaMemsetAsync(ranges, 0, 8 * (size_t)vt.n_tiles, s));
-    MGS_TRY_CUDA(build_ranges(tk[tcur], n_keys, (uint32_t)vt.n_tiles, ranges, s));
+    MGS_TRY_CUDA(build_ranges(tk[tcur], n_keys, (uint32_t)vt.n_tiles, ranges, s, keys_dev));
   }
+  if (async && status_pinned)
+    MGS_TRY_CUDA(cudaMemcpyAsync(status_pinned, status, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s));
   {
     ProfScope ps(kProfBlendFwd, s);
     MGS_TRY_CUDA(launch_blend_fwd(vt, rec, tv[tcur], ranges, s));
@@ -317,6 +352,16 @@ mgs_status mgs_render(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_
   if (!why.empty()) return fail(MGS_ERR_INVALID, why);
   return render_impl(g, 1, nullptr, cams, n_views, out, workspace, workspace_bytes, n_keys_host,
                      (cudaStream_t)stream);
+}
+
+mgs_status mgs_render_async(const mgs_gaussians* g, const mgs_camera* cams, int32_t n_views,
+                            const mgs_image* out, void* workspace, size_t workspace_bytes, int64_t* status_pinned,
+                            void* stream) {
+  set_error("");
+  std::string why = check_gaussians(g, false);
+  if (!why.empty()) return fail(MGS_ERR_INVALID, why);
+  return render_impl(g, 1, nullptr, cams, n_views, out, workspace, workspace_bytes, nullptr, (cudaStream_t)stream,
+                     true, status_pinned);
 }
 
 size_t mgs_render_multi_workspace_size(const mgs_gaussians* maps, int32_t n_maps, const int32_t* map_of_view,
@@ -432,13 +477,11 @@ size_t mgs_voxel_merge_workspace_size(int64_t n) {
   return merge_workspace_bytes(n, nullptr, nullptr);
 }
 
-mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_merge_params* p,
-                           const mgs_gaussians_mut* out, int32_t* partner, int32_t* voxel,
-                           int64_t* n_out_host, void* workspace, size_t workspace_bytes, void* stream) {
-  set_error("");
+static mgs_status merge_args(const mgs_gaussians* in, float voxel_size, const mgs_merge_params* p,
+                             const mgs_gaussians_mut* out, void* workspace, size_t workspace_bytes) {
   std::string why = check_gaussians(in, true);
   if (!why.empty()) return fail(MGS_ERR_INVALID, why);
-  if (!p || !out || !n_out_host) return fail(MGS_ERR_INVALID, "params, out or n_out_host is NULL");
+  if (!p || !out) return fail(MGS_ERR_INVALID, "params or out is NULL");
   if (!(voxel_size > 0) || !std::isfinite(voxel_size)) return fail(MGS_ERR_INVALID, "voxel_size must be > 0");
   if (!(p->chi2 > 0)) return fail(MGS_ERR_INVALID, "chi2 must be > 0");
   if (p->solver != 0 && p->solver != 1) return fail(MGS_ERR_INVALID, "solver must be 0 (closed form) or 1 (L-BFGS)");
@@ -450,17 +493,61 @@ mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_
   if (in->n >= (int64_t)INT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "n must be < 2^31");
   if (!workspace || workspace_bytes < merge_workspace_bytes(in->n, nullptr, nullptr))
     return fail(MGS_ERR_WORKSPACE, "merge workspace too small");
+  return MGS_OK;
+}
+
+mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_merge_params* p,
+                           const mgs_gaussians_mut* out, int32_t* partner, int32_t* voxel,
+                           int64_t* n_out_host, void* workspace, size_t workspace_bytes, void* stream) {
+  set_error("");
+  if (!n_out_host) return fail(MGS_ERR_INVALID, "n_out_host is NULL");
+  mgs_status st = merge_args(in, voxel_size, p, out, workspace, workspace_bytes);
+  if (st != MGS_OK) return st;
   if (in->n == 0) {
     *n_out_host = 0;
     return MGS_OK;
   }
-  int unsupported = 0;
-  ProfScope ps(kProfMerge, (cudaStream_t)stream);
-  cudaError_t e = run_voxel_merge(*in, voxel_size, *p, *out, partner, voxel, n_out_host,
-                                  static_cast<char*>(workspace), (cudaStream_t)stream, &unsupported);
-  if (e != cudaSuccess) return cuda_status(e, "voxel merge");
-  if (unsupported == 1) return fail(MGS_ERR_UNSUPPORTED, "voxel coordinate outside +-2^20");
-  if (unsupported == 3) return fail(MGS_ERR_UNSUPPORTED, "occupied voxel box needs more than 31 key bits");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* hdr = nullptr;
+  {
+    ProfScope ps(kProfMerge, s);
+    cudaError_t e = run_voxel_merge(*in, voxel_size, *p, *out, partner, voxel, static_cast<char*>(workspace), s, &hdr);
+    if (e != cudaSuccess) return cuda_status(e, "voxel merge");
+  }
+  int32_t h[16];
+  MGS_TRY_CUDA(cudaMemcpyAsync(h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MGS_TRY_CUDA(cudaStreamSynchronize(s));
+  *n_out_host = (int64_t)(uint32_t)h[10];
+  unsigned long long it = 0;
+  std::memcpy(&it, h + 12, sizeof(it));
+  last_merge_stats().pairs = (int64_t)(uint32_t)h[11];
+  last_merge_stats().lbfgs_iterations = (int64_t)it;
+  if (h[7] & 1) return fail(MGS_ERR_UNSUPPORTED, "voxel coordinate outside +-2^20 (nothing merged)");
+  if (h[7] & 4) return fail(MGS_ERR_UNSUPPORTED, "occupied voxel box needs more than 31 key bits (nothing merged)");
+  return MGS_OK;
+}
+
+mgs_status mgs_voxel_merge_async(const mgs_gaussians* in, float voxel_size, const mgs_merge_params* p,
+                                 const mgs_gaussians_mut* out, int32_t* partner, int32_t* voxel,
+                                 int32_t* status_pinned, void* workspace, size_t workspace_bytes, void* stream) {
+  set_error("");
+  mgs_status st = merge_args(in, voxel_size, p, out, workspace, workspace_bytes);
+  if (st != MGS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (in->n == 0) {
+    if (status_pinned) status_pinned[0] = status_pinned[1] = 0;
+    return MGS_OK;
+  }
+  int32_t* hdr = nullptr;
+  {
+    ProfScope ps(kProfMerge, s);
+    cudaError_t e = run_voxel_merge(*in, voxel_size, *p, *out, partner, voxel, static_cast<char*>(workspace), s, &hdr);
+    if (e != cudaSuccess) return cuda_status(e, "voxel merge");
+  }
+  if (status_pinned) {
+    MGS_TRY_CUDA(cudaMemcpyAsync(status_pinned, hdr + 10, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    MGS_TRY_CUDA(cudaMemcpyAsync(status_pinned + 1, hdr + 7, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  }
   return MGS_OK;
 }
 

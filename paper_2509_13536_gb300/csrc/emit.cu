@@ -102,7 +102,9 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n_vis, int64_t N, const ui
                                               const uint32_t* __restrict__ touched,
                                               const uint2* __restrict__ rects, const float4* __restrict__ rec,
                                               const __grid_constant__ ViewTable vt,
-                                              uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals) {
+                                              uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals,
+                                              const uint32_t* __restrict__ n_vis_dev) {
+  if (n_vis_dev) n_vis = min(n_vis, (int64_t)*n_vis_dev);
   const int lane = threadIdx.x & 31;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if ((k & ~int64_t(31)) >= n_vis) return;  // whole warp beyond the end
@@ -128,10 +130,10 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n_vis, int64_t N, const ui
 
 cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const uint32_t* offsets,
                         const uint32_t* touched, const uint2* rects, const float4* rec, const ViewTable& vt,
-                        uint32_t* tkeys, uint32_t* tvals, cudaStream_t s) {
+                        uint32_t* tkeys, uint32_t* tvals, cudaStream_t s, const uint32_t* n_vis_dev) {
   if (n_vis <= 0) return cudaSuccess;
   k_emit<<<(unsigned)div_up(n_vis, 256), 256, 0, s>>>(n_vis, N, dvals, offsets, touched, rects, rec, vt, tkeys,
-                                                       tvals);
+                                                       tvals, n_vis_dev);
   count_launch();
   return cudaGetLastError();
 }

@@ -45,25 +45,30 @@ int64_t sort_scratch_words(int64_t n);
 
 // Exclusive scan out[i] = sum_{k<i} in[gather ? gather[k] : k]; out may alias in.
 // *total_dev (optional) receives the sum.  scratch: sort_scratch_words(n) words.
+// n_dev (optional): the item count in device memory (<= n, which sizes the launch).
 cudaError_t scan_exclusive_u32(const uint32_t* in, const uint32_t* gather, uint32_t* out,
                                int64_t n, uint32_t* scratch, uint32_t* total_dev,
-                               cudaStream_t s);
+                               cudaStream_t s, const uint32_t* n_dev = nullptr);
 
 // Stable LSD radix sort of (k[0], v[0]) on bits [begin, end).  When vals_iota the input
 // values are the positions 0..n-1 (v[0] is not read).  With n_keep >= 0 the first pass
 // drops every pair whose key is kSortDrop, and n_keep (the number of other keys, known
 // to the caller) pairs remain for the later passes and in the result.  Returns the index
-// (0 or 1) of the buffer pair that holds the result.
+// (0 or 1) of the buffer pair that holds the result.  n_dev (optional): the pair count
+// in device memory (<= n, which sizes the launches); n_keep_dev (optional, with
+// n_keep >= 0): the kept count in device memory, for the passes after the first.
 constexpr uint32_t kSortDrop = 0xffffffffu;
 int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, int end_bit,
                      bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err,
-                     int64_t n_keep = -1);
+                     int64_t n_keep = -1, const uint32_t* n_dev = nullptr,
+                     const uint32_t* n_keep_dev = nullptr);
 inline int radix_passes(int begin_bit, int end_bit) {
   return end_bit > begin_bit ? (end_bit - begin_bit + 7) / 8 : 0;
 }
 
 // [start, end) of every key value < n_valid present in sorted keys (absent values untouched).
-cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s);
+cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s,
+                         const uint32_t* n_dev = nullptr);
 
 // Patch-Grid sampling (pg.cu): workspace layout for one keyframe.
 struct PgLayout {

@@ -506,24 +506,50 @@ __global__ void __launch_bounds__(256) k_voxel_prep(int64_t n, const float* __re
   }
 }
 
+// The key layout from the bounding box of the occupied voxels, on the device (no host
+// round trip): bits per axis in hdr[15] = by << 8 | bz.  A box that needs more than 31
+// key bits, or a coordinate outside +-2^20 (flag 1 of hdr[7]), sets flag 4: then no
+// Gaussian is eligible (hdr[6] = 0) and nothing merges.
+__global__ void k_merge_plan(int32_t* hdr) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  auto bits_of = [](int64_t range) { int b = 0; while (b < 40 && (int64_t(1) << b) < range) ++b; return b; };
+  const int64_t n_elig = hdr[6];
+  int bx = 0, by = 0, bz = 0;
+  if (n_elig > 0) {
+    bx = bits_of((int64_t)hdr[3] - hdr[0] + 1);
+    by = bits_of((int64_t)hdr[4] - hdr[1] + 1);
+    bz = bits_of((int64_t)hdr[5] - hdr[2] + 1);
+  }
+  if ((hdr[7] & 1) || bx + by + bz > 31) {
+    hdr[7] |= 4;
+    hdr[6] = 0;
+    by = bz = 0;
+  }
+  hdr[15] = (by << 8) | bz;
+}
+
 __global__ void k_voxel_pack(int64_t n, const int32_t* __restrict__ vox, const int32_t* __restrict__ hdr,
-                             int by, int bz, uint32_t* __restrict__ keys) {
+                             uint32_t* __restrict__ keys) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int x = vox[3 * i];
-  if (x == INT32_MIN) { keys[i] = kNoKey; return; }
+  if (x == INT32_MIN || (hdr[7] & 4)) { keys[i] = kNoKey; return; }
+  const int by = hdr[15] >> 8, bz = hdr[15] & 0xff;
   uint32_t rx = (uint32_t)(x - hdr[0]), ry = (uint32_t)(vox[3 * i + 1] - hdr[1]), rz = (uint32_t)(vox[3 * i + 2] - hdr[2]);
   keys[i] = (rx << (by + bz)) | (ry << bz) | rz;
 }
 
-__global__ void k_heads(int64_t n_elig, const uint32_t* __restrict__ keys, uint32_t* __restrict__ flags) {
+__global__ void k_heads(int64_t n, const int32_t* __restrict__ n_elig_p, const uint32_t* __restrict__ keys,
+                        uint32_t* __restrict__ flags) {
+  const int64_t n_elig = min(n, (int64_t)*n_elig_p);
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_elig) return;
   flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
 }
 
-__global__ void k_starts(int64_t n_elig, const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
-                         uint32_t* __restrict__ starts, const uint32_t* n_vox) {
+__global__ void k_starts(int64_t n, const int32_t* __restrict__ n_elig_p, const uint32_t* __restrict__ flags,
+                         const uint32_t* __restrict__ pos, uint32_t* __restrict__ starts, const uint32_t* n_vox) {
+  const int64_t n_elig = min(n, (int64_t)*n_elig_p);
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n_elig && flags[k]) starts[pos[k]] = (uint32_t)k;
   if (k == 0) starts[*n_vox] = (uint32_t)n_elig;
@@ -996,17 +1022,21 @@ __global__ void k_compact(int64_t n, int K3, const float* __restrict__ means, co
   if (obirth) obirth[w] = birth[i];
 }
 
+// The whole merge, asynchronous on s: every launch is sized from n and reads the
+// counts it needs (eligible Gaussians, voxels, pairs) from hdr on the device.  The
+// survivor count lands in hdr[10], the error flags in hdr[7].
 template <typename T>
 cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params& p,
-                    const mgs_gaussians_mut& out, int32_t* partner_out, int32_t* vox_out,
-                    int64_t* n_out_host, MergeWs& ws, cudaStream_t s, int* unsupported) {
+                    const mgs_gaussians_mut& out, int32_t* partner_out, int32_t* vox_out, MergeWs& ws,
+                    cudaStream_t s) {
   const int64_t n = in.n;
   const Geom geo{in.log_scales, in.quats, in.geom_dtype};
   const T* ol = (const T*)in.opacity_logit;
   const T* sh = (const T*)in.sh;
   const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
   const unsigned grid = (unsigned)div_up(n, 256);
-  int32_t init[16] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, INT32_MIN, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  static const int32_t init[16] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, INT32_MIN,
+                                   0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(ws.hdr, init, sizeof(init), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   int32_t* partner = partner_out ? partner_out : ws.partner;
@@ -1014,55 +1044,44 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
   if (e != cudaSuccess) return e;
   int32_t* vox = vox_out ? vox_out : ws.vox;
   k_voxel_prep<T><<<(unsigned)std::min<int64_t>(grid, kPersistBlocks), 256, 0, s>>>(n, in.means, voxel, p, vox, ws.hdr);
+  k_merge_plan<<<1, 32, 0, s>>>(ws.hdr);
+  k_voxel_pack<<<grid, 256, 0, s>>>(n, vox, ws.hdr, ws.keys[0]);
+  count_launch(3);
+  // ineligible Gaussians carry the all-ones key and sort last; eligible keys use <= 31 bits
+  int cur = radix_sort_pairs(ws.keys, ws.perm, n, 0, 32, true, ws.scratch, s, &e);
+  if (e != cudaSuccess) return e;
+  const uint32_t* keys = ws.keys[cur];
+  const uint32_t* perm = ws.perm[cur];
+  const int32_t* n_elig = ws.hdr + 6;
+  k_heads<<<grid, 256, 0, s>>>(n, n_elig, keys, ws.flags);
   count_launch();
-  int32_t h[16];
-  e = cudaMemcpyAsync(h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, s);
+  uint32_t* n_vox = (uint32_t*)(ws.hdr + 8);
+  uint32_t* n_big = (uint32_t*)(ws.hdr + 9);
+  e = scan_exclusive_u32(ws.flags, nullptr, ws.pos, n, ws.scratch, n_vox, s, (const uint32_t*)n_elig);
   if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(s);
+  k_starts<<<grid, 256, 0, s>>>(n, n_elig, ws.flags, ws.pos, ws.starts, n_vox);
+  count_launch(3);  // with the two pairing kernels below
+  const unsigned gv = (unsigned)std::min<int64_t>(std::max<int64_t>(1, div_up(n, 4)), kPersistBlocks);
+  uint32_t* n_pairs = (uint32_t*)(ws.hdr + 11);
+  k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, geo, in.birth, perm, ws.starts, n_vox, p.chi2,
+                                      p.greedy, partner, ws.pairs, n_pairs, ws.big, n_big);
+  uint32_t* n_huge = (uint32_t*)(ws.hdr + 14);
+  k_voxel_pairs_big<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n / 33), 152 * 2), kBlockVoxel, 0, s>>>(
+      in.means, geo, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
+      ws.pairs, n_pairs, ws.huge, n_huge);
+  k_voxel_pairs_huge<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n / 257), 152), kBlockVoxel, 0, s>>>(
+      in.means, geo, in.birth, perm, ws.starts, ws.huge, n_huge, p.chi2, p.greedy, partner, ws.pairs, n_pairs,
+      ws.h_idx, ws.h_mu, ws.h_P, ws.h_match);
+  count_launch();
+  const unsigned gp = (unsigned)div_up(n / 2 + 1, 128);
+  unsigned long long* iters = reinterpret_cast<unsigned long long*>(ws.hdr + 12);
+  if (p.solver == 1)
+    k_merge_pairs<T, 1><<<gp, 128, 0, s>>>(in.means, geo, ws.pairs, n_pairs, ws.mmean, ws.mquat, ws.mlogs, iters);
+  else
+    k_merge_pairs<T, 0><<<gp, 128, 0, s>>>(in.means, geo, ws.pairs, n_pairs, ws.mmean, ws.mquat, ws.mlogs, iters);
+  count_launch();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (h[7]) { *unsupported = 1; return cudaSuccess; }
-  const int64_t n_elig = h[6];
-  if (n_elig >= 2) {
-    auto bits_of = [](int64_t range) { int b = 0; while ((int64_t(1) << b) < range) ++b; return b; };
-    int bx = bits_of((int64_t)h[3] - h[0] + 1), by = bits_of((int64_t)h[4] - h[1] + 1), bz = bits_of((int64_t)h[5] - h[2] + 1);
-    if (bx + by + bz > 31) { *unsupported = 3; return cudaSuccess; }
-    k_voxel_pack<<<grid, 256, 0, s>>>(n, vox, ws.hdr, by, bz, ws.keys[0]);
-    count_launch();
-    int cur = radix_sort_pairs(ws.keys, ws.perm, n, 0, std::max(1, bx + by + bz + 1), true, ws.scratch, s, &e);
-    if (e != cudaSuccess) return e;
-    const uint32_t* keys = ws.keys[cur];
-    const uint32_t* perm = ws.perm[cur];
-    unsigned ge = (unsigned)div_up(n_elig, 256);
-    k_heads<<<ge, 256, 0, s>>>(n_elig, keys, ws.flags);
-    count_launch();
-    uint32_t* n_vox = (uint32_t*)(ws.hdr + 8);
-    uint32_t* n_big = (uint32_t*)(ws.hdr + 9);
-    e = scan_exclusive_u32(ws.flags, nullptr, ws.pos, n_elig, ws.scratch, n_vox, s);
-    if (e != cudaSuccess) return e;
-    k_starts<<<ge, 256, 0, s>>>(n_elig, ws.flags, ws.pos, ws.starts, n_vox);
-    count_launch(3);  // with the two pairing kernels below
-    unsigned gv = (unsigned)std::min<int64_t>(div_up(n_elig, 4), kPersistBlocks);
-    uint32_t* n_pairs = (uint32_t*)(ws.hdr + 11);
-    k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, geo, in.birth, perm, ws.starts, n_vox, p.chi2,
-                                        p.greedy, partner, ws.pairs, n_pairs, ws.big, n_big);
-    uint32_t* n_huge = (uint32_t*)(ws.hdr + 14);
-    k_voxel_pairs_big<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n_elig / 33), 152 * 2), kBlockVoxel, 0, s>>>(
-        in.means, geo, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
-        ws.pairs, n_pairs, ws.huge, n_huge);
-    k_voxel_pairs_huge<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n_elig / 257), 152), kBlockVoxel, 0, s>>>(
-        in.means, geo, in.birth, perm, ws.starts, ws.huge, n_huge, p.chi2, p.greedy, partner, ws.pairs, n_pairs,
-        ws.h_idx, ws.h_mu, ws.h_P, ws.h_match);
-    count_launch();
-    const unsigned gp = (unsigned)div_up(n_elig / 2 + 1, 128);
-    unsigned long long* iters = reinterpret_cast<unsigned long long*>(ws.hdr + 12);
-    if (p.solver == 1)
-      k_merge_pairs<T, 1><<<gp, 128, 0, s>>>(in.means, geo, ws.pairs, n_pairs, ws.mmean, ws.mquat, ws.mlogs, iters);
-    else
-      k_merge_pairs<T, 0><<<gp, 128, 0, s>>>(in.means, geo, ws.pairs, n_pairs, ws.mmean, ws.mquat, ws.mlogs, iters);
-    count_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
   k_keep<<<grid, 256, 0, s>>>(n, partner, in.birth, ws.flags);
   count_launch(2);  // with the compaction below
   uint32_t* n_out_dev = (uint32_t*)(ws.hdr + 10);
@@ -1071,18 +1090,7 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
   k_compact<T><<<grid, 256, 0, s>>>(n, K3, in.means, geo, ol, sh, in.birth, ws.flags, ws.pos, partner,
                                     ws.mmean, ws.mquat, ws.mlogs, out.means, out.log_scales,
                                     out.quats, (T*)out.opacity_logit, (T*)out.sh, out.birth);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return e;
-  *n_out_host = (int64_t)(uint32_t)h[10];
-  unsigned long long it = 0;
-  std::memcpy(&it, h + 12, sizeof(it));
-  last_merge_stats().pairs = (int64_t)(uint32_t)h[11];
-  last_merge_stats().lbfgs_iterations = (int64_t)it;
-  return cudaSuccess;
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -1122,17 +1130,19 @@ size_t merge_workspace_bytes(int64_t n, MergeWs* ws, char* base) {
   return off;
 }
 
-// Returns a cuda error; *unsupported != 0 for a size outside what the kernels handle.
+// Asynchronous merge on s; the survivor count (hdr[10]) and the error flags (hdr[7]:
+// 1 coordinate outside +-2^20, 4 no merge because of it or of a box needing more than
+// 31 key bits) stay in the workspace header, status_dev = &hdr[0] of its 16 ints.
 cudaError_t run_voxel_merge(const mgs_gaussians& in, float voxel, const mgs_merge_params& p,
-                            const mgs_gaussians_mut& out, int32_t* partner, int32_t* vox,
-                            int64_t* n_out_host, char* ws_base, cudaStream_t s, int* unsupported) {
+                            const mgs_gaussians_mut& out, int32_t* partner, int32_t* vox, char* ws_base,
+                            cudaStream_t s, int32_t** hdr_dev) {
   MergeWs ws;
   merge_workspace_bytes(in.n, &ws, ws_base);
-  *unsupported = 0;
+  if (hdr_dev) *hdr_dev = ws.hdr;
   switch (in.attr_dtype) {
-    case MGS_F16: return merge_t<__half>(in, voxel, p, out, partner, vox, n_out_host, ws, s, unsupported);
-    case MGS_BF16: return merge_t<__nv_bfloat16>(in, voxel, p, out, partner, vox, n_out_host, ws, s, unsupported);
-    default: return merge_t<float>(in, voxel, p, out, partner, vox, n_out_host, ws, s, unsupported);
+    case MGS_F16: return merge_t<__half>(in, voxel, p, out, partner, vox, ws, s);
+    case MGS_BF16: return merge_t<__nv_bfloat16>(in, voxel, p, out, partner, vox, ws, s);
+    default: return merge_t<float>(in, voxel, p, out, partner, vox, ws, s);
   }
 }
 

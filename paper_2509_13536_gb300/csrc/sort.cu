@@ -19,9 +19,18 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // --- scan ---
+// n_dev (optional): the item count in device memory, at most n (the grid's size); the
+// kernels below take it in place of n, so a launch sized for a capacity needs no host
+// round trip to learn the count.
+__device__ __forceinline__ int64_t count_of(int64_t n, const uint32_t* n_dev) {
+  return n_dev ? min(n, (int64_t)*n_dev) : n;
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_scan_reduce(const uint32_t* __restrict__ in,
                                                               const uint32_t* __restrict__ gather,
-                                                              int64_t n, uint32_t* __restrict__ sums) {
+                                                              int64_t n, uint32_t* __restrict__ sums,
+                                                              const uint32_t* __restrict__ n_dev) {
+  n = count_of(n, n_dev);
   int64_t base = (int64_t)blockIdx.x * kSortTile;
   uint32_t acc = 0;
 #pragma unroll
@@ -80,7 +89,8 @@ __global__ void __launch_bounds__(1024) k_scan_spine(uint32_t* sums, int64_t nb,
 __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* in,
                                                             const uint32_t* __restrict__ gather,
                                                             int64_t n, const uint32_t* __restrict__ sums,
-                                                            uint32_t* out) {
+                                                            uint32_t* out, const uint32_t* __restrict__ n_dev) {
+  n = count_of(n, n_dev);
   __shared__ uint32_t tile[kSortTile];
   __shared__ uint32_t s[kWarps];
   int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -126,7 +136,9 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* in,
 // come in long runs).
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                              int64_t n, int shift, uint32_t mask, int nb,
-                                                             uint32_t* __restrict__ hist, bool drop) {
+                                                             uint32_t* __restrict__ hist, bool drop,
+                                                             const uint32_t* __restrict__ n_dev) {
+  n = count_of(n, n_dev);
   __shared__ uint32_t h[kWarps][256];
   const int t = threadIdx.x, w = t >> 5;
 #pragma unroll
@@ -183,7 +195,8 @@ template <bool kBallot>
 __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
     uint32_t mask, int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, bool drop) {
+    uint32_t* __restrict__ vout, bool drop, const uint32_t* __restrict__ n_dev) {
+  n = count_of(n, n_dev);
   constexpr int kPerWarp = kSortTile / kWarps;  // 512
   constexpr int kRounds = kPerWarp / 32;        // 16
   __shared__ uint32_t s_wcnt[kWarps][256];      // per-warp digit counts, then exclusive offsets
@@ -285,7 +298,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
 // Tile ranges of the sorted keys: four keys per thread (one vector load), neighbours
 // at the ends from the adjacent threads' keys.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, int64_t n, uint32_t n_valid,
-                         uint2* __restrict__ ranges) {
+                         uint2* __restrict__ ranges, const uint32_t* __restrict__ n_dev) {
+  n = count_of(n, n_dev);
   const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (k0 >= n) return;
   uint32_t kk[4];
@@ -320,22 +334,24 @@ int64_t sort_scratch_words(int64_t n) {
 }
 
 cudaError_t scan_exclusive_u32(const uint32_t* in, const uint32_t* gather, uint32_t* out,
-                               int64_t n, uint32_t* scratch, uint32_t* total_dev, cudaStream_t s) {
+                               int64_t n, uint32_t* scratch, uint32_t* total_dev, cudaStream_t s,
+                               const uint32_t* n_dev) {
   if (n <= 0) {
     if (total_dev) return cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
     return cudaSuccess;
   }
   int64_t nb = div_up(n, kSortTile);
   uint32_t* sums = scratch;
-  k_scan_reduce<<<(unsigned)nb, kSortThreads, 0, s>>>(in, gather, n, sums);
+  k_scan_reduce<<<(unsigned)nb, kSortThreads, 0, s>>>(in, gather, n, sums, n_dev);
   k_scan_spine<<<1, 1024, 0, s>>>(sums, nb, total_dev);
-  k_scan_down<<<(unsigned)nb, kSortThreads, 0, s>>>(in, gather, n, sums, out);
+  k_scan_down<<<(unsigned)nb, kSortThreads, 0, s>>>(in, gather, n, sums, out, n_dev);
   count_launch(3);
   return cudaGetLastError();
 }
 
 int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, int end_bit,
-                     bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err, int64_t n_keep) {
+                     bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err, int64_t n_keep,
+                     const uint32_t* n_dev, const uint32_t* n_keep_dev) {
   *err = cudaSuccess;
   int cur = 0;
   if (n <= 0) return 0;
@@ -347,7 +363,7 @@ int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, i
     if (n <= 0) break;
     const int nb = (int)div_up(n, kSortTile);
     const uint32_t mask = (1u << std::min(8, end_bit - shift)) - 1u;
-    k_radix_hist<<<nb, kSortThreads, 0, s>>>(k[cur], n, shift, mask, nb, hist, drop);
+    k_radix_hist<<<nb, kSortThreads, 0, s>>>(k[cur], n, shift, mask, nb, hist, drop, n_dev);
     count_launch(2);
     *err = scan_exclusive_u32(hist, nullptr, hist, (int64_t)256 * nb, spine, nullptr, s);
     if (*err != cudaSuccess) return cur;
@@ -358,14 +374,17 @@ int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, i
     // per round and keep the match instruction.
     if (mask == 0xffu && !drop && shift < 24)
       k_radix_scatter<true><<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, mask, nb, hist, k[cur ^ 1],
-                                                        v[cur ^ 1], drop);
+                                                        v[cur ^ 1], drop, n_dev);
     else
       k_radix_scatter<false><<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, mask, nb, hist, k[cur ^ 1],
-                                                         v[cur ^ 1], drop);
+                                                         v[cur ^ 1], drop, n_dev);
     cur ^= 1;
     first = false;
     if (drop) {
-      n = n_keep;
+      // the kept keys: a host count shrinks the grid, a device count keeps the grid and
+      // bounds the kernels
+      if (n_keep_dev) n_dev = n_keep_dev;
+      else n = n_keep;
       drop = false;
     }
     *err = cudaGetLastError();
@@ -378,9 +397,10 @@ int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, i
   return cur;
 }
 
-cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s) {
+cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s,
+                         const uint32_t* n_dev) {
   if (n <= 0) return cudaSuccess;
-  k_ranges<<<(unsigned)div_up(div_up(n, 4), 256), 256, 0, s>>>(keys, n, n_valid, ranges);
+  k_ranges<<<(unsigned)div_up(div_up(n, 4), 256), 256, 0, s>>>(keys, n, n_valid, ranges, n_dev);
   count_launch();
   return cudaGetLastError();
 }

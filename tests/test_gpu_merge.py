@@ -263,3 +263,20 @@ def test_merge_voxels_of_300_and_1000_members(orc, greedy):
     assert sorted(counts)[-2:][0] > 256  # both big voxels are still past the block path
     pairs, n = compare_merge(orc, sc, 0.02, greedy=greedy)
     assert pairs > (100 if greedy else 2)
+
+
+def test_async_merge_matches_the_synchronous_one(orc):
+    """mgs_voxel_merge_async (no host round trip) writes what mgs_voxel_merge writes and
+    its status carries the survivor count."""
+    rng = np.random.default_rng(12)
+    sc = _voxel_scene(rng, 60, 6)
+    g = api.Gaussians.from_scene(sc, "cuda")
+    out_s, part_s, vox_s = api.mgs_voxel_merge(g, 0.02)
+    status = torch.zeros(2, dtype=torch.int32, pin_memory=True)
+    out_a, part_a, vox_a = api.mgs_voxel_merge(g, 0.02, status=status)
+    torch.cuda.synchronize()
+    k = int(status[0])
+    assert k == out_s.n and int(status[1]) == 0
+    assert torch.equal(part_a, part_s) and torch.equal(vox_a, vox_s)
+    for a, b in zip(out_s.params(), out_a.params()):
+        assert torch.equal(a, b[:k])

@@ -189,3 +189,33 @@ def test_workspace_regrowth_and_determinism(orc):
     api.mgs_render(g, cams, b, ws)
     torch.cuda.synchronize()
     assert torch.equal(a[0].rgb, b[0].rgb) and torch.equal(a[0].alpha, b[0].alpha)
+
+
+def test_async_render_matches_and_reports_overflow():
+    """mgs_render_async (no host round trip) gives the images and the backward state of
+    mgs_render bit for bit; with a workspace too small for its keys it blends nothing,
+    reports the overflow through its status, and the binding's check() raises."""
+    scene, cams = sg.workload("box10k")
+    g = api.Gaussians.from_scene(scene, "cuda")
+    ref, ws0 = api.render(g, cams)
+    ws = api.RenderWorkspace("cuda")
+    api.mgs_render(g, cams, api.new_images(cams), ws)  # sizes the workspace
+    out = api.new_images(cams)
+    assert api.mgs_render(g, cams, out, ws, sync=False) == -1
+    assert ws.check() == ws0.n_keys
+    for plane in ("rgb", "depth", "alpha"):
+        assert torch.equal(getattr(out[0], plane), getattr(ref[0], plane)), plane
+    cot_np, dL = _gpu.cotangents(cams, 4)
+    a = api.render_backward(g, cams, dL, ws)
+    b = api.render_backward(g, cams, dL, ws0)
+    torch.cuda.synchronize()
+    for x, y in zip(a.tensors(), b.tensors()):
+        assert torch.allclose(x, y, rtol=1e-5, atol=1e-7 * float(y.abs().max()))
+    small = api.RenderWorkspace("cuda")
+    small.ensure(g.n, cams, ws0.n_keys // 2)
+    out = api.new_images(cams)
+    api.mgs_render(g, cams, out, small, sync=False)
+    with pytest.raises(Exception, match="exceeded"):
+        small.check()
+    assert int(small.status[1]) == 1 and int(small.status[0]) == ws0.n_keys
+    assert float(out[0].alpha.abs().max()) == 0.0  # nothing blended
