@@ -605,7 +605,7 @@ def run_ours(args):
         loss_iso = torch.zeros(1, device=dev)
         state.update(ws=ws, loss=loss_v, loss_views=loss_v, loss_iso=loss_iso)
 
-        ws.headroom = 1.5
+        ws.headroom = 1.1
 
         def step():
             state["step"] += 1

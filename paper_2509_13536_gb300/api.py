@@ -624,7 +624,7 @@ class MappingStep:
         self.iso_ws = torch.empty(max(1, L.mgs_iso_loss_workspace_size(g.n)), dtype=torch.uint8, device=dev)
         self.step_count = 0
         self._dL = [Image(self.g_rgb[v], self.g_depth[v], None) for v in range(V)]
-        self.ws.headroom = 1.5
+        self.ws.headroom = 1.1
 
     def __call__(self, target_rgb: torch.Tensor, target_depth: Optional[torch.Tensor] = None):
         """One step against keyframe images target_rgb [V,3,H,W] (and target_depth [V,H,W])."""

@@ -139,8 +139,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
                                                              uint32_t* __restrict__ hist, bool drop,
                                                              const uint32_t* __restrict__ n_dev) {
   n = count_of(n, n_dev);
-  __shared__ uint32_t h[kWarps][256];
   const int t = threadIdx.x, w = t >> 5;
+  if ((int64_t)blockIdx.x * kSortTile >= n) {  // past the device count: an empty column
+    hist[(int64_t)t * nb + blockIdx.x] = 0;
+    return;
+  }
+  __shared__ uint32_t h[kWarps][256];
 #pragma unroll
   for (int ww = 0; ww < kWarps; ++ww) h[ww][t] = 0;
   __syncthreads();
@@ -197,6 +201,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     uint32_t mask, int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, bool drop, const uint32_t* __restrict__ n_dev) {
   n = count_of(n, n_dev);
+  if ((int64_t)blockIdx.x * kSortTile >= n) return;  // past the device count: nothing to move
   constexpr int kPerWarp = kSortTile / kWarps;  // 512
   constexpr int kRounds = kPerWarp / 32;        // 16
   __shared__ uint32_t s_wcnt[kWarps][256];      // per-warp digit counts, then exclusive offsets
