@@ -66,6 +66,7 @@ def parse():
     p.add_argument("--views", type=int, default=8, help="keyframes per step (8 = the benchmark workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-precision", action="store_true")
+    p.add_argument("--precision-modes", nargs="*", default=None, help="subset of the storage layouts to measure")
     p.add_argument("--no-eq12", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-requests", type=int, default=2000)
@@ -233,11 +234,16 @@ def precision_leg(args, api, torch, scene, cams, make_step, dev):
     ref_g = oracle.render_backward(scene, cam, *cot, tiles=tiles)
     ok = mask & (ref["flags"] == 0)
     out = {}
-    modes = (("f32", torch.float32, torch.float32), ("f16", torch.float16, torch.float32),
-             ("bf16", torch.bfloat16, torch.float32), ("f16_all", torch.float16, torch.float16),
-             ("bf16_all", torch.bfloat16, torch.bfloat16))
-    for name, dt, gdt in modes:
-        g = api.Gaussians.from_scene(scene, dev, dt, gdt)
+    f32, f16, bf16 = torch.float32, torch.float16, torch.bfloat16
+    # (name, opacity + SH, log-scales, quaternions)
+    modes = (("f32", f32, f32, f32), ("f16", f16, f32, f32), ("f16_quat16", f16, f32, f16),
+             ("f16_logscale16", f16, f16, f32), ("f16_all", f16, f16, f16),
+             ("bf16", bf16, f32, f32), ("bf16_quat16", bf16, f32, bf16), ("bf16_quatf16", bf16, f32, f16),
+             ("bf16_all", bf16, bf16, bf16))
+    if args.precision_modes:
+        modes = tuple(m for m in modes if m[0] in args.precision_modes)
+    for name, dt, gdt, qdt in modes:
+        g = api.Gaussians.from_scene(scene, dev, dt, gdt, qdt)
         imgs, wsp = api.render(g, [cam])
         dL = [api.Image(*(torch.from_numpy(x).to(dev) for x in cot))]
         grads = api.render_backward(g, [cam], dL, wsp)
@@ -271,8 +277,9 @@ def precision_leg(args, api, torch, scene, cams, make_step, dev):
         del g, step, st
         torch.cuda.empty_cache()
     out["sample"] = f"keyframe 0, {len(tiles)} seeded tiles ({int(mask.sum())} px); oracle fed the FP32 attributes"
-    out["modes"] = ("f16/bf16: opacity and SH stored reduced, means/log-scales/quaternions f32; "
-                    "*_all: log-scales and quaternions reduced too")
+    out["modes"] = ("f16/bf16: opacity and SH stored reduced, means, log-scales and quaternions f32; "
+                    "*_quat16: quaternions reduced too (bf16_quatf16: quaternions f16); *_logscale16: log-scales "
+                    "reduced too; *_all: log-scales and quaternions reduced")
     return out
 
 

@@ -56,8 +56,8 @@ typedef struct {
   int64_t n;
   int32_t sh_degree;   /* 0..3 */
   int32_t attr_dtype;  /* mgs_dtype of opacity_logit and sh */
-  int32_t geom_dtype;  /* mgs_dtype of log_scales and quats */
-  int32_t reserved;
+  int32_t geom_dtype;  /* mgs_dtype of log_scales */
+  int32_t quat_dtype;  /* mgs_dtype of quats */
   const float* means;
   const void* log_scales;
   const void* quats;
@@ -71,7 +71,7 @@ typedef struct {
   int32_t sh_degree;
   int32_t attr_dtype;
   int32_t geom_dtype;
-  int32_t reserved;
+  int32_t quat_dtype;
   float* means;
   void* log_scales;
   void* quats;

@@ -32,7 +32,7 @@ EXPORTS = ["mgs_render_workspace_size", "mgs_render", "mgs_render_backward", "mg
 
 class mgs_gaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("attr_dtype", C.c_int32),
-                ("geom_dtype", C.c_int32), ("reserved", C.c_int32), ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("geom_dtype", C.c_int32), ("quat_dtype", C.c_int32), ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("birth", C.c_void_p)]
 
 

@@ -63,13 +63,15 @@ class Gaussians:
         return self.log_scales.dtype
 
     @staticmethod
-    def from_scene(scene, device="cuda", attr_dtype=torch.float32, geom_dtype=torch.float32) -> "Gaussians":
-        """Upload a scene; opacity/SH stored as attr_dtype, log-scales/quaternions as
-        geom_dtype (means are always f32)."""
+    def from_scene(scene, device="cuda", attr_dtype=torch.float32, geom_dtype=torch.float32,
+                   quat_dtype=None) -> "Gaussians":
+        """Upload a scene; opacity/SH stored as attr_dtype, log-scales as geom_dtype,
+        quaternions as quat_dtype (default: geom_dtype); means are always f32."""
         d = torch.device(device)
         f = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(d).to(dt).contiguous()
         return Gaussians(f(scene.means, torch.float32), f(scene.log_scales, geom_dtype),
-                         f(scene.quats, geom_dtype), f(scene.opacity_logit, attr_dtype),
+                         f(scene.quats, geom_dtype if quat_dtype is None else quat_dtype),
+                         f(scene.opacity_logit, attr_dtype),
                          f(scene.sh, attr_dtype), torch.from_numpy(scene.birth.astype(np.int64)).to(d))
 
     def params(self):
@@ -78,10 +80,10 @@ class Gaussians:
     def struct(self) -> _abi.mgs_gaussians:
         if self.means.dtype != torch.float32:
             raise ValueError("means must be float32")
-        if self.quats.dtype != self.log_scales.dtype or self.opacity_logit.dtype != self.sh.dtype:
-            raise ValueError("log_scales/quats and opacity_logit/sh must each share one dtype")
+        if self.opacity_logit.dtype != self.sh.dtype:
+            raise ValueError("opacity_logit and sh must share one dtype")
         return _abi.mgs_gaussians(self.n, self.sh_degree, _DTYPES[self.sh.dtype], _DTYPES[self.log_scales.dtype],
-                                  0, _ptr(self.means),
+                                  _DTYPES[self.quats.dtype], _ptr(self.means),
                                   _ptr(self.log_scales), _ptr(self.quats), _ptr(self.opacity_logit),
                                   _ptr(self.sh), _ptr(self.birth))
 

@@ -130,7 +130,7 @@ cudaError_t launch_adam(const mgs_gaussians_mut& p, const mgs_grads& g, const mg
   struct Seg { void* p; int dt; float* g; float* m; float* v; int64_t n; } list[5] = {
       {p.means, MGS_F32, g.means, m.means, v.means, 3 * n},
       {p.log_scales, p.geom_dtype, g.log_scales, m.log_scales, v.log_scales, 3 * n},
-      {p.quats, p.geom_dtype, g.quats, m.quats, v.quats, 4 * n},
+      {p.quats, p.quat_dtype, g.quats, m.quats, v.quats, 4 * n},
       {p.opacity_logit, p.attr_dtype, g.opacity_logit, m.opacity_logit, v.opacity_logit, n},
       {p.sh, p.attr_dtype, g.sh, m.sh, v.sh, K3 * n}};
   AdamTable tab{};

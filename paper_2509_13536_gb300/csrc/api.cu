@@ -183,6 +183,7 @@ std::string check_gaussians(const mgs_gaussians* g, bool need_birth) {
   if (g->sh_degree < 0 || g->sh_degree > 3) return "sh_degree must be 0..3";
   if (g->attr_dtype < MGS_F32 || g->attr_dtype > MGS_BF16) return "attr_dtype must be MGS_F32, MGS_F16 or MGS_BF16";
   if (g->geom_dtype < MGS_F32 || g->geom_dtype > MGS_BF16) return "geom_dtype must be MGS_F32, MGS_F16 or MGS_BF16";
+  if (g->quat_dtype < MGS_F32 || g->quat_dtype > MGS_BF16) return "quat_dtype must be MGS_F32, MGS_F16 or MGS_BF16";
   if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logit || !g->sh))
     return "parameter pointer is NULL";
   if (need_birth && g->n > 0 && !g->birth) return "birth is NULL";
@@ -486,8 +487,8 @@ static mgs_status merge_args(const mgs_gaussians* in, float voxel_size, const mg
   if (!(p->chi2 > 0)) return fail(MGS_ERR_INVALID, "chi2 must be > 0");
   if (p->solver != 0 && p->solver != 1) return fail(MGS_ERR_INVALID, "solver must be 0 (closed form) or 1 (L-BFGS)");
   if (out->n < in->n || out->sh_degree != in->sh_degree || out->attr_dtype != in->attr_dtype ||
-      out->geom_dtype != in->geom_dtype)
-    return fail(MGS_ERR_INVALID, "out must have capacity >= n and the same sh_degree / attr_dtype / geom_dtype");
+      out->geom_dtype != in->geom_dtype || out->quat_dtype != in->quat_dtype)
+    return fail(MGS_ERR_INVALID, "out must have capacity >= n and the same sh_degree and storage types");
   if (in->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logit || !out->sh))
     return fail(MGS_ERR_INVALID, "output pointer is NULL");
   if (in->n >= (int64_t)INT32_MAX) return fail(MGS_ERR_UNSUPPORTED, "n must be < 2^31");
@@ -559,8 +560,8 @@ mgs_status mgs_adam_step(const mgs_gaussians_mut* params, const mgs_grads* grads
   if (params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3 || step < 1)
     return fail(MGS_ERR_INVALID, "need n >= 0, sh_degree 0..3, step >= 1");
   if (params->attr_dtype < MGS_F32 || params->attr_dtype > MGS_BF16 || params->geom_dtype < MGS_F32 ||
-      params->geom_dtype > MGS_BF16)
-    return fail(MGS_ERR_INVALID, "bad attr_dtype / geom_dtype");
+      params->geom_dtype > MGS_BF16 || params->quat_dtype < MGS_F32 || params->quat_dtype > MGS_BF16)
+    return fail(MGS_ERR_INVALID, "bad attr_dtype / geom_dtype / quat_dtype");
   if (!(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
     return fail(MGS_ERR_INVALID, "need 0 <= beta < 1 and eps > 0");
   {
@@ -571,7 +572,7 @@ mgs_status mgs_adam_step(const mgs_gaussians_mut* params, const mgs_grads* grads
                           m->means, m->log_scales, m->quats, m->opacity_logit, m->sh,
                           v->means, v->log_scales, v->quats, v->opacity_logit, v->sh, params->means,
                           params->geom_dtype == MGS_F32 ? params->log_scales : nullptr,
-                          params->geom_dtype == MGS_F32 ? params->quats : nullptr,
+                          params->quat_dtype == MGS_F32 ? params->quats : nullptr,
                           params->attr_dtype == MGS_F32 ? params->opacity_logit : nullptr,
                           params->attr_dtype == MGS_F32 ? params->sh : nullptr};
     for (const void* q : f32s)

@@ -79,11 +79,12 @@ __device__ __forceinline__ void st(float* p, float x) { *p = x; }
 __device__ __forceinline__ void st(__half* p, float x) { *p = __float2half_rn(x); }
 __device__ __forceinline__ void st(__nv_bfloat16* p, float x) { *p = __float2bfloat16_rn(x); }
 
-// Geometry group of a map (log-scales, quaternions) with its runtime storage type.
+// Geometry group of a map (log-scales, quaternions) with their runtime storage types.
 struct Geom {
   const void* ls;
   const void* qs;
-  int dt;
+  int dt;   // log-scales
+  int qdt;  // quaternions
 };
 
 // runtime-typed access for the small geometry groups (log-scales, quaternions)

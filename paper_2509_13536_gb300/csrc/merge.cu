@@ -57,7 +57,7 @@ __device__ __forceinline__ bool older(uint64_t ba, int64_t a, uint64_t bb, int64
 }
 
 __device__ __forceinline__ void load_qs(const Geom& geo, int64_t i, float q[4], float s[3]) {
-  for (int k = 0; k < 4; ++k) q[k] = ld_dt(geo.qs, geo.dt, 4 * i + k);
+  for (int k = 0; k < 4; ++k) q[k] = ld_dt(geo.qs, geo.qdt, 4 * i + k);
   float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   for (int k = 0; k < 4; ++k) q[k] *= n;
   for (int k = 0; k < 3; ++k) s[k] = expf(ld_dt(geo.ls, geo.dt, 3 * i + k));
@@ -1013,10 +1013,10 @@ __global__ void k_compact(int64_t n, int K3, const float* __restrict__ means, co
   int64_t w = pos[i];
   if (partner[i] >= 0) {
     for (int k = 0; k < 3; ++k) { omeans[3 * w + k] = mmean[3 * i + k]; st_dt(ols, geo.dt, 3 * w + k, mlogs[3 * i + k]); }
-    for (int k = 0; k < 4; ++k) st_dt(oqs, geo.dt, 4 * w + k, mquat[4 * i + k]);
+    for (int k = 0; k < 4; ++k) st_dt(oqs, geo.qdt, 4 * w + k, mquat[4 * i + k]);
   } else {
     for (int k = 0; k < 3; ++k) { omeans[3 * w + k] = means[3 * i + k]; cp_dt(ols, geo.ls, geo.dt, 3 * w + k, 3 * i + k); }
-    for (int k = 0; k < 4; ++k) cp_dt(oqs, geo.qs, geo.dt, 4 * w + k, 4 * i + k);
+    for (int k = 0; k < 4; ++k) cp_dt(oqs, geo.qs, geo.qdt, 4 * w + k, 4 * i + k);
   }
   ool[w] = ol[i];
   if (obirth) obirth[w] = birth[i];
@@ -1030,7 +1030,7 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
                     const mgs_gaussians_mut& out, int32_t* partner_out, int32_t* vox_out, MergeWs& ws,
                     cudaStream_t s) {
   const int64_t n = in.n;
-  const Geom geo{in.log_scales, in.quats, in.geom_dtype};
+  const Geom geo{in.log_scales, in.quats, in.geom_dtype, in.quat_dtype};
   const T* ol = (const T*)in.opacity_logit;
   const T* sh = (const T*)in.sh;
   const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;

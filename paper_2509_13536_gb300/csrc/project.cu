@@ -25,7 +25,7 @@ __device__ __forceinline__ void load_gauss(int64_t g, const float* means, const 
                                            GaussPre& G) {
   for (int k = 0; k < 3; ++k) G.mu[k] = __ldg(means + 3 * g + k);
   float q[4];
-  for (int k = 0; k < 4; ++k) q[k] = ld_dt(geo.qs, geo.dt, 4 * g + k);
+  for (int k = 0; k < 4; ++k) q[k] = ld_dt(geo.qs, geo.qdt, 4 * g + k);
   G.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   float inv = 1.f / G.qnorm;
   for (int k = 0; k < 4; ++k) G.qn[k] = q[k] * inv;
@@ -425,7 +425,7 @@ cudaError_t launch_pre_t(int deg, int64_t N, const mgs_gaussians& g, const ViewT
                          float4* rec, uint2* rects, uint32_t* touched, uint32_t* dkeys,
                          unsigned long long* counters, cudaStream_t s) {
   unsigned grid = (unsigned)div_up(N, 256);
-  const Geom geo{g.log_scales, g.quats, g.geom_dtype};
+  const Geom geo{g.log_scales, g.quats, g.geom_dtype, g.quat_dtype};
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
@@ -443,7 +443,7 @@ cudaError_t launch_bwd_t(int deg, int64_t N, const mgs_gaussians& g, const ViewT
                          const float4* moments, const uint32_t* touched, const uint2* rects,
                          const mgs_grads& gr, cudaStream_t s) {
   unsigned grid = (unsigned)div_up(N, 128);
-  const Geom geo{g.log_scales, g.quats, g.geom_dtype};
+  const Geom geo{g.log_scales, g.quats, g.geom_dtype, g.quat_dtype};
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
@@ -461,7 +461,7 @@ cudaError_t launch_proj_t(int deg, int64_t N, const mgs_gaussians& g, const View
                           float* conic, float* rgb, float* depth, int32_t* radius, int32_t* rect,
                           cudaStream_t s) {
   unsigned grid = (unsigned)div_up(N, 256);
-  const Geom geo{g.log_scales, g.quats, g.geom_dtype};
+  const Geom geo{g.log_scales, g.quats, g.geom_dtype, g.quat_dtype};
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
