@@ -12,6 +12,22 @@ namespace mgs {
 constexpr int kTile = MGS_TILE;             // tile edge, px
 constexpr int kTilePix = kTile * kTile;     // 256 pixels = 256 threads per tile CTA
 constexpr float kAlphaMin = 1.0f / 255.0f;  // skip below
+constexpr float kLog2AlphaMin = -7.994353436858858f;  // log2(1/255): the same test on the base-2 exponent of alpha
+constexpr float kLog2_255 = 7.994353436858858f;
+
+// Whether the 0.99 clamp can bind for a projected record (A', B', C', log2 o): alpha =
+// 2^e, e = p2 + log2 o, p2 = A' dx^2 + B' dx dy + C' dy^2 <= 0.  The blends evaluate e with
+// five roundings, which move it by at most 3 eps tr' |d|^2 + eps |log2 o| (tr' = -(A' + C');
+// |B'| |dx dy| <= tr' |d|^2 / 2), while -p2 >= (det' / tr') |d|^2.  When tr'^2 <= 1e5 det'
+// the first bound is far below -p2, so the evaluated e stays at or below log2 o (1 - 2 eps),
+// and with o <= 0.98 the evaluated alpha (ex2.approx, relative error ~2^-22) stays below
+// 0.99: the clamp and its zero derivative never apply.  Blend loops skip both for groups
+// of such entries.
+__device__ __forceinline__ bool clamp_possible(float4 r1) {
+  const float tr = -(r1.x + r1.z);
+  const float det = __fsub_rn(__fmul_rn(r1.x, r1.z), __fmul_rn(0.25f, __fmul_rn(r1.y, r1.y)));
+  return !(r1.w <= -0.029146346f) || !(__fmul_rn(tr, tr) <= __fmul_rn(1e5f, det));  // log2(0.98)
+}
 constexpr float kAlphaMax = 0.99f;          // clamp
 constexpr float kTStop = 1e-4f;             // stop once T falls below
 constexpr float kDilation = 0.3f;           // px^2 added to the 2D covariance diagonal
@@ -217,22 +233,26 @@ __device__ __forceinline__ void sh_basis(const float d[3], float* Y, float (*dY)
   }
 }
 
-// Fragment evaluation shared by the forward and backward blend so that both take
-// identical decisions.  xy: Gaussian centre relative to the tile origin; co: conic
-// pre-scaled by -log2(e)/2 (A, C) and -log2(e) (B), plus opacity.  Returns the
-// exponent in base 2 (> 0 means "skip").
+// Fragment evaluation in the blend kernels' rounding (the counting pass uses it; the
+// blends evaluate the same operations on packed pairs).  xy: Gaussian centre relative
+// to the tile origin; co: conic pre-scaled by -log2(e)/2 (A, C) and -log2(e) (B), plus
+// log2(opacity).  Returns the base-2 exponent of alpha before the clamp:
+// alpha = min(0.99, 2^e), and the Gaussian passes the 1/255 cutoff iff e >= log2(1/255).
+// The exponent of a positive-definite conic is never positive, so there is no separate
+// "exponent > 0" test: a float32 evaluation that comes out positive is rounding near the
+// centre, where the exact alpha is the opacity.
 __device__ __forceinline__ float frag_exp2(float2 xy, float4 co, float pxf, float pyf, float& dx,
                                            float& dy) {
   dx = __fsub_rn(xy.x, pxf);
   dy = __fsub_rn(xy.y, pyf);
   float t = __fmaf_rn(co.x, dx, __fmul_rn(co.y, dy));
-  return __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(co.z, dy), dy));
+  return __fmaf_rn(t, dx, __fmaf_rn(__fmul_rn(co.z, dy), dy, co.w));
 }
 
 // ---- exact tile culling ----------------------------------------------------------
 // A Gaussian can only pass the alpha >= 1/255 test where o 2^p2 >= 1/255, i.e. inside
 // the ellipse  a dx^2 + 2 b dx dy + c dy^2 <= kappa  with (a, 2b, c) = -(A', B', C')
-// from the projected record and kappa = log2(255 o).  Tiles of the 3-sigma rect that
+// from the projected record and kappa = log2(255 o) = log2(o) + log2(255).  Tiles of the 3-sigma rect that
 // this ellipse does not reach hold no pixel where the Gaussian contributes, so
 // dropping them changes no output.  The ellipse is enlarged (kappa by 1e-4 relative +
 // 1e-3, extents by 1e-2 px), far beyond the error of the approximate MUFU
@@ -256,7 +276,7 @@ __device__ __forceinline__ Cull make_cull(float4 r0, float4 r1) {
   q.a = -r1.x;
   q.b = __fmul_rn(-0.5f, r1.y);
   q.c = -r1.z;
-  q.kappa = __fmaf_rn(__log2f(__fmul_rn(255.f, r1.w)), 1.0001f, 1e-3f);
+  q.kappa = __fmaf_rn(__fadd_rn(r1.w, kLog2_255), 1.0001f, 1e-3f);  // r1.w = log2(o)
   q.none = !(q.kappa > 0.f);
   q.det = __fsub_rn(__fmul_rn(q.a, q.c), __fmul_rn(q.b, q.b));
   q.full = !(q.det > 0.f) || !(q.a > 0.f) || !(q.c > 0.f);

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
         load_sh<DEG>(g, sh, c);  // per drawn view: the coefficients come from L1 after the first
         colour<DEG>(c, P.dir, raw);
         float4 r0 = make_float4(P.u_hi, P.v_hi, P.u_lo, P.v_lo);
-        float4 r1 = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, G.o);
+        float4 r1 = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, log2f(G.o));
         rec[3 * item + 0] = r0;
         rec[3 * item + 1] = r1;
         rec[3 * item + 2] = make_float4(fmaxf(0.f, raw[0]), fmaxf(0.f, raw[1]), fmaxf(0.f, raw[2]), P.tz);

@@ -45,9 +45,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant
                                                           const uint2* __restrict__ ranges) {
   __shared__ float4 s_xy[kTilePix];   // (x, x, y, y) tile-relative centre
   __shared__ float4 s_ab[kTilePix];   // (A, A, B, B) scaled conic
-  __shared__ float4 s_co[kTilePix];   // (C, C, o, o)
+  __shared__ float4 s_co[kTilePix];   // (C, C, log2 o, log2 o)
   __shared__ float4 s_rg[kTilePix];   // (r, r, g, g)
   __shared__ float4 s_bd[kTilePix];   // (b, b, depth, depth)
+  __shared__ uint32_t s_clamp[kFwdThreads / 32];  // per warp: its bits of the batch's 32 group flags
   const int tile = blockIdx.x;
   const View& V = vt.v[view_of_tile(vt, tile)];
   const int local = tile - V.tile_base;
@@ -62,12 +63,15 @@ __global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant
   const int n = (int)(range.y - range.x);
   float2 T = f2(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f);
   float2 C0 = f2(0.f, 0.f), C1 = C0, C2 = C0, D = C0;
+  const float2 m1 = f2(-1.f, -1.f);
   uint32_t last0 = 0, last1 = 0;
   for (int b = 0; b < n; b += kTilePix) {
     if (__syncthreads_count(T.x >= kTStop || T.y >= kTStop) == 0) break;
+    uint32_t clamp_bits = 0;  // bit g: the clamp may bind for an entry of group g (entries 8g..8g+7)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int k = t + h * kFwdThreads, e = b + k;
+      bool cl = false;
       if (e < n) {
         const uint32_t idx = vals[range.x + e];
         const float4 r0 = rec[3 * (size_t)idx], r1 = rec[3 * (size_t)idx + 1], r2 = rec[3 * (size_t)idx + 2];
@@ -77,24 +81,35 @@ __global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant
         s_co[k] = make_float4(r1.z, r1.z, r1.w, r1.w);
         s_rg[k] = make_float4(r2.x, r2.x, r2.y, r2.y);
         s_bd[k] = make_float4(r2.z, r2.z, r2.w, r2.w);
+        cl = clamp_possible(r1);
       }
+      // lanes 8q..8q+7 of warp w hold group 4 w + 16 h + q
+      const uint32_t bal = __ballot_sync(0xffffffffu, cl);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if ((bal >> (8 * q)) & 0xffu) clamp_bits |= 1u << (4 * (t >> 5) + 16 * h + q);
     }
+    if ((t & 31) == 0) s_clamp[t >> 5] = clamp_bits;
     __syncthreads();
+    uint32_t clamp_mask = 0;
+#pragma unroll
+    for (int w = 0; w < kFwdThreads / 32; ++w) clamp_mask |= s_clamp[w];
     const int cnt = min(kTilePix, n - b);
     for (int j0 = 0; j0 < cnt; j0 += 8) {
       if (__all_sync(0xffffffffu, T.x < kTStop && T.y < kTStop)) break;
       const int jn = min(8, cnt - j0);
-      auto entry = [&](int jj) {
+      auto entry = [&](int jj, auto clampc) {
           const int j = j0 + jj;
           const float4 xy = s_xy[j], ab = s_ab[j], co = s_co[j];
           const float2 dx = __fadd2_rn(f2(xy.x, xy.y), npx);
           const float2 dy = __fadd2_rn(f2(xy.z, xy.w), npy);
           const float2 tt = __ffma2_rn(f2(ab.x, ab.y), dx, __fmul2_rn(f2(ab.z, ab.w), dy));
-          const float2 p2 = __ffma2_rn(tt, dx, __fmul2_rn(__fmul2_rn(f2(co.x, co.y), dy), dy));
-          const float2 a = __fmul2_rn(f2(co.z, co.w), f2(ex2_approx(p2.x), ex2_approx(p2.y)));
-          const float2 al = f2(fminf(kAlphaMax, a.x), fminf(kAlphaMax, a.y));
-          const bool on0 = T.x >= kTStop && p2.x <= 0.f && al.x >= kAlphaMin;
-          const bool on1 = T.y >= kTStop && p2.y <= 0.f && al.y >= kAlphaMin;
+          // base-2 exponent of alpha, log2 o folded in: alpha = min(0.99, 2^ee)
+          const float2 ee = __ffma2_rn(tt, dx, __ffma2_rn(__fmul2_rn(f2(co.x, co.y), dy), dy, f2(co.z, co.w)));
+          float2 al = f2(ex2_approx(ee.x), ex2_approx(ee.y));
+          if constexpr (decltype(clampc)::value) al = f2(fminf(kAlphaMax, al.x), fminf(kAlphaMax, al.y));
+          const bool on0 = T.x >= kTStop && ee.x >= kLog2AlphaMin;
+          const bool on1 = T.y >= kTStop && ee.y >= kLog2AlphaMin;
           const float2 wt = __fmul2_rn(al, T);
           const float2 w = f2(on0 ? wt.x : 0.f, on1 ? wt.y : 0.f);
           const float4 rg = s_rg[j], bd = s_bd[j];
@@ -102,17 +117,22 @@ __global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant
           C1 = __ffma2_rn(f2(rg.z, rg.w), w, C1);
           C2 = __ffma2_rn(f2(bd.x, bd.y), w, C2);
           D = __ffma2_rn(f2(bd.z, bd.w), w, D);
-          T = __fadd2_rn(T, f2(-w.x, -w.y));
+          T = __ffma2_rn(w, m1, T);  // T - w, rounded once
           last0 = on0 ? (uint32_t)(b + j + 1) : last0;
           last1 = on1 ? (uint32_t)(b + j + 1) : last1;
       };
-      if (jn == 8) {
+      using Clamp = std::true_type;
+      using NoClamp = std::false_type;
+      if (jn == 8 && !((clamp_mask >> (j0 >> 3)) & 1u)) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) entry(jj);
+        for (int jj = 0; jj < 8; ++jj) entry(jj, NoClamp{});
+      } else if (jn == 8) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) entry(jj, Clamp{});
       } else {
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj)
-          if (jj < jn) entry(jj);
+          if (jj < jn) entry(jj, Clamp{});
       }
     }
   }
@@ -149,10 +169,11 @@ struct BwdSmem {
   // entries 2p and 2p+1 side by side, so one 16-byte load gives two operand pairs
   float4 q_xy[2][kBwdBatch / 2];            // (x, x', y, y') tile-relative centre
   float4 q_ab[2][kBwdBatch / 2];            // (A, A', B, B') scaled conic
-  float4 q_co[2][kBwdBatch / 2];            // (C, C', o, o')
+  float4 q_co[2][kBwdBatch / 2];            // (C, C', log2 o, log2 o')
   float4 q_rg[2][kBwdBatch / 2];            // (r, r', g, g')
   float4 q_bd[2][kBwdBatch / 2];            // (b, b', depth, depth')
   uint32_t idx[2][kBwdBatch];
+  int clamp[2];                             // the 0.99 clamp may bind for an entry of the batch
   int lmax;
 };
 
@@ -227,6 +248,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
       // reads finite values (they enter with alpha = 0)
       float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
       float x = 0.f, y = 0.f;
+      bool cl = false;
       if (t < cnt) {
         r0 = S.raw[buf][t][0];
         r1 = S.raw[buf][t][1];
@@ -234,7 +256,10 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
         x = __fadd_rn(__fsub_rn(r0.x, x0f), r0.z);
         y = __fadd_rn(__fsub_rn(r0.y, y0f), r0.w);
         S.idx[buf][t] = idx_cur;
+        cl = clamp_possible(r1);
       }
+      const uint32_t bal = __ballot_sync((1u << kBwdBatch) - 1u, cl);
+      if (t == 0) S.clamp[buf] = bal != 0u;
       const int pp = t >> 1, sl = t & 1;
       float* const qxy = reinterpret_cast<float*>(&S.q_xy[buf][pp]);
       float* const qab = reinterpret_cast<float*>(&S.q_ab[buf][pp]);
@@ -268,21 +293,24 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
       const float2 npx = make_float2(-pxf, -pxf), npy = make_float2(-pyf, -pyf);
       const float2 gR2 = make_float2(gR, gR), gG2 = make_float2(gG, gG), gB2 = make_float2(gB, gB),
                    gD2 = make_float2(gD, gD), gAT2 = make_float2(gAT, gAT);
-      auto pair = [&](int p, auto chk) {
+      const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
+      auto pair = [&](int p, auto chk, auto clampc) {
+          constexpr bool kClamp = decltype(clampc)::value;
           const float4 xy = S.q_xy[buf][p], ab = S.q_ab[buf][p], co = S.q_co[buf][p];
           const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), npx);
           const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), npy);
           const float2 tt = __ffma2_rn(make_float2(ab.x, ab.y), dx, __fmul2_rn(make_float2(ab.z, ab.w), dy));
-          const float2 p2 = __ffma2_rn(tt, dx, __fmul2_rn(__fmul2_rn(make_float2(co.x, co.y), dy), dy));
-          const float2 a = __fmul2_rn(make_float2(co.z, co.w), make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
-          const float al0 = fminf(kAlphaMax, a.x), al1 = fminf(kAlphaMax, a.y);
-          bool on0 = p2.x <= 0.f && al0 >= kAlphaMin, on1 = p2.y <= 0.f && al1 >= kAlphaMin;
+          const float2 ee = __ffma2_rn(tt, dx, __ffma2_rn(__fmul2_rn(make_float2(co.x, co.y), dy), dy,
+                                                          make_float2(co.z, co.w)));
+          const float2 a = make_float2(ex2_approx(ee.x), ex2_approx(ee.y));  // alpha before the clamp
+          bool on0 = ee.x >= kLog2AlphaMin, on1 = ee.y >= kLog2AlphaMin;
           if constexpr (decltype(chk)::value) {
             on0 = on0 && 2 * p < lim;
             on1 = on1 && 2 * p + 1 < lim;
           }
-          const float2 alc = make_float2(on0 ? al0 : 0.f, on1 ? al1 : 0.f);
-          const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-alc.x, -alc.y));
+          const float2 alc = kClamp ? make_float2(on0 ? fminf(kAlphaMax, a.x) : 0.f, on1 ? fminf(kAlphaMax, a.y) : 0.f)
+                                    : make_float2(on0 ? a.x : 0.f, on1 ? a.y : 0.f);
+          const float2 om = __ffma2_rn(alc, m1, one2);  // 1 - alpha
           const float2 rom = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
           const float4 rg = S.q_rg[buf][p], bd = S.q_bd[buf][p];
           const float2 cg = __ffma2_rn(make_float2(rg.x, rg.y), gR2,
@@ -299,23 +327,36 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
           const float dLda0 = fmaf(Tb0, d0, gar.x);
           sig = fmaf(alc.x, d0, sig);
           T = Tb0;
-          const float2 gp = __fmul2_rn(make_float2(dLda0, dLda1), a);
+          // dL/dalpha * alpha where alpha is unclamped (alc = alpha there; 0 when skipped)
+          const float2 gp = __fmul2_rn(make_float2(dLda0, dLda1), alc);
           const float2 w = __fmul2_rn(alc, make_float2(Tb0, Tb1));
           *reinterpret_cast<float4*>(&S.gw[t][2 * p]) =
-              make_float4((on0 && a.x <= kAlphaMax) ? gp.x : 0.f, w.x, (on1 && a.y <= kAlphaMax) ? gp.y : 0.f, w.y);
+              kClamp ? make_float4(a.x <= kAlphaMax ? gp.x : 0.f, w.x, a.y <= kAlphaMax ? gp.y : 0.f, w.y)
+                     : make_float4(gp.x, w.x, gp.y, w.y);
       };
       using Yes = std::true_type;
       using No = std::false_type;
+      const bool bclamp = S.clamp[buf] != 0;
       if (cnt == kBwdBatch && __all_sync(0xffffffffu, lim >= kBwdBatch)) {  // every pixel walks it all
+        if (bclamp) {
 #pragma unroll
-        for (int p = kBwdBatch / 2 - 1; p >= 0; --p) pair(p, No{});
+          for (int p = kBwdBatch / 2 - 1; p >= 0; --p) pair(p, No{}, Yes{});
+        } else {
+#pragma unroll
+          for (int p = kBwdBatch / 2 - 1; p >= 0; --p) pair(p, No{}, No{});
+        }
       } else if (cnt == kBwdBatch) {  // full batch: no per-entry guard
+        if (bclamp) {
 #pragma unroll
-        for (int p = kBwdBatch / 2 - 1; p >= 0; --p) pair(p, Yes{});
+          for (int p = kBwdBatch / 2 - 1; p >= 0; --p) pair(p, Yes{}, Yes{});
+        } else {
+#pragma unroll
+          for (int p = kBwdBatch / 2 - 1; p >= 0; --p) pair(p, Yes{}, No{});
+        }
       } else {
 #pragma unroll
         for (int p = kBwdBatch / 2 - 1; p >= 0; --p)
-          if (2 * p < cnt) pair(p, Yes{});
+          if (2 * p < cnt) pair(p, Yes{}, Yes{});
       }
     }
     // Gaussian phase for the 32 pixels this warp just walked (skipped when all of them
@@ -416,10 +457,7 @@ __global__ void __launch_bounds__(kTilePix) k_frag_stats(const __grid_constant__
       float4 r0 = rec[3 * (size_t)idx], r1 = rec[3 * (size_t)idx + 1];
       float2 xy = make_float2(__fadd_rn(__fsub_rn(r0.x, x0f), r0.z), __fadd_rn(__fsub_rn(r0.y, y0f), r0.w));
       float dx, dy;
-      float p2 = frag_exp2(xy, r1, (float)lx, (float)ly, dx, dy);
-      if (p2 > 0.f) continue;
-      float a = __fmul_rn(r1.w, ex2_approx(p2));
-      if (fminf(kAlphaMax, a) >= kAlphaMin) ++co;
+      if (frag_exp2(xy, r1, (float)lx, (float)ly, dx, dy) >= kLog2AlphaMin) ++co;
     }
     ev = ne;
     bw = nc;
