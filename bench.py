@@ -45,6 +45,31 @@ NCU_TRAFFIC_SOURCES = ["paper_2509_13536_gb300/csrc/raster.cu", "paper_2509_1353
 NCU_TRAFFIC = {"sha256_16": "a2986c3f9f38a8c2", "blend_bwd": 490.74e6 + 58.04e6, "blend_fwd": 251.72e6 + 144.70e6}
 
 
+def algorithmic_bytes(n, views, stats, pb, pixels):
+    """HBM bytes per step each kernel group must move at least (model, per the kernels'
+    data layout): n Gaussians of pb parameter bytes, views x n (view, Gaussian) items of
+    which `drawn_items` are drawn, `keys` (Gaussian, tile) keys, `pixels` output pixels.
+    Gradients and Adam state are f32 (236 B per SH3 Gaussian)."""
+    d, k, vn = stats["drawn_items"], stats["keys"], views * n
+    g32 = 4 * 59  # f32 gradient bytes of an SH3 Gaussian
+    return {
+        "preprocess": (n * pb + 16 * vn + 48 * d,
+                       "parameters once + 16 B per item (rect, count, depth key) + 48 B record per drawn item"),
+        "depth_sort": (8 * vn + 80 * d, "first pass over all items (4 B histogram + 4 B key read; the values are "
+                                        "the item index), 8 B written per drawn item, three more passes of 20 B "
+                                        "per drawn item, the scan of the key counts (12 B per drawn item)"),
+        "emit": (52 * d + 8 * k, "52 B read per drawn item (order, offset, count, rect, conic), 8 B per key written"),
+        "tile_sort": (44 * k, "two passes of 20 B per key (histogram read, key and value read and written) "
+                              "+ 4 B per key for the tile ranges"),
+        "preprocess_bwd": (n * (pb + 2 * g32 + 16) + 12 * vn + 48 * d,
+                           "parameters + f32 gradients read and written + Eq. 3 sums, 12 B per item, "
+                           "48 B moments per drawn item"),
+        "adam": (n * 59 * 32, "per f32 parameter: parameter, gradient, m, v read; parameter, m, v written; "
+                              "gradient zeroed"),
+        "l1_loss": (48 * pixels, "per pixel: rgb and depth read, targets read, cotangents written (4 B each)"),
+    }
+
+
 def recorded_traffic(kernel):
     import hashlib
     h = hashlib.sha256()
@@ -712,25 +737,39 @@ def run_ours(args):
     fp32_peak = props.multi_processor_count * 128 * 2 * f_mhz * 1e6 / 1e12  # TFLOP/s (FMA = 2)
     flops = {"blend_fwd": FWD_FLOP_EVAL * stats["evaluated"] + FWD_FLOP_CONTRIB * stats["contributing"],
              "blend_bwd": BWD_FLOP_EVAL * stats["backward_walked"] + BWD_FLOP_CONTRIB * stats["contributing"]}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    pb = sum(t[0].numel() * t.element_size() for t in g.params())  # parameter bytes per Gaussian
+    hbm_bytes = algorithmic_bytes(g.n, V, stats, pb, V * W * H)
+    for k, e in kern.items():
+        dur = e["ms_per_step"] / 1e3
+        if k in flops:
+            e.update(flops_per_step=flops[k], achieved_tflops=flops[k] / dur / 1e12,
+                     frac_of_fp32=flops[k] / dur / 1e12 / fp32_peak)
+        elif k in hbm_bytes:
+            e.update(bytes_per_step=hbm_bytes[k][0], achieved_gbs=hbm_bytes[k][0] / dur / 1e9,
+                     frac_of_hbm=hbm_bytes[k][0] / dur / 1e9 / hbm, bytes_basis=hbm_bytes[k][1])
+
+    def alu_roofline(name):
+        e = kern[name]
+        return {"kernel": name, "bound": "alu", "achieved": e["achieved_tflops"], "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": e["frac_of_fp32"], "traffic": recorded_traffic(name),
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {f_mhz:.0f} MHz "
+                              "(median sampled SM clock)",
+                "flops_per_launch": flops[name]}
+
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
-    roofline = None
     if dom in flops:
-        dur = kern[dom]["ms_per_step"] / 1e3
-        ach = flops[dom] / dur / 1e12
-        roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp32_peak, "traffic": recorded_traffic(dom),
-                    "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {f_mhz:.0f} MHz "
-                                  "(median sampled SM clock)",
-                    "flops_per_launch": flops[dom]}
+        roofline = alu_roofline(dom)
     else:
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except OSError:
-            pass
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        roofline = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-                    "traffic": None}
+        e = kern[dom]
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": e.get("achieved_gbs"), "peak": hbm, "unit": "GB/s",
+                    "frac": e.get("frac_of_hbm"), "traffic": None}
+    roofline_fwd = alu_roofline("blend_fwd") if "blend_fwd" in kern and dom != "blend_fwd" else None
 
     # the same step with the kernels called directly through the C ABI (no autograd)
     direct = None
@@ -775,6 +814,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (236 MB parameters, 384 MB projected records, "
                              f"{stats['keys']} tile keys per step)"},
             "roofline": roofline,
+            "roofline_blend_fwd": roofline_fwd,
             "e2e": ({"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": host_loss[0].numel() * 4} if n_e2e > 0 else None),
             "gpu_launches": launches, "clocks": csum, "kernels": kern, "fragments": stats,

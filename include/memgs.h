@@ -389,10 +389,11 @@ mgs_status mgs_server_destroy(mgs_server* s);
  * each, NUL-terminated), total milliseconds and launch count.  Returns the number
  * of kinds.
  * mgs_render_stats: counting pass over the saved state of the last mgs_render on
- * `workspace` (same g, cams, n_views), stats_host[8]: [0] (pixel, entry) pairs the
+ * `workspace` (same g, cams, n_views), stats_host[9]: [0] (pixel, entry) pairs the
  * forward evaluated, [1] contributing pairs (alpha >= 1/255), [2] pairs the backward
  * walks, [3] (Gaussian, tile) keys, [4]/[5] forward/backward pairs padded to each
- * tile's longest pixel list (x 256 pixels), [6]/[7] the same padded per 32-pixel warp.
+ * tile's longest pixel list (x 256 pixels), [6]/[7] the same padded per 32-pixel warp,
+ * [8] drawn (view, Gaussian) items.
  * Synchronises `stream`.
  * ------------------------------------------------------------------------------ */
 uint64_t mgs_launch_count(void);

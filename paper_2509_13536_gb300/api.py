@@ -505,13 +505,13 @@ def profile_read():
 
 def render_stats(g: Gaussians, cams, ws: RenderWorkspace, stream=None):
     """Fragment counts of the last render on ``ws``: evaluated, contributing, walked by the
-    backward pass, and (Gaussian, tile) keys."""
-    st = (C.c_uint64 * 8)()
+    backward pass, (Gaussian, tile) keys, padded counts, and drawn (view, Gaussian) items."""
+    st = (C.c_uint64 * 9)()
     check(load().mgs_render_stats(C.byref(g.struct()), _cam_array(cams), len(cams), _ptr(ws.buf),
                                   ws.buf.numel(), st, _stream(stream)), "mgs_render_stats")
     return dict(evaluated=int(st[0]), contributing=int(st[1]), backward_walked=int(st[2]), keys=int(st[3]),
                 fwd_padded_tile=int(st[4]), bwd_padded_tile=int(st[5]), fwd_padded_warp=int(st[6]),
-                bwd_padded_warp=int(st[7]))
+                bwd_padded_warp=int(st[7]), drawn_items=int(st[8]))
 
 
 # ---------------------------------------------------------------------------------

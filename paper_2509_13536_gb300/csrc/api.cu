@@ -458,6 +458,7 @@ mgs_status mgs_render_stats(const mgs_gaussians* g, const mgs_camera* cams, int3
   stats[5] = h[12];
   stats[6] = h[13];
   stats[7] = h[14];
+  stats[8] = h[1];
   return MGS_OK;
 }
 

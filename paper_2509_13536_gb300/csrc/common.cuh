@@ -163,6 +163,13 @@ __device__ __forceinline__ DF df_axpc(float a, DF x, float c) {
   return fast_two_sum(s.hi, __fadd_rn(s.lo, p.lo));
 }
 
+// 1/x by the MUFU reciprocal (x in [0.01, 1] where the blends use it).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

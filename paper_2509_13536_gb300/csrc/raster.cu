@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
           const float2 alc = kClamp ? make_float2(on0 ? fminf(kAlphaMax, a.x) : 0.f, on1 ? fminf(kAlphaMax, a.y) : 0.f)
                                     : make_float2(on0 ? a.x : 0.f, on1 ? a.y : 0.f);
           const float2 om = __ffma2_rn(alc, m1, one2);  // 1 - alpha
-          const float2 rom = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
+          const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
           const float4 rg = S.q_rg[buf][p], bd = S.q_bd[buf][p];
           const float2 cg = __ffma2_rn(make_float2(rg.x, rg.y), gR2,
                                        __ffma2_rn(make_float2(rg.z, rg.w), gG2,
