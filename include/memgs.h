@@ -392,8 +392,9 @@ mgs_status mgs_server_destroy(mgs_server* s);
  * `workspace` (same g, cams, n_views), stats_host[9]: [0] (pixel, entry) pairs the
  * forward evaluated, [1] contributing pairs (alpha >= 1/255), [2] pairs the backward
  * walks, [3] (Gaussian, tile) keys, [4]/[5] forward/backward pairs padded to each
- * tile's longest pixel list (x 256 pixels), [6]/[7] the same padded per 32-pixel warp,
- * [8] drawn (view, Gaussian) items.
+ * tile's longest pixel list (x 256 pixels), [6]/[7] the same padded per warp of the
+ * blend kernels (forward: 8x8-pixel blocks, backward: 8x4), [8] drawn (view, Gaussian)
+ * items.
  * Synchronises `stream`.
  * ------------------------------------------------------------------------------ */
 uint64_t mgs_launch_count(void);

@@ -13,9 +13,10 @@
 // two entries at a time so that what does not depend on the running T goes through
 // packed f32 pairs, and writes two numbers per (pixel, entry) into shared memory:
 // gp = dL/dpower and the blend weight w.  In the
-// Gaussian phase each half-warp owns one tile row and each of its lanes one entry; it
-// sums gp, k gp, k^2 gp (k the column) and w times the cotangent along the row and forms
-// the ten moments the per-Gaussian chain rule needs; the eight warps' partial sums meet
+// Gaussian phase each half-warp owns its 16 pixels (two rows of the warp's 8x4 block) and
+// each of its lanes one entry; it sums gp, k gp, k^2 gp (k the column) and w times the
+// cotangent along each row and forms the ten moments the per-Gaussian chain rule needs;
+// the eight warps' partial sums meet
 // in shared memory, are added by all threads (half-warp = entry, lane = moment) and go
 // out as three 16-byte vector atomics per entry.
 // There is no per-fragment shuffle or atomic.
@@ -54,7 +55,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant
   const int local = tile - V.tile_base;
   const int x0 = (local % V.tiles_x) * kTile, y0 = (local / V.tiles_x) * kTile;
   const int t = threadIdx.x;
-  const int lx = t & (kTile - 1), ly = 2 * (t / kTile);
+  // each warp an 8x8 block of the tile (its pixels stop at similar list positions), each
+  // thread two vertically adjacent pixels
+  const int wq = t >> 5, ln = t & 31;
+  const int lx = 8 * (wq & 1) + (ln & 7), ly = 8 * (wq >> 1) + 2 * (ln >> 3);
   const int px = x0 + lx, py = y0 + ly;
   const bool in0 = px < V.width && py < V.height, in1 = px < V.width && py + 1 < V.height;
   const float x0f = (float)x0, y0f = (float)y0;
@@ -196,7 +200,9 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
   const int local = tile - V.tile_base;
   const int x0 = (local % V.tiles_x) * kTile, y0 = (local / V.tiles_x) * kTile;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int lx = t & (kTile - 1), ly = t / kTile;
+  // each warp an 8x4 block of the tile (bx = warp & 1, by = warp >> 1); half-warp h holds
+  // its rows 2h and 2h + 1, eight pixels each
+  const int lx = 8 * (warp & 1) + (lane & 7), ly = 4 * (warp >> 1) + (lane >> 3);
   const int px = x0 + lx, py = y0 + ly;
   const bool inside = px < V.width && py < V.height;
   const float pxf = (float)lx, pyf = (float)ly, x0f = (float)x0, y0f = (float)y0;
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
   const int L = S.lmax;
   const float gAT = gA * Tf;
   float sig = 0.f;
-  // Gaussian-phase lane roles: entry e of the batch, tile row 2 warp + half
+  // Gaussian-phase lane roles: entry e of the batch, the half-warp's two pixel rows
   const int e = lane & (kBwdBatch - 1), half = lane >> 4;
   const int prow = warp * 32 + half * kTile;
   float* const red_own = reinterpret_cast<float*>(&S.gw[warp * 32][0]);
@@ -361,38 +367,43 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
     }
     // Gaussian phase for the 32 pixels this warp just walked (skipped when all of them
     // ended before the batch; tracking per-pixel contributions costs more than it
-    // saves): per row sums of gp, k gp, k^2 gp with
-    // k the column offset from the tile centre, then the moments about the centre of
-    // the Gaussian (dx = xy.x - 7.5 - k, dy constant along the row).
+    // saves): per row sums of gp, k gp, k^2 gp with k the column offset from the centre
+    // of the block's eight columns, then the moments about the centre of the Gaussian
+    // (dx = xy.x - x_centre - k, dy constant along each row).
     __syncwarp();  // this warp's gw rows are written by its own lanes
     float m[kMom];
 #pragma unroll
     for (int k = 0; k < kMom; ++k) m[k] = 0.f;
     if (wrun && e < cnt) {
-      float s0 = 0.f, k1 = 0.f, k2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
+      float s0[2] = {0.f, 0.f}, k1[2] = {0.f, 0.f}, k2[2] = {0.f, 0.f};
+      float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
 #pragma unroll
       for (int k = 0; k < kTile; ++k) {
         const float2 gw = S.gw[prow + k][e];
         const float4 gg = S.g[prow + k];
-        constexpr float c0 = -7.5f;
-        const float kc = c0 + (float)k;
-        s0 += gw.x;
-        k1 = fmaf(kc, gw.x, k1);
-        k2 = fmaf(kc * kc, gw.x, k2);
+        constexpr float c0 = -3.5f;
+        const float kc = c0 + (float)(k & 7);
+        const int r = k >> 3;
+        s0[r] += gw.x;
+        k1[r] = fmaf(kc, gw.x, k1[r]);
+        k2[r] = fmaf(kc * kc, gw.x, k2[r]);
         w0 = fmaf(gw.y, gg.x, w0);
         w1 = fmaf(gw.y, gg.y, w1);
         w2 = fmaf(gw.y, gg.z, w2);
         w3 = fmaf(gw.y, gg.w, w3);
       }
       const float* const qxy = reinterpret_cast<const float*>(&S.q_xy[buf][e >> 1]);
-      const float xc = qxy[e & 1] - 7.5f, dy = qxy[2 + (e & 1)] - (float)(prow / kTile);
-      const float m1 = fmaf(xc, s0, -k1);                    // sum gp (xc - kc)
-      m[0] = s0;
-      m[1] = m1;
-      m[2] = dy * s0;
-      m[3] = fmaf(xc, fmaf(xc, s0, -2.f * k1), k2);          // sum gp (xc - kc)^2
-      m[4] = dy * m1;
-      m[5] = dy * dy * s0;
+      const float xc = qxy[e & 1] - (float)(8 * (warp & 1)) - 3.5f;
+      const float dy0 = qxy[2 + (e & 1)] - (float)(4 * (warp >> 1) + 2 * half);
+      const float dy1 = dy0 - 1.f;
+      const float ma = fmaf(xc, s0[0], -k1[0]), mb = fmaf(xc, s0[1], -k1[1]);  // sum gp (xc - kc)
+      m[0] = s0[0] + s0[1];
+      m[1] = ma + mb;
+      m[2] = fmaf(dy0, s0[0], dy1 * s0[1]);
+      m[3] = fmaf(xc, fmaf(xc, s0[0], -2.f * k1[0]), k2[0]) +   // sum gp (xc - kc)^2
+             fmaf(xc, fmaf(xc, s0[1], -2.f * k1[1]), k2[1]);
+      m[4] = fmaf(dy0, ma, dy1 * mb);
+      m[5] = fmaf(dy0 * dy0, s0[0], dy1 * dy1 * s0[1]);
       m[6] = w0;
       m[7] = w1;
       m[8] = w2;
@@ -462,31 +473,33 @@ __global__ void __launch_bounds__(kTilePix) k_frag_stats(const __grid_constant__
     ev = ne;
     bw = nc;
   }
-  // padded work: a warp (tile) issues its longest pixel's list for all its lanes (pixels)
-  unsigned long long ev_w = ev, bw_w = bw;
+  // padded work: a warp (tile) issues its longest pixel's list for all its lanes (pixels).
+  // Forward warps hold 8x8 pixel blocks (four per tile), backward warps 8x4 blocks (eight).
+  __shared__ unsigned long long s_max[2], s_fw[4], s_bw[8];
+  if (threadIdx.x < 4) s_fw[threadIdx.x] = 0;
+  if (threadIdx.x < 8) s_bw[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_max[0] = s_max[1] = 0;
+  __syncthreads();
+  atomicMax(&s_fw[2 * (ly >> 3) + (lx >> 3)], ev);
+  atomicMax(&s_bw[2 * (ly >> 2) + (lx >> 3)], bw);
+  atomicMax(&s_max[0], ev);
+  atomicMax(&s_max[1], bw);
   for (int s = 16; s; s >>= 1) {
     ev += __shfl_xor_sync(0xffffffffu, ev, s);
     co += __shfl_xor_sync(0xffffffffu, co, s);
     bw += __shfl_xor_sync(0xffffffffu, bw, s);
-    ev_w = max(ev_w, __shfl_xor_sync(0xffffffffu, ev_w, s));
-    bw_w = max(bw_w, __shfl_xor_sync(0xffffffffu, bw_w, s));
   }
-  __shared__ unsigned long long s_max[2];
-  if (threadIdx.x == 0) s_max[0] = s_max[1] = 0;
-  __syncthreads();
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&out[0], ev);
     atomicAdd(&out[1], co);
     atomicAdd(&out[2], bw);
-    atomicAdd(&out[5], 32ull * ev_w);
-    atomicAdd(&out[6], 32ull * bw_w);
-    atomicMax(&s_max[0], ev_w);
-    atomicMax(&s_max[1], bw_w);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     atomicAdd(&out[3], (unsigned long long)kTilePix * s_max[0]);
     atomicAdd(&out[4], (unsigned long long)kTilePix * s_max[1]);
+    atomicAdd(&out[5], 64ull * (s_fw[0] + s_fw[1] + s_fw[2] + s_fw[3]));
+    atomicAdd(&out[6], 32ull * (s_bw[0] + s_bw[1] + s_bw[2] + s_bw[3] + s_bw[4] + s_bw[5] + s_bw[6] + s_bw[7]));
   }
 }
 
