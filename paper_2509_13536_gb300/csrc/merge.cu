@@ -4,7 +4,8 @@
 //                    bounding box of the occupied voxels.
 //  2. k_voxel_pack   voxel coordinates packed relative to the box into one u32 key
 //                    (ineligible Gaussians get the all-ones key and sort last).
-//  3. radix sort of (key, index); segment heads -> one (start, end) per voxel.
+//  3. radix sort of (key, index); segment heads -> one (start, end) per voxel with two
+//                    or more members (a single member has no pair).
 //  4. k_voxel_pairs  8 lanes per voxel of <= 8 members, a whole warp per voxel of
 //                    9..32, a block per voxel of 33..256 (members in shared
 //                    memory) or of more (members in global scratch): members ranked by
@@ -26,7 +27,7 @@ struct MergeWs {
   uint32_t* perm[2];       // [n]
   uint32_t* flags;         // [n] segment heads, then keep flags
   uint32_t* pos;           // [n] exclusive scans
-  uint32_t* starts;        // [n + 1]
+  uint2* segs;             // [n] (first, end) of the sorted positions of each voxel with >= 2 members
   int32_t* partner;        // [n]
   float* mmean;            // [n][3] merged mean (valid where the Gaussian survives a merge)
   float* mquat;            // [n][4]
@@ -539,20 +540,27 @@ __global__ void k_voxel_pack(int64_t n, const int32_t* __restrict__ vox, const i
   keys[i] = (rx << (by + bz)) | (ry << bz) | rz;
 }
 
+// Voxels with one member have no pair: only the first sorted position of each voxel with
+// two or more members is flagged, and k_segs gives those voxels (first, end) segments.
 __global__ void k_heads(int64_t n, const int32_t* __restrict__ n_elig_p, const uint32_t* __restrict__ keys,
                         uint32_t* __restrict__ flags) {
   const int64_t n_elig = min(n, (int64_t)*n_elig_p);
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_elig) return;
-  flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
+  const bool head = k == 0 || keys[k] != keys[k - 1];
+  flags[k] = (head && k + 1 < n_elig && keys[k + 1] == keys[k]) ? 1u : 0u;
 }
 
-__global__ void k_starts(int64_t n, const int32_t* __restrict__ n_elig_p, const uint32_t* __restrict__ flags,
-                         const uint32_t* __restrict__ pos, uint32_t* __restrict__ starts, const uint32_t* n_vox) {
+__global__ void k_segs(int64_t n, const int32_t* __restrict__ n_elig_p, const uint32_t* __restrict__ keys,
+                       const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                       uint2* __restrict__ segs) {
   const int64_t n_elig = min(n, (int64_t)*n_elig_p);
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n_elig && flags[k]) starts[pos[k]] = (uint32_t)k;
-  if (k == 0) starts[*n_vox] = (uint32_t)n_elig;
+  if (k >= n_elig || !flags[k]) return;
+  const uint32_t key = keys[k];
+  int64_t e = k + 2;  // the voxel has at least two members
+  while (e < n_elig && keys[e] == key) ++e;
+  segs[pos[k]] = make_uint2((uint32_t)k, (uint32_t)e);
 }
 
 struct PairCand {
@@ -573,7 +581,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_voxel_pairs(
     const float* __restrict__ means, const Geom geo,
     const uint64_t* __restrict__ birth, const uint32_t* __restrict__ perm,
-    const uint32_t* __restrict__ starts, const uint32_t* __restrict__ n_vox_p, float chi2, int greedy,
+    const uint2* __restrict__ segs, const uint32_t* __restrict__ n_vox_p, float chi2, int greedy,
     int32_t* __restrict__ partner, uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs,
     uint32_t* __restrict__ big, uint32_t* __restrict__ n_big) {
   __shared__ float s_d2[4][kWarpVoxel][kWarpVoxel + 1];
@@ -584,9 +592,9 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
   const int64_t n_vox = (int64_t)*n_vox_p;
   // whole-warp pairing of voxel v (2..32 members; more go to the big list)
   auto warp_voxel = [&](int64_t v) {
-  const uint32_t st = starts[v], en = starts[v + 1];
-  const int nm = (int)(en - st);
-  if (nm < 2) return;
+  const uint2 sg = segs[v];
+  const uint32_t st = sg.x;
+  const int nm = (int)(sg.y - sg.x);
   if (nm > kWarpVoxel) {
     if (lane == 0) big[atomicAdd(n_big, 1u)] = (uint32_t)v;
     return;
@@ -670,8 +678,9 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     uint32_t st = 0;
     int nm = 0;
     if (v < n_vox) {
-      st = starts[v];
-      nm = (int)(starts[v + 1] - st);
+      const uint2 sg = segs[v];
+      st = sg.x;
+      nm = (int)(sg.y - sg.x);
     }
     const bool small = nm >= 2 && nm <= kGroupVoxel;
     const bool mine = small && gl < nm;
@@ -774,7 +783,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
     const float* __restrict__ means, const Geom geo,
     const uint64_t* __restrict__ birth, const uint32_t* __restrict__ perm,
-    const uint32_t* __restrict__ starts, const uint32_t* __restrict__ big,
+    const uint2* __restrict__ segs, const uint32_t* __restrict__ big,
     const uint32_t* __restrict__ n_big_p, float chi2, int greedy, int32_t* __restrict__ partner,
     uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs, uint32_t* __restrict__ huge,
     uint32_t* __restrict__ n_huge) {
@@ -793,7 +802,7 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
   // Block-stride loop over the big voxels (every branch below is uniform per block).
   for (uint32_t bv = blockIdx.x; bv < n_big; bv += gridDim.x) {
   const uint32_t v = big[bv];
-  const uint32_t st = starts[v], en = starts[v + 1];
+  const uint32_t st = segs[v].x, en = segs[v].y;
   const int nm = (int)(en - st);
   if (nm > kBlockVoxel) {  // left to the global-memory path
     if (t == 0) huge[atomicAdd(n_huge, 1u)] = v;
@@ -872,7 +881,7 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_big(
 template <typename T>
 __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_huge(
     const float* __restrict__ means, const Geom geo, const uint64_t* __restrict__ birth,
-    const uint32_t* __restrict__ perm, const uint32_t* __restrict__ starts, const uint32_t* __restrict__ huge,
+    const uint32_t* __restrict__ perm, const uint2* __restrict__ segs, const uint32_t* __restrict__ huge,
     const uint32_t* __restrict__ n_huge_p, float chi2, int greedy, int32_t* __restrict__ partner,
     uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs, int64_t* __restrict__ h_idx,
     float* __restrict__ h_mu, float* __restrict__ h_P, int32_t* __restrict__ h_match) {
@@ -882,8 +891,8 @@ __global__ void __launch_bounds__(kBlockVoxel) k_voxel_pairs_huge(
   const int t = threadIdx.x;
   for (uint32_t hv = blockIdx.x; hv < n_huge; hv += gridDim.x) {
     const uint32_t v = huge[hv];
-    const uint32_t st = starts[v];
-    const int nm = (int)(starts[v + 1] - st);
+    const uint32_t st = segs[v].x;
+    const int nm = (int)(segs[v].y - st);
     for (int m = t; m < nm; m += kBlockVoxel) {
       const int64_t i = perm[st + m];
       const uint64_t bi = birth[i];
@@ -1059,18 +1068,19 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
   uint32_t* n_big = (uint32_t*)(ws.hdr + 9);
   e = scan_exclusive_u32(ws.flags, nullptr, ws.pos, n, ws.scratch, n_vox, s, (const uint32_t*)n_elig);
   if (e != cudaSuccess) return e;
-  k_starts<<<grid, 256, 0, s>>>(n, n_elig, ws.flags, ws.pos, ws.starts, n_vox);
+  k_segs<<<grid, 256, 0, s>>>(n, n_elig, keys, ws.flags, ws.pos, ws.segs);
   count_launch(3);  // with the two pairing kernels below
-  const unsigned gv = (unsigned)std::min<int64_t>(std::max<int64_t>(1, div_up(n, 4)), kPersistBlocks);
+  // 10 blocks of 128 threads per SM fit by registers (48) and shared memory (19 KB)
+  const unsigned gv = (unsigned)std::min<int64_t>(std::max<int64_t>(1, div_up(n, 4)), 152 * 10);
   uint32_t* n_pairs = (uint32_t*)(ws.hdr + 11);
-  k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, geo, in.birth, perm, ws.starts, n_vox, p.chi2,
+  k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, geo, in.birth, perm, ws.segs, n_vox, p.chi2,
                                       p.greedy, partner, ws.pairs, n_pairs, ws.big, n_big);
   uint32_t* n_huge = (uint32_t*)(ws.hdr + 14);
   k_voxel_pairs_big<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n / 33), 152 * 2), kBlockVoxel, 0, s>>>(
-      in.means, geo, in.birth, perm, ws.starts, ws.big, n_big, p.chi2, p.greedy, partner,
+      in.means, geo, in.birth, perm, ws.segs, ws.big, n_big, p.chi2, p.greedy, partner,
       ws.pairs, n_pairs, ws.huge, n_huge);
   k_voxel_pairs_huge<T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(1, n / 257), 152), kBlockVoxel, 0, s>>>(
-      in.means, geo, in.birth, perm, ws.starts, ws.huge, n_huge, p.chi2, p.greedy, partner, ws.pairs, n_pairs,
+      in.means, geo, in.birth, perm, ws.segs, ws.huge, n_huge, p.chi2, p.greedy, partner, ws.pairs, n_pairs,
       ws.h_idx, ws.h_mu, ws.h_P, ws.h_match);
   count_launch();
   const unsigned gp = (unsigned)div_up(n / 2 + 1, 128);
@@ -1113,7 +1123,7 @@ size_t merge_workspace_bytes(int64_t n, MergeWs* ws, char* base) {
   w.perm[1] = (uint32_t*)take(4 * m);
   w.flags = (uint32_t*)take(4 * m);
   w.pos = (uint32_t*)take(4 * m);
-  w.starts = (uint32_t*)take(4 * (m + 1));
+  w.segs = (uint2*)take(8 * m);
   w.partner = (int32_t*)take(4 * m);
   w.mmean = (float*)take(12 * m);
   w.mquat = (float*)take(16 * m);
