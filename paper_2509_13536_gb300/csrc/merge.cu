@@ -585,6 +585,8 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     int32_t* __restrict__ partner, uint2* __restrict__ pairs, uint32_t* __restrict__ n_pairs,
     uint32_t* __restrict__ big, uint32_t* __restrict__ n_big) {
   __shared__ float s_d2[4][kWarpVoxel][kWarpVoxel + 1];
+  __shared__ float s_mu[4][kWarpVoxel][3];   // member means, by rank
+  __shared__ float s_P[4][kWarpVoxel][7];    // member precisions (6 used, odd stride), by rank
   __shared__ int64_t s_idx[4][kWarpVoxel];
   __shared__ uint64_t s_birth[4][kWarpVoxel];
   __shared__ int s_pairs[4][kWarpVoxel / 2][2];
@@ -599,28 +601,38 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     if (lane == 0) big[atomicAdd(n_big, 1u)] = (uint32_t)v;
     return;
   }
+  // each lane loads its own member (independent loads), then places it by rank
   int64_t my = lane < nm ? (int64_t)perm[st + lane] : -1;
-  uint64_t mb = lane < nm ? birth[my] : ~0ull;
+  uint64_t mb = ~0ull;
+  float P[6], mu[3];
+  if (lane < nm) {
+    mb = birth[my];
+    precision_of(geo, my, P);
+    mu[0] = means[3 * my]; mu[1] = means[3 * my + 1]; mu[2] = means[3 * my + 2];
+  }
   int rank = 0;
   for (int m = 0; m < nm; ++m) {
     int64_t oi = __shfl_sync(0xffffffffu, my, m);
     uint64_t ob = __shfl_sync(0xffffffffu, mb, m);
     if (lane < nm && older(ob, oi, mb, my)) ++rank;
   }
-  if (lane < nm) { s_idx[wib][rank] = my; s_birth[wib][rank] = mb; }
+  if (lane < nm) {
+    s_idx[wib][rank] = my;
+    s_birth[wib][rank] = mb;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s_mu[wib][rank][k] = mu[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s_P[wib][rank][k] = P[k];
+  }
   __syncwarp();
   // Eq. 4 rows: lane a (older) against every younger b
   if (lane < nm) {
-    int64_t ia = s_idx[wib][lane];
-    float P[6];
-    precision_of(geo, ia, P);
-    const float* ma = means + 3 * ia;
-    float mav[3] = {ma[0], ma[1], ma[2]};
-    for (int b = lane + 1; b < nm; ++b) {
-      const float* mb3 = means + 3 * s_idx[wib][b];
-      float mbv[3] = {mb3[0], mb3[1], mb3[2]};
-      s_d2[wib][lane][b] = mahalanobis2(P, mav, mbv);
-    }
+    float Pa[6], mav[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Pa[k] = s_P[wib][lane][k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mav[k] = s_mu[wib][lane][k];
+    for (int b = lane + 1; b < nm; ++b) s_d2[wib][lane][b] = mahalanobis2(Pa, mav, s_mu[wib][b]);
   }
   __syncwarp();
   uint32_t matched = 0;
@@ -684,8 +696,15 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     }
     const bool small = nm >= 2 && nm <= kGroupVoxel;
     const bool mine = small && gl < nm;
+    // each lane loads its own member (independent loads), then places it by rank
     const int64_t my = mine ? (int64_t)perm[st + gl] : -1;
-    const uint64_t mb = mine ? birth[my] : ~0ull;
+    uint64_t mb = ~0ull;
+    float P[6], mu[3];
+    if (mine) {
+      mb = birth[my];
+      precision_of(geo, my, P);
+      mu[0] = means[3 * my]; mu[1] = means[3 * my + 1]; mu[2] = means[3 * my + 2];
+    }
     int rank = 0;
 #pragma unroll
     for (int m = 0; m < kGroupVoxel; ++m) {
@@ -696,19 +715,19 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     if (mine) {
       s_idx[wib][gbase + rank] = my;
       s_birth[wib][gbase + rank] = mb;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) s_mu[wib][gbase + rank][k] = mu[k];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s_P[wib][gbase + rank][k] = P[k];
     }
     __syncwarp();
     if (mine) {  // Eq. 4 row: rank gl (older) against every younger rank
-      const int64_t ia = s_idx[wib][gbase + gl];
-      float P[6];
-      precision_of(geo, ia, P);
-      const float* ma = means + 3 * ia;
-      const float mav[3] = {ma[0], ma[1], ma[2]};
-      for (int b = gl + 1; b < nm; ++b) {
-        const float* mb3 = means + 3 * s_idx[wib][gbase + b];
-        const float mbv[3] = {mb3[0], mb3[1], mb3[2]};
-        s_d2[wib][gbase + gl][b] = mahalanobis2(P, mav, mbv);
-      }
+      float Pa[6], mav[3];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Pa[k] = s_P[wib][gbase + gl][k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) mav[k] = s_mu[wib][gbase + gl][k];
+      for (int b = gl + 1; b < nm; ++b) s_d2[wib][gbase + gl][b] = mahalanobis2(Pa, mav, s_mu[wib][gbase + b]);
     }
     __syncwarp();
     uint32_t matched = 0;
@@ -1070,8 +1089,8 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
   if (e != cudaSuccess) return e;
   k_segs<<<grid, 256, 0, s>>>(n, n_elig, keys, ws.flags, ws.pos, ws.segs);
   count_launch(3);  // with the two pairing kernels below
-  // 10 blocks of 128 threads per SM fit by registers (48) and shared memory (19 KB)
-  const unsigned gv = (unsigned)std::min<int64_t>(std::max<int64_t>(1, div_up(n, 4)), 152 * 10);
+  // 8 blocks of 128 threads per SM fit by registers (64) and shared memory (24 KB)
+  const unsigned gv = (unsigned)std::min<int64_t>(std::max<int64_t>(1, div_up(n, 4)), kPersistBlocks);
   uint32_t* n_pairs = (uint32_t*)(ws.hdr + 11);
   k_voxel_pairs<T><<<gv, 128, 0, s>>>(in.means, geo, in.birth, perm, ws.segs, n_vox, p.chi2,
                                       p.greedy, partner, ws.pairs, n_pairs, ws.big, n_big);
