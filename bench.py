@@ -42,7 +42,7 @@ BWD_FLOP_EVAL, BWD_FLOP_CONTRIB = 10, 47
 # of the full workload (8 views, one launch per step; profiles/ has the command).  A value
 # is reported only while the kernel sources still hash to the captured version.
 NCU_TRAFFIC_SOURCES = ["paper_2509_13536_gb300/csrc/raster.cu", "paper_2509_13536_gb300/csrc/common.cuh"]
-NCU_TRAFFIC = {"sha256_16": "a2986c3f9f38a8c2", "blend_bwd": 490.74e6 + 58.04e6, "blend_fwd": 251.72e6 + 144.70e6}
+NCU_TRAFFIC = {"sha256_16": "7255695988e9033f", "blend_bwd": 491.88e6 + 58.39e6, "blend_fwd": 251.74e6 + 144.65e6}
 
 
 def algorithmic_bytes(n, views, stats, pb, pixels):
@@ -743,6 +743,8 @@ def run_ours(args):
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_source = ("measured copy bandwidth (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks
+                  else "fallback 6.8 TB/s (no MEASURED_PEAKS.json on this machine)")
     pb = sum(t[0].numel() * t.element_size() for t in g.params())  # parameter bytes per Gaussian
     hbm_bytes = algorithmic_bytes(g.n, V, stats, pb, V * W * H)
     for k, e in kern.items():
@@ -752,7 +754,8 @@ def run_ours(args):
                      frac_of_fp32=flops[k] / dur / 1e12 / fp32_peak)
         elif k in hbm_bytes:
             e.update(bytes_per_step=hbm_bytes[k][0], achieved_gbs=hbm_bytes[k][0] / dur / 1e9,
-                     frac_of_hbm=hbm_bytes[k][0] / dur / 1e9 / hbm, bytes_basis=hbm_bytes[k][1])
+                     frac_of_hbm=hbm_bytes[k][0] / dur / 1e9 / hbm, hbm_peak_gbs=hbm, hbm_peak_source=hbm_source,
+                     bytes_basis=hbm_bytes[k][1])
 
     def alu_roofline(name):
         e = kern[name]
@@ -768,7 +771,7 @@ def run_ours(args):
     else:
         e = kern[dom]
         roofline = {"kernel": dom, "bound": "hbm", "achieved": e.get("achieved_gbs"), "peak": hbm, "unit": "GB/s",
-                    "frac": e.get("frac_of_hbm"), "traffic": None}
+                    "frac": e.get("frac_of_hbm"), "traffic": None, "peak_basis": hbm_source}
     roofline_fwd = alu_roofline("blend_fwd") if "blend_fwd" in kern and dom != "blend_fwd" else None
 
     # the same step with the kernels called directly through the C ABI (no autograd)
