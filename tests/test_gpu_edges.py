@@ -75,6 +75,46 @@ def test_transmittance_stop_scene_and_its_gradient(orc):
     _gpu.check_grads(grads, refg)
 
 
+def test_clamp_entries_mixed_with_plain_ones(orc):
+    """Entries whose opacity exceeds 0.98 can reach the 0.99 clamp and take the clamped
+    path of both blends (the 8-entry groups of the forward, the 16-entry batches of the
+    backward); they share tiles and batches with entries that skip it.  Two views at a
+    ragged 150x110: images against the oracle's outcomes and every gradient element
+    within the element-wise bound."""
+    rng = np.random.default_rng(11)
+    n = 400
+    means = rng.uniform(-1.0, 1.0, size=(n, 3)) + np.array([0.0, 0.0, 3.0])
+    scales = np.exp(rng.uniform(math.log(0.02), math.log(0.15), size=(n, 3)))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    op = rng.uniform(0.1, 0.9, size=n)
+    op[::3] = rng.uniform(0.985, 0.9999, size=op[::3].shape)  # a third can reach the clamp
+    sh = rng.normal(0, 0.3, size=(n, 4, 3))
+    sh[:, 0, :] = (rng.random((n, 3)) - 0.5) / (0.5 / math.sqrt(math.pi))
+    sc = make_scene(means, scales, q, op, None, 1, sh)
+    th = 0.2
+    Ry = np.array([[math.cos(th), 0, math.sin(th)], [0, 1, 0], [-math.sin(th), 0, math.cos(th)]])
+    cams = [camera(150, 110, 100, 100, 74.5, 54.5),
+            camera(150, 110, 110, 105, 70.0, 58.0, R=Ry, t=-Ry @ np.array([0.3, 0.0, -0.2]))]
+    # the scene does what it is for (oracle projection of view 0): entries reach the
+    # clamp at a pixel centre
+    p = orc.project(sc, cams[0])
+    u = np.rint(p["mean2d"])
+    d = u - p["mean2d"]
+    A, B, C = p["conic"][:, 0], p["conic"][:, 1], p["conic"][:, 2]
+    a_peak = p["opacity"] * np.exp(-0.5 * (A * d[:, 0] ** 2 + 2 * B * d[:, 0] * d[:, 1] + C * d[:, 1] ** 2))
+    inside = (u[:, 0] >= 0) & (u[:, 0] < 150) & (u[:, 1] >= 0) & (u[:, 1] < 110)
+    assert ((p["visible"] > 0) & inside & (a_peak > 0.99)).sum() >= 5
+    g, imgs, ws = _render(sc, cams)
+    refs = [orc.render_outcomes(sc, c) for c in cams]
+    for v in range(2):
+        _gpu.check_image(imgs[v], refs[v], what=f"clamp mix view {v}")
+    cot_np, dL = _gpu.masked_cotangents(cams, refs, 12)
+    grads = api.render_backward(g, cams, dL, ws)
+    torch.cuda.synchronize()
+    _gpu.check_grads(grads, _gpu.oracle_backward(orc, sc, cams, cot_np), what="clamp mix")
+
+
 def test_depth_tie_keeps_index_order(orc):
     cols = [[1, 0, 0], [0, 1, 0]]
     sc = make_scene([[0, 0, 2.0], [0, 0, 2.0]], [[0.3] * 3] * 2, [[1, 0, 0, 0]] * 2, [0.6, 0.5], cols)
