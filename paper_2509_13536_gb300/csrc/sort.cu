@@ -32,6 +32,10 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_reduce(const uint32_t* __
                                                               const uint32_t* __restrict__ n_dev) {
   n = count_of(n, n_dev);
   int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base >= n) {  // a block past the device count (grid sized for a capacity)
+    if (threadIdx.x == 0) sums[blockIdx.x] = 0u;
+    return;
+  }
   uint32_t acc = 0;
 #pragma unroll
   for (int i = 0; i < kSortPerThread; ++i) {
@@ -94,6 +98,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_down(const uint32_t* in,
   __shared__ uint32_t tile[kSortTile];
   __shared__ uint32_t s[kWarps];
   int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base >= n) return;  // nothing of this block's range exists
 #pragma unroll
   for (int i = 0; i < kSortPerThread; ++i) {
     int idx = i * kSortThreads + threadIdx.x;
