@@ -526,6 +526,7 @@ mgs_status mgs_voxel_merge(const mgs_gaussians* in, float voxel_size, const mgs_
   last_merge_stats().lbfgs_iterations = (int64_t)it;
   if (h[7] & 1) return fail(MGS_ERR_UNSUPPORTED, "voxel coordinate outside +-2^20 (nothing merged)");
   if (h[7] & 4) return fail(MGS_ERR_UNSUPPORTED, "occupied voxel box needs more than 31 key bits (nothing merged)");
+  if (h[7] & 8) return fail(MGS_ERR_UNSUPPORTED, "voxel grouping table full");
   return MGS_OK;
 }
 

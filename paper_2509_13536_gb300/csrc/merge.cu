@@ -27,7 +27,12 @@ struct MergeWs {
   uint32_t* perm[2];       // [n]
   uint32_t* flags;         // [n] segment heads, then keep flags
   uint32_t* pos;           // [n] exclusive scans
-  uint2* segs;             // [n] (first, end) of the sorted positions of each voxel with >= 2 members
+  uint2* segs;             // [n] (first, end) in perm of each voxel with >= 2 members
+  uint32_t tsize;          // hash table slots: a power of two >= 2n
+  uint32_t* tkey;          // [tsize] voxel key of each slot (kNoKey: empty)
+  uint32_t* tcount;        // [tsize] members per slot
+  uint32_t* toff;          // [tsize] first position of each slot's members in perm
+  uint32_t* tscratch;      // scan scratch over the table
   int32_t* partner;        // [n]
   float* mmean;            // [n][3] merged mean (valid where the Gaussian survives a merge)
   float* mquat;            // [n][4]
@@ -540,27 +545,66 @@ __global__ void k_voxel_pack(int64_t n, const int32_t* __restrict__ vox, const i
   keys[i] = (rx << (by + bz)) | (ry << bz) | rz;
 }
 
-// Voxels with one member have no pair: only the first sorted position of each voxel with
-// two or more members is flagged, and k_segs gives those voxels (first, end) segments.
-__global__ void k_heads(int64_t n, const int32_t* __restrict__ n_elig_p, const uint32_t* __restrict__ keys,
-                        uint32_t* __restrict__ flags) {
-  const int64_t n_elig = min(n, (int64_t)*n_elig_p);
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_elig) return;
-  const bool head = k == 0 || keys[k] != keys[k - 1];
-  flags[k] = (head && k + 1 < n_elig && keys[k + 1] == keys[k]) ? 1u : 0u;
+// Grouping by voxel: members only need to be contiguous per voxel (the pairing ranks
+// them by (birth, index) itself), so an open-addressing hash table of packed voxel keys
+// replaces a sort.  Each eligible Gaussian finds or claims its key's slot (linear
+// probing; the table has at least twice as many slots as Gaussians, so a free slot is
+// always reached) and takes a rank in it with one atomic; a scan of the slot counts
+// gives each slot's first position, and voxels with two or more members are listed as
+// (first, end) segments in any order.
+__device__ __forceinline__ uint32_t voxel_hash(uint32_t key) {
+  key ^= key >> 16;
+  key *= 0x7feb352du;
+  key ^= key >> 15;
+  key *= 0x846ca68bu;
+  return key ^ (key >> 16);
 }
 
-__global__ void k_segs(int64_t n, const int32_t* __restrict__ n_elig_p, const uint32_t* __restrict__ keys,
-                       const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
-                       uint2* __restrict__ segs) {
-  const int64_t n_elig = min(n, (int64_t)*n_elig_p);
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_elig || !flags[k]) return;
-  const uint32_t key = keys[k];
-  int64_t e = k + 2;  // the voxel has at least two members
-  while (e < n_elig && keys[e] == key) ++e;
-  segs[pos[k]] = make_uint2((uint32_t)k, (uint32_t)e);
+__global__ void k_hash_insert(int64_t n, const uint32_t* __restrict__ keys, uint32_t* tkey,
+                              uint32_t* __restrict__ tcount, uint32_t tmask, uint32_t* __restrict__ slot,
+                              uint32_t* __restrict__ rank, int32_t* __restrict__ hdr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t key = keys[i];
+  if (key == kNoKey) { slot[i] = kNoKey; return; }
+  uint32_t h = voxel_hash(key) & tmask;
+  for (uint32_t probe = 0; probe <= tmask; ++probe) {
+    uint32_t cur = *(volatile uint32_t*)&tkey[h];
+    if (cur == kNoKey) cur = atomicCAS(&tkey[h], kNoKey, key);
+    if (cur == kNoKey || cur == key) {
+      slot[i] = h;
+      rank[i] = atomicAdd(&tcount[h], 1u);
+      return;
+    }
+    h = (h + 1) & tmask;
+  }
+  slot[i] = kNoKey;  // the table is full: cannot happen with >= 2n slots
+  atomicOr(&hdr[7], 8);
+}
+
+__global__ void k_hash_scatter(int64_t n, const uint32_t* __restrict__ slot, const uint32_t* __restrict__ rank,
+                               const uint32_t* __restrict__ toff, uint32_t* __restrict__ perm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t s = slot[i];
+  if (s != kNoKey) perm[toff[s] + rank[i]] = (uint32_t)i;
+}
+
+__global__ void k_hash_segs(uint32_t tsize, const uint32_t* __restrict__ tcount, const uint32_t* __restrict__ toff,
+                            uint2* __restrict__ segs, uint32_t* __restrict__ n_vox) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t c = t < tsize ? tcount[t] : 0u;
+  const bool multi = c >= 2;
+  const uint32_t mask = __ballot_sync(0xffffffffu, multi);
+  if (!mask) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(n_vox, (uint32_t)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (multi) {
+    const uint32_t f = toff[t];
+    segs[base + __popc(mask & ((1u << lane) - 1u))] = make_uint2(f, f + c);
+  }
 }
 
 struct PairCand {
@@ -1075,20 +1119,24 @@ cudaError_t merge_t(const mgs_gaussians& in, float voxel, const mgs_merge_params
   k_merge_plan<<<1, 32, 0, s>>>(ws.hdr);
   k_voxel_pack<<<grid, 256, 0, s>>>(n, vox, ws.hdr, ws.keys[0]);
   count_launch(3);
-  // ineligible Gaussians carry the all-ones key and sort last; eligible keys use <= 31 bits
-  int cur = radix_sort_pairs(ws.keys, ws.perm, n, 0, 32, true, ws.scratch, s, &e);
+  // group the eligible Gaussians by voxel (ineligible ones carry the all-ones key)
+  uint32_t* slot = ws.keys[1];
+  uint32_t* rank = ws.flags;
+  uint32_t* perm_w = ws.perm[0];
+  e = cudaMemsetAsync(ws.tkey, 0xff, 4 * (size_t)ws.tsize, s);
   if (e != cudaSuccess) return e;
-  const uint32_t* keys = ws.keys[cur];
-  const uint32_t* perm = ws.perm[cur];
-  const int32_t* n_elig = ws.hdr + 6;
-  k_heads<<<grid, 256, 0, s>>>(n, n_elig, keys, ws.flags);
+  e = cudaMemsetAsync(ws.tcount, 0, 4 * (size_t)ws.tsize, s);
+  if (e != cudaSuccess) return e;
+  k_hash_insert<<<grid, 256, 0, s>>>(n, ws.keys[0], ws.tkey, ws.tcount, ws.tsize - 1, slot, rank, ws.hdr);
   count_launch();
+  e = scan_exclusive_u32(ws.tcount, nullptr, ws.toff, (int64_t)ws.tsize, ws.tscratch, nullptr, s);
+  if (e != cudaSuccess) return e;
+  k_hash_scatter<<<grid, 256, 0, s>>>(n, slot, rank, ws.toff, perm_w);
   uint32_t* n_vox = (uint32_t*)(ws.hdr + 8);
   uint32_t* n_big = (uint32_t*)(ws.hdr + 9);
-  e = scan_exclusive_u32(ws.flags, nullptr, ws.pos, n, ws.scratch, n_vox, s, (const uint32_t*)n_elig);
-  if (e != cudaSuccess) return e;
-  k_segs<<<grid, 256, 0, s>>>(n, n_elig, keys, ws.flags, ws.pos, ws.segs);
-  count_launch(3);  // with the two pairing kernels below
+  k_hash_segs<<<(unsigned)div_up(ws.tsize, 256), 256, 0, s>>>(ws.tsize, ws.tcount, ws.toff, ws.segs, n_vox);
+  count_launch(4);  // with the two pairing kernels below
+  const uint32_t* perm = perm_w;
   // 8 blocks of 128 threads per SM fit by registers (64) and shared memory (24 KB)
   const unsigned gv = (unsigned)std::min<int64_t>(std::max<int64_t>(1, div_up(n, 4)), kPersistBlocks);
   uint32_t* n_pairs = (uint32_t*)(ws.hdr + 11);
@@ -1143,6 +1191,13 @@ size_t merge_workspace_bytes(int64_t n, MergeWs* ws, char* base) {
   w.flags = (uint32_t*)take(4 * m);
   w.pos = (uint32_t*)take(4 * m);
   w.segs = (uint2*)take(8 * m);
+  uint32_t ts = 1024;
+  while ((int64_t)ts < 2 * m) ts <<= 1;
+  w.tsize = ts;
+  w.tkey = (uint32_t*)take(4 * (size_t)ts);
+  w.tcount = (uint32_t*)take(4 * (size_t)ts);
+  w.toff = (uint32_t*)take(4 * ((size_t)ts + 1));
+  w.tscratch = (uint32_t*)take(4 * (size_t)(ts / kSortTile + 4));
   w.partner = (int32_t*)take(4 * m);
   w.mmean = (float*)take(12 * m);
   w.mquat = (float*)take(16 * m);
