@@ -61,11 +61,10 @@ def algorithmic_bytes(n, views, stats, pb, pixels):
         "emit": (52 * d + 8 * k, "52 B read per drawn item (order, offset, count, rect, conic), 8 B per key written"),
         "tile_sort": (44 * k, "two passes of 20 B per key (histogram read, key and value read and written) "
                               "+ 4 B per key for the tile ranges"),
-        "preprocess_bwd": (n * (pb + 2 * g32 + 16) + 12 * vn + 48 * d,
-                           "parameters + f32 gradients read and written + Eq. 3 sums, 12 B per item, "
-                           "48 B moments per drawn item"),
-        "adam": (n * 59 * 32, "per f32 parameter: parameter, gradient, m, v read; parameter, m, v written; "
-                              "gradient zeroed"),
+        "preprocess_bwd": (n * (pb + g32 + 16) + 12 * vn + 48 * d,
+                           "parameters read, f32 gradients written (the step's backward stores them), "
+                           "Eq. 3 sums read and written, 12 B per item, 48 B moments per drawn item"),
+        "adam": (n * 59 * 28, "per f32 parameter: parameter, gradient, m, v read; parameter, m, v written"),
         "l1_loss": (48 * pixels, "per pixel: rgb and depth read, targets read, cotangents written (4 B each)"),
     }
 
@@ -621,6 +620,7 @@ def run_ours(args):
 
             return step, state
         grads = api.Grads.zeros_like(g)
+        grads.overwrite = True  # the backward stores each step's gradients: no clearing
         m = api.Grads.zeros_like(g, stats=False)
         v = api.Grads.zeros_like(g, stats=False)
         rgb = torch.empty(V, 3, H, W, device=dev)
@@ -647,7 +647,7 @@ def run_ours(args):
             api.mgs_render_backward(g, cams, dL, ws, grads)
             if w_iso > 0:
                 api.iso_loss(g, w_iso, grads, loss=loss_iso, workspace=iws)
-            api.mgs_adam_step(g, grads, m, v, 1e-3, 0.9, 0.999, 1e-8, state["step"], zero_grads=True)
+            api.mgs_adam_step(g, grads, m, v, 1e-3, 0.9, 0.999, 1e-8, state["step"], zero_grads=False)
             api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox, status=mstatus)
 
         return step, state

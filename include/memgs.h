@@ -98,7 +98,11 @@ typedef struct {
 
 /* Gradient accumulators, f32, same layouts as the parameters (always f32).
  * grad_stat / vis_count (optional, [n]) collect the Eq. 3 statistic: per view in
- * which the Gaussian is drawn, += |dL/dmean| and += 1. */
+ * which the Gaussian is drawn, += |dL/dmean| and += 1.
+ * overwrite (read by mgs_render_backward only): 0 adds the call's gradients to the
+ * arrays; nonzero stores them, zeros for Gaussians drawn in no view (the arrays need
+ * no clearing before the call, which saves a read and a write of every element);
+ * grad_stat / vis_count are added to either way. */
 typedef struct {
   float* means;
   float* log_scales;
@@ -107,6 +111,8 @@ typedef struct {
   float* sh;
   float* grad_stat;
   float* vis_count;
+  int32_t overwrite;
+  int32_t reserved;
 } mgs_grads;
 
 /* ------------------------------------------------------------------------------
@@ -172,7 +178,8 @@ mgs_status mgs_render_multi(const mgs_gaussians* maps_host, int32_t n_maps, cons
 
 /* Reverse pass of the last mgs_render on `workspace` (same g, cams, n_views).
  * dL_host[v] gives dL/drgb, dL/ddepth, dL/dalpha planes of view v (any plane may
- * be NULL = zero).  Gradients of all views are ADDED to `grads` (f32).  Asynchronous. */
+ * be NULL = zero).  Gradients of all views are ADDED to `grads` (f32), or stored when
+ * grads->overwrite is nonzero.  Asynchronous. */
 mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams_host,
                                int32_t n_views, const mgs_image* dL_host, void* workspace,
                                size_t workspace_bytes, const mgs_grads* grads, void* stream);

@@ -51,7 +51,8 @@ class mgs_image(C.Structure):
 
 class mgs_grads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logit", "sh",
-                                          "grad_stat", "vis_count")]
+                                          "grad_stat", "vis_count")] + \
+               [("overwrite", C.c_int32), ("reserved", C.c_int32)]
 
 
 class mgs_server_config(C.Structure):

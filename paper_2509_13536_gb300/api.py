@@ -144,6 +144,7 @@ class Grads:
     sh: torch.Tensor
     grad_stat: Optional[torch.Tensor] = None
     vis_count: Optional[torch.Tensor] = None
+    overwrite: bool = False  # mgs_render_backward stores (instead of adds) the call's gradients
 
     @staticmethod
     def zeros_like(g: Gaussians, stats: bool = True) -> "Grads":
@@ -159,7 +160,7 @@ class Grads:
     def struct(self) -> _abi.mgs_grads:
         return _abi.mgs_grads(_ptr(self.means), _ptr(self.log_scales), _ptr(self.quats),
                               _ptr(self.opacity_logit), _ptr(self.sh), _ptr(self.grad_stat),
-                              _ptr(self.vis_count))
+                              _ptr(self.vis_count), int(self.overwrite), 0)
 
 
 class RenderWorkspace:
@@ -566,7 +567,11 @@ class RenderFn(torch.autograd.Function):
             arr[v] = _abi.mgs_image(None if g_rgb is None else _ptr(g_rgb[v]),
                                     None if g_depth is None else _ptr(g_depth[v]),
                                     None if g_alpha is None else _ptr(g_alpha[v]))
-        grads = ctx.grads if ctx.grads is not None else Grads.zeros_like(g, stats=False)
+        if ctx.grads is not None:
+            grads = ctx.grads
+        else:  # fresh tensors the library stores into (no zero fill needed)
+            e = lambda t: torch.empty(t.shape, dtype=torch.float32, device=t.device)
+            grads = Grads(e(means), e(log_scales), e(quats), e(opacity_logit), e(sh), overwrite=True)
         check(load().mgs_render_backward(C.byref(g.struct()), _cam_array(ctx.cams), V, arr,
                                          _ptr(ws.buf), ws.buf.numel(), C.byref(grads.struct()),
                                          _stream()), "mgs_render_backward")
@@ -590,9 +595,10 @@ class MappingStep:
     RenderFn (forward A1-A4), the mapping loss against the keyframe images
     (mgs_mapping_loss: Eq. 12, lambda = 0 gives its plain L1 form, plus the
     isotropic term when w_iso > 0), torch.autograd.backward from the rendered images
-    with the loss kernel's cotangents (RenderFn.backward: A5-A6 into the gradient
-    buffers, in place), then the in-kernel Adam step, which also clears the
-    gradients.  Every kernel of the step is the library's; the parameter tensors are
+    with the loss kernel's cotangents (RenderFn.backward: A5-A6 store the gradients
+    into the step's buffers, which therefore need no clearing), the isotropic term's
+    gradient added when w_iso > 0, then the in-kernel Adam step.  The Eq. 3 sums keep
+    accumulating over steps.  Every kernel of the step is the library's; the parameter tensors are
     updated in place.  Returns the device loss tensor [V, 3] (weighted L1, SSIM and
     depth parts per view); ``loss_iso`` holds the isotropic term.
 
@@ -610,6 +616,7 @@ class MappingStep:
         self.lambda_ssim, self.w_depth, self.w_iso = float(lambda_ssim), float(w_depth), float(w_iso)
         self.params = [p.requires_grad_(True) for p in g.params()]
         self.grads = Grads.zeros_like(g, stats=stats)
+        self.grads.overwrite = True  # the render backward stores each step's gradients
         self.m = Grads.zeros_like(g, stats=False)
         self.v = Grads.zeros_like(g, stats=False)
         self.ws = RenderWorkspace(g.means.device)
@@ -644,7 +651,7 @@ class MappingStep:
             mgs_iso_loss(g, self.w_iso, self.grads, loss=self.loss_iso, workspace=self.iso_ws)
         with torch.no_grad():
             mgs_adam_step(g, self.grads, self.m, self.v, self.lr, self.betas[0], self.betas[1], self.eps,
-                          self.step_count, zero_grads=True)
+                          self.step_count, zero_grads=False)
         return self.loss
 
     def check(self) -> int:

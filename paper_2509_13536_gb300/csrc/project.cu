@@ -286,7 +286,18 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(int64_t N, const floa
   for (int v = 0; v < vt.n_views; ++v)  // drawn, but reaching no pixel: zero gradient
     if (((drawn >> v) & 1u) && touched[(int64_t)v * N + g] != 0) todo |= 1u << v;
   const float vis = (float)__popc(drawn);
-  if (drawn == 0) return;
+  const bool ow = grads.overwrite != 0;
+  if (drawn == 0) {  // no view draws it: a zero gradient (stored only when overwriting)
+    if (ow) {
+      for (int k = 0; k < 3; ++k) grads.means[3 * g + k] = 0.f;
+      for (int k = 0; k < 3; ++k) grads.log_scales[3 * g + k] = 0.f;
+      for (int k = 0; k < 4; ++k) grads.quats[4 * g + k] = 0.f;
+      grads.opacity_logit[g] = 0.f;
+      float* gsh = grads.sh + g * 3 * K;
+      for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.f;
+    }
+    return;
+  }
   GaussPre G;
   load_gauss(g, means, geo, ol, G);
   float c[3 * K];
@@ -409,13 +420,14 @@ __global__ void __launch_bounds__(128, 3) k_preprocess_bwd(int64_t N, const floa
   quat_rot_vjp(G.qn, dR, dqn);
   float dot = dqn[0] * G.qn[0] + dqn[1] * G.qn[1] + dqn[2] * G.qn[2] + dqn[3] * G.qn[3];
   float iq = 1.f / G.qnorm;
-  for (int k = 0; k < 3; ++k) grads.means[3 * g + k] += dmu[k];
-  for (int k = 0; k < 3; ++k) grads.log_scales[3 * g + k] += dls[k];
-  for (int k = 0; k < 4; ++k) grads.quats[4 * g + k] += (dqn[k] - G.qn[k] * dot) * iq;
-  grads.opacity_logit[g] += dop * G.o * (1.f - G.o);
+  auto put = [ow](float* p, float v) { *p = ow ? v : *p + v; };
+  for (int k = 0; k < 3; ++k) put(grads.means + 3 * g + k, dmu[k]);
+  for (int k = 0; k < 3; ++k) put(grads.log_scales + 3 * g + k, dls[k]);
+  for (int k = 0; k < 4; ++k) put(grads.quats + 4 * g + k, (dqn[k] - G.qn[k] * dot) * iq);
+  put(grads.opacity_logit + g, dop * G.o * (1.f - G.o));
   float* gsh = grads.sh + g * 3 * K;
 #pragma unroll
-  for (int k = 0; k < 3 * K; ++k) gsh[k] += dsh[k];
+  for (int k = 0; k < 3 * K; ++k) put(gsh + k, dsh[k]);
   if (grads.grad_stat) grads.grad_stat[g] += stat;
   if (grads.vis_count) grads.vis_count[g] += vis;
 }

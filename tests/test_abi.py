@@ -39,7 +39,7 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(_abi.mgs_gaussians) == 72
     assert C.sizeof(_abi.mgs_camera) == 80
     assert C.sizeof(_abi.mgs_image) == 24
-    assert C.sizeof(_abi.mgs_grads) == 56
+    assert C.sizeof(_abi.mgs_grads) == 64
     assert C.sizeof(_abi.mgs_merge_params) == 48
 
 

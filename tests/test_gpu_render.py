@@ -219,3 +219,35 @@ def test_async_render_matches_and_reports_overflow():
         small.check()
     assert int(small.status[1]) == 1 and int(small.status[0]) == ws0.n_keys
     assert float(out[0].alpha.abs().max()) == 0.0  # nothing blended
+
+
+def test_backward_store_mode_equals_accumulating_into_zeros():
+    """grads.overwrite: the backward stores the call's gradients -- what adding them to
+    zeroed arrays gives, up to the rounding order of the float atomics that sum the
+    per-tile moments (relative L2 <= 1e-5) -- with exact zeros for Gaussians no view
+    draws (here a quarter behind the camera), whatever the arrays held; the Eq. 3 sums
+    still accumulate."""
+    rng = np.random.default_rng(21)
+    sc = random_scene(rng, 800, sh_degree=1)
+    sc.means[::4, 2] = -2.0  # behind the camera in both views
+    cams = [camera(96, 80, 90, 90, 47.5, 39.5), camera(96, 80, 100, 95, 45.0, 41.0)]
+    g, imgs, ws = _gpu.render_gpu(sc, cams)
+    grng = np.random.default_rng(22)
+    dL = [api.Image(*(torch.from_numpy(grng.uniform(-1, 1, s).astype(np.float32)).cuda()
+                      for s in ((3, 80, 96), (80, 96), (80, 96)))) for _ in cams]
+    acc = api.Grads.zeros_like(g)
+    api.mgs_render_backward(g, cams, dL, ws, acc)
+    junk = lambda t: torch.full(t.shape, float("nan"), dtype=torch.float32, device=t.device)
+    st = api.Grads(junk(g.means), junk(g.log_scales), junk(g.quats), junk(g.opacity_logit), junk(g.sh),
+                   torch.ones(g.n, device="cuda"), torch.ones(g.n, device="cuda"), overwrite=True)
+    for _ in range(2):  # a second call stores again (the sums keep accumulating)
+        api.mgs_render_backward(g, cams, dL, ws, st)
+    torch.cuda.synchronize()
+    for a, b in zip(acc.tensors(), st.tensors()):
+        assert torch.isfinite(b).all()
+        assert float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(a)) <= 1e-5
+    assert (acc.vis_count[::4] == 0).all()
+    for t in st.tensors():
+        assert (t[::4] == 0).all()
+    torch.testing.assert_close(st.grad_stat, 1 + 2 * acc.grad_stat, rtol=1e-6, atol=0)
+    assert torch.equal(st.vis_count, 1 + 2 * acc.vis_count)
