@@ -331,10 +331,10 @@ static mgs_status render_impl(const mgs_gaussians* maps, int n_maps, const int32
   int tcur = 0;
   {
     ProfScope ps(kProfTileSort, s);
-    tcur = radix_sort_pairs(tk, tv, n_keys, 0, tile_bits(vt.n_tiles), false, scratch, s, &e, -1, keys_dev);
+    // the last pass also writes each tile's [start, end) (sentinel keys, id n_tiles, left out)
+    tcur = radix_sort_pairs(tk, tv, n_keys, 0, tile_bits(vt.n_tiles), false, scratch, s, &e, -1, keys_dev,
+                            nullptr, ranges, (uint32_t)vt.n_tiles);
     if (e != cudaSuccess) return cuda_status(e, "tile sort");
-    MGS_TRY_CUDA(cudaMemsetAsync(ranges, 0, 8 * (size_t)vt.n_tiles, s));
-    MGS_TRY_CUDA(build_ranges(tk[tcur], n_keys, (uint32_t)vt.n_tiles, ranges, s, keys_dev));
   }
   if (async && status_pinned)
     MGS_TRY_CUDA(cudaMemcpyAsync(status_pinned, status, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s));

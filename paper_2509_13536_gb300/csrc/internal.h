@@ -57,18 +57,17 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, const uint32_t* gather, uint3
 // (0 or 1) of the buffer pair that holds the result.  n_dev (optional): the pair count
 // in device memory (<= n, which sizes the launches); n_keep_dev (optional, with
 // n_keep >= 0): the kept count in device memory, for the passes after the first.
+// ranges (optional): filled with [start, end) of every key value < n_valid in the sorted
+// keys ((0, 0) for absent values), by the last pass.
 constexpr uint32_t kSortDrop = 0xffffffffu;
 int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, int end_bit,
                      bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err,
                      int64_t n_keep = -1, const uint32_t* n_dev = nullptr,
-                     const uint32_t* n_keep_dev = nullptr);
+                     const uint32_t* n_keep_dev = nullptr, uint2* ranges = nullptr, uint32_t n_valid = 0);
 inline int radix_passes(int begin_bit, int end_bit) {
   return end_bit > begin_bit ? (end_bit - begin_bit + 7) / 8 : 0;
 }
 
-// [start, end) of every key value < n_valid present in sorted keys (absent values untouched).
-cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s,
-                         const uint32_t* n_dev = nullptr);
 
 // Patch-Grid sampling (pg.cu): workspace layout for one keyframe.
 struct PgLayout {

@@ -204,7 +204,8 @@ template <bool kBallot>
 __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
     uint32_t mask, int nb, const uint32_t* __restrict__ hist, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, bool drop, const uint32_t* __restrict__ n_dev) {
+    uint32_t* __restrict__ vout, bool drop, const uint32_t* __restrict__ n_dev, uint32_t* __restrict__ rng,
+    uint32_t n_valid) {
   n = count_of(n, n_dev);
   if ((int64_t)blockIdx.x * kSortTile >= n) return;  // past the device count: nothing to move
   constexpr int kPerWarp = kSortTile / kWarps;  // 512
@@ -302,37 +303,30 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const uint32_t pos = s_goff[d] + (uint32_t)i - s_boff[d];
     kout[pos] = k;
     vout[pos] = s_val[i];
+    if (rng && k < n_valid) {
+      // Ranges of equal keys, on the last pass: the block's run of digit d is sorted by
+      // key (earlier passes sorted the lower digits), so a change of key inside the run
+      // is a range boundary; a run's first and last keys may continue in the runs of the
+      // neighbouring blocks, so those take atomic min / max (rng: (first, end) pairs).
+      const uint32_t ii = (uint32_t)i, re = d < 255 ? s_boff[d + 1] : s_nkeep;
+      if (ii == s_boff[d]) atomicMin(rng + 2 * k, pos);
+      else if (s_key[i - 1] != k) rng[2 * k] = pos;
+      if (ii + 1 == re) atomicMax(rng + 2 * k + 1, pos + 1);
+      else if (s_key[i + 1] != k) rng[2 * k + 1] = pos + 1;
+    }
   }
 }
 
-// Tile ranges of the sorted keys: four keys per thread (one vector load), neighbours
-// at the ends from the adjacent threads' keys.
-__global__ void k_ranges(const uint32_t* __restrict__ keys, int64_t n, uint32_t n_valid,
-                         uint2* __restrict__ ranges, const uint32_t* __restrict__ n_dev) {
-  n = count_of(n, n_dev);
-  const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  if (k0 >= n) return;
-  uint32_t kk[4];
-  if (k0 + 4 <= n && (reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
-    const uint4 q = *reinterpret_cast<const uint4*>(keys + k0);
-    kk[0] = q.x; kk[1] = q.y; kk[2] = q.z; kk[3] = q.w;
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) kk[q] = k0 + q < n ? keys[k0 + q] : 0xffffffffu;
-  }
-  const uint32_t prev = k0 > 0 ? keys[k0 - 1] : 0xffffffffu;
-  const uint32_t next = k0 + 4 < n ? keys[k0 + 4] : 0xffffffffu;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t k = k0 + q;
-    const uint32_t key = kk[q];
-    if (k >= n || key >= n_valid) continue;  // past the end, or sentinel keys
-    const uint32_t left = q ? kk[q - 1] : prev;
-    const uint32_t right = q < 3 ? kk[q + 1] : next;
-    if (k == 0 || left != key) ranges[key].x = (uint32_t)k;
-    if (k == n - 1 || right != key) ranges[key].y = (uint32_t)(k + 1);
-  }
+__global__ void k_ranges_init(uint2* __restrict__ ranges, uint32_t n) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) ranges[t] = make_uint2(0xffffffffu, 0u);
 }
+
+__global__ void k_ranges_fix(uint2* __restrict__ ranges, uint32_t n) {  // keys absent: empty range
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n && ranges[t].x == 0xffffffffu) ranges[t] = make_uint2(0u, 0u);
+}
+
 
 }  // namespace
 
@@ -361,10 +355,21 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, const uint32_t* gather, uint3
 
 int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, int end_bit,
                      bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err, int64_t n_keep,
-                     const uint32_t* n_dev, const uint32_t* n_keep_dev) {
+                     const uint32_t* n_dev, const uint32_t* n_keep_dev, uint2* ranges, uint32_t n_valid) {
   *err = cudaSuccess;
   int cur = 0;
-  if (n <= 0) return 0;
+  if (ranges) {  // every key value below n_valid starts empty; the last pass fills the ranges
+    k_ranges_init<<<(unsigned)div_up(std::max<uint32_t>(n_valid, 1), 256), 256, 0, s>>>(ranges, n_valid);
+    count_launch();
+  }
+  if (n <= 0) {
+    if (ranges) {
+      k_ranges_fix<<<(unsigned)div_up(std::max<uint32_t>(n_valid, 1), 256), 256, 0, s>>>(ranges, n_valid);
+      count_launch();
+      *err = cudaGetLastError();
+    }
+    return 0;
+  }
   bool drop = n_keep >= 0;  // first pass drops kSortDrop keys; n_keep of them remain
   uint32_t* hist = scratch;
   uint32_t* spine = scratch + align_up((size_t)256 * div_up(n, kSortTile), 64);
@@ -382,12 +387,13 @@ int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, i
     // ids, middle bytes of depths) a warp's 32 keys hold nearly 32 distinct digits.  The
     // top byte and the first, dropping pass of the depth sort hold few distinct digits
     // per round and keep the match instruction.
+    uint32_t* rng = (ranges && shift + 8 >= end_bit) ? reinterpret_cast<uint32_t*>(ranges) : nullptr;
     if (mask == 0xffu && !drop && shift < 24)
       k_radix_scatter<true><<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, mask, nb, hist, k[cur ^ 1],
-                                                        v[cur ^ 1], drop, n_dev);
+                                                        v[cur ^ 1], drop, n_dev, rng, n_valid);
     else
       k_radix_scatter<false><<<nb, kSortThreads, 0, s>>>(k[cur], vin, n, shift, mask, nb, hist, k[cur ^ 1],
-                                                         v[cur ^ 1], drop, n_dev);
+                                                         v[cur ^ 1], drop, n_dev, rng, n_valid);
     cur ^= 1;
     first = false;
     if (drop) {
@@ -404,15 +410,13 @@ int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, i
     // no pass ran: materialise the identity permutation
     *err = cudaErrorInvalidValue;
   }
+  if (ranges && *err == cudaSuccess) {
+    k_ranges_fix<<<(unsigned)div_up(std::max<uint32_t>(n_valid, 1), 256), 256, 0, s>>>(ranges, n_valid);
+    count_launch();
+    *err = cudaGetLastError();
+  }
   return cur;
 }
 
-cudaError_t build_ranges(const uint32_t* keys, int64_t n, uint32_t n_valid, uint2* ranges, cudaStream_t s,
-                         const uint32_t* n_dev) {
-  if (n <= 0) return cudaSuccess;
-  k_ranges<<<(unsigned)div_up(div_up(n, 4), 256), 256, 0, s>>>(keys, n, n_valid, ranges, n_dev);
-  count_launch();
-  return cudaGetLastError();
-}
 
 }  // namespace mgs
