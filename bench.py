@@ -59,8 +59,8 @@ def algorithmic_bytes(n, views, stats, pb, pixels):
                                         "the item index), 8 B written per drawn item, three more passes of 20 B "
                                         "per drawn item, the scan of the key counts (12 B per drawn item)"),
         "emit": (52 * d + 8 * k, "52 B read per drawn item (order, offset, count, rect, conic), 8 B per key written"),
-        "tile_sort": (44 * k, "two passes of 20 B per key (histogram read, key and value read and written) "
-                              "+ 4 B per key for the tile ranges"),
+        "tile_sort": (40 * k, "two passes of 20 B per key (histogram read, key and value read and written); "
+                              "the last pass also writes the tile ranges"),
         "preprocess_bwd": (n * (pb + g32 + 16) + 12 * vn + 48 * d,
                            "parameters read, f32 gradients written (the step's backward stores them), "
                            "Eq. 3 sums read and written, 12 B per item, 48 B moments per drawn item"),
