@@ -203,40 +203,6 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(int W, int H, const Window win
   }
 }
 
-// lambda = 0 (the L1 form of Eq. 12): no SSIM term.  Same grid and partial layout as
-// k_ssim_fwd (the SSIM slot of each partial is 0, which lambda = 0 ignores), and the
-// cotangent k_ssim_bwd would write: sign(x - y) / n.
-__global__ void __launch_bounds__(256) k_l1_rgb(int W, int H, const __grid_constant__ Planes P,
-                                                float* __restrict__ part) {
-  __shared__ float red[8];
-  const int v = blockIdx.z / 3, c = blockIdx.z % 3;
-  const size_t HW = (size_t)W * H;
-  const float* X = P.x[v] + c * HW;
-  const float* Y = P.y[v] + c * HW;
-  float* G = P.grgb[v] + c * HW;
-  const float inv_n = 1.f / (3.f * (float)HW);
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  float l1 = 0.f;
-  for (int i = threadIdx.x; i < kTX * kTY; i += blockDim.x) {
-    const int gx = x0 + (i % kTX), gy = y0 + i / kTX;
-    if (gx >= W || gy >= H) continue;
-    const size_t q = (size_t)gy * W + gx;
-    const float diff = X[q] - Y[q];
-    l1 += fabsf(diff);
-    G[q] = (diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f)) * inv_n;
-  }
-  for (int o = 16; o; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l1;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float b = 0.f;
-    for (int k = 0; k < 8; ++k) b += red[k];
-    const size_t bi = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    part[2 * bi] = 0.f;
-    part[2 * bi + 1] = b;
-  }
-}
-
 // Depth residual: one thread per pixel of every view; block partials of |d - dt|.
 __global__ void __launch_bounds__(256) k_depth_l1(int W, int H, float w_depth,
                                                   const __grid_constant__ Planes P, float* __restrict__ part) {
@@ -267,19 +233,105 @@ __global__ void __launch_bounds__(256) k_depth_l1(int W, int H, float w_depth,
   }
 }
 
+// The loss with lambda = 0 (no SSIM): the rgb L1 and the depth residual of 4
+// consecutive pixels per thread in one pass (16-byte accesses when every plane allows),
+// block partials (0, l1) into part_rgb and the depth sums into part_depth, both at
+// view v's stride.
+constexpr int kFlatPx = 4 * 256;  // pixels per block of k_l1_depth
+
+__device__ __forceinline__ float sgn(float d) { return d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f); }
+
+__global__ void __launch_bounds__(256) k_l1_depth(int W, int H, float w_depth, const __grid_constant__ Planes P,
+                                                  bool vec, float* __restrict__ part_rgb, size_t stride_rgb,
+                                                  float* __restrict__ part_depth, size_t stride_depth) {
+  __shared__ float red[2][8];
+  const size_t HW = (size_t)W * H;
+  const int v = blockIdx.y;
+  const size_t p0 = (size_t)blockIdx.x * kFlatPx + 4 * threadIdx.x;
+  const float inv_rgb = 1.f / (3.f * (float)HW);
+  const float* Dt = P.dt[v];
+  float l1 = 0.f, dd = 0.f;
+  if (vec && p0 + 4 <= HW) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float4 x = *reinterpret_cast<const float4*>(P.x[v] + c * HW + p0);
+      const float4 y = *reinterpret_cast<const float4*>(P.y[v] + c * HW + p0);
+      const float4 d = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+      l1 += fabsf(d.x) + fabsf(d.y) + fabsf(d.z) + fabsf(d.w);
+      *reinterpret_cast<float4*>(P.grgb[v] + c * HW + p0) =
+          make_float4(sgn(d.x) * inv_rgb, sgn(d.y) * inv_rgb, sgn(d.z) * inv_rgb, sgn(d.w) * inv_rgb);
+    }
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (Dt) {
+      const float4 t = *reinterpret_cast<const float4*>(Dt + p0);
+      const float4 r = *reinterpret_cast<const float4*>(P.d[v] + p0);
+      const float e[4] = {r.x - t.x, r.y - t.y, r.z - t.z, r.w - t.w};
+      const float tt[4] = {t.x, t.y, t.z, t.w};
+      float gg[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool on = tt[k] > 0.f;
+        dd += on ? fabsf(e[k]) : 0.f;
+        gg[k] = on ? w_depth * sgn(e[k]) / (float)HW : 0.f;
+      }
+      g = make_float4(gg[0], gg[1], gg[2], gg[3]);
+    }
+    if (P.gd[v]) *reinterpret_cast<float4*>(P.gd[v] + p0) = g;
+  } else {
+    for (size_t p = p0; p < p0 + 4 && p < HW; ++p) {
+      for (int c = 0; c < 3; ++c) {
+        const float d = P.x[v][c * HW + p] - P.y[v][c * HW + p];
+        l1 += fabsf(d);
+        P.grgb[v][c * HW + p] = sgn(d) * inv_rgb;
+      }
+      float g = 0.f;
+      if (Dt) {
+        const float t = Dt[p], e = P.d[v][p] - t;
+        if (t > 0.f) {
+          dd += fabsf(e);
+          g = w_depth * sgn(e) / (float)HW;
+        }
+      }
+      if (P.gd[v]) P.gd[v][p] = g;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = l1;
+    red[1][threadIdx.x >> 5] = dd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f, b = 0.f;
+    for (int k = 0; k < 8; ++k) {
+      a += red[0][k];
+      b += red[1][k];
+    }
+    part_rgb[2 * (v * stride_rgb + blockIdx.x)] = 0.f;
+    part_rgb[2 * (v * stride_rgb + blockIdx.x) + 1] = a;
+    part_depth[v * stride_depth + blockIdx.x] = b;
+  }
+}
+
 // Per view: add the block partials in a fixed order (double accumulator) and weight them.
-__global__ void k_loss_reduce(int n_views, int nb_ssim, int nb_depth, const float* __restrict__ part_ssim,
+// View v's rgb partials are (ssim, l1) pairs n_rgb_parts long at v * stride_rgb, its
+// depth partials n_depth_parts long at v * stride_depth.
+__global__ void k_loss_reduce(int n_views, int n_rgb_parts, size_t stride_rgb, int n_depth_parts,
+                              size_t stride_depth, const float* __restrict__ part_ssim,
                               const float* __restrict__ part_depth, float lambda, float w_depth,
                               double n_rgb, double n_px, float* __restrict__ loss) {
   const int v = blockIdx.x;
   __shared__ double red[3][256];
   double s = 0, l1 = 0, dd = 0;
-  for (int i = threadIdx.x; i < 3 * nb_ssim; i += blockDim.x) {
-    const size_t bi = (size_t)v * 3 * nb_ssim + i;
+  for (int i = threadIdx.x; i < n_rgb_parts; i += blockDim.x) {
+    const size_t bi = (size_t)v * stride_rgb + i;
     s += part_ssim[2 * bi];
     l1 += part_ssim[2 * bi + 1];
   }
-  for (int i = threadIdx.x; i < nb_depth; i += blockDim.x) dd += part_depth[(size_t)v * nb_depth + i];
+  for (int i = threadIdx.x; i < n_depth_parts; i += blockDim.x) dd += part_depth[(size_t)v * stride_depth + i];
   red[0][threadIdx.x] = s; red[1][threadIdx.x] = l1; red[2][threadIdx.x] = dd;
   __syncthreads();
   for (int o = blockDim.x / 2; o; o >>= 1) {
@@ -386,18 +438,31 @@ cudaError_t launch_mapping_loss(int n_views, int width, int height, const LossLa
   float* part_depth = reinterpret_cast<float*>(ws + L.part_depth);
   const Window win = make_window();
   const dim3 grid(L.tiles_x, L.tiles_y, 3 * n_views);
-  if (lambda == 0.f) {
-    k_l1_rgb<<<grid, 256, 0, s>>>(width, height, P, part_ssim);
-  } else {
-    k_ssim_fwd<<<grid, 256, 0, s>>>(width, height, win, P, dmaps, part_ssim);
-    k_ssim_bwd<<<grid, 256, 0, s>>>(width, height, win, lambda, P, dmaps);
-    count_launch();
-  }
-  k_depth_l1<<<dim3(L.nb_depth, n_views), 256, 0, s>>>(width, height, w_depth, P, part_depth);
   const double HW = (double)width * height;
-  k_loss_reduce<<<n_views, 256, 0, s>>>(n_views, L.nb_ssim, L.nb_depth, part_ssim, part_depth, lambda, w_depth,
+  if (lambda == 0.f) {
+    // one pass for the rgb L1 and the depth residual; its partials fit the SSIM layout
+    // (HW / 1024 blocks per view <= 3 x 32x32 tiles, HW / 1024 <= HW / 256)
+    const size_t hw = (size_t)width * height;
+    bool vec = hw % 4 == 0;
+    for (int v = 0; v < n_views && vec; ++v)
+      for (const void* q : {(const void*)P.x[v], (const void*)P.y[v], (const void*)P.d[v], (const void*)P.dt[v],
+                            (const void*)P.grgb[v], (const void*)P.gd[v]})
+        vec = vec && (reinterpret_cast<uintptr_t>(q) & 15) == 0;
+    const int nbf = (int)div_up(hw, (size_t)kFlatPx);
+    k_l1_depth<<<dim3(nbf, n_views), 256, 0, s>>>(width, height, w_depth, P, vec, part_ssim,
+                                                  (size_t)3 * L.nb_ssim, part_depth, (size_t)L.nb_depth);
+    k_loss_reduce<<<n_views, 256, 0, s>>>(n_views, nbf, (size_t)3 * L.nb_ssim, nbf, (size_t)L.nb_depth,
+                                          part_ssim, part_depth, lambda, w_depth, 3.0 * HW, HW, loss);
+    count_launch(2);
+    return cudaGetLastError();
+  }
+  k_ssim_fwd<<<grid, 256, 0, s>>>(width, height, win, P, dmaps, part_ssim);
+  k_ssim_bwd<<<grid, 256, 0, s>>>(width, height, win, lambda, P, dmaps);
+  k_depth_l1<<<dim3(L.nb_depth, n_views), 256, 0, s>>>(width, height, w_depth, P, part_depth);
+  k_loss_reduce<<<n_views, 256, 0, s>>>(n_views, 3 * L.nb_ssim, (size_t)3 * L.nb_ssim, L.nb_depth,
+                                        (size_t)L.nb_depth, part_ssim, part_depth, lambda, w_depth,
                                         3.0 * HW, HW, loss);
-  count_launch(3);
+  count_launch(4);
   return cudaGetLastError();
 }
 
