@@ -37,7 +37,8 @@ struct AdamTable {
   int n_seg;
 };
 constexpr int kAdamThreads = 256;
-constexpr int kAdamPerBlock = 4 * kAdamThreads;
+constexpr int kAdamUnroll = 2;  // 16-byte groups per thread, strided by the block's width
+constexpr int kAdamPerBlock = 4 * kAdamThreads * kAdamUnroll;
 
 template <typename T>
 __device__ __forceinline__ void adam_seg(T* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
@@ -82,11 +83,15 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(const __grid_constant__ A
   while (s + 1 < tab.n_seg && (int)blockIdx.x >= tab.seg[s].block_end) ++s;
   const AdamSeg& q = tab.seg[s];
   const int b0 = s ? tab.seg[s - 1].block_end : 0;
-  const int64_t i = ((int64_t)((int)blockIdx.x - b0) * kAdamThreads + threadIdx.x) * 4;
-  switch (q.dt) {  // uniform per block
-    case MGS_F16: adam_seg((__half*)q.p, q.g, q.m, q.v, q.n, i, h); break;
-    case MGS_BF16: adam_seg((__nv_bfloat16*)q.p, q.g, q.m, q.v, q.n, i, h); break;
-    default: adam_seg((float*)q.p, q.g, q.m, q.v, q.n, i, h); break;
+  const int64_t i0 = (int64_t)((int)blockIdx.x - b0) * kAdamPerBlock + 4 * threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < kAdamUnroll; ++u) {
+    const int64_t i = i0 + (int64_t)u * 4 * kAdamThreads;
+    switch (q.dt) {  // uniform per block
+      case MGS_F16: adam_seg((__half*)q.p, q.g, q.m, q.v, q.n, i, h); break;
+      case MGS_BF16: adam_seg((__nv_bfloat16*)q.p, q.g, q.m, q.v, q.n, i, h); break;
+      default: adam_seg((float*)q.p, q.g, q.m, q.v, q.n, i, h); break;
+    }
   }
 }
 
