@@ -161,14 +161,18 @@ __global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant
 // entry into the ten moments the chain rule of Eq. 1-2 needs.
 constexpr int kBwdBatch = 16;
 constexpr int kBwdStride = kBwdBatch + 2;  // padded row: 16-byte aligned, conflict-free both ways
-constexpr int kBwdWarps = kTilePix / 32;
+// CTAs per tile: each takes 16 / kBwdSplit rows, so its barriers wait only for the pixels
+// of its own part and it walks only down to its own longest list
+constexpr int kBwdSplit = 1;
+constexpr int kBwdThreads = kTilePix / kBwdSplit;
+constexpr int kBwdWarps = kBwdThreads / 32;
 constexpr int kMom = 10;
 constexpr int kRedStride = kMom + 1;     // per-entry row of partial moments (odd: no conflicts)
 
 struct BwdSmem {
-  float2 gw[kTilePix][kBwdStride];          // (gp, w) per pixel and entry; after the Gaussian
+  float2 gw[kBwdThreads][kBwdStride];       // (gp, w) per pixel and entry; after the Gaussian
                                             // phase each warp's rows hold its partial moments
-  float4 g[kTilePix];                       // per pixel dL/d(r, g, b, depth)
+  float4 g[kBwdThreads];                    // per pixel dL/d(r, g, b, depth)
   float4 raw[2][kBwdBatch][3];              // records of the next batch, landed by cp.async
   // entries 2p and 2p+1 side by side, so one 16-byte load gives two operand pairs
   float4 q_xy[2][kBwdBatch / 2];            // (x, x', y, y') tile-relative centre
@@ -188,21 +192,22 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-__global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant__ ViewTable vt,
+__global__ void __launch_bounds__(kBwdThreads, 5 * kBwdSplit) k_blend_bwd(const __grid_constant__ ViewTable vt,
                                                            const float4* __restrict__ rec,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint2* __restrict__ ranges,
                                                            float4* __restrict__ moments) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
-  const int tile = blockIdx.x;
+  const int tile = blockIdx.x / kBwdSplit, part = blockIdx.x % kBwdSplit;
+  const int row0 = part * (kTile / kBwdSplit);  // first tile row of this CTA's part
   const View& V = vt.v[view_of_tile(vt, tile)];
   const int local = tile - V.tile_base;
   const int x0 = (local % V.tiles_x) * kTile, y0 = (local / V.tiles_x) * kTile;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   // each warp an 8x4 block of the tile (bx = warp & 1, by = warp >> 1); half-warp h holds
   // its rows 2h and 2h + 1, eight pixels each
-  const int lx = 8 * (warp & 1) + (lane & 7), ly = 4 * (warp >> 1) + (lane >> 3);
+  const int lx = 8 * (warp & 1) + (lane & 7), ly = row0 + 4 * (warp >> 1) + (lane >> 3);
   const int px = x0 + lx, py = y0 + ly;
   const bool inside = px < V.width && py < V.height;
   const float pxf = (float)lx, pyf = (float)ly, x0f = (float)x0, y0f = (float)y0;
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
       }
       const float* const qxy = reinterpret_cast<const float*>(&S.q_xy[buf][e >> 1]);
       const float xc = qxy[e & 1] - (float)(8 * (warp & 1)) - 3.5f;
-      const float dy0 = qxy[2 + (e & 1)] - (float)(4 * (warp >> 1) + 2 * half);
+      const float dy0 = qxy[2 + (e & 1)] - (float)(row0 + 4 * (warp >> 1) + 2 * half);
       const float dy1 = dy0 - 1.f;
       const float ma = fmaf(xc, s0[0], -k1[0]), mb = fmaf(xc, s0[1], -k1[1]);  // sum gp (xc - kc)
       m[0] = s0[0] + s0[1];
@@ -417,10 +422,11 @@ __global__ void __launch_bounds__(kTilePix, 5) k_blend_bwd(const __grid_constant
       for (int k = 0; k < kMom; ++k) red_own[e * kRedStride + k] = m[k];
     }
     __syncthreads();
-    // Cross-warp sum, spread over all threads: half-warp q owns entry q, its lane k
-    // moment k; lanes 0, 4, 8 then add four consecutive moments with one vector atomic.
-    {
-      const int q = 2 * warp + half, k = e;
+    // Cross-warp sum, spread over all threads: half-warp q owns entries q, q + 2 warps, ...,
+    // its lane k moment k; lanes 0, 4, 8 then add four consecutive moments with one
+    // vector atomic.
+    for (int q = 2 * warp + half; q < kBwdBatch; q += 2 * kBwdWarps) {
+      const int k = e;
       float r = 0.f;
       if (q < cnt && k < kMom) {
 #pragma unroll
@@ -530,7 +536,7 @@ cudaError_t launch_blend_bwd(const ViewTable& vt, const float4* rec, const uint3
   cudaError_t e = cudaFuncSetAttribute(k_blend_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(BwdSmem));
   if (e != cudaSuccess) return e;
-  k_blend_bwd<<<vt.n_tiles, kTilePix, sizeof(BwdSmem), s>>>(vt, rec, vals, ranges, moments);
+  k_blend_bwd<<<vt.n_tiles * kBwdSplit, kBwdThreads, sizeof(BwdSmem), s>>>(vt, rec, vals, ranges, moments);
   count_launch();
   return cudaGetLastError();
 }
