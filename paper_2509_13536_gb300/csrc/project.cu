@@ -64,6 +64,15 @@ struct ViewGeom {
   float dir[3], vnorm;
 };
 
+// Unit view direction mu - C (the camera centre as a double-float pair) and its length.
+__device__ __forceinline__ void view_direction(const float mu[3], const View& V, float dir[3], float& vnorm) {
+  float d[3] = {__fsub_rn(__fsub_rn(mu[0], V.C[0]), V.C_lo[0]), __fsub_rn(__fsub_rn(mu[1], V.C[1]), V.C_lo[1]),
+                __fsub_rn(__fsub_rn(mu[2], V.C[2]), V.C_lo[2])};
+  vnorm = sqrtf(__fmaf_rn(d[2], d[2], __fmaf_rn(d[1], d[1], __fmul_rn(d[0], d[0]))));
+  const float iv = __frcp_rn(vnorm);
+  dir[0] = __fmul_rn(d[0], iv); dir[1] = __fmul_rn(d[1], iv); dir[2] = __fmul_rn(d[2], iv);
+}
+
 __device__ __forceinline__ void view_geom(const GaussPre& G, const View& V, ViewGeom& P) {
   DF p[3];
 #pragma unroll
@@ -118,11 +127,7 @@ __device__ __forceinline__ void view_geom(const GaussPre& G, const View& V, View
   P.A = P.c * idet;
   P.B = -P.b * idet;
   P.C = P.a * idet;
-  float d[3] = {__fsub_rn(__fsub_rn(G.mu[0], V.C[0]), V.C_lo[0]), __fsub_rn(__fsub_rn(G.mu[1], V.C[1]), V.C_lo[1]),
-                __fsub_rn(__fsub_rn(G.mu[2], V.C[2]), V.C_lo[2])};
-  P.vnorm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-  float iv = 1.f / P.vnorm;
-  P.dir[0] = d[0] * iv; P.dir[1] = d[1] * iv; P.dir[2] = d[2] * iv;
+  view_direction(G.mu, V, P.dir, P.vnorm);
 }
 
 // Tile rect of the square of half-width r around the centre (inclusive bounds).
@@ -163,6 +168,11 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
                                                     uint32_t* __restrict__ touched,
                                                     uint32_t* __restrict__ dkeys,
                                                     unsigned long long* __restrict__ counters) {
+  // Two loops per Gaussian: the first projects it into every view (the geometry words of
+  // the record, the rect, the depth bits) and notes the views that draw it; the second
+  // walks only those views for the SH colour and the tile count.  A warp then runs the
+  // colour and culling code as often as its busiest lane has drawn views, not once for
+  // every view some lane draws.
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long my_keys = 0;
   unsigned int my_vis = 0;
@@ -170,33 +180,48 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
     GaussPre G;
     load_gauss(g, means, geo, ol, G);
     constexpr int K3 = (DEG + 1) * (DEG + 1) * 3;
+    const float lo = log2f(G.o);
+    uint32_t drawn = 0;
     for (int v = 0; v < vt.n_views; ++v) {
       const View& V = vt.v[v];
-      int64_t item = (int64_t)v * N + g;
+      const int64_t item = (int64_t)v * N + g;
       ViewGeom P;
       view_geom(G, V, P);
       int r = 0, rc[4];
-      bool vis = P.ok && tile_rect(P, V, r, rc);
-      uint32_t count = 0;
-      if (vis) {
-        float raw[3];
-        float c[K3];
-        load_sh<DEG>(g, sh, c);  // per drawn view: the coefficients come from L1 after the first
-        colour<DEG>(c, P.dir, raw);
-        float4 r0 = make_float4(P.u_hi, P.v_hi, P.u_lo, P.v_lo);
-        float4 r1 = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, log2f(G.o));
-        rec[3 * item + 0] = r0;
-        rec[3 * item + 1] = r1;
-        rec[3 * item + 2] = make_float4(fmaxf(0.f, raw[0]), fmaxf(0.f, raw[1]), fmaxf(0.f, raw[2]), P.tz);
+      if (P.ok && tile_rect(P, V, r, rc)) {
+        rec[3 * item + 0] = make_float4(P.u_hi, P.v_hi, P.u_lo, P.v_lo);
+        rec[3 * item + 1] = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, lo);
         rects[item] = make_uint2((uint32_t)rc[0] | ((uint32_t)rc[1] << 16), (uint32_t)rc[2] | ((uint32_t)rc[3] << 16));
-        count = cull_count(make_cull(r0, r1), rc);
+        dkeys[item] = __float_as_uint(P.tz);  // the second loop keeps it or drops the item
+        drawn |= 1u << v;
       } else {
         rects[item] = make_uint2(1u, 0u);  // empty rect: x0 = 1 > x1 = 0
+        touched[item] = 0;
+        dkeys[item] = kSortDrop;  // undrawn: left out by the depth sort
       }
-      touched[item] = count;
-      dkeys[item] = count ? __float_as_uint(P.tz) : kSortDrop;  // undrawn: left out by the depth sort
-      my_keys += count;
-      my_vis += count ? 1u : 0u;
+    }
+    if (drawn) {
+      float c[K3];
+      load_sh<DEG>(g, sh, c);
+      while (drawn) {
+        const int v = __ffs(drawn) - 1;
+        drawn &= drawn - 1;
+        const View& V = vt.v[v];
+        const int64_t item = (int64_t)v * N + g;
+        const float4 r0 = rec[3 * item + 0], r1 = rec[3 * item + 1];
+        const uint2 pr = rects[item];
+        const int rc[4] = {(int)(pr.x & 0xffff), (int)(pr.x >> 16), (int)(pr.y & 0xffff), (int)(pr.y >> 16)};
+        const uint32_t count = cull_count(make_cull(r0, r1), rc);
+        float dir[3], vnorm, raw[3];
+        view_direction(G.mu, V, dir, vnorm);
+        colour<DEG>(c, dir, raw);
+        const float tz = __uint_as_float(dkeys[item]);
+        rec[3 * item + 2] = make_float4(fmaxf(0.f, raw[0]), fmaxf(0.f, raw[1]), fmaxf(0.f, raw[2]), tz);
+        touched[item] = count;
+        if (!count) dkeys[item] = kSortDrop;
+        my_keys += count;
+        my_vis += count ? 1u : 0u;
+      }
     }
   }
   for (int o = 16; o; o >>= 1) {
