@@ -201,8 +201,6 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
       }
     }
     if (drawn) {
-      float c[K3];
-      load_sh<DEG>(g, sh, c);
       while (drawn) {
         const int v = __ffs(drawn) - 1;
         drawn &= drawn - 1;
@@ -214,7 +212,19 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
         const uint32_t count = cull_count(make_cull(r0, r1), rc);
         float dir[3], vnorm, raw[3];
         view_direction(G.mu, V, dir, vnorm);
-        colour<DEG>(c, dir, raw);
+        {  // colour: the coefficients stream from L1 (the row is read again for every drawn view)
+          constexpr int K = (DEG + 1) * (DEG + 1);
+          float Y[K];
+          sh_basis<DEG>(dir, Y, nullptr);
+          const T* p = sh + g * K3;
+#pragma unroll
+          for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = __fmaf_rn(ld(p + 3 * k + ch), Y[k], acc);
+            raw[ch] = acc;
+          }
+        }
         const float tz = __uint_as_float(dkeys[item]);
         rec[3 * item + 2] = make_float4(fmaxf(0.f, raw[0]), fmaxf(0.f, raw[1]), fmaxf(0.f, raw[2]), tz);
         touched[item] = count;
