@@ -590,20 +590,32 @@ __global__ void k_hash_scatter(int64_t n, const uint32_t* __restrict__ slot, con
   if (s != kNoKey) perm[toff[s] + rank[i]] = (uint32_t)i;
 }
 
-__global__ void k_hash_segs(uint32_t tsize, const uint32_t* __restrict__ tcount, const uint32_t* __restrict__ toff,
-                            uint2* __restrict__ segs, uint32_t* __restrict__ n_vox) {
+// One atomic on the voxel counter per block (its warps' counts meet in shared memory):
+// one per warp serialised tens of thousands of atomics on a single address.
+__global__ void __launch_bounds__(256) k_hash_segs(uint32_t tsize, const uint32_t* __restrict__ tcount,
+                                                   const uint32_t* __restrict__ toff, uint2* __restrict__ segs,
+                                                   uint32_t* __restrict__ n_vox) {
+  __shared__ uint32_t s_cnt[8], s_base;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t c = t < tsize ? tcount[t] : 0u;
   const bool multi = c >= 2;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t mask = __ballot_sync(0xffffffffu, multi);
-  if (!mask) return;
-  const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(n_vox, (uint32_t)__popc(mask));
-  base = __shfl_sync(0xffffffffu, base, leader);
+  if (lane == 0) s_cnt[w] = (uint32_t)__popc(mask);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t x = s_cnt[k];
+      s_cnt[k] = tot;
+      tot += x;
+    }
+    s_base = tot ? atomicAdd(n_vox, tot) : 0u;
+  }
+  __syncthreads();
   if (multi) {
     const uint32_t f = toff[t];
-    segs[base + __popc(mask & ((1u << lane) - 1u))] = make_uint2(f, f + c);
+    segs[s_base + s_cnt[w] + __popc(mask & ((1u << lane) - 1u))] = make_uint2(f, f + c);
   }
 }
 
