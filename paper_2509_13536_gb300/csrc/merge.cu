@@ -834,8 +834,18 @@ __global__ void __launch_bounds__(128) k_voxel_pairs(
     }
     __syncwarp();
     uint32_t slot = 0;
-    if (gl == 0 && np > 0) slot = atomicAdd(n_pairs, (uint32_t)np);
-    slot = __shfl_sync(0xffffffffu, slot, gbase);
+    {  // one atomic per warp for the pairs of its groups (np is uniform within a group)
+      uint32_t tot = 0, pre = 0;
+#pragma unroll
+      for (int q = 0; q < 32 / kGroupVoxel; ++q) {
+        const uint32_t x = (uint32_t)__shfl_sync(0xffffffffu, np, q * kGroupVoxel);
+        if (q < grp) pre += x;
+        tot += x;
+      }
+      uint32_t base = 0;
+      if (lane == 0 && tot) base = atomicAdd(n_pairs, tot);
+      slot = __shfl_sync(0xffffffffu, base, 0) + pre;
+    }
     if (gl < np) {
       const int64_t i = s_idx[wib][gbase + s_pairs[wib][grp * (kGroupVoxel / 2) + gl][0]];
       const int64_t j = s_idx[wib][gbase + s_pairs[wib][grp * (kGroupVoxel / 2) + gl][1]];

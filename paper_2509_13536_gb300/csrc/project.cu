@@ -238,9 +238,25 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
     my_keys += __shfl_xor_sync(0xffffffffu, my_keys, o);
     my_vis += __shfl_xor_sync(0xffffffffu, my_vis, o);
   }
-  if ((threadIdx.x & 31) == 0 && (my_keys || my_vis)) {
-    atomicAdd(&counters[0], my_keys);
-    atomicAdd(&counters[1], (unsigned long long)my_vis);
+  // one pair of atomics per block: per warp, tens of thousands of atomics on two
+  // addresses serialise
+  __shared__ unsigned long long s_keys[8];
+  __shared__ unsigned int s_vis[8];
+  if ((threadIdx.x & 31) == 0) {
+    s_keys[threadIdx.x >> 5] = my_keys;
+    s_vis[threadIdx.x >> 5] = my_vis;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long k = 0, vv = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      k += s_keys[w];
+      vv += s_vis[w];
+    }
+    if (k || vv) {
+      atomicAdd(&counters[0], k);
+      atomicAdd(&counters[1], vv);
+    }
   }
 }
 
