@@ -13,8 +13,8 @@ cudaError_t launch_preprocess(const mgs_gaussians& g, const ViewTable& vt, float
                               uint32_t* touched, uint32_t* dkeys, unsigned long long* counters,
                               cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const mgs_gaussians& g, const ViewTable& vt, const float4* moments,
-                                  const uint32_t* touched, const uint2* rects, const mgs_grads& gr,
-                                  cudaStream_t s);
+                                  const uint32_t* touched, const uint2* rects, const BwdPlan& pl,
+                                  const mgs_grads& gr, cudaStream_t s);
 cudaError_t launch_project_one(const mgs_gaussians& g, const View& V, float* mean2d, float* conic,
                                float* rgb, float* depth, int32_t* radius, int32_t* rect, cudaStream_t s);
 cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const uint32_t* offsets,
@@ -49,7 +49,7 @@ mgs_status fail(mgs_status st, const std::string& msg) {
 struct RenderLayout {
   int64_t N = 0, VN = 0, pixels = 0, tiles = 0, key_cap = 0;
   size_t hdr, rec, rects, touched, dkeys[2], dvals[2], offsets, tkeys[2], tvals[2], ranges,
-      tfinal, ncontrib, moments, scratch, total;
+      tfinal, ncontrib, moments, plan, scratch, total;
 };
 
 bool cams_valid(const mgs_camera* cams, int nv, std::string* why) {
@@ -111,6 +111,7 @@ RenderLayout render_layout(const ViewItems& items, const mgs_camera* cams, int n
   L.tfinal = take(4 * (size_t)L.pixels);
   L.ncontrib = take(4 * (size_t)L.pixels);
   L.moments = take(48 * vn);
+  L.plan = take(2 * kPlanCountWords * sizeof(uint32_t));
   L.scratch = take(4 * (size_t)sort_scratch_words(std::max<int64_t>(L.VN, key_cap)));
   L.total = off;
   return L;
@@ -422,8 +423,13 @@ mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams, i
   }
   {
     ProfScope ps(kProfPreprocessBwd, s);
+    // the work plan takes the depth-sort buffers, free once the forward has emitted its
+    // keys (each holds 4 x VN >= 4 x N bytes)
+    const BwdPlan pl{at<uint32_t>(workspace, L.dvals[1]), at<uint32_t>(workspace, L.offsets),
+                     at<uint32_t>(workspace, L.plan), at<uint32_t>(workspace, L.dkeys[0]),
+                     at<uint32_t>(workspace, L.dkeys[1]), at<uint32_t>(workspace, L.dvals[0])};
     MGS_TRY_CUDA(launch_preprocess_bwd(*g, vt, moments, at<uint32_t>(workspace, L.touched),
-                                       at<uint2>(workspace, L.rects), *grads, s));
+                                       at<uint2>(workspace, L.rects), pl, *grads, s));
   }
   return MGS_OK;
 }

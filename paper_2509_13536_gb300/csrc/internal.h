@@ -68,6 +68,19 @@ inline int radix_passes(int begin_bit, int end_bit) {
   return end_bit > begin_bit ? (end_bit - begin_bit + 7) / 8 : 0;
 }
 
+// Work plan of the reverse projection (project.cu): device buffers of N words each,
+// except `counts`, which holds 2 x kPlanCountWords words (bucket sizes, then the
+// scatter's cursors) and is cleared by the launch.
+constexpr int kPlanCountWords = 64;
+struct BwdPlan {
+  uint32_t* gdrawn;  // per Gaussian: views that draw it
+  uint32_t* gtodo;   // per Gaussian: drawing views in which it reached a tile
+  uint32_t* counts;
+  uint32_t* list;    // plan order: Gaussian index, its drawing views, its gradient views
+  uint32_t* ldrawn;
+  uint32_t* ltodo;
+};
+
 
 // Patch-Grid sampling (pg.cu): workspace layout for one keyframe.
 struct PgLayout {
