@@ -21,9 +21,11 @@ cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const u
                         const uint32_t* touched, const uint2* rects, const float4* rec, const ViewTable& vt,
                         uint32_t* tkeys, uint32_t* tvals, cudaStream_t s, const uint32_t* n_vis_dev = nullptr);
 cudaError_t launch_blend_fwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
-                             const uint2* ranges, cudaStream_t s);
+                             const uint2* ranges, const uint32_t* order, cudaStream_t s);
 cudaError_t launch_blend_bwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
-                             const uint2* ranges, float4* moments, cudaStream_t s);
+                             const uint2* ranges, const uint32_t* order, float4* moments, cudaStream_t s);
+cudaError_t launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* counts, uint32_t* order,
+                              cudaStream_t s);
 cudaError_t launch_frag_stats(const ViewTable& vt, const float4* rec, const uint32_t* vals,
                               const uint2* ranges, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_adam(const mgs_gaussians_mut& p, const mgs_grads& g, const mgs_grads& m,
@@ -49,7 +51,7 @@ mgs_status fail(mgs_status st, const std::string& msg) {
 struct RenderLayout {
   int64_t N = 0, VN = 0, pixels = 0, tiles = 0, key_cap = 0;
   size_t hdr, rec, rects, touched, dkeys[2], dvals[2], offsets, tkeys[2], tvals[2], ranges,
-      tfinal, ncontrib, moments, plan, scratch, total;
+      order, ocounts, tfinal, ncontrib, moments, plan, scratch, total;
 };
 
 bool cams_valid(const mgs_camera* cams, int nv, std::string* why) {
@@ -108,6 +110,8 @@ RenderLayout render_layout(const ViewItems& items, const mgs_camera* cams, int n
   L.tvals[0] = take(4 * kc);
   L.tvals[1] = take(4 * kc);
   L.ranges = take(8 * (size_t)L.tiles);
+  L.order = take(4 * (size_t)L.tiles);
+  L.ocounts = take(512);
   L.tfinal = take(4 * (size_t)L.pixels);
   L.ncontrib = take(4 * (size_t)L.pixels);
   L.moments = take(48 * vn);
@@ -336,12 +340,16 @@ static mgs_status render_impl(const mgs_gaussians* maps, int n_maps, const int32
     tcur = radix_sort_pairs(tk, tv, n_keys, 0, tile_bits(vt.n_tiles), false, scratch, s, &e, -1, keys_dev,
                             nullptr, ranges, (uint32_t)vt.n_tiles);
     if (e != cudaSuccess) return cuda_status(e, "tile sort");
+    // the blend launches (forward, and the reverse pass on this workspace) take the tiles
+    // longest list first
+    MGS_TRY_CUDA(launch_tile_order(ranges, (int)vt.n_tiles, at<uint32_t>(workspace, L.ocounts),
+                                   at<uint32_t>(workspace, L.order), s));
   }
   if (async && status_pinned)
     MGS_TRY_CUDA(cudaMemcpyAsync(status_pinned, status, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s));
   {
     ProfScope ps(kProfBlendFwd, s);
-    MGS_TRY_CUDA(launch_blend_fwd(vt, rec, tv[tcur], ranges, s));
+    MGS_TRY_CUDA(launch_blend_fwd(vt, rec, tv[tcur], ranges, at<uint32_t>(workspace, L.order), s));
   }
   return MGS_OK;
 }
@@ -419,6 +427,7 @@ mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams, i
     ProfScope ps(kProfBlendBwd, s);
     MGS_TRY_CUDA(cudaMemsetAsync(moments, 0, 48 * (size_t)L.VN, s));
     MGS_TRY_CUDA(launch_blend_bwd(vt, at<float4>(workspace, L.rec), tv[tcur], at<uint2>(workspace, L.ranges),
+                                  at<uint32_t>(workspace, L.order),
                                   moments, s));
   }
   {

@@ -58,7 +58,8 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, const uint32_t* gather, uint3
 // in device memory (<= n, which sizes the launches); n_keep_dev (optional, with
 // n_keep >= 0): the kept count in device memory, for the passes after the first.
 // ranges (optional): filled with [start, end) of every key value < n_valid in the sorted
-// keys ((0, 0) for absent values), by the last pass.
+// keys ((0, 0) for absent values), by the last pass, which then writes the sorted values
+// and not the keys (the result's key buffer is left as it was).
 constexpr uint32_t kSortDrop = 0xffffffffu;
 int radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], int64_t n, int begin_bit, int end_bit,
                      bool vals_iota, uint32_t* scratch, cudaStream_t s, cudaError_t* err,

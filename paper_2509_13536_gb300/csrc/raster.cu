@@ -43,14 +43,15 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 __global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant__ ViewTable vt,
                                                           const float4* __restrict__ rec,
                                                           const uint32_t* __restrict__ vals,
-                                                          const uint2* __restrict__ ranges) {
+                                                          const uint2* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ order) {
   __shared__ float4 s_xy[kTilePix];   // (x, x, y, y) tile-relative centre
   __shared__ float4 s_ab[kTilePix];   // (A, A, B, B) scaled conic
   __shared__ float4 s_co[kTilePix];   // (C, C, log2 o, log2 o)
   __shared__ float4 s_rg[kTilePix];   // (r, r, g, g)
   __shared__ float4 s_bd[kTilePix];   // (b, b, depth, depth)
   __shared__ uint32_t s_clamp[kFwdThreads / 32];  // per warp: its bits of the batch's 32 group flags
-  const int tile = blockIdx.x;
+  const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const View& V = vt.v[view_of_tile(vt, tile)];
   const int local = tile - V.tile_base;
   const int x0 = (local % V.tiles_x) * kTile, y0 = (local / V.tiles_x) * kTile;
@@ -196,10 +197,12 @@ __global__ void __launch_bounds__(kBwdThreads, 5 * kBwdSplit) k_blend_bwd(const 
                                                            const float4* __restrict__ rec,
                                                            const uint32_t* __restrict__ vals,
                                                            const uint2* __restrict__ ranges,
+                                                           const uint32_t* __restrict__ order,
                                                            float4* __restrict__ moments) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
-  const int tile = blockIdx.x / kBwdSplit, part = blockIdx.x % kBwdSplit;
+  const int tile = order ? (int)order[blockIdx.x / kBwdSplit] : (int)(blockIdx.x / kBwdSplit);
+  const int part = blockIdx.x % kBwdSplit;
   const int row0 = part * (kTile / kBwdSplit);  // first tile row of this CTA's part
   const View& V = vt.v[view_of_tile(vt, tile)];
   const int local = tile - V.tile_base;
@@ -509,7 +512,77 @@ __global__ void __launch_bounds__(kTilePix) k_frag_stats(const __grid_constant__
   }
 }
 
+// Longest-first tile order: the blend grids are dispatched in block order, so tiles are
+// given to blocks by list length (classes of 128 entries, longest class first; inside a
+// class, runs of tiles in index order).  Long tiles then start early instead of running
+// alone at the end of the grid.
+constexpr int kOrderBuckets = 64;
+
+__device__ __forceinline__ int order_class(uint2 r) {  // 0 = the longest lists
+  const uint32_t len = r.y - r.x;
+  return kOrderBuckets - 1 - (int)min(len >> 7, (uint32_t)(kOrderBuckets - 1));
+}
+
+__global__ void __launch_bounds__(256) k_order_count(const uint2* __restrict__ ranges, int n_tiles,
+                                                     uint32_t* __restrict__ counts) {
+  __shared__ uint32_t s_cnt[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_tiles) atomicAdd(&s_cnt[order_class(ranges[t])], 1u);
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets && s_cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) k_order_scatter(const uint2* __restrict__ ranges, int n_tiles,
+                                                       const uint32_t* __restrict__ counts,
+                                                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_wcnt[8][kOrderBuckets];  // per warp and class, then exclusive offsets
+  __shared__ uint32_t s_base[kOrderBuckets];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < 8 * kOrderBuckets; k += blockDim.x) (&s_wcnt[0][0])[k] = 0;
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = t < n_tiles ? order_class(ranges[t]) : kOrderBuckets;
+  // rank among the earlier lanes of the same class, so each block's run of a class
+  // keeps tile order
+  const uint32_t peers = __match_any_sync(0xffffffffu, c);
+  const uint32_t rank_w = __popc(peers & ((1u << lane) - 1u));
+  if (c < kOrderBuckets && rank_w == 0) s_wcnt[w][c] = __popc(peers);
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets) {
+    const int k = threadIdx.x;
+    uint32_t run = 0;
+    for (int ww = 0; ww < 8; ++ww) {
+      const uint32_t x = s_wcnt[ww][k];
+      s_wcnt[ww][k] = run;
+      run += x;
+    }
+    uint32_t base = 0;
+    for (int h = 0; h < k; ++h) base += counts[h];
+    s_base[k] = run ? base + atomicAdd(&cursor[k], run) : 0u;
+  }
+  __syncthreads();
+  if (c < kOrderBuckets) {
+    const uint32_t pos = s_base[c] + s_wcnt[w][c] + rank_w;  // < n_tiles: the classes partition the tiles
+    if (pos < (uint32_t)n_tiles) order[pos] = (uint32_t)t;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* counts, uint32_t* order,
+                              cudaStream_t s) {
+  if (n_tiles <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counts, 0, 2 * kOrderBuckets * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)div_up(n_tiles, 256);
+  k_order_count<<<grid, 256, 0, s>>>(ranges, n_tiles, counts);
+  count_launch();
+  k_order_scatter<<<grid, 256, 0, s>>>(ranges, n_tiles, counts, counts + kOrderBuckets, order);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_frag_stats(const ViewTable& vt, const float4* rec, const uint32_t* vals,
                               const uint2* ranges, unsigned long long* out, cudaStream_t s) {
@@ -523,20 +596,20 @@ cudaError_t launch_frag_stats(const ViewTable& vt, const float4* rec, const uint
 size_t blend_bwd_smem() { return sizeof(BwdSmem); }
 
 cudaError_t launch_blend_fwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
-                             const uint2* ranges, cudaStream_t s) {
+                             const uint2* ranges, const uint32_t* order, cudaStream_t s) {
   if (vt.n_tiles <= 0) return cudaSuccess;
-  k_blend_fwd<<<vt.n_tiles, kFwdThreads, 0, s>>>(vt, rec, vals, ranges);
+  k_blend_fwd<<<vt.n_tiles, kFwdThreads, 0, s>>>(vt, rec, vals, ranges, order);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_blend_bwd(const ViewTable& vt, const float4* rec, const uint32_t* vals,
-                             const uint2* ranges, float4* moments, cudaStream_t s) {
+                             const uint2* ranges, const uint32_t* order, float4* moments, cudaStream_t s) {
   if (vt.n_tiles <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_blend_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(BwdSmem));
   if (e != cudaSuccess) return e;
-  k_blend_bwd<<<vt.n_tiles * kBwdSplit, kBwdThreads, sizeof(BwdSmem), s>>>(vt, rec, vals, ranges, moments);
+  k_blend_bwd<<<vt.n_tiles * kBwdSplit, kBwdThreads, sizeof(BwdSmem), s>>>(vt, rec, vals, ranges, order, moments);
   count_launch();
   return cudaGetLastError();
 }

@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const uint32_t k = s_key[i];
     const uint32_t d = (k >> shift) & mask;
     const uint32_t pos = s_goff[d] + (uint32_t)i - s_boff[d];
-    kout[pos] = k;
+    if (!rng) kout[pos] = k;  // a ranged sort keeps the ranges and values, not the keys
     vout[pos] = s_val[i];
     if (rng && k < n_valid) {
       // Ranges of equal keys, on the last pass: the block's run of digit d is sorted by
