@@ -42,7 +42,7 @@ BWD_FLOP_EVAL, BWD_FLOP_CONTRIB = 10, 47
 # of the full workload (8 views, one launch per step; profiles/ has the command).  A value
 # is reported only while the kernel sources still hash to the captured version.
 NCU_TRAFFIC_SOURCES = ["paper_2509_13536_gb300/csrc/raster.cu", "paper_2509_13536_gb300/csrc/common.cuh"]
-NCU_TRAFFIC = {"sha256_16": "deda572fbc1481e5", "blend_bwd": 491.57e6 + 58.44e6, "blend_fwd": 251.55e6 + 145.20e6}
+NCU_TRAFFIC = {"sha256_16": "78bd82b7d5de3364", "blend_bwd": 672.47e6 + 92.86e6, "blend_fwd": 356.88e6 + 143.08e6}
 
 
 def algorithmic_bytes(n, views, stats, pb, pixels):
