@@ -11,10 +11,9 @@ namespace mgs {
 // kernels of the other translation units
 cudaError_t launch_preprocess(const mgs_gaussians& g, const ViewTable& vt, float4* rec, uint2* rects,
                               uint32_t* touched, uint32_t* dkeys, unsigned long long* counters,
-                              cudaStream_t s);
-cudaError_t launch_preprocess_bwd(const mgs_gaussians& g, const ViewTable& vt, const float4* moments,
-                                  const uint32_t* touched, const uint2* rects, const BwdPlan& pl,
-                                  const mgs_grads& gr, cudaStream_t s);
+                              const FwdPlanOut& fb, cudaStream_t s);
+cudaError_t launch_preprocess_bwd(const mgs_gaussians& g, const ViewTable& vt, float4* moments,
+                                  const BwdPlan& pl, const mgs_grads& gr, cudaStream_t s);
 cudaError_t launch_project_one(const mgs_gaussians& g, const View& V, float* mean2d, float* conic,
                                float* rgb, float* depth, int32_t* radius, int32_t* rect, cudaStream_t s);
 cudaError_t launch_emit(int64_t n_vis, int64_t N, const uint32_t* dvals, const uint32_t* offsets,
@@ -51,7 +50,7 @@ mgs_status fail(mgs_status st, const std::string& msg) {
 struct RenderLayout {
   int64_t N = 0, VN = 0, pixels = 0, tiles = 0, key_cap = 0;
   size_t hdr, rec, rects, touched, dkeys[2], dvals[2], offsets, tkeys[2], tvals[2], ranges,
-      order, ocounts, tfinal, ncontrib, moments, plan, scratch, total;
+      order, ocounts, tfinal, ncontrib, moments, plan, gmask, scratch, total;
 };
 
 bool cams_valid(const mgs_camera* cams, int nv, std::string* why) {
@@ -116,6 +115,7 @@ RenderLayout render_layout(const ViewItems& items, const mgs_camera* cams, int n
   L.ncontrib = take(4 * (size_t)L.pixels);
   L.moments = take(48 * vn);
   L.plan = take(2 * kPlanCountWords * sizeof(uint32_t));
+  L.gmask = take(8 * (size_t)std::max<int64_t>(L.N, 1));
   L.scratch = take(4 * (size_t)sort_scratch_words(std::max<int64_t>(L.VN, key_cap)));
   L.total = off;
   return L;
@@ -275,9 +275,17 @@ static mgs_status render_impl(const mgs_gaussians* maps, int n_maps, const int32
   auto* ranges = at<uint2>(workspace, L.ranges);
   auto* scratch = at<uint32_t>(workspace, L.scratch);
 
+  // a render of one map may be followed by the reverse pass: its projection clears the
+  // drawn items' moments and leaves the masks and bucket counts of the reverse
+  // projection's work plan
+  FwdPlanOut fb{nullptr, nullptr, nullptr};
+  if (!map_of_view)
+    fb = FwdPlanOut{at<float4>(workspace, L.moments), at<uint2>(workspace, L.gmask),
+                    at<uint32_t>(workspace, L.plan)};
   {
     ProfScope ps(kProfPreprocess, s);
     MGS_TRY_CUDA(cudaMemsetAsync(counters, 0, 256, s));
+    if (fb.bcounts) MGS_TRY_CUDA(cudaMemsetAsync(fb.bcounts, 0, kPlanCountWords * sizeof(uint32_t), s));
     // one projection launch per run of consecutive views that share a map: each thread
     // projects one Gaussian into every view of the run (its items are consecutive)
     for (int v0 = 0; v0 < n_views;) {
@@ -289,7 +297,8 @@ static mgs_status render_impl(const mgs_gaussians* maps, int n_maps, const int32
       sub.n_tiles = vt.n_tiles;
       for (int v = v0; v < v1; ++v) sub.v[v - v0] = vt.v[v];
       const int64_t ib = vt.v[v0].item_base;
-      MGS_TRY_CUDA(launch_preprocess(maps[m], sub, rec + 3 * ib, rects + ib, touched + ib, dk[0] + ib, counters, s));
+      MGS_TRY_CUDA(launch_preprocess(maps[m], sub, rec + 3 * ib, rects + ib, touched + ib, dk[0] + ib, counters,
+                                     fb, s));
       v0 = v1;
     }
   }
@@ -425,20 +434,21 @@ mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams, i
   auto* moments = at<float4>(workspace, L.moments);
   {
     ProfScope ps(kProfBlendBwd, s);
-    MGS_TRY_CUDA(cudaMemsetAsync(moments, 0, 48 * (size_t)L.VN, s));
+    // the forward cleared the drawn items' moments; a second reverse pass of the same
+    // render clears the whole buffer first
+    MGS_TRY_CUDA(launch_moments_clear(moments, 3 * L.VN, at<uint32_t>(workspace, L.plan) + kPlanDirtyWord, s));
     MGS_TRY_CUDA(launch_blend_bwd(vt, at<float4>(workspace, L.rec), tv[tcur], at<uint2>(workspace, L.ranges),
                                   at<uint32_t>(workspace, L.order),
                                   moments, s));
   }
   {
     ProfScope ps(kProfPreprocessBwd, s);
-    // the work plan takes the depth-sort buffers, free once the forward has emitted its
+    // the plan lists take the depth-sort buffers, free once the forward has emitted its
     // keys (each holds 4 x VN >= 4 x N bytes)
-    const BwdPlan pl{at<uint32_t>(workspace, L.dvals[1]), at<uint32_t>(workspace, L.offsets),
-                     at<uint32_t>(workspace, L.plan), at<uint32_t>(workspace, L.dkeys[0]),
-                     at<uint32_t>(workspace, L.dkeys[1]), at<uint32_t>(workspace, L.dvals[0])};
-    MGS_TRY_CUDA(launch_preprocess_bwd(*g, vt, moments, at<uint32_t>(workspace, L.touched),
-                                       at<uint2>(workspace, L.rects), pl, *grads, s));
+    const BwdPlan pl{at<uint2>(workspace, L.gmask), at<uint32_t>(workspace, L.plan),
+                     at<uint32_t>(workspace, L.dkeys[0]), at<uint32_t>(workspace, L.dkeys[1]),
+                     at<uint32_t>(workspace, L.dvals[0])};
+    MGS_TRY_CUDA(launch_preprocess_bwd(*g, vt, moments, pl, *grads, s));
   }
   return MGS_OK;
 }

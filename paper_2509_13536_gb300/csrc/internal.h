@@ -69,18 +69,30 @@ inline int radix_passes(int begin_bit, int end_bit) {
   return end_bit > begin_bit ? (end_bit - begin_bit + 7) / 8 : 0;
 }
 
-// Work plan of the reverse projection (project.cu): device buffers of N words each,
-// except `counts`, which holds 2 x kPlanCountWords words (bucket sizes, then the
-// scatter's cursors) and is cleared by the launch.
+// Work plan of the reverse projection (project.cu).  The forward projection of a render
+// that a reverse pass may follow fills FwdPlanOut (all three null otherwise): it clears
+// the drawn items' moment accumulators, leaves per Gaussian its drawing and gradient
+// view masks (gmask, N entries) and adds the bucket sizes into bcounts (kPlanCountWords
+// words, cleared by the caller; its last word, kPlanDirtyWord, is nonzero once a reverse
+// pass has added into the moments since).  BwdPlan: those masks and counts, the
+// scatter's cursors (the kPlanCountWords words after the counts, cleared by the launch)
+// and three N-word buffers for the plan (Gaussian index, drawing views, gradient views).
 constexpr int kPlanCountWords = 64;
+constexpr int kPlanDirtyWord = kPlanCountWords - 1;
+struct FwdPlanOut {
+  float4* moments;
+  uint2* gmask;
+  uint32_t* bcounts;
+};
 struct BwdPlan {
-  uint32_t* gdrawn;  // per Gaussian: views that draw it
-  uint32_t* gtodo;   // per Gaussian: drawing views in which it reached a tile
+  const uint2* gmask;
   uint32_t* counts;
-  uint32_t* list;    // plan order: Gaussian index, its drawing views, its gradient views
+  uint32_t* list;
   uint32_t* ldrawn;
   uint32_t* ltodo;
 };
+// Clears the n float4 moment accumulators if the word at `dirty` is nonzero.
+cudaError_t launch_moments_clear(float4* moments, int64_t n, const uint32_t* dirty, cudaStream_t s);
 
 
 // Patch-Grid sampling (pg.cu): workspace layout for one keyframe.

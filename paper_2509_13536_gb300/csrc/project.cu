@@ -159,6 +159,11 @@ __device__ __forceinline__ void colour(const float* c, const float dir[3], float
   }
 }
 
+// Buckets of the reverse projection's work plan: Gaussians by the number of views they
+// take a gradient from (0..MGS_MAX_VIEWS).
+constexpr int kPlanBuckets = MGS_MAX_VIEWS + 1;
+static_assert(kPlanBuckets <= kPlanDirtyWord, "the bucket counts end before the dirty word");
+
 template <int DEG, typename T>
 __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* __restrict__ means,
                                                     const Geom geo,
@@ -167,12 +172,22 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
                                                     float4* __restrict__ rec, uint2* __restrict__ rects,
                                                     uint32_t* __restrict__ touched,
                                                     uint32_t* __restrict__ dkeys,
-                                                    unsigned long long* __restrict__ counters) {
+                                                    unsigned long long* __restrict__ counters,
+                                                    float4* __restrict__ moments, uint2* __restrict__ gmask,
+                                                    uint32_t* __restrict__ bcounts) {
   // Two loops per Gaussian: the first projects it into every view (the geometry words of
   // the record, the rect, the depth bits) and notes the views that draw it; the second
   // walks only those views for the SH colour and the tile count.  A warp then runs the
   // colour and culling code as often as its busiest lane has drawn views, not once for
   // every view some lane draws.
+  // For a render that a reverse pass may follow (moments, gmask and bcounts given), the
+  // second loop also clears the drawn items' moment accumulators, and each Gaussian
+  // leaves its drawing views, its gradient views (drawn and reaching a tile) and its
+  // bucket count for the reverse projection's work plan.
+  __shared__ uint32_t s_bucket[kPlanBuckets];
+  if (bcounts)
+    for (int b = threadIdx.x; b < kPlanBuckets; b += blockDim.x) s_bucket[b] = 0;
+  __syncthreads();
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long my_keys = 0;
   unsigned int my_vis = 0;
@@ -200,6 +215,8 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
         dkeys[item] = kSortDrop;  // undrawn: left out by the depth sort
       }
     }
+    const uint32_t drawn0 = drawn;
+    uint32_t todo = 0;
     if (drawn) {
       while (drawn) {
         const int v = __ffs(drawn) - 1;
@@ -229,10 +246,19 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
         rec[3 * item + 2] = make_float4(fmaxf(0.f, raw[0]), fmaxf(0.f, raw[1]), fmaxf(0.f, raw[2]), tz);
         touched[item] = count;
         if (!count) dkeys[item] = kSortDrop;
+        if (moments) {
+          const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+          moments[3 * item] = z;
+          moments[3 * item + 1] = z;
+          moments[3 * item + 2] = z;
+        }
+        todo |= (count ? 1u : 0u) << v;
         my_keys += count;
         my_vis += count ? 1u : 0u;
       }
     }
+    if (gmask) gmask[g] = make_uint2(drawn0, todo);
+    if (bcounts) atomicAdd(&s_bucket[__popc(todo)], 1u);
   }
   for (int o = 16; o; o >>= 1) {
     my_keys += __shfl_xor_sync(0xffffffffu, my_keys, o);
@@ -258,6 +284,9 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
       atomicAdd(&counters[1], vv);
     }
   }
+  if (bcounts)
+    for (int b = threadIdx.x; b < kPlanBuckets; b += blockDim.x)
+      if (s_bucket[b]) atomicAdd(&bcounts[b], s_bucket[b]);
 }
 
 template <int DEG, typename T>
@@ -305,49 +334,22 @@ __global__ void __launch_bounds__(256) k_project_one(int64_t N, const float* __r
 // most first, so that the lanes of a warp walk the same number of views (in index
 // order a warp runs as many view iterations as its busiest lane, 2.7x the mean on a
 // map whose neighbouring indices lie in different views).  Bucket b holds the
-// Gaussians with b such views.  A counting pass, then a scatter whose blocks reserve
-// their slots with one atomic per bucket; the order inside a bucket changes no result
-// (each Gaussian is still one thread's sum over its views in view order).
-constexpr int kPlanBuckets = MGS_MAX_VIEWS + 1;
-
-// Views that draw Gaussian g, and those of them in which it reached a tile (only
-// these carry a gradient).
-__device__ __forceinline__ void view_masks(int64_t g, int64_t N, int nv, const uint2* __restrict__ rects,
-                                           const uint32_t* __restrict__ touched, uint32_t& drawn,
-                                           uint32_t& todo) {
-  drawn = 0;
-  todo = 0;
-  for (int v = 0; v < nv; ++v) {
-    const uint2 rc = rects[(int64_t)v * N + g];
-    if ((rc.x & 0xffff) <= (rc.y & 0xffff)) {
-      drawn |= 1u << v;
-      if (touched[(int64_t)v * N + g] != 0) todo |= 1u << v;
-    }
-  }
+// Gaussians with b such views; the forward projection counted the buckets and left
+// each Gaussian's view masks.  The scatter's blocks reserve their slots with one atomic
+// per bucket; the order inside a bucket changes no result (each Gaussian is still one
+// thread's sum over its views in view order).
+// Moment accumulators before a reverse pass: the forward projection cleared those of the
+// drawn items and marked them clean; a reverse pass marks them dirty.  A second reverse
+// pass of the same render finds them dirty and clears the whole buffer.
+__global__ void __launch_bounds__(256) k_moments_clear(float4* __restrict__ moments, int64_t n,
+                                                       const uint32_t* __restrict__ dirty) {
+  if (*dirty == 0u) return;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    moments[i] = z;
 }
 
-__global__ void __launch_bounds__(256) k_bwd_count(int64_t N, int nv, const uint2* __restrict__ rects,
-                                                   const uint32_t* __restrict__ touched,
-                                                   uint32_t* __restrict__ gdrawn, uint32_t* __restrict__ gtodo,
-                                                   uint32_t* __restrict__ counts) {
-  __shared__ uint32_t s_cnt[kPlanBuckets];
-  for (int b = threadIdx.x; b < kPlanBuckets; b += blockDim.x) s_cnt[b] = 0;
-  __syncthreads();
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < N) {
-    uint32_t drawn, todo;
-    view_masks(g, N, nv, rects, touched, drawn, todo);
-    gdrawn[g] = drawn;
-    gtodo[g] = todo;
-    atomicAdd(&s_cnt[__popc(todo)], 1u);
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < kPlanBuckets; b += blockDim.x)
-    if (s_cnt[b]) atomicAdd(&counts[b], s_cnt[b]);
-}
-
-__global__ void __launch_bounds__(256) k_bwd_scatter(int64_t N, const uint32_t* __restrict__ gdrawn,
-                                                     const uint32_t* __restrict__ gtodo,
+__global__ void __launch_bounds__(256) k_bwd_scatter(int64_t N, const uint2* __restrict__ gmask,
                                                      const uint32_t* __restrict__ counts,
                                                      uint32_t* __restrict__ cursor, uint32_t* __restrict__ list,
                                                      uint32_t* __restrict__ ldrawn, uint32_t* __restrict__ ltodo) {
@@ -358,8 +360,9 @@ __global__ void __launch_bounds__(256) k_bwd_scatter(int64_t N, const uint32_t* 
   uint32_t drawn = 0, todo = 0, rank = 0;
   int b = 0;
   if (g < N) {
-    drawn = gdrawn[g];
-    todo = gtodo[g];
+    const uint2 mk = gmask[g];
+    drawn = mk.x;
+    todo = mk.y;
     b = __popc(todo);
     rank = atomicAdd(&s_cnt[b], 1u);
   }
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(kPreBwdThreads, 3) k_preprocess_bwd(int64_t N,
                                                         const uint32_t* __restrict__ list,
                                                         const uint32_t* __restrict__ ldrawn,
                                                         const uint32_t* __restrict__ ltodo,
-                                                        mgs_grads grads) {
+                                                        uint32_t* __restrict__ dirty, mgs_grads grads) {
   // Thread t takes the t-th Gaussian of the work plan (its views with a gradient,
   // `todo`, and its drawing views) and walks its own views in view order; the lanes of
   // a warp run the per-view body together on different views, with the view constants
@@ -408,6 +411,7 @@ __global__ void __launch_bounds__(kPreBwdThreads, 3) k_preprocess_bwd(int64_t N,
   }
   __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *dirty = 1u;  // the moments now hold this pass's sums
   if (t >= N) return;
   constexpr int K = (DEG + 1) * (DEG + 1);
   const int64_t g = list[t];
@@ -563,42 +567,39 @@ __global__ void __launch_bounds__(kPreBwdThreads, 3) k_preprocess_bwd(int64_t N,
 template <typename T>
 cudaError_t launch_pre_t(int deg, int64_t N, const mgs_gaussians& g, const ViewTable& vt,
                          float4* rec, uint2* rects, uint32_t* touched, uint32_t* dkeys,
-                         unsigned long long* counters, cudaStream_t s) {
+                         unsigned long long* counters, const FwdPlanOut& fb, cudaStream_t s) {
   unsigned grid = (unsigned)div_up(N, 256);
   const Geom geo{g.log_scales, g.quats, g.geom_dtype, g.quat_dtype};
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
-    case 0: k_preprocess<0, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
-    case 1: k_preprocess<1, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
-    case 2: k_preprocess<2, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
-    default: k_preprocess<3, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters); break;
+    case 0: k_preprocess<0, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
+    case 1: k_preprocess<1, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
+    case 2: k_preprocess<2, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
+    default: k_preprocess<3, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
   }
   count_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_bwd_t(int deg, int64_t N, const mgs_gaussians& g, const ViewTable& vt,
-                         const float4* moments, const uint32_t* touched, const uint2* rects,
+cudaError_t launch_bwd_t(int deg, int64_t N, const mgs_gaussians& g, const ViewTable& vt, float4* moments,
                          const BwdPlan& pl, const mgs_grads& gr, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(pl.counts, 0, 2 * kPlanCountWords * sizeof(uint32_t), s);
+  cudaError_t e = cudaMemsetAsync(pl.counts + kPlanCountWords, 0, kPlanCountWords * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   const unsigned pgrid = (unsigned)div_up(N, 256);
-  k_bwd_count<<<pgrid, 256, 0, s>>>(N, vt.n_views, rects, touched, pl.gdrawn, pl.gtodo, pl.counts);
-  count_launch();
-  k_bwd_scatter<<<pgrid, 256, 0, s>>>(N, pl.gdrawn, pl.gtodo, pl.counts, pl.counts + kPlanCountWords, pl.list,
-                                       pl.ldrawn, pl.ltodo);
+  k_bwd_scatter<<<pgrid, 256, 0, s>>>(N, pl.gmask, pl.counts, pl.counts + kPlanCountWords, pl.list, pl.ldrawn,
+                                       pl.ltodo);
   count_launch();
   unsigned grid = (unsigned)div_up(N, kPreBwdThreads);
   const Geom geo{g.log_scales, g.quats, g.geom_dtype, g.quat_dtype};
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
-    case 0: k_preprocess_bwd<0, T><<<grid, kPreBwdThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, pl.list, pl.ldrawn, pl.ltodo, gr); break;
-    case 1: k_preprocess_bwd<1, T><<<grid, kPreBwdThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, pl.list, pl.ldrawn, pl.ltodo, gr); break;
-    case 2: k_preprocess_bwd<2, T><<<grid, kPreBwdThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, pl.list, pl.ldrawn, pl.ltodo, gr); break;
-    default: k_preprocess_bwd<3, T><<<grid, kPreBwdThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, pl.list, pl.ldrawn, pl.ltodo, gr); break;
+    case 0: k_preprocess_bwd<0, T><<<grid, kPreBwdThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, pl.list, pl.ldrawn, pl.ltodo, pl.counts + kPlanDirtyWord, gr); break;
+    case 1: k_preprocess_bwd<1, T><<<grid, kPreBwdThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, pl.list, pl.ldrawn, pl.ltodo, pl.counts + kPlanDirtyWord, gr); break;
+    case 2: k_preprocess_bwd<2, T><<<grid, kPreBwdThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, pl.list, pl.ldrawn, pl.ltodo, pl.counts + kPlanDirtyWord, gr); break;
+    default: k_preprocess_bwd<3, T><<<grid, kPreBwdThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, moments, pl.list, pl.ldrawn, pl.ltodo, pl.counts + kPlanDirtyWord, gr); break;
   }
   count_launch();
   return cudaGetLastError();
@@ -626,23 +627,30 @@ cudaError_t launch_proj_t(int deg, int64_t N, const mgs_gaussians& g, const View
 
 cudaError_t launch_preprocess(const mgs_gaussians& g, const ViewTable& vt, float4* rec,
                               uint2* rects, uint32_t* touched, uint32_t* dkeys,
-                              unsigned long long* counters, cudaStream_t s) {
+                              unsigned long long* counters, const FwdPlanOut& fb, cudaStream_t s) {
   if (g.n <= 0) return cudaSuccess;
   switch (g.attr_dtype) {
-    case MGS_F16: return launch_pre_t<__half>(g.sh_degree, g.n, g, vt, rec, rects, touched, dkeys, counters, s);
-    case MGS_BF16: return launch_pre_t<__nv_bfloat16>(g.sh_degree, g.n, g, vt, rec, rects, touched, dkeys, counters, s);
-    default: return launch_pre_t<float>(g.sh_degree, g.n, g, vt, rec, rects, touched, dkeys, counters, s);
+    case MGS_F16: return launch_pre_t<__half>(g.sh_degree, g.n, g, vt, rec, rects, touched, dkeys, counters, fb, s);
+    case MGS_BF16: return launch_pre_t<__nv_bfloat16>(g.sh_degree, g.n, g, vt, rec, rects, touched, dkeys, counters, fb, s);
+    default: return launch_pre_t<float>(g.sh_degree, g.n, g, vt, rec, rects, touched, dkeys, counters, fb, s);
   }
 }
 
-cudaError_t launch_preprocess_bwd(const mgs_gaussians& g, const ViewTable& vt, const float4* moments,
-                                  const uint32_t* touched, const uint2* rects, const BwdPlan& pl,
-                                  const mgs_grads& gr, cudaStream_t s) {
+cudaError_t launch_moments_clear(float4* moments, int64_t n, const uint32_t* dirty, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>(div_up(n, 256), 152 * 8);
+  k_moments_clear<<<(unsigned)blocks, 256, 0, s>>>(moments, n, dirty);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_bwd(const mgs_gaussians& g, const ViewTable& vt, float4* moments,
+                                  const BwdPlan& pl, const mgs_grads& gr, cudaStream_t s) {
   if (g.n <= 0) return cudaSuccess;
   switch (g.attr_dtype) {
-    case MGS_F16: return launch_bwd_t<__half>(g.sh_degree, g.n, g, vt, moments, touched, rects, pl, gr, s);
-    case MGS_BF16: return launch_bwd_t<__nv_bfloat16>(g.sh_degree, g.n, g, vt, moments, touched, rects, pl, gr, s);
-    default: return launch_bwd_t<float>(g.sh_degree, g.n, g, vt, moments, touched, rects, pl, gr, s);
+    case MGS_F16: return launch_bwd_t<__half>(g.sh_degree, g.n, g, vt, moments, pl, gr, s);
+    case MGS_BF16: return launch_bwd_t<__nv_bfloat16>(g.sh_degree, g.n, g, vt, moments, pl, gr, s);
+    default: return launch_bwd_t<float>(g.sh_degree, g.n, g, vt, moments, pl, gr, s);
   }
 }
 
