@@ -176,10 +176,11 @@ mgs_status mgs_render_multi(const mgs_gaussians* maps_host, int32_t n_maps, cons
                             const mgs_camera* cams_host, int32_t n_views, const mgs_image* out_host,
                             void* workspace, size_t workspace_bytes, int64_t* n_keys_host, void* stream);
 
-/* Reverse pass of the last mgs_render on `workspace` (same g, cams, n_views).
- * dL_host[v] gives dL/drgb, dL/ddepth, dL/dalpha planes of view v (any plane may
- * be NULL = zero).  Gradients of all views are ADDED to `grads` (f32), or stored when
- * grads->overwrite is nonzero.  Asynchronous. */
+/* Reverse pass of the last mgs_render / mgs_render_async on `workspace` (same g, cams,
+ * n_views).  dL_host[v] gives dL/drgb, dL/ddepth, dL/dalpha planes of view v (any plane
+ * may be NULL = zero).  Gradients of all views are ADDED to `grads` (f32), or stored when
+ * grads->overwrite is nonzero.  It may be called more than once for the same render
+ * (each call computes that render's gradients afresh).  Asynchronous. */
 mgs_status mgs_render_backward(const mgs_gaussians* g, const mgs_camera* cams_host,
                                int32_t n_views, const mgs_image* dL_host, void* workspace,
                                size_t workspace_bytes, const mgs_grads* grads, void* stream);
