@@ -159,13 +159,40 @@ __device__ __forceinline__ void colour(const float* c, const float dir[3], float
   }
 }
 
+// Whether Gaussian (mu, largest scale smax) can be drawn in view V: false only where the
+// full test (in front of the near plane, a tile rect that meets the image) must fail.
+// The rect is the square of half-width ceil(3 sqrt(lambda_max)) around the projected
+// centre; lambda_max <= trace = |J W R S|_F^2 + 0.6 <= smax^2 |J|_F^2 + 0.6 (R S has
+// spectral norm smax, W is a rotation), and the rect's own lambda estimate exceeds
+// lambda_max by at most sqrt(0.1).  The bound is widened by 1 % and 2 px; NaNs,
+// overflow, or a depth within 1e-5 of the near plane leave the decision to the full
+// test.
+__device__ __forceinline__ bool maybe_drawn(const float mu[3], float smax, const View& V) {
+  const float tz = fmaf(V.R[6], mu[0], fmaf(V.R[7], mu[1], fmaf(V.R[8], mu[2], V.t[2])));
+  if (tz <= V.near_z - 1e-5f) return false;
+  if (!(tz > V.near_z + 1e-5f)) return true;
+  const float tx = fmaf(V.R[0], mu[0], fmaf(V.R[1], mu[1], fmaf(V.R[2], mu[2], V.t[0])));
+  const float ty = fmaf(V.R[3], mu[0], fmaf(V.R[4], mu[1], fmaf(V.R[5], mu[2], V.t[1])));
+  const float itz = 1.f / tz, xr = tx * itz, yr = ty * itz;
+  const float xc = fminf(V.limx, fmaxf(-V.limx, xr)), yc = fminf(V.limy, fmaxf(-V.limy, yr));
+  const float tr = smax * smax * (V.fx * V.fx * (1.f + xc * xc) + V.fy * V.fy * (1.f + yc * yc)) * itz * itz + 1.f;
+  const float r = 3.03f * sqrtf(tr) + 2.f;
+  const float u = fmaf(V.fx, xr, V.cx), v = fmaf(V.fy, yr, V.cy);
+  if (!(r < 1e30f) || !(fabsf(u) < 1e30f) || !(fabsf(v) < 1e30f)) return true;
+  return u - r < 16.f * (float)V.tiles_x + 1.f && u + r > -1.f && v - r < 16.f * (float)V.tiles_y + 1.f &&
+         v + r > -1.f;
+}
+
 // Buckets of the reverse projection's work plan: Gaussians by the number of views they
 // take a gradient from (0..MGS_MAX_VIEWS).
 constexpr int kPlanBuckets = MGS_MAX_VIEWS + 1;
 static_assert(kPlanBuckets <= kPlanDirtyWord, "the bucket counts end before the dirty word");
+constexpr int kPreThreads = 256;
+constexpr int kPreWarps = kPreThreads / 32;
+constexpr int kOwnWords = 13;  // per Gaussian, for the items of its warp: mean, R S, log2 o
 
 template <int DEG, typename T>
-__global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* __restrict__ means,
+__global__ void __launch_bounds__(kPreThreads, 4) k_preprocess(int64_t N, const float* __restrict__ means,
                                                     const Geom geo,
                                                     const T* __restrict__ ol, const T* __restrict__ sh,
                                                     const __grid_constant__ ViewTable vt,
@@ -175,65 +202,100 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
                                                     unsigned long long* __restrict__ counters,
                                                     float4* __restrict__ moments, uint2* __restrict__ gmask,
                                                     uint32_t* __restrict__ bcounts) {
-  // Two loops per Gaussian: the first projects it into every view (the geometry words of
-  // the record, the rect, the depth bits) and notes the views that draw it; the second
-  // walks only those views for the SH colour and the tile count.  A warp then runs the
-  // colour and culling code as often as its busiest lane has drawn views, not once for
-  // every view some lane draws.
-  // For a render that a reverse pass may follow (moments, gmask and bcounts given), the
-  // second loop also clears the drawn items' moment accumulators, and each Gaussian
-  // leaves its drawing views, its gradient views (drawn and reaching a tile) and its
-  // bucket count for the reverse projection's work plan.
+  // Each thread takes one Gaussian through a cheap test per view (maybe_drawn) and writes
+  // the empty outputs of the views it cannot be drawn in.  The (Gaussian, view) items
+  // that remain -- a quarter of them on the room map, where most of the map is behind
+  // the camera or outside the image -- are then dealt out to the lanes of the warp, 32 at
+  // a time, so that the full projection, the SH colour and the tile count run with every
+  // lane busy instead of once per view for every Gaussian of the warp.  A lane reads the
+  // Gaussian it works on (mean, R S, log2 o) from shared memory and its SH row from L1.
+  // For a render that a reverse pass may follow (moments, gmask and bcounts given), an
+  // item also clears its moment accumulators, and each Gaussian leaves its drawing views,
+  // its gradient views (drawn and reaching a tile) and its bucket count for the reverse
+  // projection's work plan.
+  __shared__ View s_view[MGS_MAX_VIEWS];
+  __shared__ float s_own[kPreWarps][kOwnWords][32];
+  __shared__ uint32_t s_dr[kPreWarps][32], s_td[kPreWarps][32];
   __shared__ uint32_t s_bucket[kPlanBuckets];
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&vt.v[0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&s_view[0]);
+    const int words = vt.n_views * (int)(sizeof(View) / 4);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+  }
   if (bcounts)
     for (int b = threadIdx.x; b < kPlanBuckets; b += blockDim.x) s_bucket[b] = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  s_dr[w][lane] = 0;
+  s_td[w][lane] = 0;
   __syncthreads();
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long my_keys = 0;
-  unsigned int my_vis = 0;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t g0 = g - lane;  // the warp's first Gaussian
+  uint32_t cand = 0;            // views in which this thread's Gaussian may be drawn
   if (g < N) {
     GaussPre G;
     load_gauss(g, means, geo, ol, G);
-    constexpr int K3 = (DEG + 1) * (DEG + 1) * 3;
-    const float lo = log2f(G.o);
-    uint32_t drawn = 0;
+    const float smax = fmaxf(G.s[0], fmaxf(G.s[1], G.s[2]));
     for (int v = 0; v < vt.n_views; ++v) {
-      const View& V = vt.v[v];
-      const int64_t item = (int64_t)v * N + g;
-      ViewGeom P;
-      view_geom(G, V, P);
-      int r = 0, rc[4];
-      if (P.ok && tile_rect(P, V, r, rc)) {
-        rec[3 * item + 0] = make_float4(P.u_hi, P.v_hi, P.u_lo, P.v_lo);
-        rec[3 * item + 1] = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, lo);
-        rects[item] = make_uint2((uint32_t)rc[0] | ((uint32_t)rc[1] << 16), (uint32_t)rc[2] | ((uint32_t)rc[3] << 16));
-        dkeys[item] = __float_as_uint(P.tz);  // the second loop keeps it or drops the item
-        drawn |= 1u << v;
+      if (maybe_drawn(G.mu, smax, vt.v[v])) {
+        cand |= 1u << v;
       } else {
+        const int64_t item = (int64_t)v * N + g;
         rects[item] = make_uint2(1u, 0u);  // empty rect: x0 = 1 > x1 = 0
         touched[item] = 0;
         dkeys[item] = kSortDrop;  // undrawn: left out by the depth sort
       }
     }
-    const uint32_t drawn0 = drawn;
-    uint32_t todo = 0;
-    if (drawn) {
-      while (drawn) {
-        const int v = __ffs(drawn) - 1;
-        drawn &= drawn - 1;
-        const View& V = vt.v[v];
-        const int64_t item = (int64_t)v * N + g;
-        const float4 r0 = rec[3 * item + 0], r1 = rec[3 * item + 1];
-        const uint2 pr = rects[item];
-        const int rc[4] = {(int)(pr.x & 0xffff), (int)(pr.x >> 16), (int)(pr.y & 0xffff), (int)(pr.y >> 16)};
+    for (int k = 0; k < 3; ++k) s_own[w][k][lane] = G.mu[k];
+    for (int k = 0; k < 9; ++k) s_own[w][3 + k][lane] = G.RS[k];
+    s_own[w][12][lane] = log2f(G.o);
+  }
+  // exclusive prefix of the lanes' candidate counts
+  const uint32_t nc = __popc(cand);
+  uint32_t inc = nc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const uint32_t off = inc - nc, total = __shfl_sync(0xffffffffu, inc, 31);
+  __syncwarp();  // the warp's s_own rows are written
+  unsigned long long my_keys = 0;
+  unsigned int my_vis = 0;
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int K3 = K * 3;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t i = base + lane;
+    int owner = 0;  // the last lane whose candidates start at or before item i
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+      const uint32_t o = __shfl_sync(0xffffffffu, off, owner + step);
+      if (o <= i) owner += step;
+    }
+    const uint32_t ocand = __shfl_sync(0xffffffffu, cand, owner);
+    const uint32_t ooff = __shfl_sync(0xffffffffu, off, owner);
+    if (i < total) {
+      const int v = (int)__fns(ocand, 0u, (int)(i - ooff) + 1);
+      const View& V = s_view[v];
+      const int64_t go = g0 + owner, item = (int64_t)v * N + go;
+      GaussPre G;  // the geometry reads only the mean and R S
+      for (int k = 0; k < 3; ++k) G.mu[k] = s_own[w][k][owner];
+      for (int k = 0; k < 9; ++k) G.RS[k] = s_own[w][3 + k][owner];
+      const float lo = s_own[w][12][owner];
+      ViewGeom P;
+      view_geom(G, V, P);
+      int r = 0, rc[4];
+      if (P.ok && tile_rect(P, V, r, rc)) {
+        const float4 r0 = make_float4(P.u_hi, P.v_hi, P.u_lo, P.v_lo);
+        const float4 r1 = make_float4(-0.5f * kLog2e * P.A, -kLog2e * P.B, -0.5f * kLog2e * P.C, lo);
+        rec[3 * item + 0] = r0;
+        rec[3 * item + 1] = r1;
+        rects[item] = make_uint2((uint32_t)rc[0] | ((uint32_t)rc[1] << 16), (uint32_t)rc[2] | ((uint32_t)rc[3] << 16));
         const uint32_t count = cull_count(make_cull(r0, r1), rc);
-        float dir[3], vnorm, raw[3];
-        view_direction(G.mu, V, dir, vnorm);
-        {  // colour: the coefficients stream from L1 (the row is read again for every drawn view)
-          constexpr int K = (DEG + 1) * (DEG + 1);
+        float raw[3];
+        {  // colour: the coefficients stream from L1
           float Y[K];
-          sh_basis<DEG>(dir, Y, nullptr);
-          const T* p = sh + g * K3;
+          sh_basis<DEG>(P.dir, Y, nullptr);
+          const T* p = sh + go * K3;
 #pragma unroll
           for (int ch = 0; ch < 3; ++ch) {
             float acc = 0.5f;
@@ -242,22 +304,30 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
             raw[ch] = acc;
           }
         }
-        const float tz = __uint_as_float(dkeys[item]);
-        rec[3 * item + 2] = make_float4(fmaxf(0.f, raw[0]), fmaxf(0.f, raw[1]), fmaxf(0.f, raw[2]), tz);
+        rec[3 * item + 2] = make_float4(fmaxf(0.f, raw[0]), fmaxf(0.f, raw[1]), fmaxf(0.f, raw[2]), P.tz);
         touched[item] = count;
-        if (!count) dkeys[item] = kSortDrop;
+        dkeys[item] = count ? __float_as_uint(P.tz) : kSortDrop;
         if (moments) {
           const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
           moments[3 * item] = z;
           moments[3 * item + 1] = z;
           moments[3 * item + 2] = z;
         }
-        todo |= (count ? 1u : 0u) << v;
+        atomicOr(&s_dr[w][owner], 1u << v);
+        if (count) atomicOr(&s_td[w][owner], 1u << v);
         my_keys += count;
         my_vis += count ? 1u : 0u;
+      } else {
+        rects[item] = make_uint2(1u, 0u);
+        touched[item] = 0;
+        dkeys[item] = kSortDrop;
       }
     }
-    if (gmask) gmask[g] = make_uint2(drawn0, todo);
+  }
+  __syncwarp();  // the warp's view masks are complete
+  if (g < N) {
+    const uint32_t todo = s_td[w][lane];
+    if (gmask) gmask[g] = make_uint2(s_dr[w][lane], todo);
     if (bcounts) atomicAdd(&s_bucket[__popc(todo)], 1u);
   }
   for (int o = 16; o; o >>= 1) {
@@ -266,18 +336,18 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int64_t N, const float* _
   }
   // one pair of atomics per block: per warp, tens of thousands of atomics on two
   // addresses serialise
-  __shared__ unsigned long long s_keys[8];
-  __shared__ unsigned int s_vis[8];
-  if ((threadIdx.x & 31) == 0) {
-    s_keys[threadIdx.x >> 5] = my_keys;
-    s_vis[threadIdx.x >> 5] = my_vis;
+  __shared__ unsigned long long s_keys[kPreWarps];
+  __shared__ unsigned int s_vis[kPreWarps];
+  if (lane == 0) {
+    s_keys[w] = my_keys;
+    s_vis[w] = my_vis;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long k = 0, vv = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      k += s_keys[w];
-      vv += s_vis[w];
+    for (int ww = 0; ww < kPreWarps; ++ww) {
+      k += s_keys[ww];
+      vv += s_vis[ww];
     }
     if (k || vv) {
       atomicAdd(&counters[0], k);
