@@ -115,6 +115,35 @@ def test_clamp_entries_mixed_with_plain_ones(orc):
     _gpu.check_grads(grads, _gpu.oracle_backward(orc, sc, cams, cot_np), what="clamp mix")
 
 
+def test_gaussians_around_the_image_border(orc):
+    """Centres projected up to 60 px outside a 120x90 image, depths from just behind the
+    near plane (0.2) to 3, in two views: the projection's cheap per-view test skips
+    about half of the (Gaussian, view) items here, and may skip only those the full test
+    rejects, so both views' images match the oracle's outcomes."""
+    rng = np.random.default_rng(41)
+    n = 2000
+    W, H, f = 120, 90, 100.0
+    z = np.where(rng.random(n) < 0.08, rng.uniform(0.19, 0.23, n), rng.uniform(0.23, 3.0, n))
+    u = rng.uniform(-60, W + 60, n)
+    v = rng.uniform(-60, H + 60, n)
+    means = np.stack([(u - (W - 1) / 2) * z / f, (v - (H - 1) / 2) * z / f, z], 1)
+    smax = np.where(z < 0.23, 0.004, 0.05)
+    scales = np.exp(rng.uniform(math.log(0.002), np.log(smax)[:, None], size=(n, 3)))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    op = rng.uniform(0.05, 0.9, n)
+    sh = rng.normal(0, 0.3, size=(n, 4, 3))
+    sh[:, 0, :] = (rng.random((n, 3)) - 0.5) / (0.5 / math.sqrt(math.pi))
+    sc = make_scene(means, scales, q, op, None, 1, sh)
+    th = 0.2
+    Ry = np.array([[math.cos(th), 0, math.sin(th)], [0, 1, 0], [-math.sin(th), 0, math.cos(th)]])
+    cams = [camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2),
+            camera(W, H, f, 0.9 * f, W / 2 + 7, H / 2 - 5, R=Ry, t=np.array([0.05, -0.03, 0.02]))]
+    _, imgs, _ = _render(sc, cams)
+    for k, c in enumerate(cams):
+        _gpu.check_image(imgs[k], orc.render_outcomes(sc, c), what=f"border view {k}")
+
+
 def test_depth_tie_keeps_index_order(orc):
     cols = [[1, 0, 0], [0, 1, 0]]
     sc = make_scene([[0, 0, 2.0], [0, 0, 2.0]], [[0.3] * 3] * 2, [[1, 0, 0, 0]] * 2, [0.6, 0.5], cols)
