@@ -638,15 +638,15 @@ template <typename T>
 cudaError_t launch_pre_t(int deg, int64_t N, const mgs_gaussians& g, const ViewTable& vt,
                          float4* rec, uint2* rects, uint32_t* touched, uint32_t* dkeys,
                          unsigned long long* counters, const FwdPlanOut& fb, cudaStream_t s) {
-  unsigned grid = (unsigned)div_up(N, 256);
+  unsigned grid = (unsigned)div_up(N, kPreThreads);
   const Geom geo{g.log_scales, g.quats, g.geom_dtype, g.quat_dtype};
   const T* ol = (const T*)g.opacity_logit;
   const T* sh = (const T*)g.sh;
   switch (deg) {
-    case 0: k_preprocess<0, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
-    case 1: k_preprocess<1, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
-    case 2: k_preprocess<2, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
-    default: k_preprocess<3, T><<<grid, 256, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
+    case 0: k_preprocess<0, T><<<grid, kPreThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
+    case 1: k_preprocess<1, T><<<grid, kPreThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
+    case 2: k_preprocess<2, T><<<grid, kPreThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
+    default: k_preprocess<3, T><<<grid, kPreThreads, 0, s>>>(N, g.means, geo, ol, sh, vt, rec, rects, touched, dkeys, counters, fb.moments, fb.gmask, fb.bcounts); break;
   }
   count_launch();
   return cudaGetLastError();
