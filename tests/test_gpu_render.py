@@ -253,6 +253,42 @@ def test_backward_store_mode_equals_accumulating_into_zeros():
     assert torch.equal(st.vis_count, 1 + 2 * acc.vis_count)
 
 
+def test_reused_workspace_backward_equals_a_fresh_one():
+    """The projection clears only the drawn items' moment accumulators and the reverse
+    pass leaves them dirty: render views A and take the reverse pass, then render other
+    views B (other drawn items) on the same workspace and take theirs.  The gradients
+    equal those of B on a fresh workspace (up to the rounding order of the float atomics
+    that sum the per-tile moments: relative L2 <= 1e-5), and so do those of a second
+    reverse pass of B (the dirty buffer is cleared first)."""
+    rng = np.random.default_rng(23)
+    sc = random_scene(rng, 1500, sh_degree=1, spread=1.3)
+    th = 0.5
+    Ry = np.array([[math.cos(th), 0, math.sin(th)], [0, 1, 0], [-math.sin(th), 0, math.cos(th)]])
+    cams_a = [camera(96, 80, 90, 90, 47.5, 39.5), camera(64, 48, 70, 70, 31.5, 23.5, R=Ry)]
+    cams_b = [camera(80, 96, 100, 95, 41.0, 45.0, R=Ry.T, t=np.array([0.2, 0.0, 0.3]))]
+    grng = np.random.default_rng(24)
+
+    def cot(cams):
+        return [api.Image(*(torch.from_numpy(grng.uniform(-1, 1, s).astype(np.float32)).cuda()
+                            for s in ((3, c.height, c.width), (c.height, c.width), (c.height, c.width))))
+                for c in cams]
+
+    dL_a, dL_b = cot(cams_a), cot(cams_b)
+    g, _, ws = _gpu.render_gpu(sc, cams_a)
+    api.render_backward(g, cams_a, dL_a, ws)
+    api.render(g, cams_b, ws)
+    reused = api.render_backward(g, cams_b, dL_b, ws)
+    again = api.render_backward(g, cams_b, dL_b, ws)
+    _, _, ws2 = _gpu.render_gpu(sc, cams_b)
+    fresh = api.render_backward(g, cams_b, dL_b, ws2)
+    torch.cuda.synchronize()
+    for a, b, c in zip(fresh.tensors(), reused.tensors(), again.tensors()):
+        n = float(torch.linalg.vector_norm(a))
+        assert n > 0
+        assert float(torch.linalg.vector_norm(a - b)) <= 1e-5 * n
+        assert float(torch.linalg.vector_norm(a - c)) <= 1e-5 * n
+
+
 def test_three_pass_tile_sort_matches_single_views():
     """32 full-HD views in one launch hold 261,120 tiles: the tile sort takes three 8-bit
     passes and writes the tile ranges in the third.  Every image (and its backward
