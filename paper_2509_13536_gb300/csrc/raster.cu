@@ -332,18 +332,20 @@ __global__ void __launch_bounds__(kBwdThreads, 5 * kBwdSplit) k_blend_bwd(const 
                                                   __ffma2_rn(make_float2(bd.x, bd.y), gB2,
                                                              __fmul2_rn(make_float2(bd.z, bd.w), gD2))));
           const float2 gar = __fmul2_rn(gAT2, rom);
+          // the recursion itself (T before each entry, sigma behind it) stays scalar; the
+          // rest of dL/dalpha goes through one packed FMA
           const float Tb1 = T * rom.y;
           const float d1 = cg.y - sig;
-          const float dLda1 = fmaf(Tb1, d1, gar.y);
           sig = fmaf(alc.y, d1, sig);
           const float Tb0 = Tb1 * rom.x;
           const float d0 = cg.x - sig;
-          const float dLda0 = fmaf(Tb0, d0, gar.x);
           sig = fmaf(alc.x, d0, sig);
           T = Tb0;
+          const float2 Tb = make_float2(Tb0, Tb1);
+          const float2 dLda = __ffma2_rn(Tb, make_float2(d0, d1), gar);
           // dL/dalpha * alpha where alpha is unclamped (alc = alpha there; 0 when skipped)
-          const float2 gp = __fmul2_rn(make_float2(dLda0, dLda1), alc);
-          const float2 w = __fmul2_rn(alc, make_float2(Tb0, Tb1));
+          const float2 gp = __fmul2_rn(dLda, alc);
+          const float2 w = __fmul2_rn(alc, Tb);
           *reinterpret_cast<float4*>(&S.gw[t][2 * p]) =
               kClamp ? make_float4(a.x <= kAlphaMax ? gp.x : 0.f, w.x, a.y <= kAlphaMax ? gp.y : 0.f, w.y)
                      : make_float4(gp.x, w.x, gp.y, w.y);
