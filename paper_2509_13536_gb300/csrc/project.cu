@@ -485,8 +485,11 @@ __global__ void __launch_bounds__(kPreBwdThreads, 3) k_preprocess_bwd(int64_t N,
   if (t >= N) return;
   constexpr int K = (DEG + 1) * (DEG + 1);
   const int64_t g = list[t];
+  if (g >= N) return;  // a plan left by a render of another map: skip, never read out of bounds
   const uint32_t drawn = ldrawn[t];
-  uint32_t todo = ltodo[t];  // drawn views in which it reached a tile (else a zero gradient)
+  // drawn views in which it reached a tile (else a zero gradient); views past the call's
+  // are masked off, again against a plan left by another render
+  uint32_t todo = ltodo[t] & (vt.n_views >= 32 ? ~0u : (1u << vt.n_views) - 1u);
   const float vis = (float)__popc(drawn);
   const bool ow = grads.overwrite != 0;
   if (drawn == 0) {  // no view draws it: a zero gradient (stored only when overwriting)
