@@ -42,7 +42,7 @@ BWD_FLOP_EVAL, BWD_FLOP_CONTRIB = 10, 47
 # of the full workload (8 views, one launch per step; profiles/ has the command).  A value
 # is reported only while the kernel sources still hash to the captured version.
 NCU_TRAFFIC_SOURCES = ["paper_2509_13536_gb300/csrc/raster.cu", "paper_2509_13536_gb300/csrc/common.cuh"]
-NCU_TRAFFIC = {"sha256_16": "cc9b39e83cf6bd6e", "blend_bwd": 661.42e6 + 90.25e6, "blend_fwd": 352.74e6 + 141.89e6}
+NCU_TRAFFIC = {"sha256_16": "caa7bf7cd63bea3f", "blend_bwd": 670.48e6 + 91.39e6, "blend_fwd": 357.48e6 + 143.22e6}
 
 
 def algorithmic_bytes(n, views, stats, pb, pixels):

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_blend_fwd(const __grid_constant
   __shared__ float4 s_bd[kTilePix];   // (b, b, depth, depth)
   __shared__ uint32_t s_clamp[kFwdThreads / 32];  // per warp: its bits of the batch's 32 group flags
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+  if ((unsigned)tile >= (unsigned)vt.n_tiles) return;  // an order left by another render
   const View& V = vt.v[view_of_tile(vt, tile)];
   const int local = tile - V.tile_base;
   const int x0 = (local % V.tiles_x) * kTile, y0 = (local / V.tiles_x) * kTile;
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(kBwdThreads, 5 * kBwdSplit) k_blend_bwd(const 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
   const int tile = order ? (int)order[blockIdx.x / kBwdSplit] : (int)(blockIdx.x / kBwdSplit);
+  if ((unsigned)tile >= (unsigned)vt.n_tiles) return;  // an order left by another render
   const int part = blockIdx.x % kBwdSplit;
   const int row0 = part * (kTile / kBwdSplit);  // first tile row of this CTA's part
   const View& V = vt.v[view_of_tile(vt, tile)];
