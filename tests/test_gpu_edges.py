@@ -167,6 +167,38 @@ def test_maximum_views_in_one_launch(orc):
         api.render(api.Gaussians.from_scene(sc, "cuda"), cams + cams[:1])  # 33 views: rejected
 
 
+def test_gradients_over_many_views(orc):
+    """24 views of one map in one call, placed around it so that Gaussians take their
+    gradients from anywhere between 0 and 24 views: the reverse projection's work plan
+    (Gaussians bucketed by gradient-view count, most first) covers every bucket, and every
+    gradient element matches the oracle's sum over the views within the element-wise
+    bound."""
+    rng = np.random.default_rng(24)
+    sc = random_scene(rng, 600, sh_degree=1, spread=1.5, depth=0.0)
+    cams = []
+    for v in range(24):
+        th = 2 * math.pi * v / 24
+        W, H = [(40, 32), (48, 36), (33, 29)][v % 3]
+        d = rng.uniform(2.4, 3.0)
+        centre = np.array([d * math.sin(th), rng.uniform(-0.4, 0.4), -d * math.cos(th)])
+        fwd = -centre / np.linalg.norm(centre)
+        right = np.cross([0.0, 1.0, 0.0], fwd)
+        right /= np.linalg.norm(right)
+        down = np.cross(fwd, right)
+        R = np.stack([right, down, fwd])
+        cams.append(camera(W, H, rng.uniform(60, 90), rng.uniform(60, 90), W / 2, H / 2, R=R, t=-R @ centre))
+    g, imgs, ws = _render(sc, cams)
+    refs = [orc.render_outcomes(sc, c) for c in cams]
+    for v in range(len(cams)):
+        _gpu.check_image(imgs[v], refs[v], what=f"view {v}")
+    cot_np, dL = _gpu.masked_cotangents(cams, refs, 25)
+    grads = api.render_backward(g, cams, dL, ws)
+    torch.cuda.synchronize()
+    vis = grads.vis_count.cpu().numpy()
+    assert len(np.unique(vis)) >= 20  # drawing-view counts spread over the buckets
+    _gpu.check_grads(grads, _gpu.oracle_backward(orc, sc, cams, cot_np), what="24 views")
+
+
 def test_merge_degenerate_inputs(orc):
     from tests.test_oracle_merge import _voxel_scene
     rng = np.random.default_rng(8)
