@@ -285,12 +285,14 @@ def precision_leg(args, api, torch, scene, cams, make_step, dev):
         step, st = make_step(g)
         for _ in range(2):
             step()
+        st["join"]()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         k_steps = max(2, args.steps // 2)
         for _ in range(k_steps):
             step()
+        st["join"]()
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / k_steps
@@ -369,6 +371,7 @@ def eq12_leg(args, api, torch, scene, make_step, dev, V):
     step, st = make_step(g, "eq12")
     for _ in range(3):
         step()
+    st["join"]()
     torch.cuda.synchronize()
     k_steps = max(3, args.steps // 2)
     api.profile_enable(True)
@@ -376,6 +379,7 @@ def eq12_leg(args, api, torch, scene, make_step, dev, V):
     e0.record()
     for _ in range(k_steps):
         step()
+    st["join"]()
     e1.record()
     torch.cuda.synchronize()
     prof = api.profile_read()
@@ -609,14 +613,31 @@ def run_ours(args):
         vox = torch.empty(g.n, 3, dtype=torch.int32, device=dev)
         mws = torch.empty(api.load().mgs_voxel_merge_workspace_size(g.n), dtype=torch.uint8, device=dev)
         mstatus = torch.zeros(2, dtype=torch.int32, pin_memory=True)  # {survivors, flags}, written by the stream
-        state = {"step": 0, "merge_status": mstatus}
+        # The merge of step k runs on its own stream, alongside the start of step k+1 (the
+        # projection and the sorts, which leave the GPU room): it starts once step k's Adam
+        # update is done, and step k+1's update waits for it (the merge reads the
+        # parameters).  join() makes the calling stream wait for the last merge; every
+        # timed region ends with it.  (Released after step k+1's render instead, beside the
+        # backward pass, it measured slower.)
+        mstream = torch.cuda.Stream(dev)
+        ev_updated, ev_merged = torch.cuda.Event(), torch.cuda.Event()
+
+        def merge():
+            ev_updated.record(torch.cuda.current_stream())
+            mstream.wait_event(ev_updated)
+            api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox, status=mstatus,
+                                stream=mstream)
+            ev_merged.record(mstream)
+
+        state = {"step": 0, "merge_status": mstatus,
+                 "join": lambda: torch.cuda.current_stream().wait_event(ev_merged)}
         if autograd:
             ms = api.MappingStep(g, cams, lr=1e-3, lambda_ssim=lam, w_depth=0.1, w_iso=w_iso)
             state.update(ws=ms.ws, loss=ms.loss, loss_views=ms.loss, loss_iso=ms.loss_iso, mapping=ms)
 
             def step():
-                ms(tref["rgb"], tref["depth"])
-                api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox, status=mstatus)
+                ms(tref["rgb"], tref["depth"], before_update=ev_merged)
+                merge()
 
             return step, state
         grads = api.Grads.zeros_like(g)
@@ -647,8 +668,9 @@ def run_ours(args):
             api.mgs_render_backward(g, cams, dL, ws, grads)
             if w_iso > 0:
                 api.iso_loss(g, w_iso, grads, loss=loss_iso, workspace=iws)
+            torch.cuda.current_stream().wait_event(ev_merged)  # the previous merge has read the map
             api.mgs_adam_step(g, grads, m, v, 1e-3, 0.9, 0.999, 1e-8, state["step"], zero_grads=False)
-            api.mgs_voxel_merge(g, 0.02, workspace=mws, out=merged, partner=partner, vox=vox, status=mstatus)
+            merge()
 
         return step, state
 
@@ -663,6 +685,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
         step()
+    state["join"]()
     torch.cuda.synchronize()
     barrier()
     with ClockSampler(local) as clocks:
@@ -673,6 +696,7 @@ def run_ours(args):
         e0.record(stream)
         for _ in range(args.steps):
             step()
+        state["join"]()
         e1.record(stream)
         torch.cuda.synchronize()
         launches = api.launch_count() - launches0
@@ -721,6 +745,7 @@ def run_ours(args):
         step()
         used[cur].record(stream)
         host_loss[cur].copy_(loss, non_blocking=True)
+    state["join"]()
     e3.record(stream)
     torch.cuda.synchronize()
     tref["rgb"], tref["depth"] = target_rgb, target_depth
@@ -778,14 +803,16 @@ def run_ours(args):
     direct = None
     if world == 1:
         gd_ = api.Gaussians.from_scene(pert, dev)
-        step_d, _ = make_step(gd_, autograd=False)
+        step_d, st_d = make_step(gd_, autograd=False)
         for _ in range(3):
             step_d()
+        st_d["join"]()
         torch.cuda.synchronize()
         d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         d0.record(stream)
         for _ in range(args.steps):
             step_d()
+        st_d["join"]()
         d1.record(stream)
         torch.cuda.synchronize()
         ms_d = d0.elapsed_time(d1) / args.steps

@@ -635,8 +635,11 @@ class MappingStep:
         self._dL = [Image(self.g_rgb[v], self.g_depth[v], None) for v in range(V)]
         self.ws.headroom = 1.1
 
-    def __call__(self, target_rgb: torch.Tensor, target_depth: Optional[torch.Tensor] = None):
-        """One step against keyframe images target_rgb [V,3,H,W] (and target_depth [V,H,W])."""
+    def __call__(self, target_rgb: torch.Tensor, target_depth: Optional[torch.Tensor] = None,
+                 before_update: Optional[torch.cuda.Event] = None):
+        """One step against keyframe images target_rgb [V,3,H,W] (and target_depth [V,H,W]).
+        ``before_update``: an event the parameter update waits for on the step's stream
+        (a reader of the parameters on another stream, e.g. the previous step's merge)."""
         self.step_count += 1
         rgb, depth, alpha = RenderFn.apply(*self.params, self.cams, self.ws, self.grads, self.ws.buf is None)
         V = len(self.cams)
@@ -649,6 +652,8 @@ class MappingStep:
         g = self.g
         if self.w_iso > 0:
             mgs_iso_loss(g, self.w_iso, self.grads, loss=self.loss_iso, workspace=self.iso_ws)
+        if before_update is not None:
+            torch.cuda.current_stream().wait_event(before_update)
         with torch.no_grad():
             mgs_adam_step(g, self.grads, self.m, self.v, self.lr, self.betas[0], self.betas[1], self.eps,
                           self.step_count, zero_grads=False)
