@@ -224,3 +224,38 @@ def test_render_fn_refuses_a_reused_workspace():
     rgb2.backward(torch.ones_like(rgb2))  # the latest render's state is intact
     torch.cuda.synchronize()
     assert params[0].grad is not None and torch.isfinite(params[0].grad).all()
+
+
+def test_merge_on_a_side_stream_sees_its_own_step():
+    """The mapping step with the voxel merge of step k on a stream of its own, running
+    beside step k+1 (which renders meanwhile, its Adam update waiting for the merge
+    through ``before_update``): the merge equals a merge of the map as step k left it,
+    taken afterwards on the main stream."""
+    scene, cams = sg.workload("box10k")
+    g = api.Gaussians.from_scene(scene, "cuda")
+    step = api.MappingStep(g, cams, lr=1e-2, lambda_ssim=0.0, w_depth=0.1)
+    rng = np.random.default_rng(5)
+    y = torch.from_numpy(rng.random((1, 3, cams[0].height, cams[0].width)).astype(np.float32)).cuda()
+    dt = torch.from_numpy(rng.uniform(1, 3, (1, cams[0].height, cams[0].width)).astype(np.float32)).cuda()
+    side = torch.cuda.Stream()
+    ev_updated, ev_merged = torch.cuda.Event(), torch.cuda.Event()
+    out = g.empty_like()
+    partner = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    vox = torch.empty(g.n, 3, dtype=torch.int32, device="cuda")
+    status = torch.zeros(2, dtype=torch.int32, pin_memory=True)
+    step(y, dt)
+    snap = api.Gaussians(*(p.detach().clone() for p in g.params()), g.birth.clone())  # the map after step 1
+    ev_updated.record(torch.cuda.current_stream())
+    side.wait_event(ev_updated)
+    api.mgs_voxel_merge(g, 0.05, out=out, partner=partner, vox=vox, status=status, stream=side)
+    ev_merged.record(side)
+    for _ in range(2):  # steps 2 and 3 render while the merge runs; step 2's update waits for it
+        step(y, dt, before_update=ev_merged)
+    torch.cuda.synchronize()
+    ref, ref_partner, ref_vox = api.mgs_voxel_merge(snap, 0.05)
+    torch.cuda.synchronize()
+    k = int(status[0])
+    assert k == ref.n and k < g.n  # something merged
+    assert torch.equal(partner, ref_partner) and torch.equal(vox, ref_vox)
+    for a, b in zip(ref.params(), out.params()):
+        assert torch.equal(a, b[:k])
