@@ -1,7 +1,11 @@
 // Per-Gaussian projection (Sec. II-C, Eq. 1-2) and its reverse pass, sm_103a.
 //
-// One thread owns one Gaussian and loops over every view of the call, so each
-// parameter byte is read from HBM once per call however many keyframes are drawn.
+// Forward: one thread loads one Gaussian's parameters once for every view of the call
+// and tests each view cheaply; the warp then shares out the (Gaussian, view) items that
+// pass among its lanes (the Gaussian's mean and R S from shared memory, its SH row from
+// L1), so the parameters cross HBM about once per call however many keyframes are drawn.
+// Reverse: one thread per Gaussian, in order of its number of gradient views, sums the
+// chain rule over those views.
 // The camera-space mean and the projected centre are carried in double-float
 // (two f32 words) so that the depth key and the pixel-space centre are correctly
 // rounded; everything else is plain f32.
